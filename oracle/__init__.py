@@ -1,0 +1,191 @@
+"""CPU oracle for the constrained multilinear sieve (arXiv 2010.08423).
+
+TEST INFRASTRUCTURE ONLY: the product path (the CUDA library and its Python
+binding) never imports this package. Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` use it.
+
+The arithmetic lives in ``oracle.c`` (plain C, compiled here with gcc into
+``oracle/_build/liborc.so``); this module only marshals numpy arrays through
+ctypes. See ``oracle.c`` for the paper passages each routine follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (-O2 -fopenmp) into oracle/_build/liborc.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
+           "-Wextra", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        u64, u32, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        vp = ctypes.c_void_p
+        lib.orc_gf_mul.restype = u64
+        lib.orc_gf_mul.argtypes = [u64, u64]
+        lib.orc_gf_pow.restype = u64
+        lib.orc_gf_pow.argtypes = [u64, u64]
+        lib.orc_gf_inv.restype = u64
+        lib.orc_gf_inv.argtypes = [u64]
+        lib.orc_sm_mix.restype = u64
+        lib.orc_sm_mix.argtypes = [u64]
+        lib.orc_sm_draw.restype = u64
+        lib.orc_sm_draw.argtypes = [u64, u64]
+        lib.orc_family_key.restype = u64
+        lib.orc_family_key.argtypes = [u64, u64]
+        lib.orc_y.restype = u64
+        lib.orc_y.argtypes = [u64, u64, u32]
+        lib.orc_ztable.restype = i32
+        lib.orc_ztable.argtypes = [u32, u32, u64, vp, vp, vp]
+        lib.orc_sieve.restype = i32
+        lib.orc_sieve.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, u32, u32, u64,
+                                  vp, u32, vp, vp, i32]
+        lib.orc_gf_det.restype = u64
+        lib.orc_gf_det.argtypes = [u32, vp]
+        lib.orc_dfs_paths.restype = u64
+        lib.orc_dfs_paths.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, u32, u32, u64,
+                                      vp, vp]
+        lib.orc_max_threads.restype = i32
+        lib.orc_max_threads.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _u32(a):
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _u8(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
+
+
+# -- field and PRNG --------------------------------------------------------
+
+def gf_mul(a: int, b: int) -> int:
+    return _load().orc_gf_mul(a, b)
+
+
+def gf_pow(a: int, e: int) -> int:
+    return _load().orc_gf_pow(a, e)
+
+
+def gf_inv(a: int) -> int:
+    return _load().orc_gf_inv(a)
+
+
+def gf_det(mat) -> int:
+    a = np.array(mat, dtype=np.uint64, copy=True)
+    k = a.shape[0]
+    return _load().orc_gf_det(k, _ptr(a))
+
+
+def sm_mix(z: int) -> int:
+    return _load().orc_sm_mix(z)
+
+
+def sm_draw(key: int, i: int) -> int:
+    return _load().orc_sm_draw(key, i)
+
+
+def family_key(seed: int, tag: int) -> int:
+    return _load().orc_family_key(seed, tag)
+
+
+def y_value(seed: int, e: int, layer: int) -> int:
+    return _load().orc_y(seed, e, layer)
+
+
+def max_threads() -> int:
+    return _load().orc_max_threads()
+
+
+def ztable(n: int, k: int, seed: int, color=None, motif=None) -> np.ndarray:
+    z = np.zeros((n, k), dtype=np.uint64)
+    color, motif = _u8(color), _u8(motif)
+    rc = _load().orc_ztable(n, k, seed, _ptr(color), _ptr(motif), _ptr(z))
+    if rc:
+        raise ValueError("orc_ztable: invalid arguments")
+    return z
+
+
+# -- sieve and brute force -------------------------------------------------
+
+def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
+          per_mask: bool = False, threads: int = 0):
+    """Per-vertex sieve sums S (n uint64) over all 2^k points or ``masks``.
+
+    ``graph`` is a mapping with n, src, dst, t, delta and optionally color.
+    Returns S, or (S, per_mask_sums[nmasks, n]) when per_mask is True.
+    """
+    n = int(graph["n"])
+    src, dst, t, delta = (_u32(graph[x]) for x in ("src", "dst", "t", "delta"))
+    m = src.shape[0]
+    color = _u8(graph.get("color"))
+    motif = _u8(motif)
+    if masks is not None:
+        masks = _u32(masks)
+        nm = masks.shape[0]
+    else:
+        nm = 1 << k
+    S = np.zeros(n, dtype=np.uint64)
+    pm = np.zeros((nm, n), dtype=np.uint64) if per_mask else None
+    rc = _load().orc_sieve(n, m, _ptr(src), _ptr(dst), _ptr(t), _ptr(delta),
+                           _ptr(color), _ptr(motif), source, k, seed,
+                           _ptr(masks), 0 if masks is None else nm, _ptr(S),
+                           _ptr(pm), int(threads))
+    if rc == 1:
+        raise ValueError("orc_sieve: invalid input")
+    if rc:
+        raise MemoryError("orc_sieve: allocation failed")
+    return (S, pm) if per_mask else S
+
+
+def dfs_paths(graph, source: int, k: int, seed: int = 0, motif=None,
+              with_det: bool = False):
+    """Exhaustive temporal DFS over restless k-vertex paths from ``source``.
+
+    Returns (reach[n] uint8, Sdet[n] uint64 or None, number_of_paths).
+    """
+    n = int(graph["n"])
+    src, dst, t, delta = (_u32(graph[x]) for x in ("src", "dst", "t", "delta"))
+    m = src.shape[0]
+    color = _u8(graph.get("color"))
+    motif = _u8(motif)
+    reach = np.zeros(n, dtype=np.uint8)
+    sdet = np.zeros(n, dtype=np.uint64) if with_det else None
+    cnt = _load().orc_dfs_paths(n, m, _ptr(src), _ptr(dst), _ptr(t), _ptr(delta),
+                                _ptr(color), _ptr(motif), source, k, seed,
+                                _ptr(reach), _ptr(sdet))
+    if cnt == (1 << 64) - 1:
+        raise ValueError("orc_dfs_paths: invalid input")
+    return reach, sdet, int(cnt)

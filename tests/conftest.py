@@ -1,0 +1,37 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+    config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def read_fixture(name):
+    """Graph plus the 'source', 'expect k v...' and 'motif' lines of a fixture."""
+    from paper_2010_08423_gb300.workloads import load_edge_fixture
+    path = os.path.join(GOLDEN, name)
+    g = load_edge_fixture(path)
+    source, expect, motif = None, {}, None
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            f = line.split()
+            if f[0] == "source":
+                source = int(f[1])
+            elif f[0] == "expect":
+                expect[int(f[1])] = sorted(int(x) for x in f[2:])
+            elif f[0] == "motif":
+                motif = [int(x) for x in f[1:]]
+    return g, source, expect, motif
