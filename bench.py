@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark: k-RestlessReach sieve queries on a resident temporal graph.
+
+Workload (one step = one complete query: z-table, k-1 edge layers over all
+2^k sieve points, fused per-vertex reduce, reach bitmap):
+  uniform random directed temporal multigraph, n = 100,000, m = 1,000,000,
+  t ~ U[1, 1000], delta(v) ~ U{1..20}, k = 8, source vertex 0, plain query,
+  GF(2^64) mod x^64+x^4+x^3+x+1, splitmix64-seeded values (seed differs per step).
+
+Metric: GF(2^64) edge-updates/s counted as the nominal 2^k * k * m per query.
+`value` is device-timed (CUDA events on the launching stream, L2 flushed
+between steps, graph resident in HBM); `e2e` is the same metric through the
+host-buffer C-ABI call rr_reach_sync (result copied back every step).
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the
+same workload: the only other place this file runs oracle code.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2010_08423_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GF(2^64) edge-updates/s (2^k*k*m per query)"
+UNIT = "edge-updates/s"
+K = 8
+SOURCE = 0
+GRAPH_SEED = W.GRAPH_SEED_BASE + 2
+WORKLOAD = ("uniform temporal multigraph n=100000 m=1000000 t~U[1,1000] delta~U{1..20}; "
+            "plain k-RestlessReach k=8 from s=0")
+
+
+def units_per_query(k: int, m: int) -> float:
+    return float(2 ** k) * k * m
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for name, val in zip(names, f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(g, k, nsteps_hint=1):
+    """The oracle as it stands, on a bounded sample of the workload's sieve
+    points (one mask per host thread); value scaled to the nominal unit."""
+    import oracle
+    threads = max(1, min(os.cpu_count() or 1, 64))
+    masks = np.arange(1, threads + 1, dtype=np.uint32) * 3 % (2 ** k)
+    t0 = time.perf_counter()
+    oracle.sieve(g, SOURCE, k, GRAPH_SEED ^ 1, masks=masks, threads=threads)
+    dt = time.perf_counter() - t0
+    frac = len(masks) / 2 ** k
+    value = units_per_query(k, len(g["src"])) * frac / dt
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(masks)} of {2 ** k} sieve points of one k={k} query "
+                      f"({dt:.2f} s wall), scaled by points"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    g = W.scale_uniform()
+    m = len(g["src"])
+    import oracle
+    oracle.build()
+    threads = max(1, min(os.cpu_count() or 1, 64))
+    masks = np.arange(1, threads + 1, dtype=np.uint32) * 3 % (2 ** K)
+    frac = len(masks) / 2 ** K
+    for _ in range(args.warmup):
+        oracle.sieve(g, SOURCE, K, GRAPH_SEED ^ 1, masks=masks[:1], threads=1)
+    times = []
+    for step in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sieve(g, SOURCE, K, GRAPH_SEED ^ (step + 1), masks=masks, threads=threads)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = units_per_query(K, m) * frac * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{len(masks)} of {2 ** K} sieve points per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{len(masks)} of {2 ** K} sieve points per step, scaled by points"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dense", action="store_true", help="dense state layout (every row stored)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2010_08423_gb300 import capi
+
+    rank, world, local_rank = env_rank()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    capi.load()
+
+    g = W.scale_uniform()
+    m = len(g["src"])
+    n = g["n"]
+    t0 = time.perf_counter()
+    G = capi.Graph(g, capi.FLAG_DENSE_STATE if args.dense else 0)
+    load_s = time.perf_counter() - t0
+    info = G.info()
+    ppl, chunk = capi.rr_autotune(G.handle, K)
+
+    stream = torch.cuda.Stream()
+    d_w = torch.empty(n, dtype=torch.int64, device="cuda")
+    d_bm = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    seed_base = GRAPH_SEED ^ (rank << 20)
+
+    def step(i):
+        capi.rr_reach_device(G.handle, SOURCE, K, seed_base ^ (i + 1), d_w, d_bm, stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        sampler = ClockSampler(local_rank)
+        sampler.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = capi.rr_kernel_launches()
+        capi.rr_timing_enable(True)
+        capi.rr_timing_read(reset=True)
+        for i in range(args.steps):
+            flush.fill_(i)  # evict L2 between steps (outside the timed events)
+            evs[i][0].record(stream)
+            step(args.warmup + i)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        kt = capi.rr_timing_read(reset=True)
+        capi.rr_timing_enable(False)
+        launches = capi.rr_kernel_launches() - launches0
+        clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(ms)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    units = units_per_query(K, m)
+    value = world * args.steps * units / (tot_ms / 1e3)
+
+    # end to end through the host-buffer C ABI: result copied back every step
+    for i in range(2):
+        G.reach(SOURCE, K, seed_base ^ (1000 + i))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        G.reach(SOURCE, K, seed_base ^ (2000 + i))
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps * units / e2e_s
+
+    # roofline of the dominant kernel: the middle-layer kernel
+    peaks, peak_kind = measured_peaks()
+    mid_ms, mid_n = kt["mid_layer"]
+    prod = info["state_rows"] - 1
+    cons = info["producer_window_rows"]
+    # per launch: every producer row's state slice is written, every producer
+    # row with a window reads two slices; per-row indices read once
+    alg_bytes = (prod + 2 * cons) * chunk * 8 + m * 8 + cons * 8 + n * K * 8
+    if args.dense:
+        alg_bytes = (m + 2 * info["window_rows"]) * chunk * 8 + m * 16 + n * K * 8
+    roofline = None
+    if mid_n:
+        avg_s = mid_ms / mid_n / 1e3
+        achieved = alg_bytes / avg_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "kernel": "k_layer (middle layers)", "peak_kind": peak_kind,
+                    "avg_launch_us": avg_s * 1e6, "launches": mid_n,
+                    "alg_bytes_per_launch": alg_bytes}
+    kernel_share = {k_: round(v[0] / max(1e-9, sum(x[0] for x in kt.values())), 4)
+                    for k_, v in kt.items() if v[1]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph_seed": GRAPH_SEED, "l2": "flushed between steps",
+                       "state_layout": "dense" if args.dense else "compact",
+                       "points_per_lane": ppl, "points_per_chunk": chunk,
+                       "state_rows": info["state_rows"], "window_rows": info["window_rows"],
+                       "graph_load_s": round(load_s, 3)},
+            "roofline": roofline,
+            "kernel_time_share": kernel_share,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": n * 8 + (n + 7) // 8,
+                    "api": "rr_reach_sync (host outputs)"},
+            "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, K)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

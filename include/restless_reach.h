@@ -1,0 +1,204 @@
+/*
+ * restless_reach.h -- C ABI of the GB300 (sm_103a) constrained multilinear
+ * sieve for k-RestlessReach and k-RestlessMotifReach ("Restless reachability
+ * problems in temporal graphs", arXiv 2010.08423).
+ *
+ * What is computed (edge-layer form of Eq. (1) with the sieve of Eq. (2)/(3),
+ * the per-vertex output of Algorithm 1):
+ *   for every sieve point L subset of [k] and every edge e = (u_e, v_e, t_e):
+ *     x_u^L     = sum_{j in L} z_{u,j}
+ *     P_1^L[e]  = [u_e = s] y_{e,1} x_s^L x_{v_e}^L
+ *     P_l^L[e]  = y_{e,l} x_{v_e}^L sum_{f: v_f = u_e, t_f <= t_e <= t_f + delta(u_e)} P_{l-1}^L[f]
+ *   witness[v]  = sum_L sum_{e: v_e = v} P_{k-1}^L[e]
+ *   reach[v]    = (witness[v] != 0)
+ * All arithmetic is in GF(2^64) = GF(2)[x]/(x^64 + x^4 + x^3 + x + 1), elements
+ * stored as uint64 with bit i the coefficient of x^i; "sum" is XOR.
+ * A non-zero witness proves a restless path with exactly k vertices from s to v
+ * (whose colours agree with the motif M for motif queries); a path is missed
+ * with probability at most (3k-1)/2^64 per vertex (Schwartz-Zippel; the paper
+ * quotes (2k-1)/2^b for the uncoloured sieve).
+ *
+ * Random values (counter-form splitmix64; Steele, Lea & Flood 2014):
+ *   mix(z)        = standard splitmix64 finaliser
+ *   draw(key, i)  = mix(key + (i+1) * 0x9E3779B97F4A7C15)
+ *   key_F         = mix(seed ^ F), F = 1 (y), 2 (z), 3 (gamma), 4 (omega)
+ *   y_{e,l}       = draw(key_1, e*32 + l-1)        e = input edge index
+ *   plain:   z_{u,j} = draw(key_2, u*32 + j-1)
+ *   motif:   z_{u,j} = sum_{d in S_{c(u)}} draw(key_3, u*32 + d) * draw(key_4, d*32 + j-1)
+ *            (Eq. (3); shades d = 0..k-1 assigned colour by colour in ascending
+ *             colour order; z_{u,j} = 0 if c(u) is not in M)
+ *
+ * Conventions shared by every entry point:
+ *   - Vertices are 0..n-1; edge e is (src[e], dst[e], t[e]) with e the input
+ *     index; timestamps and waiting times are uint32; delta(v) = 0 is allowed.
+ *     The wait bound is the delta of the vertex being left, both window ends
+ *     inclusive (restless-walk definition).
+ *   - k counts path vertices (the path has k-1 edges); 2 <= k <= 20.
+ *   - Bitmaps: bit v is byte v>>3, bit v&7; ceil(n/8) bytes.
+ *   - Host buffers passed in are only read during the call; outputs are
+ *     caller-allocated. Handles are owned by the library (free with the
+ *     matching *_free / *_destroy).
+ *   - Every call returns an rr_status; on failure rr_last_error() gives a
+ *     thread-local message. No call aborts the process.
+ *   - All device work runs on the current CUDA device of the calling thread.
+ */
+#ifndef RESTLESS_REACH_H
+#define RESTLESS_REACH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RR_OK = 0,
+    RR_EINVAL = 1,    /* invalid argument (bad k, source, endpoint, self-loop, motif without colours) */
+    RR_ENOMEM = 2,    /* device memory cannot hold the request (admission refused) */
+    RR_EAGAIN = 3,    /* query queued or still running */
+    RR_ETIMEDOUT = 4, /* a bounded device wait gave up; results of that query are invalid */
+    RR_ECANCELED = 5, /* query was cancelled */
+    RR_ECUDA = 6      /* a CUDA runtime call failed */
+} rr_status;
+
+typedef struct rr_graph rr_graph;
+typedef struct rr_server rr_server;
+
+/* One reachability query. motif == NULL: plain k-RestlessReach (uncoloured
+ * sieve, Eq. (2)). motif != NULL: k-RestlessMotifReach with the multiset M
+ * given as k colour values (any order; Eq. (3)); needs a coloured graph. */
+typedef struct {
+    uint32_t source;
+    uint32_t k;
+    uint64_t seed;
+    const uint8_t *motif;
+} rr_query;
+
+typedef struct {
+    uint32_t n;
+    uint64_t m;
+    uint64_t state_rows;     /* rows of the windowed prefix state (1 + producer rows) */
+    uint64_t window_rows;    /* edges whose restless window is non-empty */
+    uint32_t max_in_degree;
+    uint32_t num_items;      /* vertex ranges the layer kernels are scheduled over */
+    uint64_t device_bytes;   /* bytes the resident graph holds on the device */
+    int has_colors;
+    int compact;             /* 1: state stores only rows inside some window */
+    uint64_t producer_window_rows; /* state rows whose own window is non-empty */
+} rr_graph_info;
+
+/* ---- graph ----------------------------------------------------------------
+ * rr_graph_load: copies the temporal multigraph to the device and builds the
+ * in-edge CSR sorted by (head, time, edge index), the restless window of
+ * every edge (Eq. (1)'s j in {0..delta}: rows of the tail's in-segment with
+ * t_e - delta(u_e) <= t_f <= t_e) and the scheduling ranges. Host arrays are
+ * read only; src/dst/t have m entries, delta n, color n (or NULL).
+ * flags: bit 0 set = keep the dense state layout (one state row per edge)
+ * instead of storing only rows that lie in some window.
+ * Errors: RR_EINVAL for n == 0, m >= 2^31, an endpoint >= n or a self-loop;
+ * RR_ENOMEM / RR_ECUDA on device failure (nothing is leaked). */
+rr_status rr_graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                        const uint32_t *t, const uint32_t *delta, const uint8_t *color,
+                        uint32_t flags, rr_graph **out);
+rr_status rr_graph_free(rr_graph *g);
+rr_status rr_graph_get_info(const rr_graph *g, rr_graph_info *out);
+
+/* ---- one query, one launch sequence (the plain GPU form) --------------------
+ * rr_reach_sync: runs one query to completion on the library's internal
+ * stream and copies results to HOST buffers bitmap (ceil(n/8) bytes, may be
+ * NULL) and witness (n uint64, may be NULL). Thread-safe per graph (calls on
+ * one graph are serialised). */
+rr_status rr_reach_sync(const rr_graph *g, const rr_query *q, uint8_t *bitmap,
+                        uint64_t *witness);
+
+/* rr_reach_device: same computation, enqueued on `stream` (a cudaStream_t,
+ * NULL = legacy default stream) with DEVICE outputs d_bitmap (ceil(n/8)
+ * bytes, may be NULL) and d_witness (n uint64, required). Returns once the
+ * work is enqueued; the graph's scratch state is reused by the next call, so
+ * calls on one graph must be ordered on one stream. */
+rr_status rr_reach_device(const rr_graph *g, const rr_query *q, uint8_t *d_bitmap,
+                          uint64_t *d_witness, void *stream);
+
+/* ---- many queries, one persistent launch (batched form) --------------------
+ * rr_reach_batch_device: runs nq queries of any mix of k, sources and motifs
+ * in ONE persistent kernel launch. Work is split into (query, point chunk,
+ * layer, vertex range) items drained from a device queue in dependency order;
+ * a layer item waits (bounded spin) for the previous layer of its chunk.
+ * Outputs: d_witness (nq*n uint64, row q = query q) and d_bitmaps (nq *
+ * ceil(n/8) bytes, may be NULL), device memory, enqueued on `stream`.
+ * d_status (nq int32, device, may be NULL) receives RR_OK or RR_ETIMEDOUT per
+ * query. Results equal rr_reach_device's bit for bit. */
+rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t nq,
+                                uint8_t *d_bitmaps, uint64_t *d_witness, int32_t *d_status,
+                                void *stream);
+
+/* ---- serving: continuous batching over a resident graph --------------------
+ * rr_server_create: starts a server thread that admits queries while device
+ * memory (device_mem_budget bytes of scratch, 0 = 60% of free memory) and
+ * max_slots (concurrent point chunks, 0 = automatic) allow, runs every
+ * admitted chunk's layers as they become ready, and retires queries as their
+ * last chunk finishes, so that queries arriving while others run share the
+ * GPU with them. Results are identical to rr_reach_sync's. */
+rr_status rr_server_create(const rr_graph *g, uint64_t device_mem_budget, uint32_t max_slots,
+                           rr_server **out);
+rr_status rr_server_destroy(rr_server *s);
+/* Copies the query (and motif); returns a ticket. RR_ENOMEM if the query can
+ * never fit the budget, RR_EINVAL on a bad query. */
+rr_status rr_query_submit(rr_server *s, const rr_query *q, uint64_t *ticket);
+/* Waits up to timeout_ms (0 = do not wait, <0 = forever). RR_OK: results
+ * copied to the host buffers (either may be NULL) and the ticket released;
+ * RR_EAGAIN: not finished; RR_ECANCELED / RR_ETIMEDOUT: final, ticket released. */
+rr_status rr_query_poll(rr_server *s, uint64_t ticket, int32_t timeout_ms, uint8_t *bitmap,
+                        uint64_t *witness);
+rr_status rr_query_cancel(rr_server *s, uint64_t ticket);
+/* Per-ticket timing in microseconds: submit->admit, submit->done. */
+rr_status rr_query_times(rr_server *s, uint64_t ticket, double *queue_us, double *total_us);
+
+/* ---- tuning ----------------------------------------------------------------
+ * Kernel shape used for a (graph, k): points per lane (2 or 4) and points per
+ * chunk. rr_autotune times the candidates on the resident graph for the given
+ * k and stores the winner in the graph; rr_set_tuning forces one. */
+rr_status rr_autotune(rr_graph *g, uint32_t k, uint32_t *best_ppl, uint32_t *best_chunk);
+rr_status rr_set_tuning(rr_graph *g, uint32_t k, uint32_t ppl, uint32_t chunk);
+
+/* ---- verification entry points ---------------------------------------------
+ * rr_debug_point_sums: per-vertex sums of single sieve points: out[p*n + v] =
+ * sum_{e: v_e = v} P_{k-1}^{L_p}[e] for L_p = masks[p] (HOST arrays). */
+rr_status rr_debug_point_sums(const rr_graph *g, const rr_query *q, const uint32_t *masks,
+                              uint32_t nmasks, uint64_t *out);
+/* rr_debug_graph: copies the build's CSR back to HOST arrays: off (n+1),
+ * row_eid, row_lo, row_hi (m each; window [lo,hi) as absolute CSR rows of the
+ * tail's segment). Any pointer may be NULL. */
+rr_status rr_debug_graph(const rr_graph *g, uint32_t *off, uint32_t *row_eid, uint32_t *row_lo,
+                         uint32_t *row_hi);
+/* rr_debug_ztable: z_{u,j} table of a query (HOST out, n*k, row u). */
+rr_status rr_debug_ztable(const rr_graph *g, const rr_query *q, uint64_t *out);
+/* rr_debug_gf_mul: out[i] = a[i]*b[i] in GF(2^64) on the device, HOST arrays. */
+rr_status rr_debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count);
+/* rr_debug_draw: out[i] = draw(key, first + i) on the device, HOST out. */
+rr_status rr_debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out);
+
+/* ---- kernel timing ---------------------------------------------------------
+ * While enabled (process-wide), every kernel launch of the sieve is bracketed
+ * by CUDA events on the stream it is launched on; rr_timing_read waits for the
+ * recorded events and returns the summed durations and launch counts per
+ * kind: 0 = first layer, 1 = middle layers, 2 = last layer with the fused
+ * per-vertex reduce, 3 = z-table, 4 = persistent batched kernel. */
+typedef struct {
+    double ms[5];
+    uint64_t launches[5];
+} rr_kernel_times;
+rr_status rr_timing_enable(int enable);
+rr_status rr_timing_read(rr_kernel_times *out, int reset);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char *rr_last_error(void);
+/* Number of kernel launches this library issued since load (all threads). */
+uint64_t rr_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RESTLESS_REACH_H */

@@ -49,6 +49,8 @@ def _load():
         vp = ctypes.c_void_p
         lib.orc_gf_mul.restype = u64
         lib.orc_gf_mul.argtypes = [u64, u64]
+        lib.orc_gf_mul_many.restype = None
+        lib.orc_gf_mul_many.argtypes = [vp, vp, vp, u64]
         lib.orc_gf_pow.restype = u64
         lib.orc_gf_pow.argtypes = [u64, u64]
         lib.orc_gf_inv.restype = u64
@@ -93,6 +95,14 @@ def _u8(a):
 
 def gf_mul(a: int, b: int) -> int:
     return _load().orc_gf_mul(a, b)
+
+
+def gf_mul_many(a, b) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    out = np.zeros_like(a)
+    _load().orc_gf_mul_many(_ptr(a), _ptr(b), _ptr(out), a.shape[0])
+    return out
 
 
 def gf_pow(a: int, e: int) -> int:

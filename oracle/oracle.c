@@ -70,6 +70,13 @@ uint64_t orc_gf_mul(uint64_t a, uint64_t b)
     return r;
 }
 
+/* out[i] = a[i] * b[i] for i < count (bulk form of orc_gf_mul for tests). */
+void orc_gf_mul_many(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count)
+{
+    for (uint64_t i = 0; i < count; ++i)
+        out[i] = orc_gf_mul(a[i], b[i]);
+}
+
 /* a^e by square-and-multiply. */
 uint64_t orc_gf_pow(uint64_t a, uint64_t e)
 {

@@ -1,0 +1,335 @@
+"""Thin ctypes binding of include/restless_reach.h (argument marshalling only).
+
+Every function has the C entry point's name and raises ``RRError`` on a
+non-OK status. Host arrays are numpy arrays; device arrays are anything with a
+``data_ptr()`` (torch tensors) or raw integer addresses. All computation runs
+in the CUDA library; if the library is missing or cannot be loaded this module
+raises at import-time use, it never falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RR_OK, RR_EINVAL, RR_ENOMEM, RR_EAGAIN, RR_ETIMEDOUT, RR_ECANCELED, RR_ECUDA = range(7)
+STATUS_NAMES = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_EAGAIN",
+                4: "RR_ETIMEDOUT", 5: "RR_ECANCELED", 6: "RR_ECUDA"}
+FLAG_DENSE_STATE = 1
+
+
+class RRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rr_query(ctypes.Structure):
+    _fields_ = [("source", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("motif", ctypes.c_void_p)]
+
+
+class rr_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("m", ctypes.c_uint64),
+                ("state_rows", ctypes.c_uint64), ("window_rows", ctypes.c_uint64),
+                ("max_in_degree", ctypes.c_uint32), ("num_items", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64), ("has_colors", ctypes.c_int),
+                ("compact", ctypes.c_int), ("producer_window_rows", ctypes.c_uint64)]
+
+
+class rr_kernel_times(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_uint64 * 5)]
+
+
+TIMING_KINDS = ["first_layer", "mid_layer", "last_layer", "ztable", "batch"]
+
+
+EXPORTED = [
+    "rr_graph_load", "rr_graph_free", "rr_graph_get_info", "rr_reach_sync",
+    "rr_reach_device", "rr_reach_batch_device", "rr_server_create", "rr_server_destroy",
+    "rr_query_submit", "rr_query_poll", "rr_query_cancel", "rr_query_times", "rr_autotune",
+    "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
+    "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
+    "rr_timing_enable", "rr_timing_read",
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads librestless_reach.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or (build_if_missing and not _build.up_to_date()):
+        if not build_if_missing:
+            raise RRError(RR_ECUDA, f"CUDA library not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+    pq = ctypes.POINTER(rr_query)
+    sig = {
+        "rr_graph_load": [u32, u64, vp, vp, vp, vp, vp, u32, ctypes.POINTER(vp)],
+        "rr_graph_free": [vp],
+        "rr_graph_get_info": [vp, ctypes.POINTER(rr_graph_info)],
+        "rr_reach_sync": [vp, pq, vp, vp],
+        "rr_reach_device": [vp, pq, vp, vp, vp],
+        "rr_reach_batch_device": [vp, pq, u32, vp, vp, vp, vp],
+        "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
+        "rr_server_destroy": [vp],
+        "rr_query_submit": [vp, pq, ctypes.POINTER(u64)],
+        "rr_query_poll": [vp, u64, i32, vp, vp],
+        "rr_query_cancel": [vp, u64],
+        "rr_query_times": [vp, u64, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)],
+        "rr_autotune": [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)],
+        "rr_set_tuning": [vp, u32, u32, u32],
+        "rr_debug_point_sums": [vp, pq, vp, u32, vp],
+        "rr_debug_graph": [vp, vp, vp, vp, vp],
+        "rr_debug_ztable": [vp, pq, vp],
+        "rr_debug_gf_mul": [vp, vp, vp, u64],
+        "rr_debug_draw": [u64, u64, u64, vp],
+        "rr_timing_enable": [ctypes.c_int],
+        "rr_timing_read": [ctypes.POINTER(rr_kernel_times), ctypes.c_int],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.rr_last_error.restype = ctypes.c_char_p
+    lib.rr_last_error.argtypes = []
+    lib.rr_kernel_launches.restype = ctypes.c_uint64
+    lib.rr_kernel_launches.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != RR_OK:
+        raise RRError(st, (_lib.rr_last_error() or b"").decode())
+    return st
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data
+
+
+def _dp(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def make_query(source: int, k: int, seed: int, motif=None):
+    """Returns (rr_query, keepalive) -- keep the second item alive during the call."""
+    m = None if motif is None else np.ascontiguousarray(motif, dtype=np.uint8)
+    q = rr_query(int(source), int(k), int(seed) & ((1 << 64) - 1),
+                 None if m is None else m.ctypes.data)
+    return q, m
+
+
+# -- entry points (same names as the C ABI) ----------------------------------
+
+def rr_graph_load(n, src, dst, t, delta, color=None, flags: int = 0):
+    lib = load()
+    src, dst, t = _host(src, np.uint32), _host(dst, np.uint32), _host(t, np.uint32)
+    delta, color = _host(delta, np.uint32), _host(color, np.uint8)
+    out = ctypes.c_void_p()
+    _check(lib.rr_graph_load(int(n), int(src.shape[0]), _hp(src), _hp(dst), _hp(t), _hp(delta),
+                             _hp(color), int(flags), ctypes.byref(out)))
+    return out.value
+
+
+def rr_graph_free(g):
+    _check(load().rr_graph_free(g))
+
+
+def rr_graph_get_info(g) -> dict:
+    info = rr_graph_info()
+    _check(load().rr_graph_get_info(g, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in rr_graph_info._fields_}
+
+
+def rr_reach_sync(g, n, source, k, seed, motif=None):
+    """Returns (bitmap uint8[ceil(n/8)], witness uint64[n])."""
+    q, keep = make_query(source, k, seed, motif)
+    bm = np.zeros((n + 7) // 8, dtype=np.uint8)
+    w = np.zeros(n, dtype=np.uint64)
+    _check(load().rr_reach_sync(g, ctypes.byref(q), _hp(bm), _hp(w)))
+    del keep
+    return bm, w
+
+
+def rr_reach_device(g, source, k, seed, d_witness, d_bitmap=None, stream=None, motif=None):
+    q, keep = make_query(source, k, seed, motif)
+    _check(load().rr_reach_device(g, ctypes.byref(q), _dp(d_bitmap), _dp(d_witness),
+                                  _dp(stream)))
+    del keep
+
+
+def _query_array(queries):
+    arr = (rr_query * len(queries))()
+    keep = []
+    for i, qd in enumerate(queries):
+        q, m = make_query(qd["source"], qd["k"], qd["seed"], qd.get("motif"))
+        arr[i] = q
+        keep.append(m)
+    return arr, keep
+
+
+def rr_reach_batch_device(g, queries, d_witness, d_bitmaps=None, d_status=None, stream=None):
+    arr, keep = _query_array(queries)
+    _check(load().rr_reach_batch_device(g, arr, len(queries), _dp(d_bitmaps), _dp(d_witness),
+                                        _dp(d_status), _dp(stream)))
+    del keep
+
+
+def rr_server_create(g, budget: int = 0, max_slots: int = 0):
+    out = ctypes.c_void_p()
+    _check(load().rr_server_create(g, int(budget), int(max_slots), ctypes.byref(out)))
+    return out.value
+
+
+def rr_server_destroy(s):
+    _check(load().rr_server_destroy(s))
+
+
+def rr_query_submit(s, source, k, seed, motif=None) -> int:
+    q, keep = make_query(source, k, seed, motif)
+    t = ctypes.c_uint64()
+    _check(load().rr_query_submit(s, ctypes.byref(q), ctypes.byref(t)))
+    del keep
+    return t.value
+
+
+def rr_query_poll(s, ticket, n, timeout_ms=-1):
+    """Returns (status, bitmap, witness); status RR_EAGAIN means not finished."""
+    bm = np.zeros((n + 7) // 8, dtype=np.uint8)
+    w = np.zeros(n, dtype=np.uint64)
+    st = load().rr_query_poll(s, int(ticket), int(timeout_ms), _hp(bm), _hp(w))
+    if st == RR_EAGAIN:
+        return st, None, None
+    _check(st)
+    return st, bm, w
+
+
+def rr_query_cancel(s, ticket):
+    _check(load().rr_query_cancel(s, int(ticket)))
+
+
+def rr_query_times(s, ticket):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().rr_query_times(s, int(ticket), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def rr_autotune(g, k):
+    p, c = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().rr_autotune(g, int(k), ctypes.byref(p), ctypes.byref(c)))
+    return p.value, c.value
+
+
+def rr_set_tuning(g, k, ppl, chunk):
+    _check(load().rr_set_tuning(g, int(k), int(ppl), int(chunk)))
+
+
+def rr_debug_point_sums(g, n, source, k, seed, masks, motif=None):
+    q, keep = make_query(source, k, seed, motif)
+    masks = _host(masks, np.uint32)
+    out = np.zeros((masks.shape[0], n), dtype=np.uint64)
+    _check(load().rr_debug_point_sums(g, ctypes.byref(q), _hp(masks), masks.shape[0], _hp(out)))
+    del keep
+    return out
+
+
+def rr_debug_graph(g, n, m):
+    off = np.zeros(n + 1, dtype=np.uint32)
+    eid = np.zeros(m, dtype=np.uint32)
+    lo = np.zeros(m, dtype=np.uint32)
+    hi = np.zeros(m, dtype=np.uint32)
+    _check(load().rr_debug_graph(g, _hp(off), _hp(eid), _hp(lo), _hp(hi)))
+    return off, eid, lo, hi
+
+
+def rr_debug_ztable(g, n, source, k, seed, motif=None):
+    q, keep = make_query(source, k, seed, motif)
+    out = np.zeros((n, k), dtype=np.uint64)
+    _check(load().rr_debug_ztable(g, ctypes.byref(q), _hp(out)))
+    del keep
+    return out
+
+
+def rr_debug_gf_mul(a, b):
+    a, b = _host(a, np.uint64), _host(b, np.uint64)
+    out = np.zeros_like(a)
+    _check(load().rr_debug_gf_mul(_hp(a), _hp(b), _hp(out), a.shape[0]))
+    return out
+
+
+def rr_debug_draw(key, first, count):
+    out = np.zeros(count, dtype=np.uint64)
+    _check(load().rr_debug_draw(int(key), int(first), int(count), _hp(out)))
+    return out
+
+
+def rr_timing_enable(enable: bool):
+    _check(load().rr_timing_enable(1 if enable else 0))
+
+
+def rr_timing_read(reset: bool = True) -> dict:
+    """{kind: (total_ms, launches)} for kinds in TIMING_KINDS."""
+    t = rr_kernel_times()
+    _check(load().rr_timing_read(ctypes.byref(t), 1 if reset else 0))
+    return {name: (t.ms[i], int(t.launches[i])) for i, name in enumerate(TIMING_KINDS)}
+
+
+def rr_last_error() -> str:
+    return (load().rr_last_error() or b"").decode()
+
+
+def rr_kernel_launches() -> int:
+    return int(load().rr_kernel_launches())
+
+
+class Graph:
+    """Convenience owner of an rr_graph handle (frees it on close)."""
+
+    def __init__(self, g: dict, flags: int = 0):
+        self.n = int(g["n"])
+        self.m = int(len(g["src"]))
+        self.handle = rr_graph_load(self.n, g["src"], g["dst"], g["t"], g["delta"],
+                                    g.get("color"), flags)
+
+    def info(self):
+        return rr_graph_get_info(self.handle)
+
+    def reach(self, source, k, seed, motif=None):
+        return rr_reach_sync(self.handle, self.n, source, k, seed, motif)
+
+    def point_sums(self, source, k, seed, masks, motif=None):
+        return rr_debug_point_sums(self.handle, self.n, source, k, seed, masks, motif)
+
+    def close(self):
+        if self.handle:
+            rr_graph_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,170 @@
+// rr_internal.h -- library-internal structures shared by the .cu/.cpp files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/restless_reach.h"
+
+namespace rr {
+
+// -------- errors -----------------------------------------------------------
+void set_error(const std::string &msg);
+void clear_error();
+rr_status fail(rr_status st, const std::string &msg);
+rr_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+extern std::atomic<uint64_t> g_launches;
+
+// Kernel timing (rr_timing_*): kinds as in rr_kernel_times.
+enum TimingKind { kTimeFirst = 0, kTimeMid = 1, kTimeLast = 2, kTimeZ = 3, kTimeBatch = 4 };
+extern std::atomic<bool> g_timing;
+// Records a start event on st when timing is enabled; returns an opaque slot.
+int timing_begin(cudaStream_t st);
+void timing_end(int slot, int kind, cudaStream_t st);
+
+#define RR_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t _e = (call);                                             \
+        if (_e != cudaSuccess) return ::rr::cuda_fail(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define RR_LAUNCHED()                                                        \
+    do {                                                                     \
+        ::rr::g_launches.fetch_add(1, std::memory_order_relaxed);            \
+        cudaError_t _e = cudaGetLastError();                                 \
+        if (_e != cudaSuccess) return ::rr::cuda_fail(_e, "kernel launch", __FILE__, __LINE__); \
+    } while (0)
+
+// -------- device buffer ----------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // Grows to at least `want` bytes (contents are not preserved).
+    cudaError_t reserve(size_t want)
+    {
+        if (want <= bytes && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, want ? want : 16);
+        if (e == cudaSuccess) bytes = want ? want : 16;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Scratch of one in-flight query: double-buffered prefix state, z-table,
+// witness sums, shade table and bitmap.
+struct Workspace {
+    DevBuf state;   // 2 * state_rows * chunk * 8
+    DevBuf z;       // n * k * 8
+    DevBuf S;       // n * 8
+    DevBuf shade;   // 512 uint32
+    DevBuf bitmap;  // ceil(n/8)
+    size_t bytes() const { return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes; }
+};
+
+// -------- graph ------------------------------------------------------------
+// In-edge CSR: rows sorted by (head v, time, input edge index). Vertex v owns
+// rows [off[v], off[v+1]).
+//
+// Windowed prefix state: for a point chunk, state row 0 is all zero and each
+// "producer" row r (a row inside the restless window of some edge) owns state
+// row row_s[r] >= 1 holding the XOR of its own and the earlier producer rows'
+// layer values within its head's segment. A consumer row e reads its window
+// sum as state[row_a[e]] ^ state[row_b[e]] (row_a == 0 <=> empty window).
+struct Graph {
+    uint32_t n = 0;
+    uint64_t m = 0;
+    int dev = 0;
+    bool has_colors = false;
+    bool compact = true;
+    uint64_t state_rows = 1;   // 1 + producers
+    uint64_t window_rows = 0;  // rows with a non-empty window
+    uint64_t producer_window_rows = 0;  // producer rows with a non-empty window
+    uint32_t max_in_degree = 0;
+
+    DevBuf off;      // n+1 uint32
+    DevBuf row_a;    // m uint32
+    DevBuf row_b;    // m uint32
+    DevBuf row_s;    // m uint32
+    DevBuf row_eid;  // m uint32
+    DevBuf row_src;  // m uint32
+    DevBuf row_lo;   // m uint32 (debug / tests)
+    DevBuf row_hi;   // m uint32
+    DevBuf color;    // n uint8 (if coloured)
+    DevBuf items;    // uint2 (v0, v1) vertex ranges, largest first
+    uint32_t nitems = 0;
+    std::vector<uint32_t> h_item_rows;  // rows per item (host copy, same order)
+
+    // per-graph scratch for rr_reach_device / rr_reach_sync (serialised by mu)
+    mutable std::mutex mu;
+    mutable Workspace ws;
+    mutable cudaStream_t stream = nullptr;
+
+    // tuning per k (index k): 0 = automatic
+    uint32_t tune_ppl[32] = {0};
+    uint32_t tune_chunk[32] = {0};
+
+    size_t device_bytes() const
+    {
+        return off.bytes + row_a.bytes + row_b.bytes + row_s.bytes + row_eid.bytes +
+               row_src.bytes + row_lo.bytes + row_hi.bytes + color.bytes + items.bytes;
+    }
+};
+
+// -------- query plan -------------------------------------------------------
+struct QueryKeys {
+    uint64_t key_y, key_z, key_gamma, key_omega;
+};
+
+// Shade layout of a motif: first shade and multiplicity per colour.
+struct ShadeTable {
+    uint32_t first[256];
+    uint32_t mu[256];
+};
+
+rr_status validate_query(const Graph &g, const rr_query *q);
+QueryKeys make_keys(uint64_t seed);
+void make_shades(const uint8_t *motif, uint32_t k, ShadeTable *out);
+
+// Chooses points-per-lane and points-per-chunk for a query of size k such that
+// the double-buffered state (2 * state_rows * chunk * 8 bytes) fits budget.
+// Returns false if even the smallest chunk does not fit.
+bool choose_shape(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl, uint32_t *chunk);
+
+// -------- kernels (rr_sieve.cu) --------------------------------------------
+struct LayerParams;
+rr_status launch_ztable(const Graph &g, uint32_t k, const QueryKeys &keys, bool colored,
+                        const uint32_t *d_shades /* 512 or null */, uint64_t *d_z,
+                        cudaStream_t st);
+rr_status launch_bitmap(const uint64_t *d_S, uint32_t n, uint8_t *d_bitmap, cudaStream_t st);
+
+// Runs all chunks and layers of one query; d_S must be zeroed by the caller
+// unless debug masks are given (then d_out = nmasks*n, zeroed by the caller).
+rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_z,
+                           uint64_t *d_state, uint32_t ppl, uint32_t chunk, uint64_t *d_S,
+                           const uint32_t *d_masks, uint32_t nmasks, uint64_t *d_debug_out,
+                           cudaStream_t st);
+// Runs one query on `st` with scratch `ws`; d_witness (n) required. `budget`
+// bounds the state buffers (0 = 60% of free device memory).
+rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
+                          uint64_t *d_witness, uint64_t budget, cudaStream_t st);
+// Bytes of scratch one query of size k needs with the chosen shape.
+uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint32_t chunk);
+
+}  // namespace rr
+
+struct rr_graph : public rr::Graph {};
