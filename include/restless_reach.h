@@ -120,6 +120,27 @@ rr_status rr_reach_sync(const rr_graph *g, const rr_query *q, uint8_t *bitmap,
 rr_status rr_reach_device(const rr_graph *g, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, void *stream);
 
+/* rr_reach_device_noalloc: the computation of rr_reach_device for callers that
+ * must not allocate device memory while they serve queries -- a process whose
+ * device memory is already owned by another allocator's pool, or a
+ * latency-critical loop that cannot afford the device-wide synchronisation a
+ * cudaMalloc/cudaFree brings. It calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch (z-table, shade table, both prefix-state
+ * buffers) is one static device array of 256 MiB in the library, kept by every
+ * GPU this entry point is used on until the process exits. The paper has no
+ * counterpart; this is a deployment variant of the same sieve.
+ * Arguments are those of rr_reach_device; the graph's device must be current.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * starts. Queries whose scratch would exceed 256 MiB (n*k*8 bytes of z-table
+ * plus 2 * state_rows * 64 * 8 bytes of state for the smallest point chunk)
+ * are rejected with RR_ENOMEM and a message giving both sizes. Every call
+ * shares the array and clears what must start at zero itself; calls whose
+ * work overlaps on the GPU (unordered streams) race on it, so order them on
+ * one stream. */
+rr_status rr_reach_device_noalloc(const rr_graph *g, const rr_query *q, uint8_t *d_bitmap,
+                                  uint64_t *d_witness, void *stream);
+
 /* ---- many queries, one persistent launch (batched form) --------------------
  * rr_reach_batch_device: runs nq queries of any mix of k, sources and motifs
  * in ONE persistent kernel launch. Work is split into (query, point chunk,

@@ -53,7 +53,7 @@ EXPORTED = [
     "rr_query_submit", "rr_query_poll", "rr_query_cancel", "rr_query_times", "rr_autotune",
     "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
-    "rr_timing_enable", "rr_timing_read",
+    "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc",
 ]
 
 _lib = None
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True):
         "rr_graph_get_info": [vp, ctypes.POINTER(rr_graph_info)],
         "rr_reach_sync": [vp, pq, vp, vp],
         "rr_reach_device": [vp, pq, vp, vp, vp],
+        "rr_reach_device_noalloc": [vp, pq, vp, vp, vp],
         "rr_reach_batch_device": [vp, pq, u32, vp, vp, vp, vp],
         "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
         "rr_server_destroy": [vp],
@@ -178,6 +179,15 @@ def rr_reach_device(g, source, k, seed, d_witness, d_bitmap=None, stream=None, m
     q, keep = make_query(source, k, seed, motif)
     _check(load().rr_reach_device(g, ctypes.byref(q), _dp(d_bitmap), _dp(d_witness),
                                   _dp(stream)))
+    del keep
+
+
+def rr_reach_device_noalloc(g, source, k, seed, d_witness, d_bitmap=None, stream=None,
+                            motif=None):
+    """rr_reach_device without any device allocation (static 256 MiB scratch)."""
+    q, keep = make_query(source, k, seed, motif)
+    _check(load().rr_reach_device_noalloc(g, ctypes.byref(q), _dp(d_bitmap), _dp(d_witness),
+                                          _dp(stream)))
     del keep
 
 
