@@ -215,18 +215,24 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         launches0 = capi.rr_kernel_launches()
-        capi.rr_timing_enable(True)
-        capi.rr_timing_read(reset=True)
         for i in range(args.steps):
             flush.fill_(i)  # evict L2 between steps (outside the timed events)
             evs[i][0].record(stream)
             step(args.warmup + i)
             evs[i][1].record(stream)
         torch.cuda.synchronize()
-        kt = capi.rr_timing_read(reset=True)
-        capi.rr_timing_enable(False)
         launches = capi.rr_kernel_launches() - launches0
         clocks = sampler.stop()
+        # profiling pass (not timed above): per-kernel CUDA-event durations
+        # recorded by the library on the launching stream
+        capi.rr_timing_enable(True)
+        capi.rr_timing_read(reset=True)
+        for i in range(5):
+            flush.fill_(i)
+            step(10_000 + i)
+        torch.cuda.synchronize()
+        kt = capi.rr_timing_read(reset=True)
+        capi.rr_timing_enable(False)
     ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(ms)
     if dist:
@@ -236,43 +242,62 @@ def main():
     units = units_per_query(K, m)
     value = world * args.steps * units / (tot_ms / 1e3)
 
-    # end to end through the host-buffer C ABI: result copied back every step
+    # end to end through the host-buffer C ABI (rr_reach_sync: results copied
+    # back to host memory every step), L2 flushed between steps
     for i in range(2):
         G.reach(SOURCE, K, seed_base ^ (1000 + i))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t0 = time.perf_counter()
+    e2e_s = 0.0
     for i in range(args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         G.reach(SOURCE, K, seed_base ^ (2000 + i))
-    e2e_s = time.perf_counter() - t0
+        e2e_s += time.perf_counter() - t0
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = world * args.steps * units / e2e_s
 
-    # roofline of the dominant kernel: the middle-layer kernel
+    # roofline: algorithmic bytes per launch of each kernel kind of the
+    # reduced-state engine, over its measured average launch duration
     peaks, peak_kind = measured_peaks()
-    mid_ms, mid_n = kt["mid_layer"]
-    prod = info["state_rows"] - 1
-    cons = info["producer_window_rows"]
-    # per launch: every producer row's state slice is written, every producer
-    # row with a window reads two slices; per-row indices read once
-    alg_bytes = (prod + 2 * cons) * chunk * 8 + m * 8 + cons * 8 + n * K * 8
+    srows = info["producer_window_rows"]      # state rows
+    crows = info["state_compute_rows"]        # state rows that multiply at layers >= 3
+    trows = info["tail_rows"]                 # last-layer rows
+    lg = 7 if ppl == 4 else 6
+    rstride = chunk // (32 * ppl) * (lg + 1)
+    alg = {
+        "second_layer": srows * chunk * 8 + srows * 28 + 2 * srows * K * 8,
+        "mid_layer": srows * chunk * 8 + 2 * crows * chunk * 8 + srows * 16,
+        "tail_layer": srows * rstride * 8 + 2 * crows * chunk * 8 + srows * 16,
+        "last_layer": 2 * trows * rstride * 8 + trows * 16 + n * 8,
+        "first_layer": info["state_rows"] * 8 * 2,
+        "ztable": n * K * 8,
+    }
     if args.dense:
-        alg_bytes = (m + 2 * info["window_rows"]) * chunk * 8 + m * 16 + n * K * 8
+        alg = {"mid_layer": (m + 2 * info["window_rows"]) * chunk * 8 + m * 16 + n * K * 8}
+    by_kernel = {}
+    for name, (kms, kn) in kt.items():
+        if kn and name in alg:
+            avg_s = kms / kn / 1e3
+            gbs = alg[name] / avg_s / 1e9
+            by_kernel[name] = {"avg_launch_us": round(avg_s * 1e6, 2), "launches_per_query": kn / 5,
+                               "alg_bytes_per_launch": alg[name], "achieved_gbs": round(gbs, 1),
+                               "frac": round(gbs / peaks["hbm_gbs"], 4)}
+    dom = max(by_kernel, key=lambda k_: kt[k_][0]) if by_kernel else None
     roofline = None
-    if mid_n:
-        avg_s = mid_ms / mid_n / 1e3
-        achieved = alg_bytes / avg_s / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "kernel": "k_layer (middle layers)", "peak_kind": peak_kind,
-                    "avg_launch_us": avg_s * 1e6, "launches": mid_n,
-                    "alg_bytes_per_launch": alg_bytes}
-    kernel_share = {k_: round(v[0] / max(1e-9, sum(x[0] for x in kt.values())), 4)
-                    for k_, v in kt.items() if v[1]}
+    if dom:
+        d = by_kernel[dom]
+        roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": d["frac"], "traffic": None, "kernel": dom,
+                    "peak_kind": peak_kind, "avg_launch_us": d["avg_launch_us"],
+                    "alg_bytes_per_launch": d["alg_bytes_per_launch"]}
+    tot_k = max(1e-9, sum(v[0] for v in kt.values()))
+    kernel_share = {k_: round(v[0] / tot_k, 4) for k_, v in kt.items() if v[1]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
@@ -281,13 +306,16 @@ def main():
             "config": {"workload": WORKLOAD, "graph_seed": GRAPH_SEED, "l2": "flushed between steps",
                        "state_layout": "dense" if args.dense else "compact",
                        "points_per_lane": ppl, "points_per_chunk": chunk,
-                       "state_rows": info["state_rows"], "window_rows": info["window_rows"],
+                       "state_rows": srows + 1, "state_compute_rows": crows, "tail_rows": trows,
+                       "producer_rows": info["state_rows"] - 1, "window_rows": info["window_rows"],
                        "graph_load_s": round(load_s, 3)},
             "roofline": roofline,
+            "roofline_by_kernel": by_kernel,
             "kernel_time_share": kernel_share,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "kernel_ms_per_query": round(tot_k / 5, 4),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 272,
                     "d2h_bytes_per_step": n * 8 + (n + 7) // 8,
-                    "api": "rr_reach_sync (host outputs)"},
+                    "api": "rr_reach_sync (host outputs, query descriptor uploaded per step)"},
             "gpu_launches": int(launches), "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, K)

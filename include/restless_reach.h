@@ -85,7 +85,9 @@ typedef struct {
     uint64_t device_bytes;   /* bytes the resident graph holds on the device */
     int has_colors;
     int compact;             /* 1: state stores only rows inside some window */
-    uint64_t producer_window_rows; /* state rows whose own window is non-empty */
+    uint64_t producer_window_rows; /* rows inside some window whose own window is non-empty */
+    uint64_t state_compute_rows;   /* of those, rows whose window holds another such row */
+    uint64_t tail_rows;            /* rows whose window holds a producer row with a window */
 } rr_graph_info;
 
 /* ---- graph ----------------------------------------------------------------
@@ -204,11 +206,14 @@ rr_status rr_debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *
  * While enabled (process-wide), every kernel launch of the sieve is bracketed
  * by CUDA events on the stream it is launched on; rr_timing_read waits for the
  * recorded events and returns the summed durations and launch counts per
- * kind: 0 = first layer, 1 = middle layers, 2 = last layer with the fused
- * per-vertex reduce, 3 = z-table, 4 = persistent batched kernel. */
+ * kind: 0 = first layer, 1 = middle layers reading state, 2 = last layer with
+ * the fused per-vertex reduce, 3 = z-table, 4 = persistent batched kernel,
+ * 5 = second layer (window sums from the first layer's scalar prefix),
+ * 6 = layer k-2 writing the transformed state. While timing is enabled the
+ * launches are issued one by one instead of as a captured CUDA graph. */
 typedef struct {
-    double ms[5];
-    uint64_t launches[5];
+    double ms[8];
+    uint64_t launches[8];
 } rr_kernel_times;
 rr_status rr_timing_enable(int enable);
 rr_status rr_timing_read(rr_kernel_times *out, int reset);

@@ -37,14 +37,16 @@ class rr_graph_info(ctypes.Structure):
                 ("state_rows", ctypes.c_uint64), ("window_rows", ctypes.c_uint64),
                 ("max_in_degree", ctypes.c_uint32), ("num_items", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("has_colors", ctypes.c_int),
-                ("compact", ctypes.c_int), ("producer_window_rows", ctypes.c_uint64)]
+                ("compact", ctypes.c_int), ("producer_window_rows", ctypes.c_uint64),
+                ("state_compute_rows", ctypes.c_uint64), ("tail_rows", ctypes.c_uint64)]
 
 
 class rr_kernel_times(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_uint64 * 5)]
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
 
 
-TIMING_KINDS = ["first_layer", "mid_layer", "last_layer", "ztable", "batch"]
+TIMING_KINDS = ["first_layer", "mid_layer", "last_layer", "ztable", "batch", "second_layer",
+                "tail_layer", "unused"]
 
 
 EXPORTED = [
@@ -202,6 +204,7 @@ def _query_array(queries):
 
 
 def rr_reach_batch_device(g, queries, d_witness, d_bitmaps=None, d_status=None, stream=None):
+    """queries: list of dicts with source, k, seed and optional motif."""
     arr, keep = _query_array(queries)
     _check(load().rr_reach_batch_device(g, arr, len(queries), _dp(d_bitmaps), _dp(d_witness),
                                         _dp(d_status), _dp(stream)))

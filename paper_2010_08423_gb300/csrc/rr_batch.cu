@@ -1,26 +1,547 @@
-// rr_batch.cu -- many queries in one call, and the shape autotuner.
+// rr_batch.cu -- many queries in one persistent launch, and the shape autotuner.
+//
+// A batch is cut into units (one query's chunk of sieve points). Units run in
+// waves over `nslots` memory slots (each slot: two full prefix-state buffers
+// and one transformed buffer). Every warp-sized piece of layer work -- (unit,
+// layer, scheduling range, point group) -- is a task; tasks are numbered in
+// the order wave, layer, unit, so a task only ever depends on tasks with
+// smaller numbers:
+//   layer l >= 3 of unit U needs every task of U's layers < l,
+//   layer 2 of U needs every task of the unit that used U's slot before it.
+// The persistent kernel's warps take task numbers from one atomic counter and
+// wait (bounded, with backoff) on a per-unit completion counter before they
+// start. Because a task's predecessors were all taken earlier by warps that
+// are already running, the waits always end unless the device misbehaves; a
+// wait that exceeds its time limit marks the query RR_ETIMEDOUT, sets an abort
+// flag that makes every later task skip its work, and lets the kernel finish.
+// The per-warp work is the same code as the one-query kernels
+// (rr_v2_device.cuh), so results are bit-identical.
 #include <algorithm>
 #include <cstring>
 
-#include "rr_internal.h"
+#include "rr_v2_device.cuh"
 
 namespace rr {
+
+namespace {
+
+enum BatchKind : uint32_t {
+    kSecondFull = 0,   // layer 2, window sums from the scalar prefix, full state out
+    kSecondTail = 1,   // layer 2 when k = 4, transformed state out
+    kSecondFinal = 2,  // layer 2 when k = 3, per-vertex sums out
+    kMidFull = 3,      // layers 3..k-3
+    kMidTail = 4,      // layer k-2 (k >= 5), transformed state out
+    kLast = 5          // layer k-1 from the transformed state
+};
+
+struct BatchUnit {
+    uint32_t q, k, chunk_base, chunk, ppl, slot;
+    uint32_t qi;  // the query's index in the caller's array (status slot)
+};
+
+struct BatchSeg {
+    uint32_t begin, ntasks, unit, layer, kind, ngroups;
+    int32_t wait_unit;  // unit whose completion counter gates this segment (-1: none)
+    uint32_t wait_count;
+};
+
+struct ListPtrs {
+    const uint32_t *head, *eid, *src, *a0, *b0, *a1, *b1;
+    const uint2 *items;
+    uint32_t nitems;
+};
+
+struct BatchArgs {
+    ListPtrs prod, state, win, tail;
+    uint32_t n;
+    const BatchUnit *units;
+    const BatchSeg *segs;
+    uint32_t nseg, total_tasks;
+    const QueryDesc *descs;
+    const uint64_t *z_all;
+    const uint64_t *z_off;   // per query, in words
+    const uint64_t *py_all;
+    const uint64_t *py_off;  // per query, in words
+    uint64_t *slot_base;
+    uint64_t slot_words, rows, full_words;  // rows = state rows + 1; full_words = rows * max chunk
+    uint32_t *done;       // per unit: tasks completed
+    uint32_t *ctl;        // [0] next task, [1] abort
+    int32_t *status;      // per query
+    uint64_t timeout_ns;
+};
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Lane 0 waits until *ctr >= want; false if the wait timed out or the batch
+// was aborted. The wait is bounded by timeout_ns of wall time and by an
+// iteration cap.
+__device__ bool wait_for(const BatchArgs &a, const uint32_t *ctr, uint32_t want)
+{
+    const uint64_t t0 = global_ns();
+    uint32_t sleep = 32;
+    for (uint32_t it = 0; it < 100000000u; ++it) {
+        if (ld_acquire(ctr) >= want) return true;
+        if (*(volatile uint32_t *)(a.ctl + 1)) return false;
+        if (global_ns() - t0 > a.timeout_ns) return false;
+        __nanosleep(sleep);
+        if (sleep < 2048) sleep <<= 1;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void set_list(V2Params &vp, const ListPtrs &L, bool first_window)
+{
+    vp.head = L.head;
+    vp.eid = L.eid;
+    vp.src = L.src;
+    vp.ia = first_window ? L.a0 : L.a1;
+    vp.ib = first_window ? L.b0 : L.b1;
+    vp.items = L.items;
+    vp.nitems = L.nitems;
+}
+
+template <int PPL>
+__device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg, const BatchUnit &u,
+                                         uint32_t local)
+{
+    V2Params vp{};
+    vp.qd = a.descs + u.q;
+    vp.z = a.z_all + a.z_off[u.q];
+    vp.py = a.py_all + a.py_off[u.q];
+    vp.n = a.n;
+    vp.k = u.k;
+    vp.layer = sg.layer;
+    vp.chunk_base = u.chunk_base;
+    vp.chunk = u.chunk;
+    vp.ngroups = sg.ngroups;
+    vp.npoints = 1u << u.k;
+    uint64_t *full0 = a.slot_base + (size_t)u.slot * a.slot_words;
+    uint64_t *full1 = full0 + a.full_words;
+    uint64_t *red = full1 + a.full_words;
+    uint64_t *bufs[2] = {full0, full1};
+    const uint32_t l = sg.layer;
+    const uint32_t item = sg.kind == kLast ? local : local / sg.ngroups;
+    const uint32_t group = sg.kind == kLast ? 0u : local - item * sg.ngroups;
+    switch (sg.kind) {
+    case kSecondFull:
+        set_list(vp, a.state, true);
+        vp.st_out = bufs[l & 1u];
+        layer_warp<PPL, true, 0, true>(vp, item, group);
+        break;
+    case kSecondTail:
+        set_list(vp, a.state, true);
+        vp.st_out = red;
+        layer_warp<PPL, true, 1, true>(vp, item, group);
+        break;
+    case kSecondFinal:
+        set_list(vp, a.win, true);
+        layer_warp<PPL, true, 2, true>(vp, item, group);
+        break;
+    case kMidFull:
+        set_list(vp, a.state, false);
+        vp.st_in = bufs[(l - 1) & 1u];
+        vp.st_out = bufs[l & 1u];
+        layer_warp<PPL, false, 0, true>(vp, item, group);
+        break;
+    case kMidTail:
+        set_list(vp, a.state, false);
+        vp.st_in = bufs[(l - 1) & 1u];
+        vp.st_out = red;
+        layer_warp<PPL, false, 1, true>(vp, item, group);
+        break;
+    default:
+        set_list(vp, a.tail, false);
+        vp.st_in = red;
+        last_warp<PPL == 4 ? 7 : 6, true>(vp, item);
+        break;
+    }
+}
+
+__global__ void __launch_bounds__(kW2 * 32) k_batch(const BatchArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(a.ctl, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.total_tasks) return;
+        // segment holding task t (largest begin <= t)
+        uint32_t lo = 0, hi = a.nseg;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.segs[mid].begin <= t) lo = mid; else hi = mid;
+        }
+        const BatchSeg sg = a.segs[lo];
+        const BatchUnit u = a.units[sg.unit];
+        bool ok = true;
+        if (lane == 0) {
+            if (sg.wait_unit >= 0 && sg.wait_count)
+                ok = wait_for(a, a.done + sg.wait_unit, sg.wait_count);
+            if (!ok) atomicExch(a.ctl + 1, 1u);
+            if (*(volatile uint32_t *)(a.ctl + 1)) ok = false;
+            // a skipped task leaves its query's sums incomplete
+            if (!ok) atomicExch(a.status + u.qi, (int32_t)RR_ETIMEDOUT);
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (ok) {
+            __threadfence();  // acquire side: see the predecessors' state writes
+            if (u.ppl == 4) run_task<4>(a, sg, u, t - sg.begin);
+            else run_task<2>(a, sg, u, t - sg.begin);
+        }
+        __threadfence();  // release side: publish this task's writes
+        __syncwarp();
+        if (lane == 0) atomicAdd(a.done + sg.unit, 1u);
+    }
+}
+
+// Prologue / epilogue over all queries of the batch (blockIdx.y = query).
+__global__ void k_batch_ztable(uint32_t n, const QueryDesc *__restrict__ descs,
+                               const uint8_t *__restrict__ color, uint64_t *__restrict__ z_all,
+                               const uint64_t *__restrict__ z_off)
+{
+    const QueryDesc *qd = descs + blockIdx.y;
+    const uint32_t k = qd->k;
+    uint64_t *z = z_all + z_off[blockIdx.y];
+    const uint64_t total = (uint64_t)n * k;
+    const bool colored = qd->colored != 0;
+    for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t u = idx / k;
+        const uint32_t j = (uint32_t)(idx - u * k);
+        uint64_t val = 0;
+        if (!colored) {
+            val = sm_draw(qd->key_z, u * 32u + j);
+        } else {
+            const uint32_t c = color[u];
+            const uint32_t d0 = qd->shades[c], mu = qd->shades[256 + c];
+            for (uint32_t d = d0; d < d0 + mu; ++d)
+                val ^= gf64_mul(sm_draw(qd->key_g, u * 32u + d), sm_draw(qd->key_o, (uint64_t)d * 32u + j));
+        }
+        z[idx] = val;
+    }
+}
+
+__global__ void __launch_bounds__(kW2 * 32)
+k_batch_first(ListPtrs prod, const QueryDesc *__restrict__ descs, uint64_t *__restrict__ py_all,
+              const uint64_t *__restrict__ py_off)
+{
+    uint64_t *py = py_all + py_off[blockIdx.y];
+    if (blockIdx.x == 0 && threadIdx.x == 0) py[0] = 0;
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= prod.nitems) return;
+    V2Params vp{};
+    vp.qd = descs + blockIdx.y;
+    vp.head = prod.head;
+    vp.eid = prod.eid;
+    vp.src = prod.src;
+    vp.items = prod.items;
+    vp.nitems = prod.nitems;
+    first_scalar_warp(vp, task, py);
+}
+
+__global__ void k_batch_bitmap(uint32_t n, const QueryDesc *__restrict__ descs)
+{
+    const QueryDesc *qd = descs + blockIdx.y;
+    const uint64_t *S = qd->S;
+    uint8_t *bm = qd->bitmap;
+    if (!bm) return;
+    const uint32_t nb = (n + 7) / 8;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        for (uint32_t i = 0; i < 8; ++i) {
+            const uint32_t v = b * 8 + i;
+            if (v < n && S[v] != 0) bits |= 1u << i;
+        }
+        bm[b] = (uint8_t)bits;
+    }
+}
+
+// zero row (row 0) of every slot's three buffers: `width` words of each full
+// buffer (its widest row) and 32 words of the transformed buffer
+__global__ void k_batch_zero_rows(uint64_t *slot_base, uint64_t slot_words, uint64_t full_words,
+                                  uint32_t nslots, uint32_t width)
+{
+    const uint32_t s = blockIdx.x;
+    if (s >= nslots) return;
+    uint64_t *b = slot_base + (size_t)s * slot_words;
+    for (uint32_t i = threadIdx.x; i < width; i += blockDim.x) {
+        b[i] = 0;
+        b[full_words + i] = 0;
+    }
+    for (uint32_t i = threadIdx.x; i < 32; i += blockDim.x) b[2 * full_words + i] = 0;
+}
+
+ListPtrs list_ptrs(const RowList &L)
+{
+    return ListPtrs{L.head.as<uint32_t>(), L.eid.as<uint32_t>(), L.src.as<uint32_t>(),
+                    L.a0.as<uint32_t>(),   L.b0.as<uint32_t>(),  L.a1.as<uint32_t>(),
+                    L.b1.as<uint32_t>(),   L.items.as<uint2>(),  L.nitems};
+}
+
+// Tasks of layer l of a unit with (k, ppl, chunk).
+uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, uint32_t *kind)
+{
+    if (k == 3) {
+        *kind = kSecondFinal;
+        return g.win_list.nitems * ngroups;
+    }
+    if (l == k - 1) {
+        *kind = kLast;
+        return g.tail_list.nitems;
+    }
+    if (l == 2) *kind = (k == 4) ? kSecondTail : kSecondFull;
+    else *kind = (l == k - 2) ? kMidTail : kMidFull;
+    return g.state_list.nitems * ngroups;
+}
+
+}  // namespace
+
+// Bytes of device memory one batch slot holds for max chunk `chunk`.
+static uint64_t slot_words_for(const Graph &g, uint32_t chunk)
+{
+    const uint64_t rows = g.state_list.count + 1;
+    return rows * chunk * 2 + rows * 32;
+}
 
 rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
                        uint64_t *d_witness, int32_t *d_status, cudaStream_t st)
 {
+    if (nq == 0) return RR_OK;
     const size_t nb = (g.n + 7) / 8;
+    if (d_status) RR_CUDA(cudaMemsetAsync(d_status, 0, (size_t)nq * 4, st));
+    // k = 2 queries and per-point-engine graphs run one query at a time
+    std::vector<uint32_t> bq;
     for (uint32_t i = 0; i < nq; ++i) {
+        if (uses_v2(g, qs[i].k)) {
+            bq.push_back(i);
+            continue;
+        }
         rr_status s = reach_on_stream(g, g.ws, &qs[i], d_bitmaps ? d_bitmaps + i * nb : nullptr,
                                       d_witness + (size_t)i * g.n, 0, st);
         if (s != RR_OK) return s;
     }
-    if (d_status && nq) RR_CUDA(cudaMemsetAsync(d_status, 0, (size_t)nq * 4, st));
+    if (bq.empty()) return RR_OK;
+
+    size_t free_b = 0, total_b = 0;
+    RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t budget = (uint64_t)(0.6 * (double)free_b);
+    const uint64_t rows = g.state_list.count + 1;
+    const uint64_t py_words = (g.prod_list.count + 1 + 31) / 32 * 32;
+
+    // queries are processed in groups whose z-tables and prefixes fit half the budget
+    size_t gi = 0;
+    while (gi < bq.size()) {
+        std::vector<uint32_t> grp;
+        uint64_t qbytes = 0;
+        while (gi < bq.size()) {
+            const uint64_t need = ((uint64_t)g.n * qs[bq[gi]].k + 32 + py_words) * 8;
+            if (!grp.empty() && qbytes + need > budget / 2) break;
+            qbytes += need;
+            grp.push_back(bq[gi++]);
+        }
+        // largest point chunk (<= 512) for which at least one slot fits the rest
+        uint32_t max_chunk = 512;
+        while (max_chunk > 64 && slot_words_for(g, max_chunk) * 8 > budget - std::min(budget, qbytes))
+            max_chunk >>= 1;
+        if (slot_words_for(g, max_chunk) * 8 + qbytes > budget)
+            return fail(RR_ENOMEM, "rr_reach_batch_device: one query and one slot do not fit device memory");
+
+        // units
+        std::vector<BatchUnit> units;
+        std::vector<QueryDesc> descs(grp.size());
+        std::vector<uint64_t> z_off(grp.size()), py_off(grp.size());
+        uint64_t zw = 0;
+        for (size_t j = 0; j < grp.size(); ++j) {
+            const rr_query &q = qs[grp[j]];
+            QueryDesc &hd = descs[j];
+            std::memset(&hd, 0, sizeof hd);
+            const QueryKeys keys = make_keys(q.seed);
+            hd.source = q.source;
+            hd.k = q.k;
+            hd.colored = q.motif ? 1u : 0u;
+            hd.key_y = keys.key_y;
+            hd.key_z = keys.key_z;
+            hd.key_g = keys.key_gamma;
+            hd.key_o = keys.key_omega;
+            hd.S = d_witness + (size_t)grp[j] * g.n;
+            hd.bitmap = d_bitmaps ? d_bitmaps + (size_t)grp[j] * nb : nullptr;
+            if (q.motif) {
+                ShadeTable sh;
+                make_shades(q.motif, q.k, &sh);
+                std::memcpy(hd.shades, sh.first, sizeof sh.first);
+                std::memcpy(hd.shades + 256, sh.mu, sizeof sh.mu);
+            }
+            z_off[j] = zw;
+            zw += ((uint64_t)g.n * q.k + 31) / 32 * 32;
+            py_off[j] = j * py_words;
+            const uint64_t npts = 1ull << q.k;
+            const uint32_t ppl = npts >= 128 ? 4u : 2u;
+            uint32_t chunk = (uint32_t)std::max<uint64_t>(32ull * ppl, std::min<uint64_t>(npts, max_chunk));
+            chunk = std::max<uint32_t>(chunk, 32u * ppl);
+            const uint64_t nch = (npts + chunk - 1) / chunk;
+            for (uint64_t c = 0; c < nch; ++c)
+                units.push_back(BatchUnit{(uint32_t)j, q.k, (uint32_t)(c * chunk), chunk, ppl, 0,
+                                          grp[j]});
+        }
+        const uint64_t slot_bytes = slot_words_for(g, max_chunk) * 8;
+        uint32_t nslots = (uint32_t)std::min<uint64_t>(
+            {(uint64_t)units.size(), 64ull, (budget - qbytes) / slot_bytes});
+        nslots = std::max<uint32_t>(1, nslots);
+        for (size_t i = 0; i < units.size(); ++i) units[i].slot = (uint32_t)(i % nslots);
+
+        // segments in task order: wave, layer, unit
+        std::vector<uint32_t> unit_total(units.size(), 0);
+        std::vector<std::vector<uint32_t>> per_layer(units.size());
+        for (size_t i = 0; i < units.size(); ++i) {
+            const BatchUnit &u = units[i];
+            const uint32_t ngroups = u.chunk / (32u * u.ppl);
+            per_layer[i].assign(u.k + 1, 0);
+            for (uint32_t l = 2; l <= u.k - 1; ++l) {
+                uint32_t kind;
+                per_layer[i][l] = layer_tasks(g, u.k, l, ngroups, &kind);
+                unit_total[i] += per_layer[i][l];
+            }
+        }
+        std::vector<BatchSeg> segs;
+        uint64_t total = 0;
+        for (size_t w0 = 0; w0 < units.size(); w0 += nslots) {
+            const size_t w1 = std::min(units.size(), w0 + nslots);
+            uint32_t maxl = 0;
+            for (size_t i = w0; i < w1; ++i) maxl = std::max(maxl, units[i].k - 1);
+            for (uint32_t l = 2; l <= maxl; ++l)
+                for (size_t i = w0; i < w1; ++i) {
+                    const BatchUnit &u = units[i];
+                    if (l > u.k - 1) continue;
+                    const uint32_t ngroups = u.chunk / (32u * u.ppl);
+                    uint32_t kind;
+                    const uint32_t nt = layer_tasks(g, u.k, l, ngroups, &kind);
+                    if (nt == 0) continue;
+                    BatchSeg sg{};
+                    sg.begin = (uint32_t)total;
+                    sg.ntasks = nt;
+                    sg.unit = (uint32_t)i;
+                    sg.layer = l;
+                    sg.kind = kind;
+                    sg.ngroups = ngroups;
+                    if (l == 2) {
+                        const long prev = (long)i - (long)nslots;
+                        sg.wait_unit = prev >= 0 ? (int32_t)prev : -1;
+                        sg.wait_count = prev >= 0 ? unit_total[prev] : 0;
+                    } else {
+                        uint32_t before = 0;
+                        for (uint32_t l2 = 2; l2 < l; ++l2) before += per_layer[i][l2];
+                        sg.wait_unit = (int32_t)i;
+                        sg.wait_count = before;
+                    }
+                    segs.push_back(sg);
+                    total += nt;
+                }
+        }
+        if (total >= (1ull << 32)) return fail(RR_EINVAL, "rr_reach_batch_device: batch too large");
+
+        // device buffers (kept by the graph and grown as needed)
+        BatchBuffers &B = g.batch;
+        RR_CUDA(B.units.reserve(units.size() * sizeof(BatchUnit)));
+        RR_CUDA(B.segs.reserve(std::max<size_t>(1, segs.size()) * sizeof(BatchSeg)));
+        RR_CUDA(B.descs.reserve(descs.size() * sizeof(QueryDesc)));
+        RR_CUDA(B.zoff.reserve(grp.size() * 8));
+        RR_CUDA(B.pyoff.reserve(grp.size() * 8));
+        RR_CUDA(B.z.reserve(zw * 8));
+        RR_CUDA(B.py.reserve(grp.size() * py_words * 8));
+        RR_CUDA(B.slots.reserve((size_t)nslots * slot_bytes));
+        RR_CUDA(B.done.reserve(units.size() * 4));
+        RR_CUDA(B.ctl.reserve(8));
+        if (!d_status) RR_CUDA(B.status.reserve((size_t)nq * 4));
+        int32_t *status = d_status ? d_status : B.status.as<int32_t>();
+        if (!d_status) RR_CUDA(cudaMemsetAsync(status, 0, (size_t)nq * 4, st));
+        DevBuf &d_units = B.units, &d_segs = B.segs, &d_descs = B.descs, &d_zoff = B.zoff,
+               &d_pyoff = B.pyoff, &d_z = B.z, &d_py = B.py, &d_slots = B.slots, &d_done = B.done,
+               &d_ctl = B.ctl;
+        // pageable sources: each copy is staged before the call returns
+        RR_CUDA(cudaMemcpyAsync(d_units.p, units.data(), units.size() * sizeof(BatchUnit),
+                                cudaMemcpyHostToDevice, st));
+        if (!segs.empty())
+            RR_CUDA(cudaMemcpyAsync(d_segs.p, segs.data(), segs.size() * sizeof(BatchSeg),
+                                    cudaMemcpyHostToDevice, st));
+        RR_CUDA(cudaMemcpyAsync(d_descs.p, descs.data(), descs.size() * sizeof(QueryDesc),
+                                cudaMemcpyHostToDevice, st));
+        RR_CUDA(cudaMemcpyAsync(d_zoff.p, z_off.data(), grp.size() * 8, cudaMemcpyHostToDevice, st));
+        RR_CUDA(cudaMemcpyAsync(d_pyoff.p, py_off.data(), grp.size() * 8, cudaMemcpyHostToDevice, st));
+        RR_CUDA(cudaMemsetAsync(d_done.p, 0, units.size() * 4, st));
+        RR_CUDA(cudaMemsetAsync(d_ctl.p, 0, 8, st));
+        for (uint32_t j : grp) RR_CUDA(cudaMemsetAsync(d_witness + (size_t)j * g.n, 0, (size_t)g.n * 8, st));
+
+        const unsigned gz = (unsigned)std::min<uint64_t>(1024, ((uint64_t)g.n * 20 + 255) / 256);
+        k_batch_ztable<<<dim3(gz, (unsigned)grp.size()), 256, 0, st>>>(
+            g.n, d_descs.as<QueryDesc>(), g.color.as<uint8_t>(), d_z.as<uint64_t>(),
+            d_zoff.as<uint64_t>());
+        RR_LAUNCHED();
+        const ListPtrs prod = list_ptrs(g.prod_list);
+        k_batch_first<<<dim3(std::max<uint32_t>(1, (prod.nitems + kW2 - 1) / kW2), (unsigned)grp.size()),
+                        kW2 * 32, 0, st>>>(prod, d_descs.as<QueryDesc>(), d_py.as<uint64_t>(),
+                                           d_pyoff.as<uint64_t>());
+        RR_LAUNCHED();
+        k_batch_zero_rows<<<nslots, 256, 0, st>>>(d_slots.as<uint64_t>(), slot_bytes / 8,
+                                                  rows * max_chunk, nslots, max_chunk);
+        RR_LAUNCHED();
+
+        BatchArgs a{};
+        a.prod = prod;
+        a.state = list_ptrs(g.state_list);
+        a.win = list_ptrs(g.win_list);
+        a.tail = list_ptrs(g.tail_list);
+        a.n = g.n;
+        a.units = d_units.as<BatchUnit>();
+        a.segs = d_segs.as<BatchSeg>();
+        a.nseg = (uint32_t)segs.size();
+        a.total_tasks = (uint32_t)total;
+        a.descs = d_descs.as<QueryDesc>();
+        a.z_all = d_z.as<uint64_t>();
+        a.z_off = d_zoff.as<uint64_t>();
+        a.py_all = d_py.as<uint64_t>();
+        a.py_off = d_pyoff.as<uint64_t>();
+        a.slot_base = d_slots.as<uint64_t>();
+        a.slot_words = slot_bytes / 8;
+        a.rows = rows;
+        a.full_words = rows * max_chunk;
+        a.done = d_done.as<uint32_t>();
+        a.ctl = d_ctl.as<uint32_t>();
+        a.status = status;
+        a.timeout_ns = 2000000000ull;
+        if (total) {
+            int per_sm = 0, dev = 0, sms = 0;
+            RR_CUDA(cudaGetDevice(&dev));
+            RR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kW2 * 32, 0));
+            const unsigned blocks = (unsigned)std::max(1, sms * std::max(1, per_sm));
+            const int tslot = timing_begin(st);
+            k_batch<<<blocks, kW2 * 32, 0, st>>>(a);
+            timing_end(tslot, kTimeBatch, st);
+            RR_LAUNCHED();
+        }
+        if (d_bitmaps) {
+            k_batch_bitmap<<<dim3((unsigned)std::min<uint64_t>(256, (nb + 255) / 256), (unsigned)grp.size()),
+                             256, 0, st>>>(g.n, d_descs.as<QueryDesc>());
+            RR_LAUNCHED();
+        }
+    }
     return RR_OK;
 }
 
 // Times each candidate (points per lane, points per chunk) on a plain query of
-// size k from the vertex with the most out-rows and keeps the fastest.
+// size k from vertex 0 and keeps the fastest.
 rr_status autotune(Graph &g, uint32_t k, uint32_t *best_ppl, uint32_t *best_chunk)
 {
     const uint64_t npts = 1ull << k;
@@ -44,12 +565,14 @@ rr_status autotune(Graph &g, uint32_t k, uint32_t *best_ppl, uint32_t *best_chun
     for (const Cand &c : cands) {
         g.tune_ppl[k] = c.ppl;
         g.tune_chunk[k] = c.chunk;
+        g.tune_gen++;
         size_t free_b = 0, total_b = 0;
         RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
         uint32_t ppl, chunk;
-        if (!choose_shape(g, k, (uint64_t)(0.6 * (double)(free_b + g.ws.state.bytes)), &ppl, &chunk) ||
-            chunk != c.chunk)
-            continue;
+        const uint64_t budget = (uint64_t)(0.6 * (double)(free_b + g.ws.state.bytes));
+        const bool ok = uses_v2(g, k) ? choose_shape_v2(g, k, budget, &ppl, &chunk)
+                                      : choose_shape(g, k, budget, &ppl, &chunk);
+        if (!ok || chunk != c.chunk || ppl != c.ppl) continue;
         rr_status s = reach_on_stream(g, g.ws, &q, nullptr, S.as<uint64_t>(), 0, g.stream);  // warm-up
         if (s != RR_OK) break;
         RR_CUDA(cudaEventRecord(e0, g.stream));
@@ -70,10 +593,12 @@ rr_status autotune(Graph &g, uint32_t k, uint32_t *best_ppl, uint32_t *best_chun
     if (win.ppl == 0) {
         g.tune_ppl[k] = save_ppl;
         g.tune_chunk[k] = save_chunk;
+        g.tune_gen++;
         return fail(RR_ENOMEM, "rr_autotune: no candidate shape fits device memory");
     }
     g.tune_ppl[k] = win.ppl;
     g.tune_chunk[k] = win.chunk;
+    g.tune_gen++;
     if (best_ppl) *best_ppl = win.ppl;
     if (best_chunk) *best_chunk = win.chunk;
     return RR_OK;

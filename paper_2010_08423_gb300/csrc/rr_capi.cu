@@ -19,8 +19,8 @@ struct TimingRec {
 std::mutex g_tmu;
 std::vector<TimingRec> g_tpending;      // slots handed out by timing_begin
 std::vector<int> g_tfree;               // recycled slots
-double g_tms[5] = {0, 0, 0, 0, 0};
-uint64_t g_tcount[5] = {0, 0, 0, 0, 0};
+double g_tms[kTimeKinds] = {0};
+uint64_t g_tcount[kTimeKinds] = {0};
 std::vector<int> g_tdone;               // slots whose end event is recorded
 }  // namespace
 
@@ -133,7 +133,9 @@ rr_status rr_graph_get_info(const rr_graph *g, rr_graph_info *out)
     out->device_bytes = g->device_bytes();
     out->has_colors = g->has_colors ? 1 : 0;
     out->compact = g->compact ? 1 : 0;
-    out->producer_window_rows = g->producer_window_rows;
+    out->producer_window_rows = g->state_list.count;
+    out->state_compute_rows = g->state_compute_rows;
+    out->tail_rows = g->tail_list.count;
     return RR_OK;
 }
 
@@ -204,6 +206,7 @@ rr_status rr_set_tuning(rr_graph *g, uint32_t k, uint32_t ppl, uint32_t chunk)
     std::lock_guard<std::mutex> lk(g->mu);
     g->tune_ppl[k] = ppl;
     g->tune_chunk[k] = chunk;
+    g->tune_gen++;
     return RR_OK;
 }
 
@@ -271,12 +274,12 @@ rr_status rr_timing_read(rr_kernel_times *out, int reset)
     }
     g_tdone.clear();
     if (out)
-        for (int i = 0; i < 5; ++i) {
+        for (int i = 0; i < kTimeKinds; ++i) {
             out->ms[i] = g_tms[i];
             out->launches[i] = g_tcount[i];
         }
     if (reset)
-        for (int i = 0; i < 5; ++i) {
+        for (int i = 0; i < kTimeKinds; ++i) {
             g_tms[i] = 0;
             g_tcount[i] = 0;
         }

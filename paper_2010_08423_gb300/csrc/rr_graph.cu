@@ -144,6 +144,90 @@ __global__ void k_state_index(const uint32_t *__restrict__ rank, const uint32_t 
     if (local) atomicAdd(prod_window, (unsigned long long)local);
 }
 
+__global__ void k_v2_flags(const uint32_t *__restrict__ lo_in, const uint32_t *__restrict__ hi_in,
+                           const uint32_t *__restrict__ tprod, uint64_t m,
+                           uint32_t *__restrict__ c0, uint32_t *__restrict__ c1)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = hi_in[r] > lo_in[r] ? 1u : 0u;
+        c0[r] = w;
+        c1[r] = w & tprod[r];
+    }
+}
+
+// Last entry of an inclusive rank array at or before row x inside the segment
+// that starts at s0: rank[x] if it counts a flagged row of the segment, else 0.
+__device__ __forceinline__ uint32_t rank_in_segment(const uint32_t *__restrict__ rank, int64_t x,
+                                                    uint32_t s0)
+{
+    if (x < (int64_t)s0) return 0u;
+    const uint32_t before = s0 ? rank[s0 - 1] : 0u;
+    const uint32_t at = rank[x];
+    return at > before ? at : 0u;
+}
+
+__global__ void k_v2_index(const uint32_t *__restrict__ lo_in, const uint32_t *__restrict__ hi_in,
+                           const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ off,
+                           const uint32_t *__restrict__ rank_p, const uint32_t *__restrict__ rank1,
+                           uint64_t m, uint32_t *__restrict__ a0, uint32_t *__restrict__ b0,
+                           uint32_t *__restrict__ a1, uint32_t *__restrict__ b1,
+                           uint32_t *__restrict__ c2)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t lo = lo_in[r], hi = hi_in[r];
+        if (hi > lo) {
+            const uint32_t s0 = off[row_src[r]];
+            a0[r] = rank_in_segment(rank_p, (int64_t)hi - 1, s0);
+            b0[r] = rank_in_segment(rank_p, (int64_t)lo - 1, s0);
+            a1[r] = rank_in_segment(rank1, (int64_t)hi - 1, s0);
+            b1[r] = rank_in_segment(rank1, (int64_t)lo - 1, s0);
+            c2[r] = a1[r] != b1[r] ? 1u : 0u;
+        } else {
+            a0[r] = b0[r] = a1[r] = b1[r] = 0u;
+            c2[r] = 0u;
+        }
+    }
+}
+
+struct ListOut {
+    uint32_t *head, *eid, *src, *a0, *b0, *a1, *b1;
+};
+
+__global__ void k_v2_scatter(const uint32_t *__restrict__ row_dst, const uint32_t *__restrict__ row_eid,
+                             const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ a0,
+                             const uint32_t *__restrict__ b0, const uint32_t *__restrict__ a1,
+                             const uint32_t *__restrict__ b1, const uint32_t *__restrict__ tprod,
+                             const uint32_t *__restrict__ rank_p, const uint32_t *__restrict__ c1,
+                             const uint32_t *__restrict__ rank1, const uint32_t *__restrict__ c0,
+                             const uint32_t *__restrict__ rank0, const uint32_t *__restrict__ c2,
+                             const uint32_t *__restrict__ rank2, uint64_t m, ListOut P, ListOut S,
+                             ListOut W, ListOut T)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t h = row_dst[r], e = row_eid[r], u = row_src[r];
+        if (tprod[r]) {
+            const uint32_t i = rank_p[r] - 1;
+            P.head[i] = h; P.eid[i] = e; P.src[i] = u;
+        }
+        if (c1[r]) {
+            const uint32_t i = rank1[r] - 1;
+            S.head[i] = h; S.eid[i] = e; S.src[i] = u;
+            S.a0[i] = a0[r]; S.b0[i] = b0[r]; S.a1[i] = a1[r]; S.b1[i] = b1[r];
+        }
+        if (c0[r]) {
+            const uint32_t i = rank0[r] - 1;
+            W.head[i] = h; W.eid[i] = e; W.src[i] = u; W.a0[i] = a0[r]; W.b0[i] = b0[r];
+        }
+        if (c2[r]) {
+            const uint32_t i = rank2[r] - 1;
+            T.head[i] = h; T.eid[i] = e; T.a1[i] = a1[r]; T.b1[i] = b1[r];
+        }
+    }
+}
+
 inline unsigned grid_for(uint64_t count, unsigned block)
 {
     uint64_t g = (count + block - 1) / block;
@@ -187,6 +271,131 @@ static void build_items(const std::vector<uint32_t> &off, uint32_t n,
         if (acc >= kItemRows || nv >= kItemMaxVerts) flush(v + 1);
     }
     flush(n);
+}
+
+// Head-aligned scheduling ranges over a row list: consecutive head runs are
+// packed until `target` entries; a longer run forms its own range. Largest first.
+static void build_entry_items(const std::vector<uint32_t> &head, uint32_t target,
+                              std::vector<uint2> &items)
+{
+    std::vector<uint2> tmp;
+    const uint64_t cnt = head.size();
+    uint64_t start = 0, i = 0;
+    while (i < cnt) {
+        uint64_t j = i + 1;
+        while (j < cnt && head[j] == head[i]) ++j;  // run [i, j)
+        if (j - i >= target) {
+            if (i > start) tmp.push_back(make_uint2((uint32_t)start, (uint32_t)i));
+            tmp.push_back(make_uint2((uint32_t)i, (uint32_t)j));
+            start = j;
+        } else if (j - start >= target) {
+            tmp.push_back(make_uint2((uint32_t)start, (uint32_t)j));
+            start = j;
+        }
+        i = j;
+    }
+    if (cnt > start) tmp.push_back(make_uint2((uint32_t)start, (uint32_t)cnt));
+    std::stable_sort(tmp.begin(), tmp.end(),
+                     [](const uint2 &a, const uint2 &b) { return (a.y - a.x) > (b.y - b.x); });
+    items.swap(tmp);
+}
+
+static rr_status scan_u32(const uint32_t *in, uint32_t *out, uint64_t m, DevBuf &tmp,
+                          cudaStream_t st)
+{
+    size_t tb = 0;
+    RR_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tb, in, out, (int64_t)m, st));
+    RR_CUDA(tmp.reserve(tb));
+    RR_CUDA(cub::DeviceScan::InclusiveSum(tmp.p, tb, in, out, (int64_t)m, st));
+    return RR_OK;
+}
+
+// Builds the reduced-state engine's row lists (rr_internal.h, RowList) from
+// the windows [row_lo, row_hi), the head of every row and the true producer
+// flags (rows inside some window).
+rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tprod, cudaStream_t st)
+{
+    const uint64_t m = g.m;
+    DevBuf c0, c1, c2, rank_p, rank0, rank1, rank2, a0, b0, a1, b1, tmp;
+    for (DevBuf *b : {&c0, &c1, &c2, &rank_p, &rank0, &rank1, &rank2, &a0, &b0, &a1, &b1})
+        RR_CUDA(b->reserve(m * 4));
+    k_v2_flags<<<grid_for(m, 256), 256, 0, st>>>(g.row_lo.as<uint32_t>(), g.row_hi.as<uint32_t>(),
+                                                 tprod, m, c0.as<uint32_t>(), c1.as<uint32_t>());
+    RR_LAUNCHED();
+    rr_status s;
+    if ((s = scan_u32(tprod, rank_p.as<uint32_t>(), m, tmp, st)) != RR_OK) return s;
+    if ((s = scan_u32(c0.as<uint32_t>(), rank0.as<uint32_t>(), m, tmp, st)) != RR_OK) return s;
+    if ((s = scan_u32(c1.as<uint32_t>(), rank1.as<uint32_t>(), m, tmp, st)) != RR_OK) return s;
+    k_v2_index<<<grid_for(m, 256), 256, 0, st>>>(
+        g.row_lo.as<uint32_t>(), g.row_hi.as<uint32_t>(), g.row_src.as<uint32_t>(),
+        g.off.as<uint32_t>(), rank_p.as<uint32_t>(), rank1.as<uint32_t>(), m, a0.as<uint32_t>(),
+        b0.as<uint32_t>(), a1.as<uint32_t>(), b1.as<uint32_t>(), c2.as<uint32_t>());
+    RR_LAUNCHED();
+    if ((s = scan_u32(c2.as<uint32_t>(), rank2.as<uint32_t>(), m, tmp, st)) != RR_OK) return s;
+    uint32_t counts[4] = {0, 0, 0, 0};
+    RR_CUDA(cudaMemcpyAsync(&counts[0], rank_p.as<uint32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaMemcpyAsync(&counts[1], rank1.as<uint32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaMemcpyAsync(&counts[2], rank0.as<uint32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaMemcpyAsync(&counts[3], rank2.as<uint32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    RowList *L[4] = {&g.prod_list, &g.state_list, &g.win_list, &g.tail_list};
+    ListOut out[4];
+    for (int i = 0; i < 4; ++i) {
+        RowList &R = *L[i];
+        R.count = counts[i];
+        const size_t bytes = (size_t)std::max<uint32_t>(1, counts[i]) * 4;
+        RR_CUDA(R.head.reserve(bytes));
+        RR_CUDA(R.eid.reserve(bytes));
+        if (i != 3) RR_CUDA(R.src.reserve(bytes));
+        if (i == 1 || i == 2) {
+            RR_CUDA(R.a0.reserve(bytes));
+            RR_CUDA(R.b0.reserve(bytes));
+        }
+        if (i == 1 || i == 3) {
+            RR_CUDA(R.a1.reserve(bytes));
+            RR_CUDA(R.b1.reserve(bytes));
+        }
+        out[i] = ListOut{R.head.as<uint32_t>(), R.eid.as<uint32_t>(), R.src.as<uint32_t>(),
+                         R.a0.as<uint32_t>(), R.b0.as<uint32_t>(), R.a1.as<uint32_t>(),
+                         R.b1.as<uint32_t>()};
+    }
+    k_v2_scatter<<<grid_for(m, 256), 256, 0, st>>>(
+        row_dst, g.row_eid.as<uint32_t>(), g.row_src.as<uint32_t>(), a0.as<uint32_t>(),
+        b0.as<uint32_t>(), a1.as<uint32_t>(), b1.as<uint32_t>(), tprod, rank_p.as<uint32_t>(),
+        c1.as<uint32_t>(), rank1.as<uint32_t>(), c0.as<uint32_t>(), rank0.as<uint32_t>(),
+        c2.as<uint32_t>(), rank2.as<uint32_t>(), m, out[0], out[1], out[2], out[3]);
+    RR_LAUNCHED();
+    {
+        // state rows whose window holds another state row (they multiply at layers >= 3)
+        std::vector<uint32_t> ha(g.state_list.count), hb(g.state_list.count);
+        if (g.state_list.count) {
+            RR_CUDA(cudaMemcpyAsync(ha.data(), g.state_list.a1.p, ha.size() * 4, cudaMemcpyDeviceToHost, st));
+            RR_CUDA(cudaMemcpyAsync(hb.data(), g.state_list.b1.p, hb.size() * 4, cudaMemcpyDeviceToHost, st));
+        }
+        RR_CUDA(cudaStreamSynchronize(st));
+        uint64_t cnt = 0;
+        for (size_t i = 0; i < ha.size(); ++i) cnt += ha[i] != hb[i];
+        g.state_compute_rows = cnt;
+    }
+    // scheduling ranges: about 32 warps per SM over the list, 8..128 entries each
+    for (int i = 0; i < 4; ++i) {
+        RowList &R = *L[i];
+        std::vector<uint32_t> heads(R.count);
+        if (R.count)
+            RR_CUDA(cudaMemcpyAsync(heads.data(), R.head.p, R.count * 4, cudaMemcpyDeviceToHost, st));
+        RR_CUDA(cudaStreamSynchronize(st));
+        const uint32_t target =
+            (uint32_t)std::min<uint64_t>(128, std::max<uint64_t>(8, R.count / (152 * 32)));
+        std::vector<uint2> items;
+        build_entry_items(heads, target, items);
+        R.nitems = (uint32_t)items.size();
+        RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));
+        if (!items.empty())
+            RR_CUDA(cudaMemcpyAsync(R.items.p, items.data(), items.size() * sizeof(uint2),
+                                    cudaMemcpyHostToDevice, st));
+        RR_CUDA(cudaStreamSynchronize(st));
+    }
+    return RR_OK;
 }
 
 rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
@@ -274,34 +483,34 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
                                                         g->off.as<uint32_t>());
         RR_LAUNCHED();
 
-        DevBuf diff, cover, prod, rank, counter;
+        DevBuf diff, cover, prod, tprod, rank, counter;
         RR_CUDA(counter.reserve(16));
         RR_CUDA(cudaMemsetAsync(counter.p, 0, 16, st));
-        if (g->compact) {
-            RR_CUDA(diff.reserve((mb + 1) * 4));
-            RR_CUDA(cudaMemsetAsync(diff.p, 0, (mb + 1) * 4, st));
-        }
+        RR_CUDA(diff.reserve((mb + 1) * 4));
+        RR_CUDA(cudaMemsetAsync(diff.p, 0, (mb + 1) * 4, st));
         k_windows<<<grid_for(m, 256), 256, 0, st>>>(
             row_t.as<uint32_t>(), g->row_src.as<uint32_t>(), g->off.as<uint32_t>(),
             d_delta.as<uint32_t>(), m, g->row_lo.as<uint32_t>(), g->row_hi.as<uint32_t>(),
-            g->compact ? diff.as<int32_t>() : nullptr,
-            counter.as<unsigned long long>());
+            diff.as<int32_t>(), counter.as<unsigned long long>());
         RR_LAUNCHED();
         RR_CUDA(prod.reserve(mb * 4));
+        RR_CUDA(tprod.reserve(mb * 4));
+        RR_CUDA(cover.reserve(mb * 4));
+        tmp_bytes = 0;
+        RR_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tmp_bytes, diff.as<int32_t>(),
+                                              cover.as<int32_t>(), (int64_t)m, st));
+        RR_CUDA(tmp.reserve(tmp_bytes));
+        RR_CUDA(cub::DeviceScan::InclusiveSum(tmp.p, tmp_bytes, diff.as<int32_t>(),
+                                              cover.as<int32_t>(), (int64_t)m, st));
+        k_cover_to_flags<<<grid_for(m, 256), 256, 0, st>>>(cover.as<int32_t>(), m,
+                                                           tprod.as<uint32_t>());
+        RR_LAUNCHED();
         if (g->compact) {
-            RR_CUDA(cover.reserve(mb * 4));
-            tmp_bytes = 0;
-            RR_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tmp_bytes, diff.as<int32_t>(),
-                                                  cover.as<int32_t>(), (int64_t)m, st));
-            RR_CUDA(tmp.reserve(tmp_bytes));
-            RR_CUDA(cub::DeviceScan::InclusiveSum(tmp.p, tmp_bytes, diff.as<int32_t>(),
-                                                  cover.as<int32_t>(), (int64_t)m, st));
-            k_cover_to_flags<<<grid_for(m, 256), 256, 0, st>>>(cover.as<int32_t>(), m,
-                                                               prod.as<uint32_t>());
+            RR_CUDA(cudaMemcpyAsync(prod.p, tprod.p, m * 4, cudaMemcpyDeviceToDevice, st));
         } else {
             k_dense_flags<<<grid_for(m, 256), 256, 0, st>>>(m, prod.as<uint32_t>());
+            RR_LAUNCHED();
         }
-        RR_LAUNCHED();
         RR_CUDA(rank.reserve(mb * 4));
         tmp_bytes = 0;
         RR_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tmp_bytes, prod.as<uint32_t>(),
@@ -326,6 +535,8 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
         g->state_rows = 1ull + last_rank;
         g->window_rows = nonempty;
         g->producer_window_rows = prod_window;
+        rr_status ls = build_lists_v2(*g, row_dst.as<uint32_t>(), tprod.as<uint32_t>(), st);
+        if (ls != RR_OK) return ls;
     }
 
     std::vector<uint32_t> h_off(n + 1);

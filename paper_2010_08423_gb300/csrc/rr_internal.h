@@ -20,7 +20,10 @@ rr_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 extern std::atomic<uint64_t> g_launches;
 
 // Kernel timing (rr_timing_*): kinds as in rr_kernel_times.
-enum TimingKind { kTimeFirst = 0, kTimeMid = 1, kTimeLast = 2, kTimeZ = 3, kTimeBatch = 4 };
+enum TimingKind {
+    kTimeFirst = 0, kTimeMid = 1, kTimeLast = 2, kTimeZ = 3, kTimeBatch = 4, kTimeSecond = 5,
+    kTimeTail = 6, kTimeKinds = 8
+};
 extern std::atomic<bool> g_timing;
 // Records a start event on st when timing is enabled; returns an opaque slot.
 int timing_begin(cudaStream_t st);
@@ -65,15 +68,81 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Per-query values the reduced-state engine's kernels read from device
+// memory, so that one captured launch sequence serves every query of a shape.
+struct QueryDesc {
+    uint32_t source, k, colored, pad;
+    uint64_t key_y, key_z, key_g, key_o;
+    uint64_t *S;        // witness output (n)
+    uint8_t *bitmap;    // bitmap output or null
+    uint32_t shades[512];  // first shade [0..255], multiplicity [256..511]
+};
+
 // Scratch of one in-flight query: double-buffered prefix state, z-table,
-// witness sums, shade table and bitmap.
+// witness sums, shade table and bitmap, plus the query descriptor and the
+// cache of captured launch sequences (CUDA graphs) keyed by query shape.
 struct Workspace {
-    DevBuf state;   // 2 * state_rows * chunk * 8
+    DevBuf state;   // engine scratch
     DevBuf z;       // n * k * 8
     DevBuf S;       // n * 8
     DevBuf shade;   // 512 uint32
     DevBuf bitmap;  // ceil(n/8)
-    size_t bytes() const { return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes; }
+    DevBuf desc;    // QueryDesc
+    cudaStream_t capture = nullptr;           // stream used only to capture graphs
+    std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs;
+    std::vector<uint64_t> graph_kernels;      // kernel nodes per cached graph
+    void *graph_state = nullptr;              // state.p the graphs were captured with
+    void *graph_z = nullptr;
+    // pinned staging ring for query descriptors: slot i may be rewritten once
+    // ring_ev[i] (recorded after the launch that consumed it) has completed
+    static constexpr int kRing = 64;
+    QueryDesc *h_ring = nullptr;
+    cudaEvent_t ring_ev[kRing] = {};
+    bool ring_used[kRing] = {};
+    uint32_t ring_pos = 0;
+    // shape chosen per k (0 = not chosen yet) and the tuning generation it used
+    uint32_t shape_ppl[32] = {0}, shape_chunk[32] = {0};
+    uint64_t shape_gen[32] = {0};
+    size_t bytes() const
+    {
+        return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes + desc.bytes;
+    }
+    void drop_graphs()
+    {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+        graph_kernels.clear();
+    }
+    ~Workspace()
+    {
+        drop_graphs();
+        if (capture) cudaStreamDestroy(capture);
+        for (int i = 0; i < kRing; ++i)
+            if (ring_ev[i]) cudaEventDestroy(ring_ev[i]);
+        if (h_ring) cudaFreeHost(h_ring);
+    }
+};
+
+// A list of CSR rows (a subsequence of the in-edge CSR, so still sorted by
+// head vertex, then time), with the per-entry fields some layer needs and
+// head-aligned scheduling ranges [entry_begin, entry_end).
+struct RowList {
+    uint64_t count = 0;
+    DevBuf head, eid, src;  // uint32 per entry
+    DevBuf a0, b0;          // window in producer-prefix indices (scalar first-layer prefix)
+    DevBuf a1, b1;          // window in state-row indices (state rows = producers with a window)
+    DevBuf items;           // uint2 ranges, largest first
+    uint32_t nitems = 0;
+    size_t bytes() const
+    {
+        return head.bytes + eid.bytes + src.bytes + a0.bytes + b0.bytes + a1.bytes + b1.bytes +
+               items.bytes;
+    }
+};
+
+// Device buffers of the persistent batched launch, kept per graph.
+struct BatchBuffers {
+    DevBuf units, segs, descs, zoff, pyoff, z, py, slots, done, ctl, status;
 };
 
 // -------- graph ------------------------------------------------------------
@@ -94,6 +163,7 @@ struct Graph {
     uint64_t state_rows = 1;   // 1 + producers
     uint64_t window_rows = 0;  // rows with a non-empty window
     uint64_t producer_window_rows = 0;  // producer rows with a non-empty window
+    uint64_t state_compute_rows = 0;    // state rows whose window holds a state row
     uint32_t max_in_degree = 0;
 
     DevBuf off;      // n+1 uint32
@@ -109,19 +179,29 @@ struct Graph {
     uint32_t nitems = 0;
     std::vector<uint32_t> h_item_rows;  // rows per item (host copy, same order)
 
+    // Row lists of the reduced-state engine (see rr_sieve2.cu):
+    //   prod_list  rows inside some window (first-layer scalar prefix)
+    //   state_list producers whose own window is non-empty (state rows)
+    //   win_list   rows with a non-empty window (k = 3 last layer)
+    //   tail_list  rows whose window holds at least one state row (last layer)
+    RowList prod_list, state_list, win_list, tail_list;
+
     // per-graph scratch for rr_reach_device / rr_reach_sync (serialised by mu)
     mutable std::mutex mu;
     mutable Workspace ws;
+    mutable BatchBuffers batch;
     mutable cudaStream_t stream = nullptr;
 
-    // tuning per k (index k): 0 = automatic
+    // tuning per k (index k): 0 = automatic; tune_gen changes on every update
     uint32_t tune_ppl[32] = {0};
     uint32_t tune_chunk[32] = {0};
+    uint64_t tune_gen = 1;
 
     size_t device_bytes() const
     {
         return off.bytes + row_a.bytes + row_b.bytes + row_s.bytes + row_eid.bytes +
-               row_src.bytes + row_lo.bytes + row_hi.bytes + color.bytes + items.bytes;
+               row_src.bytes + row_lo.bytes + row_hi.bytes + color.bytes + items.bytes +
+               prod_list.bytes() + state_list.bytes() + win_list.bytes() + tail_list.bytes();
     }
 };
 
@@ -162,8 +242,22 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
 // bounds the state buffers (0 = 60% of free device memory).
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st);
-// Bytes of scratch one query of size k needs with the chosen shape.
-uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint32_t chunk);
+// Bytes of scratch one query of size k needs with the shape chosen for budget.
+uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
+
+// Reduced-state engine (rr_sieve2.cu), used for k >= 3 on compact graphs.
+bool uses_v2(const Graph &g, uint32_t k);
+bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl, uint32_t *chunk);
+uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk);
+uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk);
+// Enqueues the whole launch sequence of one k >= 3 query (z-table, witness
+// clear, all layers, bitmap) reading per-query values from d_desc; returns
+// the number of kernels enqueued in *kernels.
+rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap, uint32_t ppl,
+                           uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
+                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels);
+rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
+                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st);
 
 }  // namespace rr
 

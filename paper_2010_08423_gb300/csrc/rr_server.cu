@@ -7,6 +7,7 @@
 // work of queries admitted at different times overlaps on the GPU), and
 // retires queries whose completion event has fired. Results are bit-identical
 // to rr_reach_sync: every query runs the same kernels on its own scratch.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <condition_variable>
@@ -64,9 +65,7 @@ struct Server {
 
     uint64_t need_bytes(uint32_t k, uint64_t share) const
     {
-        uint32_t ppl, chunk;
-        if (!choose_shape(*g, k, share, &ppl, &chunk)) return UINT64_MAX;
-        return query_scratch_bytes(*g, k, chunk);
+        return query_scratch_bytes(*g, k, share);
     }
 
     void run();
@@ -195,14 +194,18 @@ rr_status rr_server_create(const rr_graph *g, uint64_t device_mem_budget, uint32
     // of the budget admits, so that admission never calls cudaMalloc (which
     // would serialise the device and stop queries from overlapping).
     const uint64_t share = s->budget / max_slots;
-    uint32_t ppl = 0, chunk = 0;
-    if (!choose_shape(*g, 20, share, &ppl, &chunk))
-        return fail(RR_ENOMEM, "rr_server_create: budget too small for one point chunk per slot");
+    uint64_t state_bytes = 0;
+    for (uint32_t k = 3; k <= 20; ++k) {
+        const uint64_t b = query_scratch_bytes(*g, k, share);
+        if (b == UINT64_MAX)
+            return fail(RR_ENOMEM, "rr_server_create: budget too small for one point chunk per slot");
+        state_bytes = std::max<uint64_t>(state_bytes, b - (uint64_t)g->n * k * 8ull);
+    }
     for (auto &sl : s->slots) {
         RR_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
         RR_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
         RR_CUDA(cudaMallocHost(&sl.h_witness, (size_t)g->n * 8));
-        RR_CUDA(sl.ws.state.reserve(2ull * g->state_rows * chunk * 8ull));
+        RR_CUDA(sl.ws.state.reserve(state_bytes));
         RR_CUDA(sl.ws.z.reserve((size_t)g->n * 20 * 8));
         RR_CUDA(sl.ws.S.reserve((size_t)g->n * 8));
         RR_CUDA(sl.ws.shade.reserve(sizeof(ShadeTable)));

@@ -12,6 +12,7 @@
 // y_{e,l} x_v^L = sum_{j in L} b_j with b_j = y_{e,l} z_{v,j}: the k products
 // b_j are formed once per edge (one per lane) and each point needs a single
 // general multiplication P = W * c^L.
+#include <algorithm>
 #include <cstring>
 
 #include "rr_device.cuh"
@@ -407,9 +408,37 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
     return RR_OK;
 }
 
-uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint32_t chunk)
+bool uses_v2(const Graph &g, uint32_t k)
 {
-    return 2ull * g.state_rows * chunk * 8ull + (uint64_t)g.n * k * 8ull + 2048;
+    return g.compact && k >= 3;
+}
+
+bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl_out,
+                     uint32_t *chunk_out)
+{
+    const uint64_t npts = 1ull << k;
+    const uint32_t ppl = g.tune_ppl[k] ? g.tune_ppl[k] : (npts >= 128 ? 4u : 2u);
+    const uint64_t unit = 32ull * ppl;
+    uint64_t want = g.tune_chunk[k] ? g.tune_chunk[k] : npts;
+    want = std::max<uint64_t>(unit, std::min<uint64_t>(want, 4 * unit));  // <= 4 groups
+    want = (want + unit - 1) / unit * unit;
+    while (want > unit && v2_scratch_bytes(g, ppl, (uint32_t)want) > budget) want -= unit;
+    if (v2_scratch_bytes(g, ppl, (uint32_t)want) > budget) return false;
+    *ppl_out = ppl;
+    *chunk_out = (uint32_t)want;
+    return true;
+}
+
+uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget)
+{
+    uint32_t ppl = 0, chunk = 0;
+    const uint64_t z = (uint64_t)g.n * k * 8ull + 2048;
+    if (uses_v2(g, k)) {
+        if (!choose_shape_v2(g, k, budget, &ppl, &chunk)) return UINT64_MAX;
+        return v2_scratch_bytes(g, ppl, chunk) + z;
+    }
+    if (!choose_shape(g, k, budget, &ppl, &chunk)) return UINT64_MAX;
+    return 2ull * g.state_rows * chunk * 8ull + z;
 }
 
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
@@ -418,16 +447,32 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     rr_status vs = validate_query(g, q);
     if (vs != RR_OK) return vs;
     const uint32_t k = q->k;
-    if (budget == 0) {
-        size_t free_b = 0, total_b = 0;
-        RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        budget = (uint64_t)(0.6 * (double)(free_b + ws.state.bytes));
-    }
+    const bool v2 = uses_v2(g, k);
     uint32_t ppl = 0, chunk = 0;
-    if (!choose_shape(g, k, budget, &ppl, &chunk))
-        return fail(RR_ENOMEM, "state for one point chunk does not fit device memory");
-    RR_CUDA(ws.state.reserve(2ull * g.state_rows * chunk * 8ull));
+    if (budget == 0 && ws.shape_ppl[k] && ws.shape_gen[k] == g.tune_gen) {
+        // shape already chosen for this k on this workspace: no device query
+        ppl = ws.shape_ppl[k];
+        chunk = ws.shape_chunk[k];
+    } else {
+        const bool remember = budget == 0;
+        if (budget == 0) {
+            size_t free_b = 0, total_b = 0;
+            RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            budget = (uint64_t)(0.6 * (double)(free_b + ws.state.bytes));
+        }
+        if (v2 ? !choose_shape_v2(g, k, budget, &ppl, &chunk)
+               : !choose_shape(g, k, budget, &ppl, &chunk))
+            return fail(RR_ENOMEM, "state for one point chunk does not fit device memory");
+        if (remember) {
+            ws.shape_ppl[k] = ppl;
+            ws.shape_chunk[k] = chunk;
+            ws.shape_gen[k] = g.tune_gen;
+        }
+    }
+    RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk)
+                                : 2ull * g.state_rows * chunk * 8ull));
     RR_CUDA(ws.z.reserve((size_t)g.n * k * 8));
+    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st);
     const QueryKeys keys = make_keys(q->seed);
     const uint32_t *d_shades = nullptr;
     if (q->motif) {
@@ -440,8 +485,8 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     rr_status s = launch_ztable(g, k, keys, q->motif != nullptr, d_shades, ws.z.as<uint64_t>(), st);
     if (s != RR_OK) return s;
     RR_CUDA(cudaMemsetAsync(d_witness, 0, (size_t)g.n * 8, st));
-    s = run_query_layers(g, q, ws.z.as<uint64_t>(), ws.state.as<uint64_t>(), ppl, chunk,
-                         d_witness, nullptr, 0, nullptr, st);
+    s = run_query_layers(g, q, ws.z.as<uint64_t>(), ws.state.as<uint64_t>(), ppl, chunk, d_witness,
+                         nullptr, 0, nullptr, st);
     if (s != RR_OK) return s;
     if (d_bitmap) return launch_bitmap(d_witness, g.n, d_bitmap, st);
     return RR_OK;

@@ -1,0 +1,339 @@
+// rr_sieve2.cu -- the reduced-state engine: same per-vertex sums as the
+// per-point engine (rr_sieve.cu), with three exact rewrites of the work.
+//
+// 1. Layer 1 as a scalar. P_1^L[f] = [u_f = s] y_{f,1} x_s^L x_{v_f}^L, so
+//    the layer-2 window sum of edge e = (u, v) is W_2^L[e] = Y_e x_s^L x_u^L with
+//    the scalar Y_e = sum of y_{f,1} over the source's edges f inside e's window.
+//    Layer 1 therefore stores one GF(2^64) prefix per producer row (PY), not one
+//    per sieve point.
+// 2. State rows only where the prefix changes. For l >= 2, P_l[f] can be
+//    non-zero only for rows f whose own window is non-empty, so the per-point
+//    prefix state of layers 2..k-3 keeps just those rows ("state rows").
+// 3. The last layer as a linear form. x_v^L = sum_{j in L} z_{v,j}, hence
+//        sum_L y_e x_v^L W^L = y_e sum_j z_{v,j} T_j(W),  T_j(W) = sum_{L ni j} W^L,
+//    and T_j is XOR-linear, so layer k-2 stores for every state row and point
+//    group only the lg+1 sums T_j (j below lg = log2 of the group size) and
+//    V = sum over the group (the high labels of a group are fixed, so their
+//    T_j is V or 0), and layer k-1 needs one multiplication per stored value
+//    instead of one per sieve point.
+// Only the sieve points' order of summation changes; every result is
+// bit-identical to the per-point engine and the oracle.
+#include <cstring>
+
+#include "rr_v2_device.cuh"
+
+namespace rr {
+
+__global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uint64_t *__restrict__ py)
+{
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems) return;
+    first_scalar_warp(p, task, py);
+}
+
+template <int PPL, bool FROM_Y, int OUT>
+__global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
+{
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems * p.ngroups) return;
+    const uint32_t item = task / p.ngroups;
+    layer_warp<PPL, FROM_Y, OUT, false>(p, item, task - item * p.ngroups);
+}
+
+template <int LG>
+__global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
+{
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems) return;
+    last_warp<LG, false>(p, task);
+}
+
+static unsigned blocks_for(uint64_t tasks)
+{
+    return (unsigned)((tasks + kW2 - 1) / kW2);
+}
+
+// Fills the list fields of V2Params.
+static void set_list(V2Params &vp, const RowList &L, bool first_window)
+{
+    vp.head = L.head.as<uint32_t>();
+    vp.eid = L.eid.as<uint32_t>();
+    vp.src = L.src.as<uint32_t>();
+    vp.ia = first_window ? L.a0.as<uint32_t>() : L.a1.as<uint32_t>();
+    vp.ib = first_window ? L.b0.as<uint32_t>() : L.b1.as<uint32_t>();
+    vp.items = L.items.as<uint2>();
+    vp.nitems = L.nitems;
+}
+
+template <int PPL>
+static rr_status launch_v2(const V2Params &vp, bool from_y, int out, cudaStream_t st)
+{
+    const uint64_t tasks = (uint64_t)vp.nitems * vp.ngroups;
+    if (tasks == 0) return RR_OK;
+    const int tslot = timing_begin(st);
+    const unsigned blocks = blocks_for(tasks);
+    if (from_y) {
+        if (out == 0) k_layer_v2<PPL, true, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
+        else if (out == 1) k_layer_v2<PPL, true, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
+        else k_layer_v2<PPL, true, 2><<<blocks, kW2 * 32, 0, st>>>(vp);
+    } else {
+        if (out == 0) k_layer_v2<PPL, false, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
+        else k_layer_v2<PPL, false, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
+    }
+    timing_end(tslot, out == 2 ? kTimeLast : (from_y ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid)), st);
+    RR_LAUNCHED();
+    return RR_OK;
+}
+
+// Number of 8-byte values one transformed state row holds.
+uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk)
+{
+    const uint32_t lg = ppl == 4 ? 7u : 6u;
+    return chunk / (32u * ppl) * (lg + 1u);
+}
+
+// Scratch the reduced-state engine needs for one query (bytes): scalar
+// prefix, two full state buffers, one transformed buffer.
+uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk)
+{
+    const uint64_t rows = g.state_list.count + 1;
+    return (g.prod_list.count + 1) * 8ull + 2ull * rows * chunk * 8ull +
+           rows * v2_reduced_stride(ppl, chunk) * 8ull + 4096;
+}
+
+// z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades).
+__global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__ qd,
+                           const uint8_t *__restrict__ color, uint64_t *__restrict__ z)
+{
+    const uint64_t total = (uint64_t)n * k;
+    const bool colored = qd->colored != 0;
+    const uint64_t kz = qd->key_z, kg = qd->key_g, ko = qd->key_o;
+    for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t u = idx / k;
+        const uint32_t j = (uint32_t)(idx - u * k);
+        uint64_t val = 0;
+        if (!colored) {
+            val = sm_draw(kz, u * 32u + j);
+        } else {
+            const uint32_t c = color[u];
+            const uint32_t d0 = qd->shades[c], mu = qd->shades[256 + c];
+            for (uint32_t d = d0; d < d0 + mu; ++d)
+                val ^= gf64_mul(sm_draw(kg, u * 32u + d), sm_draw(ko, (uint64_t)d * 32u + j));
+        }
+        z[idx] = val;
+    }
+}
+
+__global__ void k_zero_q(uint32_t n, const QueryDesc *__restrict__ qd)
+{
+    uint64_t *S = qd->S;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        S[v] = 0;
+}
+
+__global__ void k_bitmap_q(uint32_t n, const QueryDesc *__restrict__ qd)
+{
+    const uint64_t *S = qd->S;
+    uint8_t *bm = qd->bitmap;
+    const uint32_t nb = (n + 7) / 8;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        for (uint32_t i = 0; i < 8; ++i) {
+            const uint32_t v = b * 8 + i;
+            if (v < n && S[v] != 0) bits |= 1u << i;
+        }
+        bm[b] = (uint8_t)bits;
+    }
+}
+
+static unsigned grid_cap(uint64_t count, unsigned block)
+{
+    uint64_t g = (count + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 152ull * 64) g = 152ull * 64;
+    return (unsigned)g;
+}
+
+rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap, uint32_t ppl,
+                           uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
+                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels)
+{
+    (void)colored;
+    uint64_t nk = 0;
+    const uint64_t rows = g.state_list.count + 1;
+    uint64_t *py = d_scratch;
+    uint64_t *full0 = py + ((g.prod_list.count + 1 + 31) / 32 * 32);
+    uint64_t *full1 = full0 + rows * chunk;
+    uint64_t *red = full1 + rows * chunk;
+    const uint32_t rstride = v2_reduced_stride(ppl, chunk);
+
+    {
+        const int tslot = timing_begin(st);
+        k_ztable_q<<<grid_cap((uint64_t)g.n * k, 256), 256, 0, st>>>(g.n, k, d_desc,
+                                                                    g.color.as<uint8_t>(), d_z);
+        timing_end(tslot, kTimeZ, st);
+        RR_LAUNCHED();
+        k_zero_q<<<grid_cap(g.n, 256), 256, 0, st>>>(g.n, d_desc);
+        RR_LAUNCHED();
+        nk += 2;
+    }
+    V2Params vp{};
+    vp.qd = d_desc;
+    vp.z = d_z;
+    vp.n = g.n;
+    vp.k = k;
+    vp.chunk = chunk;
+    vp.ngroups = chunk / (32u * ppl);
+    vp.npoints = 1u << k;
+
+    // layer 1: scalar prefix (independent of the point chunk); zero rows
+    RR_CUDA(cudaMemsetAsync(py, 0, 8, st));
+    RR_CUDA(cudaMemsetAsync(full0, 0, (size_t)chunk * 8, st));
+    RR_CUDA(cudaMemsetAsync(full1, 0, (size_t)chunk * 8, st));
+    RR_CUDA(cudaMemsetAsync(red, 0, (size_t)rstride * 8, st));
+    set_list(vp, g.prod_list, true);
+    vp.layer = 1;
+    if (vp.nitems) {
+        const int tslot = timing_begin(st);
+        k_first_scalar<<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp, py);
+        timing_end(tslot, kTimeFirst, st);
+        RR_LAUNCHED();
+        ++nk;
+    }
+    vp.py = py;
+
+    const uint64_t nchunks = ((1ull << k) + chunk - 1) / chunk;
+    for (uint64_t c = 0; c < nchunks; ++c) {
+        vp.chunk_base = (uint32_t)(c * chunk);
+        rr_status s = RR_OK;
+        if (k == 3) {
+            set_list(vp, g.win_list, true);
+            vp.layer = 2;
+            s = ppl == 4 ? launch_v2<4>(vp, true, 2, st) : launch_v2<2>(vp, true, 2, st);
+            if (s != RR_OK) return s;
+            nk += vp.nitems ? 1 : 0;
+            continue;
+        }
+        // layers 2..k-2; the last of them writes the transformed state
+        uint64_t *bufs[2] = {full0, full1};
+        for (uint32_t l = 2; l <= k - 2; ++l) {
+            const bool from_y = l == 2;
+            const int out = (l == k - 2) ? 1 : 0;
+            set_list(vp, g.state_list, from_y);
+            vp.layer = l;
+            vp.st_in = bufs[(l - 1) & 1u];
+            vp.st_out = out == 1 ? red : bufs[l & 1u];
+            s = ppl == 4 ? launch_v2<4>(vp, from_y, out, st) : launch_v2<2>(vp, from_y, out, st);
+            if (s != RR_OK) return s;
+            nk += vp.nitems ? 1 : 0;
+        }
+        // layer k-1 from the transformed state
+        set_list(vp, g.tail_list, false);
+        vp.layer = k - 1;
+        vp.st_in = red;
+        if (vp.nitems) {
+            const int tslot = timing_begin(st);
+            if (ppl == 4) k_last_v2<7><<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp);
+            else k_last_v2<6><<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp);
+            timing_end(tslot, kTimeLast, st);
+            RR_LAUNCHED();
+            ++nk;
+        }
+    }
+    if (bitmap) {
+        k_bitmap_q<<<grid_cap((g.n + 7) / 8, 256), 256, 0, st>>>(g.n, d_desc);
+        RR_LAUNCHED();
+        ++nk;
+    }
+    if (kernels) *kernels = nk;
+    return RR_OK;
+}
+
+// One query with the reduced-state engine: writes the descriptor, then replays
+// the captured launch sequence of the query's shape (capturing it on first use)
+// or, while kernel timing is enabled, enqueues the launches directly so each
+// can be timed.
+rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
+                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st)
+{
+    const uint32_t k = q->k;
+    RR_CUDA(ws.desc.reserve(sizeof(QueryDesc)));
+    QueryDesc hd{};
+    const QueryKeys keys = make_keys(q->seed);
+    hd.source = q->source;
+    hd.k = k;
+    hd.colored = q->motif ? 1u : 0u;
+    hd.key_y = keys.key_y;
+    hd.key_z = keys.key_z;
+    hd.key_g = keys.key_gamma;
+    hd.key_o = keys.key_omega;
+    hd.S = d_witness;
+    hd.bitmap = d_bitmap;
+    if (q->motif) {
+        ShadeTable sh;
+        make_shades(q->motif, k, &sh);
+        std::memcpy(hd.shades, sh.first, sizeof sh.first);
+        std::memcpy(hd.shades + 256, sh.mu, sizeof sh.mu);
+    }
+    const QueryDesc *dd = ws.desc.as<QueryDesc>();
+    // stage the descriptor in a pinned ring slot (reused only after the launch
+    // that read it has finished) and copy it in stream order
+    if (!ws.h_ring) {
+        RR_CUDA(cudaMallocHost(&ws.h_ring, sizeof(QueryDesc) * Workspace::kRing));
+        for (int i = 0; i < Workspace::kRing; ++i)
+            RR_CUDA(cudaEventCreateWithFlags(&ws.ring_ev[i], cudaEventDisableTiming));
+    }
+    const uint32_t slot = ws.ring_pos++ % Workspace::kRing;
+    if (ws.ring_used[slot]) RR_CUDA(cudaEventSynchronize(ws.ring_ev[slot]));
+    ws.h_ring[slot] = hd;
+    RR_CUDA(cudaMemcpyAsync(ws.desc.p, &ws.h_ring[slot], sizeof hd, cudaMemcpyHostToDevice, st));
+    ws.ring_used[slot] = true;
+    const bool colored = q->motif != nullptr;
+    const bool bitmap = d_bitmap != nullptr;
+    if (g_timing.load(std::memory_order_relaxed)) {
+        rr_status s = enqueue_query_v2(g, k, colored, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
+                                       ws.state.as<uint64_t>(), dd, st, nullptr);
+        RR_CUDA(cudaEventRecord(ws.ring_ev[slot], st));
+        return s;
+    }
+    if (ws.graph_state != ws.state.p || ws.graph_z != ws.z.p) {
+        ws.drop_graphs();
+        ws.graph_state = ws.state.p;
+        ws.graph_z = ws.z.p;
+    }
+    const uint64_t key = (uint64_t)k | ((uint64_t)ppl << 8) | ((uint64_t)chunk << 16) |
+                         ((uint64_t)colored << 40) | ((uint64_t)bitmap << 41);
+    cudaGraphExec_t exec = nullptr;
+    uint64_t nkern = 0;
+    for (size_t i = 0; i < ws.graphs.size(); ++i)
+        if (ws.graphs[i].first == key) {
+            exec = ws.graphs[i].second;
+            nkern = ws.graph_kernels[i];
+        }
+    if (!exec) {
+        if (!ws.capture) RR_CUDA(cudaStreamCreateWithFlags(&ws.capture, cudaStreamNonBlocking));
+        RR_CUDA(cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeThreadLocal));
+        rr_status s = enqueue_query_v2(g, k, colored, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
+                                       ws.state.as<uint64_t>(), dd, ws.capture, &nkern);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ws.capture, &graph);
+        if (s != RR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        ws.graphs.emplace_back(key, exec);
+        ws.graph_kernels.push_back(nkern);
+        g_launches.fetch_sub(nkern, std::memory_order_relaxed);  // capture launched nothing
+    }
+    RR_CUDA(cudaGraphLaunch(exec, st));
+    RR_CUDA(cudaEventRecord(ws.ring_ev[slot], st));
+    g_launches.fetch_add(nkern, std::memory_order_relaxed);
+    return RR_OK;
+}
+
+}  // namespace rr

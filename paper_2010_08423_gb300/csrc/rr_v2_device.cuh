@@ -1,0 +1,333 @@
+// rr_v2_device.cuh -- per-warp bodies of the reduced-state engine's layers,
+// shared by the one-query kernels (rr_sieve2.cu) and the persistent batched
+// kernel (rr_batch.cu).
+#pragma once
+#include <cstdint>
+
+#include "rr_device.cuh"
+#include "rr_internal.h"
+
+namespace rr {
+
+constexpr int kW2 = 4;  // warps per block
+
+struct V2Params {
+    // list
+    const uint32_t *head, *eid, *src, *ia, *ib;
+    const uint2 *items;
+    uint32_t nitems;
+    // query
+    const QueryDesc *qd;  // source, key_y and the witness pointer of the query
+    const uint64_t *z;
+    uint32_t n, k, layer;
+    // chunk
+    uint32_t chunk_base, chunk, ngroups, npoints;
+    const uint64_t *py;     // scalar layer-1 prefix, indexed by producer rank
+    const uint64_t *st_in;  // full state, stride chunk
+    uint64_t *st_out;       // full (stride chunk) or reduced (stride ngroups*(lg+1))
+};
+
+__device__ __forceinline__ uint64_t shfl64b(uint64_t v, int src)
+{
+    return __shfl_sync(0xffffffffu, (unsigned long long)v, src);
+}
+__device__ __forceinline__ uint64_t shfl64x(uint64_t v, int mask)
+{
+    return __shfl_xor_sync(0xffffffffu, (unsigned long long)v, mask);
+}
+
+// Sum over j in L of the per-label values held by lanes 0..k-1 (lane j holds
+// label j+1's value), for the lane's PPL consecutive points of a group whose
+// first point has high bits `hi_bits` (bits >= LOGP+5 of the point index).
+template <int PPL>
+__device__ __forceinline__ void combine_labels(uint64_t lane_val, uint32_t k, int lane,
+                                               uint32_t hi_bits, uint64_t (&out)[PPL])
+{
+    constexpr int LOGP = PPL == 4 ? 2 : 1;
+    uint64_t base = 0, low0 = 0, low1 = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+        const uint64_t bj = shfl64b(lane_val, (int)j);
+        if (j == 0) low0 = bj;
+        else if (LOGP == 2 && j == 1) low1 = bj;
+        else if (j < (uint32_t)LOGP + 5u) {
+            if (((uint32_t)lane >> (j - LOGP)) & 1u) base ^= bj;
+        } else if ((hi_bits >> (j - LOGP - 5u)) & 1u) {
+            base ^= bj;
+        }
+    }
+    out[0] = base;
+    out[1] = base ^ low0;
+    if constexpr (PPL == 4) {
+        out[2] = base ^ low1;
+        out[3] = base ^ low0 ^ low1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Layer 1: PY[p+1] = XOR of [src == s] y_{f,1} over the producer-list entries
+// of p's head segment up to p (segmented inclusive scan, 32 entries a step).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void first_scalar_warp(const V2Params &p, uint32_t task,
+                                                  uint64_t *__restrict__ py)
+{
+    const int lane = threadIdx.x & 31;
+    const uint2 it = p.items[task];
+    const uint32_t source = p.qd->source;
+    const uint64_t key_y = p.qd->key_y;
+    uint64_t carry = 0;
+    uint32_t carry_head = 0xFFFFFFFFu;
+    for (uint32_t base = it.x; base < it.y; base += 32) {
+        const uint32_t ent = base + lane;
+        const bool has = ent < it.y;
+        const uint32_t h = has ? p.head[ent] : 0xFFFFFFFEu;
+        uint64_t q = 0;
+        if (has && p.src[ent] == source)
+            q = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u);  // y_{f,1}
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t qq = __shfl_up_sync(0xffffffffu, (unsigned long long)q, d);
+            const uint32_t hh = __shfl_up_sync(0xffffffffu, h, d);
+            if (lane >= d && hh == h) q ^= qq;
+        }
+        if (h == carry_head) q ^= carry;
+        if (has) py[(size_t)ent + 1] = q;
+        const int last = (int)min(31u, it.y - 1 - base);
+        carry = shfl64b(q, last);
+        carry_head = __shfl_sync(0xffffffffu, h, last);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Layers 2..k-2 (and the last layer when k = 3).
+//   FROM_Y: window sum W^L = Y_e x_s^L x_u^L (layer 2), Y_e = PY[a0] ^ PY[b0];
+//   else  : W^L = state[a1] ^ state[b1] (layers >= 3).
+//   OUT 0: write the per-point prefix to the state row of the entry;
+//   OUT 1: write the group's transformed prefix (T_0..T_{lg-1}, V);
+//   OUT 2: XOR the per-vertex totals into S (last layer, k = 3).
+// One warp per (scheduling range, point group); lanes own PPL points each.
+// ---------------------------------------------------------------------------
+// COHERENT: state written earlier in the same launch is read through L2
+// (ld.global.cg) instead of the non-coherent read-only path.
+template <int PPL, bool FROM_Y, int OUT, bool COHERENT>
+__device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uint32_t group)
+{
+    constexpr int LOGP = PPL == 4 ? 2 : 1;
+    constexpr int LG = LOGP + 5;
+    const int lane = threadIdx.x & 31;
+    const uint2 it = p.items[item];
+    const uint32_t k = p.k;
+    const uint32_t source = p.qd->source;
+    const uint64_t key_y = p.qd->key_y;
+    uint64_t *const S = p.qd->S;
+    const uint32_t col = group * (32u * PPL) + (uint32_t)lane * PPL;
+    const uint32_t gbase = p.chunk_base + group * (32u * PPL);
+    const uint32_t hi_bits = gbase >> LG;
+    bool valid[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) valid[i] = gbase + (uint32_t)lane * PPL + i < p.npoints;
+
+    uint64_t xs[PPL];
+    if constexpr (FROM_Y) {
+        const uint64_t zs = (uint32_t)lane < k ? p.z[(size_t)source * k + lane] : 0ull;
+        combine_labels<PPL>(zs, k, lane, hi_bits, xs);
+    }
+
+    uint64_t acc[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) acc[i] = 0;
+    uint32_t cur = p.head[it.x];
+    uint64_t zv = (uint32_t)lane < k ? p.z[(size_t)cur * k + lane] : 0ull;
+    bool any = false;
+
+    auto flush = [&](uint32_t v) {
+        if constexpr (OUT == 2) {
+            uint64_t t = 0;
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) t ^= acc[i];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t ^= shfl64x(t, off);
+            if (lane == 0 && t) atomicXor(reinterpret_cast<unsigned long long *>(S + v),
+                                          (unsigned long long)t);
+        }
+    };
+
+    for (uint32_t base = it.x; base < it.y; base += 32) {
+        const uint32_t ent = base + lane;
+        const bool has = ent < it.y;
+        const uint32_t m_head = has ? p.head[ent] : 0u;
+        const uint32_t m_a = has ? p.ia[ent] : 0u;
+        const uint32_t m_b = has ? p.ib[ent] : 0u;
+        uint64_t m_coef = 0;
+        uint32_t m_src = 0;
+        if (has) {
+            m_coef = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u));
+            if constexpr (FROM_Y) {
+                m_coef = gf64_mul(m_coef, p.py[m_a] ^ p.py[m_b]);  // y_{e,2} * Y_e
+                m_src = p.src[ent];
+            }
+        }
+        const uint32_t nb = min(32u, it.y - base);
+        for (uint32_t t = 0; t < nb; ++t) {
+            const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
+            if (h != cur) {
+                if (any) flush(cur);
+#pragma unroll
+                for (int i = 0; i < PPL; ++i) acc[i] = 0;
+                any = false;
+                cur = h;
+                zv = (uint32_t)lane < k ? p.z[(size_t)cur * k + lane] : 0ull;
+            }
+            const uint32_t a = __shfl_sync(0xffffffffu, m_a, (int)t);
+            const uint32_t b = __shfl_sync(0xffffffffu, m_b, (int)t);
+            if (FROM_Y || a != b) {
+                const uint64_t coef = shfl64b(m_coef, (int)t);
+                uint64_t c[PPL], w[PPL];
+                combine_labels<PPL>(gf64_mul(coef, zv), k, lane, hi_bits, c);
+                if constexpr (FROM_Y) {
+                    const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
+                    const uint64_t zu = (uint32_t)lane < k ? p.z[(size_t)u * k + lane] : 0ull;
+                    uint64_t xu[PPL];
+                    combine_labels<PPL>(zu, k, lane, hi_bits, xu);
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) w[i] = gf64_mul(xs[i], xu[i]);
+                } else {
+                    const uint64_t *pa = p.st_in + (size_t)a * p.chunk + col;
+                    const uint64_t *pb = p.st_in + (size_t)b * p.chunk + col;
+                    const ulonglong2 *va = reinterpret_cast<const ulonglong2 *>(pa);
+                    const ulonglong2 *vb = reinterpret_cast<const ulonglong2 *>(pb);
+                    if constexpr (PPL == 4) {
+                        const ulonglong2 a0 = COHERENT ? __ldcg(va) : __ldg(va);
+                        const ulonglong2 a1 = COHERENT ? __ldcg(va + 1) : __ldg(va + 1);
+                        const ulonglong2 b0 = COHERENT ? __ldcg(vb) : __ldg(vb);
+                        const ulonglong2 b1 = COHERENT ? __ldcg(vb + 1) : __ldg(vb + 1);
+                        w[0] = a0.x ^ b0.x; w[1] = a0.y ^ b0.y; w[2] = a1.x ^ b1.x; w[3] = a1.y ^ b1.y;
+                    } else {
+                        const ulonglong2 a0 = COHERENT ? __ldcg(va) : __ldg(va);
+                        const ulonglong2 b0 = COHERENT ? __ldcg(vb) : __ldg(vb);
+                        w[0] = a0.x ^ b0.x; w[1] = a0.y ^ b0.y;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < PPL; ++i)
+                    acc[i] ^= valid[i] ? gf64_mul(c[i], w[i]) : 0ull;
+                any = true;
+            }
+            const size_t row = (size_t)base + t + 1;  // state row of this entry
+            if constexpr (OUT == 0) {
+                uint64_t *po = p.st_out + row * p.chunk + col;
+                if constexpr (PPL == 4) {
+                    reinterpret_cast<ulonglong2 *>(po)[0] = make_ulonglong2(acc[0], acc[1]);
+                    reinterpret_cast<ulonglong2 *>(po)[1] = make_ulonglong2(acc[2], acc[3]);
+                } else {
+                    reinterpret_cast<ulonglong2 *>(po)[0] = make_ulonglong2(acc[0], acc[1]);
+                }
+            } else if constexpr (OUT == 1) {
+                // T_j over the group's 32*PPL points: in-lane label bits from U,
+                // lane bits from the half-cube sums of V, and the total V.
+                uint64_t V = 0;
+#pragma unroll
+                for (int i = 0; i < PPL; ++i) V ^= acc[i];
+                uint64_t U0 = acc[1] ^ (PPL == 4 ? acc[3] : 0ull);
+                uint64_t U1 = PPL == 4 ? (acc[2] ^ acc[3]) : 0ull;
+                uint64_t X = V, Y[5];
+#pragma unroll
+                for (int bb = 0; bb < 5; ++bb) {
+                    const uint64_t P = shfl64x(X, 1 << bb);
+                    Y[bb] = ((lane >> bb) & 1) ? X : P;
+                    X ^= P;
+#pragma unroll
+                    for (int b2 = 0; b2 < bb; ++b2) Y[b2] ^= shfl64x(Y[b2], 1 << bb);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    U0 ^= shfl64x(U0, off);
+                    if constexpr (PPL == 4) U1 ^= shfl64x(U1, off);
+                }
+                // slot j < LG: T_j ; slot LG: V
+                uint64_t val;
+                if (LOGP == 2 && lane == 1) val = U1;
+                else if (lane == 0) val = U0;
+                else if (lane < LG) {
+                    const int bb = lane - LOGP;
+                    val = bb == 0 ? Y[0] : bb == 1 ? Y[1] : bb == 2 ? Y[2] : bb == 3 ? Y[3] : Y[4];
+                } else {
+                    val = X;
+                }
+                if (lane <= LG)
+                    p.st_out[(row * p.ngroups + group) * (LG + 1) + lane] = val;
+            }
+        }
+    }
+    if (any) flush(cur);
+}
+
+// ---------------------------------------------------------------------------
+// Last layer from the transformed state: lane (g, j) accumulates
+// sum_e y_{e,k-1} T_{g,j}(W_e) over the rows e of one head vertex v, then
+// multiplies once by z_{v,j} (j < lg) or by the XOR of z_{v,j'} over the
+// group's fixed high labels j' (slot lg), and the warp XOR-reduces into S[v].
+// ---------------------------------------------------------------------------
+template <int LG, bool COHERENT>
+__device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
+{
+    const int lane = threadIdx.x & 31;
+    const uint2 it = p.items[task];
+    const uint32_t k = p.k;
+    const uint64_t key_y = p.qd->key_y;
+    uint64_t *const S = p.qd->S;
+    const uint32_t slots = p.ngroups * (LG + 1);
+    const bool active = (uint32_t)lane < slots;
+    const uint32_t g = (uint32_t)lane / (LG + 1);
+    const uint32_t j = (uint32_t)lane - g * (LG + 1);
+    const uint32_t gbase = p.chunk_base + g * (1u << LG);
+
+    auto zsel_of = [&](uint32_t v) -> uint64_t {
+        if (!active) return 0ull;
+        if (j < (uint32_t)LG) return j < k ? p.z[(size_t)v * k + j] : 0ull;
+        uint64_t zz = 0;
+        for (uint32_t jj = LG; jj < k; ++jj)
+            if ((gbase >> jj) & 1u) zz ^= p.z[(size_t)v * k + jj];
+        return zz;
+    };
+
+    uint32_t cur = p.head[it.x];
+    uint64_t zsel = zsel_of(cur);
+    uint64_t acc = 0;
+    auto flush = [&](uint32_t v) {
+        uint64_t t = active ? gf64_mul(zsel, acc) : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t ^= shfl64x(t, off);
+        if (lane == 0 && t) atomicXor(reinterpret_cast<unsigned long long *>(S + v),
+                                      (unsigned long long)t);
+    };
+    for (uint32_t base = it.x; base < it.y; base += 32) {
+        const uint32_t ent = base + lane;
+        const bool has = ent < it.y;
+        const uint32_t m_head = has ? p.head[ent] : 0u;
+        const uint32_t m_a = has ? p.ia[ent] : 0u;
+        const uint32_t m_b = has ? p.ib[ent] : 0u;
+        const uint64_t m_y = has ? sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u)) : 0ull;
+        const uint32_t nb = min(32u, it.y - base);
+        for (uint32_t t = 0; t < nb; ++t) {
+            const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
+            if (h != cur) {
+                flush(cur);
+                acc = 0;
+                cur = h;
+                zsel = zsel_of(cur);
+            }
+            const uint32_t a = __shfl_sync(0xffffffffu, m_a, (int)t);
+            const uint32_t b = __shfl_sync(0xffffffffu, m_b, (int)t);
+            const uint64_t y = shfl64b(m_y, (int)t);
+            if (active) {
+                const uint64_t *sa = p.st_in + (size_t)a * slots + lane;
+                const uint64_t *sb = p.st_in + (size_t)b * slots + lane;
+                const uint64_t tv = COHERENT ? (__ldcg(sa) ^ __ldcg(sb)) : (*sa ^ *sb);
+                acc ^= gf64_mul(y, tv);
+            }
+        }
+    }
+    flush(cur);
+}
+
+}  // namespace rr

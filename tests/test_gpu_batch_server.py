@@ -1,0 +1,145 @@
+"""GPU tests of the batched persistent launch and the serving loop.
+
+Both must reproduce, bit for bit, what one query alone gives (and the CPU
+oracle): the batch packs queries of uneven k, sources and motifs into one
+persistent kernel; the server runs queries that arrive while others are on the
+GPU. GF(2^64) sums are exact, so the tolerance is zero.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_08423_gb300 import capi
+from paper_2010_08423_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    capi.load()
+    oracle.build()
+    g = W.uniform(3000, 40_000, 40, 0, 6, 424242, ncolors=3)
+    rng = np.random.default_rng(9)
+    qs = []
+    for i, k in enumerate([2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 5, 8, 4, 3, 9]):
+        s = int(rng.integers(0, 8))
+        motif = None
+        if i % 2 == 1:
+            motif = [int(g["color"][s])] + [int(x) for x in rng.integers(0, 3, k - 1)]
+        qs.append({"source": s, "k": k, "seed": int(rng.integers(0, 2**62)), "motif": motif})
+    return g, qs
+
+
+def _torch():
+    import torch
+    torch.cuda.set_device(0)
+    return torch
+
+
+def test_batch_matches_single_queries_and_oracle(mixed):
+    torch = _torch()
+    g, qs = mixed
+    n = g["n"]
+    nb = (n + 7) // 8
+    with capi.Graph(g) as G:
+        singles = [G.reach(q["source"], q["k"], q["seed"], motif=q["motif"]) for q in qs]
+        d_w = torch.full((len(qs), n), -1, dtype=torch.int64, device="cuda")
+        d_bm = torch.full((len(qs), nb), 255, dtype=torch.uint8, device="cuda")
+        d_st = torch.full((len(qs),), 7, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.Stream()
+        capi.rr_reach_batch_device(G.handle, qs, d_w, d_bm, d_st, stream.cuda_stream)
+        stream.synchronize()
+        w = d_w.cpu().numpy().view(np.uint64)
+        bm = d_bm.cpu().numpy()
+        assert (d_st.cpu().numpy() == 0).all()
+        nonzero = 0
+        for i, q in enumerate(qs):
+            assert np.array_equal(w[i], singles[i][1]), (i, q["k"])
+            assert np.array_equal(bm[i], singles[i][0]), i
+            nonzero += np.count_nonzero(w[i]) > 0
+        assert nonzero >= 8
+        for i in (1, 4, 7, 9):
+            q = qs[i]
+            assert np.array_equal(w[i], oracle.sieve(g, q["source"], q["k"], q["seed"],
+                                                     motif=q["motif"]))
+        # a second batch on the same graph reuses the batch buffers
+        capi.rr_reach_batch_device(G.handle, qs[::-1], d_w, None, None, stream.cuda_stream)
+        stream.synchronize()
+        w2 = d_w.cpu().numpy().view(np.uint64)
+        for i, q in enumerate(qs[::-1]):
+            assert np.array_equal(w2[i], singles[len(qs) - 1 - i][1])
+
+
+def test_batch_many_small_queries():
+    torch = _torch()
+    g = W.uniform(1500, 20_000, 25, 0, 5, 77, ncolors=2)
+    rng = np.random.default_rng(3)
+    qs = [{"source": int(rng.integers(0, 1500)), "k": int(rng.integers(4, 9)),
+           "seed": i + 1, "motif": None} for i in range(96)]
+    with capi.Graph(g) as G:
+        d_w = torch.zeros((len(qs), g["n"]), dtype=torch.int64, device="cuda")
+        capi.rr_reach_batch_device(G.handle, qs, d_w)
+        torch.cuda.synchronize()
+        w = d_w.cpu().numpy().view(np.uint64)
+        for i in range(0, len(qs), 7):
+            _, ref = G.reach(qs[i]["source"], qs[i]["k"], qs[i]["seed"])
+            assert np.array_equal(w[i], ref), i
+
+
+def test_server_result_alone_equals_result_in_mix(mixed):
+    g, qs = mixed
+    n = g["n"]
+    with capi.Graph(g) as G:
+        srv = capi.rr_server_create(G.handle, 0, 4)
+        try:
+            probe = qs[9]
+            t = capi.rr_query_submit(srv, probe["source"], probe["k"], probe["seed"], probe["motif"])
+            st, bm_alone, w_alone = capi.rr_query_poll(srv, t, n, -1)
+            assert st == capi.RR_OK
+            # the same query again, submitted while a stream of others arrives
+            tickets = []
+            for i, q in enumerate(qs * 2):
+                tickets.append((i % len(qs), capi.rr_query_submit(srv, q["source"], q["k"],
+                                                                   q["seed"], q["motif"])))
+                if i == 5:
+                    t_mix = capi.rr_query_submit(srv, probe["source"], probe["k"],
+                                                 probe["seed"], probe["motif"])
+            st, bm_mix, w_mix = capi.rr_query_poll(srv, t_mix, n, -1)
+            assert st == capi.RR_OK
+            assert np.array_equal(w_mix, w_alone) and np.array_equal(bm_mix, bm_alone)
+            for qi, t in tickets:
+                st, _, w = capi.rr_query_poll(srv, t, n, -1)
+                assert st == capi.RR_OK
+                _, ref = G.reach(qs[qi]["source"], qs[qi]["k"], qs[qi]["seed"], motif=qs[qi]["motif"])
+                assert np.array_equal(w, ref), qi
+                q_us, tot_us = capi.rr_query_times(srv, t)
+                assert 0 <= q_us <= tot_us
+        finally:
+            capi.rr_server_destroy(srv)
+
+
+def test_server_cancel_and_admission():
+    g = W.uniform(2000, 20_000, 30, 0, 5, 5)
+    with capi.Graph(g) as G:
+        srv = capi.rr_server_create(G.handle, 0, 1)
+        try:
+            ts = [capi.rr_query_submit(srv, 0, 12, i) for i in range(6)]
+            capi.rr_query_cancel(srv, ts[-1])
+            st, _, _ = capi.rr_query_poll(srv, ts[0], g["n"], -1)
+            assert st == capi.RR_OK
+            with pytest.raises(capi.RRError) as ei:
+                capi.rr_query_poll(srv, ts[-1], g["n"], -1)
+            assert ei.value.status == capi.RR_ECANCELED
+            for t in ts[1:-1]:
+                st, _, _ = capi.rr_query_poll(srv, t, g["n"], -1)
+                assert st == capi.RR_OK
+        finally:
+            capi.rr_server_destroy(srv)
+        # a budget too small for even one point chunk refuses the server
+        with pytest.raises(capi.RRError) as ei:
+            capi.rr_server_create(G.handle, 1 << 10, 1)
+        assert ei.value.status == capi.RR_ENOMEM

@@ -245,3 +245,51 @@ def test_bench_workload_sampled_points_and_one_sided():
         _, ref = oracle.sieve(g2, 0, 8, 42, masks=masks, per_mask=True)
         assert np.count_nonzero(ref) > 0
         assert np.array_equal(dev, ref)
+
+
+def test_full_size_dense_windows_full_witness():
+    """n=100,000 / m=1,000,000 with t ~ U[1,30]: windows hold several rows and
+    restless walks survive every layer; the whole witness vector must equal the
+    oracle's (all 64 points, k=6), and the per-point engine must agree too."""
+    g = W.uniform(100_000, 1_000_000, 30, 1, 20, 0x5EED0002 + 200)
+    ref = oracle.sieve(g, 7, 6, 31)
+    assert np.count_nonzero(ref) > 100
+    with _graph(g) as G:
+        _, w = G.reach(7, 6, 31)
+        assert np.array_equal(w, ref)
+    with _graph(g, capi.FLAG_DENSE_STATE) as G:
+        _, w = G.reach(7, 6, 31)
+        assert np.array_equal(w, ref)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 9, 11])
+def test_engines_agree_across_k(k):
+    # compact graphs run the reduced-state engine for k >= 3, dense-flag graphs
+    # the per-point engine; both must equal the oracle (multi-chunk for k >= 10)
+    g = _dense_uniform(800, 9_000, 12, 4, 70 + k, ncolors=2)
+    ref = oracle.sieve(g, 1, k, 1000 + k)
+    with _graph(g) as G:
+        _, w = G.reach(1, k, 1000 + k)
+        assert np.array_equal(w, ref)
+    with _graph(g, capi.FLAG_DENSE_STATE) as G:
+        _, w = G.reach(1, k, 1000 + k)
+        assert np.array_equal(w, ref)
+
+
+def test_graph_replay_and_direct_launch_agree():
+    # with kernel timing enabled the library launches kernels one by one; by
+    # default it replays a captured CUDA graph per query shape
+    g = _dense_uniform(1000, 12_000, 20, 5, 81)
+    ref = oracle.sieve(g, 4, 7, 5)
+    with _graph(g) as G:
+        capi.rr_timing_enable(True)
+        try:
+            _, w_direct = G.reach(4, 7, 5)
+        finally:
+            capi.rr_timing_enable(False)
+        times = capi.rr_timing_read(reset=True)
+        assert times["second_layer"][1] >= 1 and times["last_layer"][1] >= 1
+        _, w_graph = G.reach(4, 7, 5)
+        _, w_graph2 = G.reach(4, 7, 5)  # replay of the cached graph
+        assert np.array_equal(w_direct, ref)
+        assert np.array_equal(w_graph, ref) and np.array_equal(w_graph2, ref)
