@@ -130,6 +130,110 @@ def cpu_baseline(g, k, nsteps_hint=1):
                       f"({dt:.2f} s wall), scaled by points"}
 
 
+def batched_metrics(capi, torch, gc, nq=256, seed=GRAPH_SEED):
+    """The same graph with 8 colours; nq queries, s ~ U, k ~ U{4..12}, odd q
+    with a motif (source colour + k-1 uniform colours): one persistent batched
+    launch against one launch sequence per query, results compared bit for bit."""
+    qs = W.query_set(gc, nq, 4, 12, seed)
+    n = gc["n"]
+    m = len(gc["src"])
+    units = sum(units_per_query(q["k"], m) for q in qs)
+    with capi.Graph(gc) as G:
+        stream = torch.cuda.Stream()
+        d_b = torch.zeros((nq, n), dtype=torch.int64, device="cuda")
+        d_s = torch.zeros((nq, n), dtype=torch.int64, device="cuda")
+        d_st = torch.zeros(nq, dtype=torch.int32, device="cuda")
+        # warm-up (captures graphs / grows buffers)
+        capi.rr_reach_batch_device(G.handle, qs[:8], d_b, None, d_st, stream.cuda_stream)
+        for q in qs[:8]:
+            capi.rr_reach_device(G.handle, q["source"], q["k"], q["seed"], d_s[0], None,
+                                 stream.cuda_stream, motif=q["motif"])
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            capi.rr_reach_batch_device(G.handle, qs, d_b, None, d_st, stream.cuda_stream)
+            e1.record(stream)
+            stream.synchronize()
+            t_batch = e0.elapsed_time(e1) / 1e3
+            e0.record(stream)
+            for i, q in enumerate(qs):
+                capi.rr_reach_device(G.handle, q["source"], q["k"], q["seed"], d_s[i], None,
+                                     stream.cuda_stream, motif=q["motif"])
+            e1.record(stream)
+            stream.synchronize()
+            t_single = e0.elapsed_time(e1) / 1e3
+        same = bool(torch.equal(d_b, d_s)) and int(d_st.abs().sum().item()) == 0
+    return {"workload": f"{nq} queries on the n=100000 m=1000000 graph with 8 colours, "
+                        "k~U{4..12}, odd queries coloured (motif = source colour + k-1 uniform)",
+            "queries_per_s": nq / t_batch, "value": units / t_batch, "unit": UNIT,
+            "one_query_per_launch_queries_per_s": nq / t_single,
+            "one_query_per_launch_value": units / t_single,
+            "speedup": t_single / t_batch, "bit_exact_vs_single": same,
+            "launches": "1 persistent kernel (+ z-table, first-layer and bitmap prologue/epilogue)"}
+
+
+def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E):
+    """Serving: Poisson arrivals of plain queries (s ~ U, k ~ U{6..12}) at 0.5x,
+    0.8x and 1.1x of the server's measured capacity; latency = submit -> done."""
+    import threading
+    rng = np.random.default_rng(seed)
+    n = g["n"]
+    qs = [(int(rng.integers(0, n)), int(rng.integers(6, 13)), int(rng.integers(1, 2**62)))
+          for _ in range(nq)]
+    out = {"workload": "plain queries, k~U{6..12}, s~U, on the n=100000 m=1000000 graph",
+           "slots": 4}
+    with capi.Graph(g) as G:
+        srv = capi.rr_server_create(G.handle, 0, 4)
+        try:
+            for s_, k_, sd in qs[:8]:  # warm-up: capture each slot's graphs
+                capi.rr_query_poll(srv, capi.rr_query_submit(srv, s_, k_, sd), n, -1)
+            t0 = time.perf_counter()
+            ts = [capi.rr_query_submit(srv, s_, k_, sd) for s_, k_, sd in qs]
+            for t in ts:
+                capi.rr_query_poll(srv, t, n, -1)
+            cap = nq / (time.perf_counter() - t0)
+            out["capacity_queries_per_s"] = cap
+            loads = []
+            for frac in (0.5, 0.8, 1.1):
+                rate = frac * cap
+                gaps = rng.exponential(1.0 / rate, size=nq)
+                tickets = []
+                lock = threading.Lock()
+
+                def poller():
+                    i = 0
+                    while i < nq:
+                        with lock:
+                            have = len(tickets)
+                        if i < have:
+                            capi.rr_query_poll(srv, tickets[i], n, -1)
+                            i += 1
+                        else:
+                            time.sleep(0.0002)
+                th = threading.Thread(target=poller)
+                th.start()
+                t_start = time.perf_counter()
+                nxt = t_start
+                for (s_, k_, sd), gap in zip(qs, gaps):
+                    nxt += gap
+                    while time.perf_counter() < nxt:
+                        pass
+                    t = capi.rr_query_submit(srv, s_, k_, sd)
+                    with lock:
+                        tickets.append(t)
+                th.join()
+                wall = time.perf_counter() - t_start
+                lat = np.array([capi.rr_query_times(srv, t)[1] for t in tickets]) / 1e3
+                loads.append({"offered_frac": frac, "offered_queries_per_s": rate,
+                              "queries_per_s": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99))})
+            out["loads"] = loads
+        finally:
+            capi.rr_server_destroy(srv)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -169,6 +273,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--dense", action="store_true", help="dense state layout (every row stored)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -271,7 +376,7 @@ def main():
     lg = 7 if ppl == 4 else 6
     rstride = chunk // (32 * ppl) * (lg + 1)
     alg = {
-        "second_layer": srows * chunk * 8 + srows * 28 + 2 * srows * K * 8,
+        "second_layer": srows * K * 8 + srows * 20 + 2 * srows * 8 + srows * K * 8,
         "mid_layer": srows * chunk * 8 + 2 * crows * chunk * 8 + srows * 16,
         "tail_layer": srows * rstride * 8 + 2 * crows * chunk * 8 + srows * 16,
         "last_layer": 2 * trows * rstride * 8 + trows * 16 + n * 8,
@@ -317,6 +422,10 @@ def main():
                     "d2h_bytes_per_step": n * 8 + (n + 7) // 8,
                     "api": "rr_reach_sync (host outputs, query descriptor uploaded per step)"},
             "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and not args.no_extra:
+        gc = W.scale_uniform(ncolors=8)
+        line["batched"] = batched_metrics(capi, torch, gc)
+        line["served"] = served_metrics(capi, g)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, K)
     if rank == 0:

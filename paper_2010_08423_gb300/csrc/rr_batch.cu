@@ -30,8 +30,10 @@ enum BatchKind : uint32_t {
     kSecondTail = 1,   // layer 2 when k = 4, transformed state out
     kSecondFinal = 2,  // layer 2 when k = 3, per-vertex sums out
     kMidFull = 3,      // layers 3..k-3
-    kMidTail = 4,      // layer k-2 (k >= 5), transformed state out
-    kLast = 5          // layer k-1 from the transformed state
+    kMidTail = 4,      // layer k-2 (k >= 6), transformed state out
+    kLast = 5,         // layer k-1 from the transformed state
+    kThirdFull = 6,    // layer 3 (k >= 6) from the label-space layer-2 prefix
+    kThirdTail = 7     // layer 3 when k = 5, transformed state out
 };
 
 struct BatchUnit {
@@ -56,12 +58,15 @@ struct BatchArgs {
     uint32_t n;
     const BatchUnit *units;
     const BatchSeg *segs;
+    const uint32_t *task_seg;  // segment of every task
     uint32_t nseg, total_tasks;
     const QueryDesc *descs;
     const uint64_t *z_all;
     const uint64_t *z_off;   // per query, in words
     const uint64_t *py_all;
     const uint64_t *py_off;  // per query, in words
+    const uint64_t *pr2_all;
+    const uint64_t *pr2_off; // per query, in words
     uint64_t *slot_base;
     uint64_t slot_words, rows, full_words;  // rows = state rows + 1; full_words = rows * max chunk
     uint32_t *done;       // per unit: tasks completed
@@ -120,6 +125,7 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
     vp.qd = a.descs + u.q;
     vp.z = a.z_all + a.z_off[u.q];
     vp.py = a.py_all + a.py_off[u.q];
+    vp.pr2 = a.pr2_all + a.pr2_off[u.q];
     vp.n = a.n;
     vp.k = u.k;
     vp.layer = sg.layer;
@@ -149,6 +155,16 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
         set_list(vp, a.win, true);
         layer_warp<PPL, true, 2, true>(vp, item, group);
         break;
+    case kThirdFull:
+        set_list(vp, a.state, false);
+        vp.st_out = bufs[l & 1u];
+        layer_warp<PPL, false, 0, true, true>(vp, item, group);
+        break;
+    case kThirdTail:
+        set_list(vp, a.state, false);
+        vp.st_out = red;
+        layer_warp<PPL, false, 1, true, true>(vp, item, group);
+        break;
     case kMidFull:
         set_list(vp, a.state, false);
         vp.st_in = bufs[(l - 1) & 1u];
@@ -169,7 +185,7 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
     }
 }
 
-__global__ void __launch_bounds__(kW2 * 32) k_batch(const BatchArgs a)
+__global__ void __launch_bounds__(kW2 * 32, 4) k_batch(const BatchArgs a)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -177,13 +193,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_batch(const BatchArgs a)
         if (lane == 0) t = atomicAdd(a.ctl, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= a.total_tasks) return;
-        // segment holding task t (largest begin <= t)
-        uint32_t lo = 0, hi = a.nseg;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (a.segs[mid].begin <= t) lo = mid; else hi = mid;
-        }
-        const BatchSeg sg = a.segs[lo];
+        const BatchSeg sg = a.segs[a.task_seg[t]];
         const BatchUnit u = a.units[sg.unit];
         bool ok = true;
         if (lane == 0) {
@@ -251,6 +261,37 @@ k_batch_first(ListPtrs prod, const QueryDesc *__restrict__ descs, uint64_t *__re
     first_scalar_warp(vp, task, py);
 }
 
+// layer 2 in label space for the batch's queries with k >= 5
+__global__ void __launch_bounds__(kW2 * 32)
+k_batch_second(ListPtrs state, const QueryDesc *__restrict__ descs, const uint64_t *__restrict__ z_all,
+               const uint64_t *__restrict__ z_off, const uint64_t *__restrict__ py_all,
+               const uint64_t *__restrict__ py_off, uint64_t *__restrict__ pr2_all,
+               const uint64_t *__restrict__ pr2_off, uint32_t n)
+{
+    const QueryDesc *qd = descs + blockIdx.y;
+    const uint32_t k = qd->k;
+    if (k < 5) return;
+    uint64_t *pr2 = pr2_all + pr2_off[blockIdx.y];
+    if (blockIdx.x == 0 && threadIdx.x < k) pr2[threadIdx.x] = 0;
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= state.nitems) return;
+    V2Params vp{};
+    vp.qd = qd;
+    vp.z = z_all + z_off[blockIdx.y];
+    vp.py = py_all + py_off[blockIdx.y];
+    vp.n = n;
+    vp.k = k;
+    vp.layer = 2;
+    vp.head = state.head;
+    vp.eid = state.eid;
+    vp.src = state.src;
+    vp.ia = state.a0;
+    vp.ib = state.b0;
+    vp.items = state.items;
+    vp.nitems = state.nitems;
+    second_label_warp(vp, task, pr2);
+}
+
 __global__ void k_batch_bitmap(uint32_t n, const QueryDesc *__restrict__ descs)
 {
     const QueryDesc *qd = descs + blockIdx.y;
@@ -283,11 +324,13 @@ __global__ void k_batch_zero_rows(uint64_t *slot_base, uint64_t slot_words, uint
     for (uint32_t i = threadIdx.x; i < 32; i += blockDim.x) b[2 * full_words + i] = 0;
 }
 
-ListPtrs list_ptrs(const RowList &L)
+ListPtrs list_ptrs(const RowList &L, bool coarse)
 {
     return ListPtrs{L.head.as<uint32_t>(), L.eid.as<uint32_t>(), L.src.as<uint32_t>(),
                     L.a0.as<uint32_t>(),   L.b0.as<uint32_t>(),  L.a1.as<uint32_t>(),
-                    L.b1.as<uint32_t>(),   L.items.as<uint2>(),  L.nitems};
+                    L.b1.as<uint32_t>(),
+                    coarse ? L.items_coarse.as<uint2>() : L.items.as<uint2>(),
+                    coarse ? L.nitems_coarse : L.nitems};
 }
 
 // Tasks of layer l of a unit with (k, ppl, chunk).
@@ -295,15 +338,21 @@ uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, u
 {
     if (k == 3) {
         *kind = kSecondFinal;
-        return g.win_list.nitems * ngroups;
+        return g.win_list.nitems_coarse * ngroups;
     }
     if (l == k - 1) {
         *kind = kLast;
-        return g.tail_list.nitems;
+        return g.tail_list.nitems_coarse;
     }
-    if (l == 2) *kind = (k == 4) ? kSecondTail : kSecondFull;
-    else *kind = (l == k - 2) ? kMidTail : kMidFull;
-    return g.state_list.nitems * ngroups;
+    if (l == 2) {
+        if (k >= 5) return 0;  // label-space layer 2 runs in the prologue
+        *kind = kSecondTail;   // k = 4
+    } else if (l == 3) {
+        *kind = (k == 5) ? kThirdTail : kThirdFull;
+    } else {
+        *kind = (l == k - 2) ? kMidTail : kMidFull;
+    }
+    return g.state_list.nitems_coarse * ngroups;
 }
 
 }  // namespace
@@ -346,7 +395,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         std::vector<uint32_t> grp;
         uint64_t qbytes = 0;
         while (gi < bq.size()) {
-            const uint64_t need = ((uint64_t)g.n * qs[bq[gi]].k + 32 + py_words) * 8;
+            const uint64_t need = ((uint64_t)g.n * qs[bq[gi]].k + 64 + py_words +
+                                   rows * qs[bq[gi]].k) * 8;
             if (!grp.empty() && qbytes + need > budget / 2) break;
             qbytes += need;
             grp.push_back(bq[gi++]);
@@ -361,8 +411,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         // units
         std::vector<BatchUnit> units;
         std::vector<QueryDesc> descs(grp.size());
-        std::vector<uint64_t> z_off(grp.size()), py_off(grp.size());
-        uint64_t zw = 0;
+        std::vector<uint64_t> z_off(grp.size()), py_off(grp.size()), pr2_off(grp.size());
+        uint64_t zw = 0, pr2w = 0;
         for (size_t j = 0; j < grp.size(); ++j) {
             const rr_query &q = qs[grp[j]];
             QueryDesc &hd = descs[j];
@@ -386,6 +436,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             z_off[j] = zw;
             zw += ((uint64_t)g.n * q.k + 31) / 32 * 32;
             py_off[j] = j * py_words;
+            pr2_off[j] = pr2w;
+            if (q.k >= 5) pr2w += (rows * q.k + 31) / 32 * 32;
             const uint64_t npts = 1ull << q.k;
             const uint32_t ppl = npts >= 128 ? 4u : 2u;
             uint32_t chunk = (uint32_t)std::max<uint64_t>(32ull * ppl, std::min<uint64_t>(npts, max_chunk));
@@ -415,6 +467,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             }
         }
         std::vector<BatchSeg> segs;
+        std::vector<char> started(units.size(), 0);
         uint64_t total = 0;
         for (size_t w0 = 0; w0 < units.size(); w0 += nslots) {
             const size_t w1 = std::min(units.size(), w0 + nslots);
@@ -435,7 +488,10 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                     sg.layer = l;
                     sg.kind = kind;
                     sg.ngroups = ngroups;
-                    if (l == 2) {
+                    if (!started[i]) {
+                        // the unit's first layer reuses the slot: wait for the
+                        // unit that held it before to finish
+                        started[i] = 1;
                         const long prev = (long)i - (long)nslots;
                         sg.wait_unit = prev >= 0 ? (int32_t)prev : -1;
                         sg.wait_count = prev >= 0 ? unit_total[prev] : 0;
@@ -450,6 +506,10 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                 }
         }
         if (total >= (1ull << 32)) return fail(RR_EINVAL, "rr_reach_batch_device: batch too large");
+        std::vector<uint32_t> task_seg(total);
+        for (size_t si = 0; si < segs.size(); ++si)
+            std::fill(task_seg.begin() + segs[si].begin, task_seg.begin() + segs[si].begin + segs[si].ntasks,
+                      (uint32_t)si);
 
         // device buffers (kept by the graph and grown as needed)
         BatchBuffers &B = g.batch;
@@ -460,9 +520,16 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         RR_CUDA(B.pyoff.reserve(grp.size() * 8));
         RR_CUDA(B.z.reserve(zw * 8));
         RR_CUDA(B.py.reserve(grp.size() * py_words * 8));
+        RR_CUDA(B.pr2.reserve(std::max<uint64_t>(1, pr2w) * 8));
+        RR_CUDA(B.pr2off.reserve(grp.size() * 8));
+        RR_CUDA(cudaMemcpyAsync(B.pr2off.p, pr2_off.data(), grp.size() * 8, cudaMemcpyHostToDevice, st));
         RR_CUDA(B.slots.reserve((size_t)nslots * slot_bytes));
         RR_CUDA(B.done.reserve(units.size() * 4));
         RR_CUDA(B.ctl.reserve(8));
+        RR_CUDA(B.task_seg.reserve(std::max<size_t>(1, task_seg.size()) * 4));
+        if (!task_seg.empty())
+            RR_CUDA(cudaMemcpyAsync(B.task_seg.p, task_seg.data(), task_seg.size() * 4,
+                                    cudaMemcpyHostToDevice, st));
         if (!d_status) RR_CUDA(B.status.reserve((size_t)nq * 4));
         int32_t *status = d_status ? d_status : B.status.as<int32_t>();
         if (!d_status) RR_CUDA(cudaMemsetAsync(status, 0, (size_t)nq * 4, st));
@@ -488,10 +555,17 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             g.n, d_descs.as<QueryDesc>(), g.color.as<uint8_t>(), d_z.as<uint64_t>(),
             d_zoff.as<uint64_t>());
         RR_LAUNCHED();
-        const ListPtrs prod = list_ptrs(g.prod_list);
+        const ListPtrs prod = list_ptrs(g.prod_list, false);
         k_batch_first<<<dim3(std::max<uint32_t>(1, (prod.nitems + kW2 - 1) / kW2), (unsigned)grp.size()),
                         kW2 * 32, 0, st>>>(prod, d_descs.as<QueryDesc>(), d_py.as<uint64_t>(),
                                            d_pyoff.as<uint64_t>());
+        RR_LAUNCHED();
+        k_batch_second<<<dim3(std::max<uint32_t>(1, (g.state_list.nitems + kW2 - 1) / kW2),
+                              (unsigned)grp.size()),
+                         kW2 * 32, 0, st>>>(list_ptrs(g.state_list, false), d_descs.as<QueryDesc>(),
+                                            d_z.as<uint64_t>(), d_zoff.as<uint64_t>(),
+                                            d_py.as<uint64_t>(), d_pyoff.as<uint64_t>(),
+                                            B.pr2.as<uint64_t>(), B.pr2off.as<uint64_t>(), g.n);
         RR_LAUNCHED();
         k_batch_zero_rows<<<nslots, 256, 0, st>>>(d_slots.as<uint64_t>(), slot_bytes / 8,
                                                   rows * max_chunk, nslots, max_chunk);
@@ -499,19 +573,22 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
 
         BatchArgs a{};
         a.prod = prod;
-        a.state = list_ptrs(g.state_list);
-        a.win = list_ptrs(g.win_list);
-        a.tail = list_ptrs(g.tail_list);
+        a.state = list_ptrs(g.state_list, true);
+        a.win = list_ptrs(g.win_list, true);
+        a.tail = list_ptrs(g.tail_list, true);
         a.n = g.n;
         a.units = d_units.as<BatchUnit>();
         a.segs = d_segs.as<BatchSeg>();
         a.nseg = (uint32_t)segs.size();
+        a.task_seg = B.task_seg.as<uint32_t>();
         a.total_tasks = (uint32_t)total;
         a.descs = d_descs.as<QueryDesc>();
         a.z_all = d_z.as<uint64_t>();
         a.z_off = d_zoff.as<uint64_t>();
         a.py_all = d_py.as<uint64_t>();
         a.py_off = d_pyoff.as<uint64_t>();
+        a.pr2_all = B.pr2.as<uint64_t>();
+        a.pr2_off = B.pr2off.as<uint64_t>();
         a.slot_base = d_slots.as<uint64_t>();
         a.slot_words = slot_bytes / 8;
         a.rows = rows;

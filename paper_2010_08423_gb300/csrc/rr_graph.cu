@@ -384,14 +384,23 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         if (R.count)
             RR_CUDA(cudaMemcpyAsync(heads.data(), R.head.p, R.count * 4, cudaMemcpyDeviceToHost, st));
         RR_CUDA(cudaStreamSynchronize(st));
+        // fine ranges: enough warps for about 64 per SM even with one point
+        // group; coarse ranges for the persistent batch, whose parallelism
+        // comes from many queries at once
         const uint32_t target =
-            (uint32_t)std::min<uint64_t>(128, std::max<uint64_t>(8, R.count / (152 * 32)));
-        std::vector<uint2> items;
+            (uint32_t)std::min<uint64_t>(128, std::max<uint64_t>(1, R.count / (152 * 64)));
+        std::vector<uint2> items, coarse;
         build_entry_items(heads, target, items);
+        build_entry_items(heads, 128, coarse);
         R.nitems = (uint32_t)items.size();
+        R.nitems_coarse = (uint32_t)coarse.size();
         RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));
+        RR_CUDA(R.items_coarse.reserve(std::max<size_t>(1, coarse.size()) * sizeof(uint2)));
         if (!items.empty())
             RR_CUDA(cudaMemcpyAsync(R.items.p, items.data(), items.size() * sizeof(uint2),
+                                    cudaMemcpyHostToDevice, st));
+        if (!coarse.empty())
+            RR_CUDA(cudaMemcpyAsync(R.items_coarse.p, coarse.data(), coarse.size() * sizeof(uint2),
                                     cudaMemcpyHostToDevice, st));
         RR_CUDA(cudaStreamSynchronize(st));
     }

@@ -131,18 +131,20 @@ struct RowList {
     DevBuf head, eid, src;  // uint32 per entry
     DevBuf a0, b0;          // window in producer-prefix indices (scalar first-layer prefix)
     DevBuf a1, b1;          // window in state-row indices (state rows = producers with a window)
-    DevBuf items;           // uint2 ranges, largest first
+    DevBuf items;           // uint2 ranges, largest first (fine: one-query kernels)
     uint32_t nitems = 0;
+    DevBuf items_coarse;    // uint2 ranges of about 128 entries (persistent batch)
+    uint32_t nitems_coarse = 0;
     size_t bytes() const
     {
         return head.bytes + eid.bytes + src.bytes + a0.bytes + b0.bytes + a1.bytes + b1.bytes +
-               items.bytes;
+               items.bytes + items_coarse.bytes;
     }
 };
 
 // Device buffers of the persistent batched launch, kept per graph.
 struct BatchBuffers {
-    DevBuf units, segs, descs, zoff, pyoff, z, py, slots, done, ctl, status;
+    DevBuf units, segs, descs, zoff, pyoff, z, py, slots, done, ctl, status, task_seg, pr2, pr2off;
 };
 
 // -------- graph ------------------------------------------------------------
@@ -249,7 +251,7 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
 bool uses_v2(const Graph &g, uint32_t k);
 bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl, uint32_t *chunk);
 uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk);
-uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk);
+uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k);
 // Enqueues the whole launch sequence of one k >= 3 query (z-table, witness
 // clear, all layers, bitmap) reading per-query values from d_desc; returns
 // the number of kernels enqueued in *kernels.

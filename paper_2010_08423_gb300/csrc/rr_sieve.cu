@@ -422,8 +422,8 @@ bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl_
     uint64_t want = g.tune_chunk[k] ? g.tune_chunk[k] : npts;
     want = std::max<uint64_t>(unit, std::min<uint64_t>(want, 4 * unit));  // <= 4 groups
     want = (want + unit - 1) / unit * unit;
-    while (want > unit && v2_scratch_bytes(g, ppl, (uint32_t)want) > budget) want -= unit;
-    if (v2_scratch_bytes(g, ppl, (uint32_t)want) > budget) return false;
+    while (want > unit && v2_scratch_bytes(g, ppl, (uint32_t)want, k) > budget) want -= unit;
+    if (v2_scratch_bytes(g, ppl, (uint32_t)want, k) > budget) return false;
     *ppl_out = ppl;
     *chunk_out = (uint32_t)want;
     return true;
@@ -435,7 +435,7 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget)
     const uint64_t z = (uint64_t)g.n * k * 8ull + 2048;
     if (uses_v2(g, k)) {
         if (!choose_shape_v2(g, k, budget, &ppl, &chunk)) return UINT64_MAX;
-        return v2_scratch_bytes(g, ppl, chunk) + z;
+        return v2_scratch_bytes(g, ppl, chunk, k) + z;
     }
     if (!choose_shape(g, k, budget, &ppl, &chunk)) return UINT64_MAX;
     return 2ull * g.state_rows * chunk * 8ull + z;
@@ -469,7 +469,7 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
             ws.shape_gen[k] = g.tune_gen;
         }
     }
-    RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk)
+    RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk, k)
                                 : 2ull * g.state_rows * chunk * 8ull));
     RR_CUDA(ws.z.reserve((size_t)g.n * k * 8));
     if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st);

@@ -31,13 +31,20 @@ __global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uin
     first_scalar_warp(p, task, py);
 }
 
-template <int PPL, bool FROM_Y, int OUT>
+template <int PPL, bool FROM_Y, int OUT, bool FROM_R2 = false>
 __global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
 {
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems * p.ngroups) return;
     const uint32_t item = task / p.ngroups;
-    layer_warp<PPL, FROM_Y, OUT, false>(p, item, task - item * p.ngroups);
+    layer_warp<PPL, FROM_Y, OUT, false, FROM_R2>(p, item, task - item * p.ngroups);
+}
+
+__global__ void __launch_bounds__(kW2 * 32) k_second_label(const V2Params p, uint64_t *__restrict__ pr2)
+{
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems) return;
+    second_label_warp(p, task, pr2);
 }
 
 template <int LG>
@@ -65,22 +72,27 @@ static void set_list(V2Params &vp, const RowList &L, bool first_window)
     vp.nitems = L.nitems;
 }
 
+// src: 0 = window sums from the per-point state, 1 = from the scalar layer-1
+// prefix (layer 2), 2 = from the label-space layer-2 prefix (layer 3).
 template <int PPL>
-static rr_status launch_v2(const V2Params &vp, bool from_y, int out, cudaStream_t st)
+static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st)
 {
     const uint64_t tasks = (uint64_t)vp.nitems * vp.ngroups;
     if (tasks == 0) return RR_OK;
     const int tslot = timing_begin(st);
     const unsigned blocks = blocks_for(tasks);
-    if (from_y) {
+    if (src == 1) {
         if (out == 0) k_layer_v2<PPL, true, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
         else if (out == 1) k_layer_v2<PPL, true, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
         else k_layer_v2<PPL, true, 2><<<blocks, kW2 * 32, 0, st>>>(vp);
+    } else if (src == 2) {
+        if (out == 0) k_layer_v2<PPL, false, 0, true><<<blocks, kW2 * 32, 0, st>>>(vp);
+        else k_layer_v2<PPL, false, 1, true><<<blocks, kW2 * 32, 0, st>>>(vp);
     } else {
         if (out == 0) k_layer_v2<PPL, false, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
         else k_layer_v2<PPL, false, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
     }
-    timing_end(tslot, out == 2 ? kTimeLast : (from_y ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid)), st);
+    timing_end(tslot, out == 2 ? kTimeLast : (src == 1 ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid)), st);
     RR_LAUNCHED();
     return RR_OK;
 }
@@ -94,11 +106,24 @@ uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk)
 
 // Scratch the reduced-state engine needs for one query (bytes): scalar
 // prefix, two full state buffers, one transformed buffer.
-uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk)
+// Words of each part of the engine's scratch, in layout order: scalar layer-1
+// prefix, label-space layer-2 prefix (k per state row), two per-point buffers,
+// one transformed buffer.
+static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
+                      uint64_t *pr2_w, uint64_t *full_w, uint64_t *red_w)
 {
     const uint64_t rows = g.state_list.count + 1;
-    return (g.prod_list.count + 1) * 8ull + 2ull * rows * chunk * 8ull +
-           rows * v2_reduced_stride(ppl, chunk) * 8ull + 4096;
+    *py_w = (g.prod_list.count + 1 + 31) / 32 * 32;
+    *pr2_w = (rows * k + 31) / 32 * 32;
+    *full_w = rows * chunk;
+    *red_w = rows * v2_reduced_stride(ppl, chunk);
+}
+
+uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
+{
+    uint64_t py_w, pr2_w, full_w, red_w;
+    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &full_w, &red_w);
+    return (py_w + pr2_w + 2 * full_w + red_w) * 8ull + 4096;
 }
 
 // z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades).
@@ -161,11 +186,13 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
 {
     (void)colored;
     uint64_t nk = 0;
-    const uint64_t rows = g.state_list.count + 1;
+    uint64_t py_w, pr2_w, full_w, red_w;
+    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &full_w, &red_w);
     uint64_t *py = d_scratch;
-    uint64_t *full0 = py + ((g.prod_list.count + 1 + 31) / 32 * 32);
-    uint64_t *full1 = full0 + rows * chunk;
-    uint64_t *red = full1 + rows * chunk;
+    uint64_t *pr2 = py + py_w;
+    uint64_t *full0 = pr2 + pr2_w;
+    uint64_t *full1 = full0 + full_w;
+    uint64_t *red = full1 + full_w;
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
 
     {
@@ -202,6 +229,20 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
         ++nk;
     }
     vp.py = py;
+    vp.pr2 = pr2;
+    if (k >= 5) {
+        // layer 2 in label space (independent of the point chunk)
+        RR_CUDA(cudaMemsetAsync(pr2, 0, (size_t)k * 8, st));
+        set_list(vp, g.state_list, true);
+        vp.layer = 2;
+        if (vp.nitems) {
+            const int tslot = timing_begin(st);
+            k_second_label<<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp, pr2);
+            timing_end(tslot, kTimeSecond, st);
+            RR_LAUNCHED();
+            ++nk;
+        }
+    }
 
     const uint64_t nchunks = ((1ull << k) + chunk - 1) / chunk;
     for (uint64_t c = 0; c < nchunks; ++c) {
@@ -210,21 +251,22 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
         if (k == 3) {
             set_list(vp, g.win_list, true);
             vp.layer = 2;
-            s = ppl == 4 ? launch_v2<4>(vp, true, 2, st) : launch_v2<2>(vp, true, 2, st);
+            s = ppl == 4 ? launch_v2<4>(vp, 1, 2, st) : launch_v2<2>(vp, 1, 2, st);
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;
             continue;
         }
-        // layers 2..k-2; the last of them writes the transformed state
+        // layers 2 (k = 4) or 3 (k >= 5) .. k-2; the last of them writes the
+        // transformed state
         uint64_t *bufs[2] = {full0, full1};
-        for (uint32_t l = 2; l <= k - 2; ++l) {
-            const bool from_y = l == 2;
+        for (uint32_t l = (k >= 5 ? 3u : 2u); l <= k - 2; ++l) {
+            const int src = (l == 2) ? 1 : (l == 3 ? 2 : 0);
             const int out = (l == k - 2) ? 1 : 0;
-            set_list(vp, g.state_list, from_y);
+            set_list(vp, g.state_list, src == 1);
             vp.layer = l;
             vp.st_in = bufs[(l - 1) & 1u];
             vp.st_out = out == 1 ? red : bufs[l & 1u];
-            s = ppl == 4 ? launch_v2<4>(vp, from_y, out, st) : launch_v2<2>(vp, from_y, out, st);
+            s = ppl == 4 ? launch_v2<4>(vp, src, out, st) : launch_v2<2>(vp, src, out, st);
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;
         }

@@ -23,6 +23,7 @@ struct V2Params {
     // chunk
     uint32_t chunk_base, chunk, ngroups, npoints;
     const uint64_t *py;     // scalar layer-1 prefix, indexed by producer rank
+    const uint64_t *pr2;    // layer-2 label-space prefix, k values per state row
     const uint64_t *st_in;  // full state, stride chunk
     uint64_t *st_out;       // full (stride chunk) or reduced (stride ngroups*(lg+1))
 };
@@ -108,7 +109,9 @@ __device__ __forceinline__ void first_scalar_warp(const V2Params &p, uint32_t ta
 // ---------------------------------------------------------------------------
 // COHERENT: state written earlier in the same launch is read through L2
 // (ld.global.cg) instead of the non-coherent read-only path.
-template <int PPL, bool FROM_Y, int OUT, bool COHERENT>
+// FROM_R2: window sum of layer 2 from its label-space prefix (layer 3):
+//   W^L = x_u^L x_s^L rho^L,  rho^L = sum_{j in L} (PR2[a1][j] ^ PR2[b1][j]).
+template <int PPL, bool FROM_Y, int OUT, bool COHERENT, bool FROM_R2 = false>
 __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uint32_t group)
 {
     constexpr int LOGP = PPL == 4 ? 2 : 1;
@@ -127,20 +130,38 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     for (int i = 0; i < PPL; ++i) valid[i] = gbase + (uint32_t)lane * PPL + i < p.npoints;
 
     uint64_t xs[PPL];
-    if constexpr (FROM_Y) {
+    if constexpr (FROM_Y || FROM_R2) {
         const uint64_t zs = (uint32_t)lane < k ? p.z[(size_t)source * k + lane] : 0ull;
         combine_labels<PPL>(zs, k, lane, hi_bits, xs);
     }
 
-    uint64_t acc[PPL];
+    // FROM_Y: the prefix over the head v's entries factors as
+    //   acc^L = (x_v^L x_s^L) * R^L,  R^L = sum_e (y_{e,2} Y_e) x_{u_e}^L,
+    // and R needs no per-point multiplication (label values are multiplied
+    // lane-parallel, then combined); x_v^L x_s^L is formed once per head.
+    uint64_t acc[PPL], R[PPL], xvxs[PPL];
 #pragma unroll
-    for (int i = 0; i < PPL; ++i) acc[i] = 0;
+    for (int i = 0; i < PPL; ++i) acc[i] = R[i] = xvxs[i] = 0;
     uint32_t cur = p.head[it.x];
-    uint64_t zv = (uint32_t)lane < k ? p.z[(size_t)cur * k + lane] : 0ull;
+    uint64_t zv = 0;
+    auto enter_head = [&](uint32_t v) {
+        zv = (uint32_t)lane < k ? p.z[(size_t)v * k + lane] : 0ull;
+        if constexpr (FROM_Y) {
+            uint64_t xv[PPL];
+            combine_labels<PPL>(zv, k, lane, hi_bits, xv);
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) xvxs[i] = gf64_mul(xv[i], xs[i]);
+        }
+    };
+    enter_head(cur);
     bool any = false;
 
     auto flush = [&](uint32_t v) {
         if constexpr (OUT == 2) {
+            if constexpr (FROM_Y) {
+#pragma unroll
+                for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
+            }
             uint64_t t = 0;
 #pragma unroll
             for (int i = 0; i < PPL; ++i) t ^= acc[i];
@@ -163,8 +184,8 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
             m_coef = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u));
             if constexpr (FROM_Y) {
                 m_coef = gf64_mul(m_coef, p.py[m_a] ^ p.py[m_b]);  // y_{e,2} * Y_e
-                m_src = p.src[ent];
             }
+            if constexpr (FROM_Y || FROM_R2) m_src = p.src[ent];
         }
         const uint32_t nb = min(32u, it.y - base);
         for (uint32_t t = 0; t < nb; ++t) {
@@ -172,24 +193,41 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
             if (h != cur) {
                 if (any) flush(cur);
 #pragma unroll
-                for (int i = 0; i < PPL; ++i) acc[i] = 0;
+                for (int i = 0; i < PPL; ++i) acc[i] = R[i] = 0;
                 any = false;
                 cur = h;
-                zv = (uint32_t)lane < k ? p.z[(size_t)cur * k + lane] : 0ull;
+                enter_head(cur);
             }
             const uint32_t a = __shfl_sync(0xffffffffu, m_a, (int)t);
             const uint32_t b = __shfl_sync(0xffffffffu, m_b, (int)t);
-            if (FROM_Y || a != b) {
+            if constexpr (FROM_Y) {
+                const uint64_t coef = shfl64b(m_coef, (int)t);
+                const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
+                const uint64_t zu = (uint32_t)lane < k ? p.z[(size_t)u * k + lane] : 0ull;
+                uint64_t r[PPL];
+                combine_labels<PPL>(gf64_mul(coef, zu), k, lane, hi_bits, r);
+#pragma unroll
+                for (int i = 0; i < PPL; ++i) R[i] ^= r[i];
+                if constexpr (OUT != 2) {
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
+                }
+                any = true;
+            } else if (a != b) {
                 const uint64_t coef = shfl64b(m_coef, (int)t);
                 uint64_t c[PPL], w[PPL];
                 combine_labels<PPL>(gf64_mul(coef, zv), k, lane, hi_bits, c);
-                if constexpr (FROM_Y) {
+                if constexpr (FROM_R2) {
                     const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
                     const uint64_t zu = (uint32_t)lane < k ? p.z[(size_t)u * k + lane] : 0ull;
-                    uint64_t xu[PPL];
+                    const uint64_t rj = (uint32_t)lane < k
+                                            ? (p.pr2[(size_t)a * k + lane] ^ p.pr2[(size_t)b * k + lane])
+                                            : 0ull;
+                    uint64_t xu[PPL], rho[PPL];
                     combine_labels<PPL>(zu, k, lane, hi_bits, xu);
+                    combine_labels<PPL>(rj, k, lane, hi_bits, rho);
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) w[i] = gf64_mul(xs[i], xu[i]);
+                    for (int i = 0; i < PPL; ++i) w[i] = gf64_mul(gf64_mul(xs[i], xu[i]), rho[i]);
                 } else {
                     const uint64_t *pa = p.st_in + (size_t)a * p.chunk + col;
                     const uint64_t *pb = p.st_in + (size_t)b * p.chunk + col;
@@ -259,6 +297,47 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         }
     }
     if (any) flush(cur);
+}
+
+// ---------------------------------------------------------------------------
+// Layer 2 in label space (k >= 5): for every state row f of head v,
+//   PR2[f][j] = XOR over v's state rows f' <= f of (y_{f',2} Y_{f'}) z_{u_{f'},j}
+// so that P_2^L[f'] = x_v^L x_s^L sum_{j in L} (y Y)_{f'} z_{u_{f'},j}. Independent of
+// the point chunk; lane j owns label j (one multiplication per lane and row).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t item,
+                                                  uint64_t *__restrict__ pr2)
+{
+    const int lane = threadIdx.x & 31;
+    const uint2 it = p.items[item];
+    const uint32_t k = p.k;
+    const uint64_t key_y = p.qd->key_y;
+    uint32_t cur = p.head[it.x];
+    uint64_t acc = 0;
+    for (uint32_t base = it.x; base < it.y; base += 32) {
+        const uint32_t ent = base + lane;
+        const bool has = ent < it.y;
+        const uint32_t m_head = has ? p.head[ent] : 0u;
+        const uint32_t m_src = has ? p.src[ent] : 0u;
+        uint64_t m_coef = 0;
+        if (has)
+            m_coef = gf64_mul(sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + 1u),  // y_{e,2}
+                              p.py[p.ia[ent]] ^ p.py[p.ib[ent]]);               // Y_e
+        const uint32_t nb = min(32u, it.y - base);
+        for (uint32_t t = 0; t < nb; ++t) {
+            const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
+            if (h != cur) {
+                acc = 0;
+                cur = h;
+            }
+            const uint64_t coef = shfl64b(m_coef, (int)t);
+            const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
+            if ((uint32_t)lane < k) {
+                acc ^= gf64_mul(coef, p.z[(size_t)u * k + lane]);
+                pr2[((size_t)base + t + 1) * k + lane] = acc;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -293,3 +293,19 @@ def test_graph_replay_and_direct_launch_agree():
         _, w_graph2 = G.reach(4, 7, 5)  # replay of the cached graph
         assert np.array_equal(w_direct, ref)
         assert np.array_equal(w_graph, ref) and np.array_equal(w_graph2, ref)
+
+
+def test_point_shards_xor_to_the_full_witness():
+    # the multi-GPU design splits the points into ranges; on one GPU the XOR of
+    # the ranges' point sums must equal the full query's witness
+    from paper_2010_08423_gb300 import shard
+    g = _dense_uniform(1000, 12_000, 20, 5, 91)
+    with _graph(g) as G:
+        _, full = G.reach(2, 7, 8)
+        parts = []
+        for r in range(3):
+            f, c = shard.point_range(7, r, 3, align=16)
+            pm = G.point_sums(2, 7, 8, list(range(f, f + c)))
+            parts.append(shard.xor_combine(pm))
+        assert np.count_nonzero(full) > 0
+        assert np.array_equal(shard.xor_combine(parts), full)
