@@ -143,8 +143,8 @@ def batched_metrics(capi, torch, gc, nq=256, seed=GRAPH_SEED):
         d_b = torch.zeros((nq, n), dtype=torch.int64, device="cuda")
         d_s = torch.zeros((nq, n), dtype=torch.int64, device="cuda")
         d_st = torch.zeros(nq, dtype=torch.int32, device="cuda")
-        # warm-up (captures graphs / grows buffers)
-        capi.rr_reach_batch_device(G.handle, qs[:8], d_b, None, d_st, stream.cuda_stream)
+        # warm-up with the whole batch (captures graphs, grows the batch buffers)
+        capi.rr_reach_batch_device(G.handle, qs, d_b, None, d_st, stream.cuda_stream)
         for q in qs[:8]:
             capi.rr_reach_device(G.handle, q["source"], q["k"], q["seed"], d_s[0], None,
                                  stream.cuda_stream, motif=q["motif"])
@@ -370,16 +370,17 @@ def main():
     # roofline: algorithmic bytes per launch of each kernel kind of the
     # reduced-state engine, over its measured average launch duration
     peaks, peak_kind = measured_peaks()
-    srows = info["producer_window_rows"]      # state rows
-    crows = info["state_compute_rows"]        # state rows that multiply at layers >= 3
-    trows = info["tail_rows"]                 # last-layer rows
+    srows = info["producer_window_rows"]      # state rows (layer 2, label space)
+    drows = info["state_compute_rows"]        # deep rows: per-point state of layers >= 3
+    dc = info["deep_compute_rows"]            # deep rows that multiply at layers >= 4
+    t3 = info["deep_tail_rows"]               # last-layer rows
     lg = 7 if ppl == 4 else 6
     rstride = chunk // (32 * ppl) * (lg + 1)
     alg = {
         "second_layer": srows * K * 8 + srows * 20 + 2 * srows * 8 + srows * K * 8,
-        "mid_layer": srows * chunk * 8 + 2 * crows * chunk * 8 + srows * 16,
-        "tail_layer": srows * rstride * 8 + 2 * crows * chunk * 8 + srows * 16,
-        "last_layer": 2 * trows * rstride * 8 + trows * 16 + n * 8,
+        "mid_layer": drows * chunk * 8 + 2 * dc * chunk * 8 + drows * 20,
+        "tail_layer": drows * rstride * 8 + 2 * dc * chunk * 8 + drows * 20,
+        "last_layer": 2 * t3 * rstride * 8 + t3 * 16 + n * 8,
         "first_layer": info["state_rows"] * 8 * 2,
         "ztable": n * K * 8,
     }
@@ -411,7 +412,8 @@ def main():
             "config": {"workload": WORKLOAD, "graph_seed": GRAPH_SEED, "l2": "flushed between steps",
                        "state_layout": "dense" if args.dense else "compact",
                        "points_per_lane": ppl, "points_per_chunk": chunk,
-                       "state_rows": srows + 1, "state_compute_rows": crows, "tail_rows": trows,
+                       "state_rows": srows + 1, "deep_rows": drows, "deep_compute_rows": dc,
+                       "last_layer_rows": t3,
                        "producer_rows": info["state_rows"] - 1, "window_rows": info["window_rows"],
                        "graph_load_s": round(load_s, 3)},
             "roofline": roofline,

@@ -86,8 +86,10 @@ typedef struct {
     int has_colors;
     int compact;             /* 1: state stores only rows inside some window */
     uint64_t producer_window_rows; /* rows inside some window whose own window is non-empty */
-    uint64_t state_compute_rows;   /* of those, rows whose window holds another such row */
+    uint64_t state_compute_rows;   /* of those, rows whose window holds another such row ("deep") */
     uint64_t tail_rows;            /* rows whose window holds a producer row with a window */
+    uint64_t deep_compute_rows;    /* deep rows whose window holds a deep row */
+    uint64_t deep_tail_rows;       /* rows whose window holds a deep row */
 } rr_graph_info;
 
 /* ---- graph ----------------------------------------------------------------

@@ -38,7 +38,8 @@ class rr_graph_info(ctypes.Structure):
                 ("max_in_degree", ctypes.c_uint32), ("num_items", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("has_colors", ctypes.c_int),
                 ("compact", ctypes.c_int), ("producer_window_rows", ctypes.c_uint64),
-                ("state_compute_rows", ctypes.c_uint64), ("tail_rows", ctypes.c_uint64)]
+                ("state_compute_rows", ctypes.c_uint64), ("tail_rows", ctypes.c_uint64),
+                ("deep_compute_rows", ctypes.c_uint64), ("deep_tail_rows", ctypes.c_uint64)]
 
 
 class rr_kernel_times(ctypes.Structure):

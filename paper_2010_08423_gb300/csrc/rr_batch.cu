@@ -33,7 +33,8 @@ enum BatchKind : uint32_t {
     kMidTail = 4,      // layer k-2 (k >= 6), transformed state out
     kLast = 5,         // layer k-1 from the transformed state
     kThirdFull = 6,    // layer 3 (k >= 6) from the label-space layer-2 prefix
-    kThirdTail = 7     // layer 3 when k = 5, transformed state out
+    kThirdTail = 7,    // layer 3 when k = 5, transformed state out
+    kLastDeep = 8      // layer k-1 (k >= 5) from the transformed deep-row state
 };
 
 struct BatchUnit {
@@ -48,13 +49,13 @@ struct BatchSeg {
 };
 
 struct ListPtrs {
-    const uint32_t *head, *eid, *src, *a0, *b0, *a1, *b1;
+    const uint32_t *head, *eid, *src, *a0, *b0, *a1, *b1, *a3, *b3;
     const uint2 *items;
     uint32_t nitems;
 };
 
 struct BatchArgs {
-    ListPtrs prod, state, win, tail;
+    ListPtrs prod, state, win, tail, deep, tail3;
     uint32_t n;
     const BatchUnit *units;
     const BatchSeg *segs;
@@ -106,13 +107,13 @@ __device__ bool wait_for(const BatchArgs &a, const uint32_t *ctr, uint32_t want)
     return false;
 }
 
-__device__ __forceinline__ void set_list(V2Params &vp, const ListPtrs &L, bool first_window)
+__device__ __forceinline__ void set_list(V2Params &vp, const ListPtrs &L, int win)
 {
     vp.head = L.head;
     vp.eid = L.eid;
     vp.src = L.src;
-    vp.ia = first_window ? L.a0 : L.a1;
-    vp.ib = first_window ? L.b0 : L.b1;
+    vp.ia = win == 0 ? L.a0 : (win == 1 ? L.a1 : L.a3);
+    vp.ib = win == 0 ? L.b0 : (win == 1 ? L.b1 : L.b3);
     vp.items = L.items;
     vp.nitems = L.nitems;
 }
@@ -123,7 +124,7 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
 {
     V2Params vp{};
     vp.qd = a.descs + u.q;
-    vp.z = a.z_all + a.z_off[u.q];
+    vp.z = a.descs[u.q].colored ? a.z_all + a.z_off[u.q] : nullptr;
     vp.py = a.py_all + a.py_off[u.q];
     vp.pr2 = a.pr2_all + a.pr2_off[u.q];
     vp.n = a.n;
@@ -138,47 +139,53 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
     uint64_t *red = full1 + a.full_words;
     uint64_t *bufs[2] = {full0, full1};
     const uint32_t l = sg.layer;
-    const uint32_t item = sg.kind == kLast ? local : local / sg.ngroups;
-    const uint32_t group = sg.kind == kLast ? 0u : local - item * sg.ngroups;
+    const bool last = sg.kind == kLast || sg.kind == kLastDeep;
+    const uint32_t item = last ? local : local / sg.ngroups;
+    const uint32_t group = last ? 0u : local - item * sg.ngroups;
     switch (sg.kind) {
     case kSecondFull:
-        set_list(vp, a.state, true);
+        set_list(vp, a.state, 0);
         vp.st_out = bufs[l & 1u];
         layer_warp<PPL, true, 0, true>(vp, item, group);
         break;
     case kSecondTail:
-        set_list(vp, a.state, true);
+        set_list(vp, a.state, 0);
         vp.st_out = red;
         layer_warp<PPL, true, 1, true>(vp, item, group);
         break;
     case kSecondFinal:
-        set_list(vp, a.win, true);
+        set_list(vp, a.win, 0);
         layer_warp<PPL, true, 2, true>(vp, item, group);
         break;
     case kThirdFull:
-        set_list(vp, a.state, false);
+        set_list(vp, a.deep, 1);
         vp.st_out = bufs[l & 1u];
         layer_warp<PPL, false, 0, true, true>(vp, item, group);
         break;
     case kThirdTail:
-        set_list(vp, a.state, false);
+        set_list(vp, a.deep, 1);
         vp.st_out = red;
         layer_warp<PPL, false, 1, true, true>(vp, item, group);
         break;
     case kMidFull:
-        set_list(vp, a.state, false);
+        set_list(vp, a.deep, 3);
         vp.st_in = bufs[(l - 1) & 1u];
         vp.st_out = bufs[l & 1u];
         layer_warp<PPL, false, 0, true>(vp, item, group);
         break;
     case kMidTail:
-        set_list(vp, a.state, false);
+        set_list(vp, a.deep, 3);
         vp.st_in = bufs[(l - 1) & 1u];
         vp.st_out = red;
         layer_warp<PPL, false, 1, true>(vp, item, group);
         break;
+    case kLastDeep:
+        set_list(vp, a.tail3, 3);
+        vp.st_in = red;
+        last_warp<PPL == 4 ? 7 : 6, true>(vp, item);
+        break;
     default:
-        set_list(vp, a.tail, false);
+        set_list(vp, a.tail, 1);
         vp.st_in = red;
         last_warp<PPL == 4 ? 7 : 6, true>(vp, item);
         break;
@@ -223,9 +230,10 @@ __global__ void k_batch_ztable(uint32_t n, const QueryDesc *__restrict__ descs,
 {
     const QueryDesc *qd = descs + blockIdx.y;
     const uint32_t k = qd->k;
+    const bool colored = qd->colored != 0;
+    if (!colored) return;  // plain queries draw z on the fly
     uint64_t *z = z_all + z_off[blockIdx.y];
     const uint64_t total = (uint64_t)n * k;
-    const bool colored = qd->colored != 0;
     for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t u = idx / k;
@@ -277,7 +285,7 @@ k_batch_second(ListPtrs state, const QueryDesc *__restrict__ descs, const uint64
     if (task >= state.nitems) return;
     V2Params vp{};
     vp.qd = qd;
-    vp.z = z_all + z_off[blockIdx.y];
+    vp.z = qd->colored ? z_all + z_off[blockIdx.y] : nullptr;
     vp.py = py_all + py_off[blockIdx.y];
     vp.n = n;
     vp.k = k;
@@ -328,7 +336,7 @@ ListPtrs list_ptrs(const RowList &L, bool coarse)
 {
     return ListPtrs{L.head.as<uint32_t>(), L.eid.as<uint32_t>(), L.src.as<uint32_t>(),
                     L.a0.as<uint32_t>(),   L.b0.as<uint32_t>(),  L.a1.as<uint32_t>(),
-                    L.b1.as<uint32_t>(),
+                    L.b1.as<uint32_t>(),   L.a3.as<uint32_t>(),  L.b3.as<uint32_t>(),
                     coarse ? L.items_coarse.as<uint2>() : L.items.as<uint2>(),
                     coarse ? L.nitems_coarse : L.nitems};
 }
@@ -341,18 +349,16 @@ uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, u
         return g.win_list.nitems_coarse * ngroups;
     }
     if (l == k - 1) {
-        *kind = kLast;
-        return g.tail_list.nitems_coarse;
+        *kind = k == 4 ? kLast : kLastDeep;
+        return k == 4 ? g.tail_list.nitems_coarse : g.tail3_list.nitems_coarse;
     }
     if (l == 2) {
         if (k >= 5) return 0;  // label-space layer 2 runs in the prologue
         *kind = kSecondTail;   // k = 4
-    } else if (l == 3) {
-        *kind = (k == 5) ? kThirdTail : kThirdFull;
-    } else {
-        *kind = (l == k - 2) ? kMidTail : kMidFull;
+        return g.state_list.nitems_coarse * ngroups;
     }
-    return g.state_list.nitems_coarse * ngroups;
+    *kind = l == 3 ? ((k == 5) ? kThirdTail : kThirdFull) : ((l == k - 2) ? kMidTail : kMidFull);
+    return g.deep_list.nitems_coarse * ngroups;
 }
 
 }  // namespace
@@ -360,8 +366,8 @@ uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, u
 // Bytes of device memory one batch slot holds for max chunk `chunk`.
 static uint64_t slot_words_for(const Graph &g, uint32_t chunk)
 {
-    const uint64_t rows = g.state_list.count + 1;
-    return rows * chunk * 2 + rows * 32;
+    const uint64_t srows = g.state_list.count + 1, drows = g.deep_list.count + 1;
+    return drows * chunk * 2 + std::max(srows, drows) * 32;
 }
 
 rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
@@ -395,8 +401,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         std::vector<uint32_t> grp;
         uint64_t qbytes = 0;
         while (gi < bq.size()) {
-            const uint64_t need = ((uint64_t)g.n * qs[bq[gi]].k + 64 + py_words +
-                                   rows * qs[bq[gi]].k) * 8;
+            const uint64_t need = ((qs[bq[gi]].motif ? (uint64_t)g.n * qs[bq[gi]].k : 0ull) + 64 +
+                                   py_words + rows * qs[bq[gi]].k) * 8;
             if (!grp.empty() && qbytes + need > budget / 2) break;
             qbytes += need;
             grp.push_back(bq[gi++]);
@@ -434,7 +440,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                 std::memcpy(hd.shades + 256, sh.mu, sizeof sh.mu);
             }
             z_off[j] = zw;
-            zw += ((uint64_t)g.n * q.k + 31) / 32 * 32;
+            if (q.motif) zw += ((uint64_t)g.n * q.k + 31) / 32 * 32;
             py_off[j] = j * py_words;
             pr2_off[j] = pr2w;
             if (q.k >= 5) pr2w += (rows * q.k + 31) / 32 * 32;
@@ -448,8 +454,10 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                                           grp[j]});
         }
         const uint64_t slot_bytes = slot_words_for(g, max_chunk) * 8;
+        // as many slots as memory allows (up to every unit at once): units in
+        // flight together hide each other's layer-to-layer dependencies
         uint32_t nslots = (uint32_t)std::min<uint64_t>(
-            {(uint64_t)units.size(), 64ull, (budget - qbytes) / slot_bytes});
+            {(uint64_t)units.size(), 4096ull, (budget - qbytes) / slot_bytes});
         nslots = std::max<uint32_t>(1, nslots);
         for (size_t i = 0; i < units.size(); ++i) units[i].slot = (uint32_t)(i % nslots);
 
@@ -518,7 +526,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         RR_CUDA(B.descs.reserve(descs.size() * sizeof(QueryDesc)));
         RR_CUDA(B.zoff.reserve(grp.size() * 8));
         RR_CUDA(B.pyoff.reserve(grp.size() * 8));
-        RR_CUDA(B.z.reserve(zw * 8));
+        RR_CUDA(B.z.reserve(std::max<uint64_t>(1, zw) * 8));
         RR_CUDA(B.py.reserve(grp.size() * py_words * 8));
         RR_CUDA(B.pr2.reserve(std::max<uint64_t>(1, pr2w) * 8));
         RR_CUDA(B.pr2off.reserve(grp.size() * 8));
@@ -551,24 +559,31 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         for (uint32_t j : grp) RR_CUDA(cudaMemsetAsync(d_witness + (size_t)j * g.n, 0, (size_t)g.n * 8, st));
 
         const unsigned gz = (unsigned)std::min<uint64_t>(1024, ((uint64_t)g.n * 20 + 255) / 256);
+        int tslot = timing_begin(st);
         k_batch_ztable<<<dim3(gz, (unsigned)grp.size()), 256, 0, st>>>(
             g.n, d_descs.as<QueryDesc>(), g.color.as<uint8_t>(), d_z.as<uint64_t>(),
             d_zoff.as<uint64_t>());
+        timing_end(tslot, kTimeZ, st);
         RR_LAUNCHED();
         const ListPtrs prod = list_ptrs(g.prod_list, false);
+        tslot = timing_begin(st);
         k_batch_first<<<dim3(std::max<uint32_t>(1, (prod.nitems + kW2 - 1) / kW2), (unsigned)grp.size()),
                         kW2 * 32, 0, st>>>(prod, d_descs.as<QueryDesc>(), d_py.as<uint64_t>(),
                                            d_pyoff.as<uint64_t>());
+        timing_end(tslot, kTimeFirst, st);
         RR_LAUNCHED();
+        tslot = timing_begin(st);
         k_batch_second<<<dim3(std::max<uint32_t>(1, (g.state_list.nitems + kW2 - 1) / kW2),
                               (unsigned)grp.size()),
                          kW2 * 32, 0, st>>>(list_ptrs(g.state_list, false), d_descs.as<QueryDesc>(),
                                             d_z.as<uint64_t>(), d_zoff.as<uint64_t>(),
                                             d_py.as<uint64_t>(), d_pyoff.as<uint64_t>(),
                                             B.pr2.as<uint64_t>(), B.pr2off.as<uint64_t>(), g.n);
+        timing_end(tslot, kTimeSecond, st);
         RR_LAUNCHED();
         k_batch_zero_rows<<<nslots, 256, 0, st>>>(d_slots.as<uint64_t>(), slot_bytes / 8,
-                                                  rows * max_chunk, nslots, max_chunk);
+                                                  (g.deep_list.count + 1) * max_chunk, nslots,
+                                                  max_chunk);
         RR_LAUNCHED();
 
         BatchArgs a{};
@@ -576,6 +591,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         a.state = list_ptrs(g.state_list, true);
         a.win = list_ptrs(g.win_list, true);
         a.tail = list_ptrs(g.tail_list, true);
+        a.deep = list_ptrs(g.deep_list, true);
+        a.tail3 = list_ptrs(g.tail3_list, true);
         a.n = g.n;
         a.units = d_units.as<BatchUnit>();
         a.segs = d_segs.as<BatchSeg>();
@@ -592,7 +609,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         a.slot_base = d_slots.as<uint64_t>();
         a.slot_words = slot_bytes / 8;
         a.rows = rows;
-        a.full_words = rows * max_chunk;
+        a.full_words = (g.deep_list.count + 1) * max_chunk;
         a.done = d_done.as<uint32_t>();
         a.ctl = d_ctl.as<uint32_t>();
         a.status = status;
@@ -603,9 +620,9 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             RR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kW2 * 32, 0));
             const unsigned blocks = (unsigned)std::max(1, sms * std::max(1, per_sm));
-            const int tslot = timing_begin(st);
+            const int bslot = timing_begin(st);
             k_batch<<<blocks, kW2 * 32, 0, st>>>(a);
-            timing_end(tslot, kTimeBatch, st);
+            timing_end(bslot, kTimeBatch, st);
             RR_LAUNCHED();
         }
         if (d_bitmaps) {

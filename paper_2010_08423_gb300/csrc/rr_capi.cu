@@ -136,6 +136,8 @@ rr_status rr_graph_get_info(const rr_graph *g, rr_graph_info *out)
     out->producer_window_rows = g->state_list.count;
     out->state_compute_rows = g->state_compute_rows;
     out->tail_rows = g->tail_list.count;
+    out->deep_compute_rows = g->deep_compute_rows;
+    out->deep_tail_rows = g->tail3_list.count;
     return RR_OK;
 }
 

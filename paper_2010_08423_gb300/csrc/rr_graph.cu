@@ -192,8 +192,60 @@ __global__ void k_v2_index(const uint32_t *__restrict__ lo_in, const uint32_t *_
 }
 
 struct ListOut {
-    uint32_t *head, *eid, *src, *a0, *b0, *a1, *b1;
+    uint32_t *head, *eid, *src, *a0, *b0, *a1, *b1, *a3, *b3;
 };
+
+// deep rows: state rows (c1) whose window holds a state row (a1 != b1)
+__global__ void k_v2_deep(const uint32_t *__restrict__ c1, const uint32_t *__restrict__ a1,
+                          const uint32_t *__restrict__ b1, uint64_t m, uint32_t *__restrict__ d)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m;
+         r += (uint64_t)gridDim.x * blockDim.x)
+        d[r] = (c1[r] && a1[r] != b1[r]) ? 1u : 0u;
+}
+
+// window of every row in deep-row indices, and the flag "window holds a deep row"
+__global__ void k_v2_index3(const uint32_t *__restrict__ lo_in, const uint32_t *__restrict__ hi_in,
+                            const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ off,
+                            const uint32_t *__restrict__ rank_d, uint64_t m,
+                            uint32_t *__restrict__ a3, uint32_t *__restrict__ b3,
+                            uint32_t *__restrict__ c4)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t lo = lo_in[r], hi = hi_in[r];
+        if (hi > lo) {
+            const uint32_t s0 = off[row_src[r]];
+            a3[r] = rank_in_segment(rank_d, (int64_t)hi - 1, s0);
+            b3[r] = rank_in_segment(rank_d, (int64_t)lo - 1, s0);
+        } else {
+            a3[r] = b3[r] = 0u;
+        }
+        c4[r] = a3[r] != b3[r] ? 1u : 0u;
+    }
+}
+
+// entries of the deep list and of the k >= 5 last-layer list
+__global__ void k_v2_scatter3(const uint32_t *__restrict__ row_dst, const uint32_t *__restrict__ row_eid,
+                              const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ a1,
+                              const uint32_t *__restrict__ b1, const uint32_t *__restrict__ a3,
+                              const uint32_t *__restrict__ b3, const uint32_t *__restrict__ d,
+                              const uint32_t *__restrict__ rank_d, const uint32_t *__restrict__ c4,
+                              const uint32_t *__restrict__ rank4, uint64_t m, ListOut D, ListOut T)
+{
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        if (d[r]) {
+            const uint32_t i = rank_d[r] - 1;
+            D.head[i] = row_dst[r]; D.eid[i] = row_eid[r]; D.src[i] = row_src[r];
+            D.a1[i] = a1[r]; D.b1[i] = b1[r]; D.a3[i] = a3[r]; D.b3[i] = b3[r];
+        }
+        if (c4[r]) {
+            const uint32_t i = rank4[r] - 1;
+            T.head[i] = row_dst[r]; T.eid[i] = row_eid[r]; T.a3[i] = a3[r]; T.b3[i] = b3[r];
+        }
+    }
+}
 
 __global__ void k_v2_scatter(const uint32_t *__restrict__ row_dst, const uint32_t *__restrict__ row_eid,
                              const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ a0,
@@ -357,7 +409,7 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         }
         out[i] = ListOut{R.head.as<uint32_t>(), R.eid.as<uint32_t>(), R.src.as<uint32_t>(),
                          R.a0.as<uint32_t>(), R.b0.as<uint32_t>(), R.a1.as<uint32_t>(),
-                         R.b1.as<uint32_t>()};
+                         R.b1.as<uint32_t>(), nullptr, nullptr};
     }
     k_v2_scatter<<<grid_for(m, 256), 256, 0, st>>>(
         row_dst, g.row_eid.as<uint32_t>(), g.row_src.as<uint32_t>(), a0.as<uint32_t>(),
@@ -365,21 +417,60 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         c1.as<uint32_t>(), rank1.as<uint32_t>(), c0.as<uint32_t>(), rank0.as<uint32_t>(),
         c2.as<uint32_t>(), rank2.as<uint32_t>(), m, out[0], out[1], out[2], out[3]);
     RR_LAUNCHED();
+
+    // deep rows (layers >= 3) and the last-layer rows that read them
     {
-        // state rows whose window holds another state row (they multiply at layers >= 3)
-        std::vector<uint32_t> ha(g.state_list.count), hb(g.state_list.count);
-        if (g.state_list.count) {
-            RR_CUDA(cudaMemcpyAsync(ha.data(), g.state_list.a1.p, ha.size() * 4, cudaMemcpyDeviceToHost, st));
-            RR_CUDA(cudaMemcpyAsync(hb.data(), g.state_list.b1.p, hb.size() * 4, cudaMemcpyDeviceToHost, st));
+        DevBuf d, rank_d, a3, b3, c4, rank4;
+        for (DevBuf *b : {&d, &rank_d, &a3, &b3, &c4, &rank4}) RR_CUDA(b->reserve(m * 4));
+        k_v2_deep<<<grid_for(m, 256), 256, 0, st>>>(c1.as<uint32_t>(), a1.as<uint32_t>(),
+                                                    b1.as<uint32_t>(), m, d.as<uint32_t>());
+        RR_LAUNCHED();
+        if ((s = scan_u32(d.as<uint32_t>(), rank_d.as<uint32_t>(), m, tmp, st)) != RR_OK) return s;
+        k_v2_index3<<<grid_for(m, 256), 256, 0, st>>>(
+            g.row_lo.as<uint32_t>(), g.row_hi.as<uint32_t>(), g.row_src.as<uint32_t>(),
+            g.off.as<uint32_t>(), rank_d.as<uint32_t>(), m, a3.as<uint32_t>(), b3.as<uint32_t>(),
+            c4.as<uint32_t>());
+        RR_LAUNCHED();
+        if ((s = scan_u32(c4.as<uint32_t>(), rank4.as<uint32_t>(), m, tmp, st)) != RR_OK) return s;
+        uint32_t c3[2] = {0, 0};
+        RR_CUDA(cudaMemcpyAsync(&c3[0], rank_d.as<uint32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, st));
+        RR_CUDA(cudaMemcpyAsync(&c3[1], rank4.as<uint32_t>() + m - 1, 4, cudaMemcpyDeviceToHost, st));
+        RR_CUDA(cudaStreamSynchronize(st));
+        RowList &D = g.deep_list, &T = g.tail3_list;
+        D.count = c3[0];
+        T.count = c3[1];
+        const size_t db = (size_t)std::max<uint32_t>(1, c3[0]) * 4;
+        const size_t tb = (size_t)std::max<uint32_t>(1, c3[1]) * 4;
+        for (DevBuf *b : {&D.head, &D.eid, &D.src, &D.a1, &D.b1, &D.a3, &D.b3}) RR_CUDA(b->reserve(db));
+        for (DevBuf *b : {&T.head, &T.eid, &T.a3, &T.b3}) RR_CUDA(b->reserve(tb));
+        ListOut od{D.head.as<uint32_t>(), D.eid.as<uint32_t>(), D.src.as<uint32_t>(), nullptr, nullptr,
+                   D.a1.as<uint32_t>(), D.b1.as<uint32_t>(), D.a3.as<uint32_t>(), D.b3.as<uint32_t>()};
+        ListOut ot{T.head.as<uint32_t>(), T.eid.as<uint32_t>(), nullptr, nullptr, nullptr, nullptr,
+                   nullptr, T.a3.as<uint32_t>(), T.b3.as<uint32_t>()};
+        k_v2_scatter3<<<grid_for(m, 256), 256, 0, st>>>(
+            row_dst, g.row_eid.as<uint32_t>(), g.row_src.as<uint32_t>(), a1.as<uint32_t>(),
+            b1.as<uint32_t>(), a3.as<uint32_t>(), b3.as<uint32_t>(), d.as<uint32_t>(),
+            rank_d.as<uint32_t>(), c4.as<uint32_t>(), rank4.as<uint32_t>(), m, od, ot);
+        RR_LAUNCHED();
+        RR_CUDA(cudaStreamSynchronize(st));
+    }
+    g.state_compute_rows = g.deep_list.count;
+    {
+        std::vector<uint32_t> ha(g.deep_list.count), hb(g.deep_list.count);
+        if (g.deep_list.count) {
+            RR_CUDA(cudaMemcpyAsync(ha.data(), g.deep_list.a3.p, ha.size() * 4, cudaMemcpyDeviceToHost, st));
+            RR_CUDA(cudaMemcpyAsync(hb.data(), g.deep_list.b3.p, hb.size() * 4, cudaMemcpyDeviceToHost, st));
         }
         RR_CUDA(cudaStreamSynchronize(st));
         uint64_t cnt = 0;
         for (size_t i = 0; i < ha.size(); ++i) cnt += ha[i] != hb[i];
-        g.state_compute_rows = cnt;
+        g.deep_compute_rows = cnt;
     }
-    // scheduling ranges: about 32 warps per SM over the list, 8..128 entries each
-    for (int i = 0; i < 4; ++i) {
-        RowList &R = *L[i];
+    // scheduling ranges of every list
+    RowList *LL[6] = {&g.prod_list, &g.state_list, &g.win_list, &g.tail_list, &g.deep_list,
+                      &g.tail3_list};
+    for (int i = 0; i < 6; ++i) {
+        RowList &R = *LL[i];
         std::vector<uint32_t> heads(R.count);
         if (R.count)
             RR_CUDA(cudaMemcpyAsync(heads.data(), R.head.p, R.count * 4, cudaMemcpyDeviceToHost, st));
@@ -391,7 +482,7 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
             (uint32_t)std::min<uint64_t>(128, std::max<uint64_t>(1, R.count / (152 * 64)));
         std::vector<uint2> items, coarse;
         build_entry_items(heads, target, items);
-        build_entry_items(heads, 128, coarse);
+        build_entry_items(heads, 32, coarse);
         R.nitems = (uint32_t)items.size();
         R.nitems_coarse = (uint32_t)coarse.size();
         RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));

@@ -131,14 +131,16 @@ struct RowList {
     DevBuf head, eid, src;  // uint32 per entry
     DevBuf a0, b0;          // window in producer-prefix indices (scalar first-layer prefix)
     DevBuf a1, b1;          // window in state-row indices (state rows = producers with a window)
+    DevBuf a3, b3;          // window in deep-row indices (deep rows = state rows whose window
+                            // holds a state row: the only rows non-zero at layers >= 3)
     DevBuf items;           // uint2 ranges, largest first (fine: one-query kernels)
     uint32_t nitems = 0;
-    DevBuf items_coarse;    // uint2 ranges of about 128 entries (persistent batch)
+    DevBuf items_coarse;    // uint2 ranges of about 32 entries (persistent batch)
     uint32_t nitems_coarse = 0;
     size_t bytes() const
     {
         return head.bytes + eid.bytes + src.bytes + a0.bytes + b0.bytes + a1.bytes + b1.bytes +
-               items.bytes + items_coarse.bytes;
+               a3.bytes + b3.bytes + items.bytes + items_coarse.bytes;
     }
 };
 
@@ -166,6 +168,7 @@ struct Graph {
     uint64_t window_rows = 0;  // rows with a non-empty window
     uint64_t producer_window_rows = 0;  // producer rows with a non-empty window
     uint64_t state_compute_rows = 0;    // state rows whose window holds a state row
+    uint64_t deep_compute_rows = 0;     // deep rows whose window holds a deep row
     uint32_t max_in_degree = 0;
 
     DevBuf off;      // n+1 uint32
@@ -185,8 +188,10 @@ struct Graph {
     //   prod_list  rows inside some window (first-layer scalar prefix)
     //   state_list producers whose own window is non-empty (state rows)
     //   win_list   rows with a non-empty window (k = 3 last layer)
-    //   tail_list  rows whose window holds at least one state row (last layer)
-    RowList prod_list, state_list, win_list, tail_list;
+    //   tail_list  rows whose window holds at least one state row (last layer, k = 4)
+    //   deep_list  state rows whose window holds a state row (layers >= 3)
+    //   tail3_list rows whose window holds a deep row (last layer, k >= 5)
+    RowList prod_list, state_list, win_list, tail_list, deep_list, tail3_list;
 
     // per-graph scratch for rr_reach_device / rr_reach_sync (serialised by mu)
     mutable std::mutex mu;
@@ -203,7 +208,8 @@ struct Graph {
     {
         return off.bytes + row_a.bytes + row_b.bytes + row_s.bytes + row_eid.bytes +
                row_src.bytes + row_lo.bytes + row_hi.bytes + color.bytes + items.bytes +
-               prod_list.bytes() + state_list.bytes() + win_list.bytes() + tail_list.bytes();
+               prod_list.bytes() + state_list.bytes() + win_list.bytes() + tail_list.bytes() +
+               deep_list.bytes() + tail3_list.bytes();
     }
 };
 

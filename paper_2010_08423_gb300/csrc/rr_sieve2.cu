@@ -18,6 +18,7 @@
 //    instead of one per sieve point.
 // Only the sieve points' order of summation changes; every result is
 // bit-identical to the per-point engine and the oracle.
+#include <algorithm>
 #include <cstring>
 
 #include "rr_v2_device.cuh"
@@ -60,14 +61,15 @@ static unsigned blocks_for(uint64_t tasks)
     return (unsigned)((tasks + kW2 - 1) / kW2);
 }
 
-// Fills the list fields of V2Params.
-static void set_list(V2Params &vp, const RowList &L, bool first_window)
+// Fills the list fields of V2Params; `win` selects the window indices:
+// 0 = producer prefix (a0, b0), 1 = state rows (a1, b1), 3 = deep rows (a3, b3).
+static void set_list(V2Params &vp, const RowList &L, int win)
 {
     vp.head = L.head.as<uint32_t>();
     vp.eid = L.eid.as<uint32_t>();
     vp.src = L.src.as<uint32_t>();
-    vp.ia = first_window ? L.a0.as<uint32_t>() : L.a1.as<uint32_t>();
-    vp.ib = first_window ? L.b0.as<uint32_t>() : L.b1.as<uint32_t>();
+    vp.ia = win == 0 ? L.a0.as<uint32_t>() : (win == 1 ? L.a1.as<uint32_t>() : L.a3.as<uint32_t>());
+    vp.ib = win == 0 ? L.b0.as<uint32_t>() : (win == 1 ? L.b1.as<uint32_t>() : L.b3.as<uint32_t>());
     vp.items = L.items.as<uint2>();
     vp.nitems = L.nitems;
 }
@@ -112,11 +114,12 @@ uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk)
 static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
                       uint64_t *pr2_w, uint64_t *full_w, uint64_t *red_w)
 {
-    const uint64_t rows = g.state_list.count + 1;
+    const uint64_t srows = g.state_list.count + 1;  // layer 2 (label space; k = 4 transformed)
+    const uint64_t drows = g.deep_list.count + 1;   // layers >= 3
     *py_w = (g.prod_list.count + 1 + 31) / 32 * 32;
-    *pr2_w = (rows * k + 31) / 32 * 32;
-    *full_w = rows * chunk;
-    *red_w = rows * v2_reduced_stride(ppl, chunk);
+    *pr2_w = (srows * k + 31) / 32 * 32;
+    *full_w = drows * chunk;
+    *red_w = std::max(srows, drows) * v2_reduced_stride(ppl, chunk);
 }
 
 uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
@@ -184,7 +187,6 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels)
 {
-    (void)colored;
     uint64_t nk = 0;
     uint64_t py_w, pr2_w, full_w, red_w;
     v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &full_w, &red_w);
@@ -196,18 +198,21 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
 
     {
-        const int tslot = timing_begin(st);
-        k_ztable_q<<<grid_cap((uint64_t)g.n * k, 256), 256, 0, st>>>(g.n, k, d_desc,
-                                                                    g.color.as<uint8_t>(), d_z);
-        timing_end(tslot, kTimeZ, st);
-        RR_LAUNCHED();
+        if (colored) {  // plain queries draw z on the fly
+            const int tslot = timing_begin(st);
+            k_ztable_q<<<grid_cap((uint64_t)g.n * k, 256), 256, 0, st>>>(g.n, k, d_desc,
+                                                                        g.color.as<uint8_t>(), d_z);
+            timing_end(tslot, kTimeZ, st);
+            RR_LAUNCHED();
+            ++nk;
+        }
         k_zero_q<<<grid_cap(g.n, 256), 256, 0, st>>>(g.n, d_desc);
         RR_LAUNCHED();
-        nk += 2;
+        ++nk;
     }
     V2Params vp{};
     vp.qd = d_desc;
-    vp.z = d_z;
+    vp.z = colored ? d_z : nullptr;
     vp.n = g.n;
     vp.k = k;
     vp.chunk = chunk;
@@ -219,7 +224,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
     RR_CUDA(cudaMemsetAsync(full0, 0, (size_t)chunk * 8, st));
     RR_CUDA(cudaMemsetAsync(full1, 0, (size_t)chunk * 8, st));
     RR_CUDA(cudaMemsetAsync(red, 0, (size_t)rstride * 8, st));
-    set_list(vp, g.prod_list, true);
+    set_list(vp, g.prod_list, 0);
     vp.layer = 1;
     if (vp.nitems) {
         const int tslot = timing_begin(st);
@@ -233,7 +238,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
     if (k >= 5) {
         // layer 2 in label space (independent of the point chunk)
         RR_CUDA(cudaMemsetAsync(pr2, 0, (size_t)k * 8, st));
-        set_list(vp, g.state_list, true);
+        set_list(vp, g.state_list, 0);
         vp.layer = 2;
         if (vp.nitems) {
             const int tslot = timing_begin(st);
@@ -249,7 +254,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
         vp.chunk_base = (uint32_t)(c * chunk);
         rr_status s = RR_OK;
         if (k == 3) {
-            set_list(vp, g.win_list, true);
+            set_list(vp, g.win_list, 0);
             vp.layer = 2;
             s = ppl == 4 ? launch_v2<4>(vp, 1, 2, st) : launch_v2<2>(vp, 1, 2, st);
             if (s != RR_OK) return s;
@@ -262,7 +267,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
         for (uint32_t l = (k >= 5 ? 3u : 2u); l <= k - 2; ++l) {
             const int src = (l == 2) ? 1 : (l == 3 ? 2 : 0);
             const int out = (l == k - 2) ? 1 : 0;
-            set_list(vp, g.state_list, src == 1);
+            // layer 2 (k = 4) runs over the state rows; layers >= 3 over the deep rows,
+            // layer 3 reading the label-space prefix at state-row indices
+            if (src == 1) set_list(vp, g.state_list, 0);
+            else set_list(vp, g.deep_list, src == 2 ? 1 : 3);
             vp.layer = l;
             vp.st_in = bufs[(l - 1) & 1u];
             vp.st_out = out == 1 ? red : bufs[l & 1u];
@@ -270,8 +278,9 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;
         }
-        // layer k-1 from the transformed state
-        set_list(vp, g.tail_list, false);
+        // layer k-1 from the transformed state (state-row indices when k = 4)
+        if (k == 4) set_list(vp, g.tail_list, 1);
+        else set_list(vp, g.tail3_list, 3);
         vp.layer = k - 1;
         vp.st_in = red;
         if (vp.nitems) {

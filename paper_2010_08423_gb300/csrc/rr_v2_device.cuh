@@ -28,6 +28,14 @@ struct V2Params {
     uint64_t *st_out;       // full (stride chunk) or reduced (stride ngroups*(lg+1))
 };
 
+// z_{u,j}: from the table when the query has one (motif queries, Eq. 3), else
+// drawn on the fly (plain queries: z_{u,j} = draw(key_z, 32u + j), the same
+// value the table would hold).
+__device__ __forceinline__ uint64_t zval(const V2Params &p, uint64_t u, uint32_t j)
+{
+    return p.z ? p.z[u * p.k + j] : sm_draw(p.qd->key_z, u * 32u + j);
+}
+
 __device__ __forceinline__ uint64_t shfl64b(uint64_t v, int src)
 {
     return __shfl_sync(0xffffffffu, (unsigned long long)v, src);
@@ -131,7 +139,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 
     uint64_t xs[PPL];
     if constexpr (FROM_Y || FROM_R2) {
-        const uint64_t zs = (uint32_t)lane < k ? p.z[(size_t)source * k + lane] : 0ull;
+        const uint64_t zs = (uint32_t)lane < k ? zval(p, source, lane) : 0ull;
         combine_labels<PPL>(zs, k, lane, hi_bits, xs);
     }
 
@@ -145,7 +153,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     uint32_t cur = p.head[it.x];
     uint64_t zv = 0;
     auto enter_head = [&](uint32_t v) {
-        zv = (uint32_t)lane < k ? p.z[(size_t)v * k + lane] : 0ull;
+        zv = (uint32_t)lane < k ? zval(p, v, lane) : 0ull;
         if constexpr (FROM_Y) {
             uint64_t xv[PPL];
             combine_labels<PPL>(zv, k, lane, hi_bits, xv);
@@ -203,7 +211,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
             if constexpr (FROM_Y) {
                 const uint64_t coef = shfl64b(m_coef, (int)t);
                 const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
-                const uint64_t zu = (uint32_t)lane < k ? p.z[(size_t)u * k + lane] : 0ull;
+                const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
                 uint64_t r[PPL];
                 combine_labels<PPL>(gf64_mul(coef, zu), k, lane, hi_bits, r);
 #pragma unroll
@@ -219,7 +227,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 combine_labels<PPL>(gf64_mul(coef, zv), k, lane, hi_bits, c);
                 if constexpr (FROM_R2) {
                     const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
-                    const uint64_t zu = (uint32_t)lane < k ? p.z[(size_t)u * k + lane] : 0ull;
+                    const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
                     const uint64_t rj = (uint32_t)lane < k
                                             ? (p.pr2[(size_t)a * k + lane] ^ p.pr2[(size_t)b * k + lane])
                                             : 0ull;
@@ -333,7 +341,7 @@ __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t it
             const uint64_t coef = shfl64b(m_coef, (int)t);
             const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
             if ((uint32_t)lane < k) {
-                acc ^= gf64_mul(coef, p.z[(size_t)u * k + lane]);
+                acc ^= gf64_mul(coef, zval(p, u, lane));
                 pr2[((size_t)base + t + 1) * k + lane] = acc;
             }
         }
@@ -362,10 +370,10 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
 
     auto zsel_of = [&](uint32_t v) -> uint64_t {
         if (!active) return 0ull;
-        if (j < (uint32_t)LG) return j < k ? p.z[(size_t)v * k + j] : 0ull;
+        if (j < (uint32_t)LG) return j < k ? zval(p, v, j) : 0ull;
         uint64_t zz = 0;
         for (uint32_t jj = LG; jj < k; ++jj)
-            if ((gbase >> jj) & 1u) zz ^= p.z[(size_t)v * k + jj];
+            if ((gbase >> jj) & 1u) zz ^= zval(p, v, jj);
         return zz;
     };
 
