@@ -51,6 +51,25 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
+    workload, or None if the kernel sources changed since that capture."""
+    import glob
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic_k8_uniform_n1e5_m1e6.json")) as fh:
+            rec = json.load(fh)
+    except OSError:
+        return None
+    h = hashlib.sha1()
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_2010_08423_gb300", "csrc", "*"))):
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec.get("source_sha1"):
+        return None
+    return rec.get("dram_bytes_per_launch", {}).get(kernel)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -399,7 +418,8 @@ def main():
     if dom:
         d = by_kernel[dom]
         roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": d["frac"], "traffic": None, "kernel": dom,
+                    "unit": "GB/s", "frac": d["frac"],
+                    "traffic": None if args.dense else recorded_traffic(dom), "kernel": dom,
                     "peak_kind": peak_kind, "avg_launch_us": d["avg_launch_us"],
                     "alg_bytes_per_launch": d["alg_bytes_per_launch"]}
     tot_k = max(1e-9, sum(v[0] for v in kt.values()))
