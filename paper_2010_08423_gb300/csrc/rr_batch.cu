@@ -34,8 +34,21 @@ enum BatchKind : uint32_t {
     kLast = 5,         // layer k-1 from the transformed state
     kThirdFull = 6,    // layer 3 (k >= 6) from the label-space layer-2 prefix
     kThirdTail = 7,    // layer 3 when k = 5, transformed state out
-    kLastDeep = 8      // layer k-1 (k >= 5) from the transformed deep-row state
+    kLastDeep = 8,     // layer k-1 (k >= 5) from the transformed deep-row state
+    kFix1 = 9,         // carry fix-up of cut segments, phase 1 (one task per cut segment)
+    kFix2 = 10         // carry fix-up, phase 2 (one task per kFixRows row slots)
 };
+
+// does a layer of this kind write prefix state (that cut segments must fix)?
+__host__ __device__ inline bool writes_state(uint32_t kind)
+{
+    return kind == kSecondTail || kind == kThirdFull || kind == kThirdTail || kind == kMidFull ||
+           kind == kMidTail;
+}
+__host__ __device__ inline bool writes_transformed(uint32_t kind)
+{
+    return kind == kSecondTail || kind == kThirdTail || kind == kMidTail;
+}
 
 struct BatchUnit {
     uint32_t q, k, chunk_base, chunk, ppl, slot;
@@ -44,6 +57,7 @@ struct BatchUnit {
 
 struct BatchSeg {
     uint32_t begin, ntasks, unit, layer, kind, ngroups;
+    uint32_t fixed_kind;  // kFix1/kFix2: kind of the layer whose output is fixed
     int32_t wait_unit;  // unit whose completion counter gates this segment (-1: none)
     uint32_t wait_count;
 };
@@ -52,6 +66,8 @@ struct ListPtrs {
     const uint32_t *head, *eid, *src, *a0, *b0, *a1, *b1, *a3, *b3;
     const uint2 *items;
     uint32_t nitems;
+    const uint2 *chains, *fix2;
+    uint32_t nchains, nfix2;
 };
 
 struct BatchArgs {
@@ -179,6 +195,24 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
         vp.st_out = red;
         layer_warp<PPL, false, 1, true>(vp, item, group);
         break;
+    case kFix1:
+    case kFix2: {
+        const ListPtrs &L = sg.fixed_kind == kSecondTail ? a.state : a.deep;
+        constexpr uint32_t LG = PPL == 4 ? 7u : 6u;
+        const bool tr = writes_transformed(sg.fixed_kind);
+        uint64_t *buf = tr ? red : bufs[l & 1u];
+        const uint32_t width = tr ? (u.chunk / (32u * PPL)) * (LG + 1) : u.chunk;
+        const int lane = threadIdx.x & 31;
+        if (sg.kind == kFix1) {
+            const uint2 ch = L.chains[local];
+            fixup_phase1<true>(buf, width, ch.x, ch.y, (uint32_t)lane, 32u);
+        } else {
+            const uint2 t = L.fix2[local];
+            const uint2 ch = L.chains[t.x];
+            fixup_phase2<true>(buf, width, ch.x, ch.y, t.y, (uint32_t)lane, 32u);
+        }
+        break;
+    }
     case kLastDeep:
         set_list(vp, a.tail3, 3);
         vp.st_in = red;
@@ -338,7 +372,46 @@ ListPtrs list_ptrs(const RowList &L, bool coarse)
                     L.a0.as<uint32_t>(),   L.b0.as<uint32_t>(),  L.a1.as<uint32_t>(),
                     L.b1.as<uint32_t>(),   L.a3.as<uint32_t>(),  L.b3.as<uint32_t>(),
                     coarse ? L.items_coarse.as<uint2>() : L.items.as<uint2>(),
-                    coarse ? L.nitems_coarse : L.nitems};
+                    coarse ? L.nitems_coarse : L.nitems,
+                    L.chains.as<uint2>(),  L.fix2.as<uint2>(),   L.nchains, L.nfix2};
+}
+
+// prologue fix-ups of the per-query scalar (width 1) or label-space (width k,
+// queries with k >= 5 only) prefixes: blockIdx.y = query
+__global__ void k_batch_fix1(ListPtrs L, uint64_t *base, const uint64_t *__restrict__ off,
+                             const QueryDesc *__restrict__ descs, int label_space)
+{
+    if (blockIdx.x >= L.nchains) return;
+    const uint32_t k = descs[blockIdx.y].k;
+    if (label_space && k < 5) return;
+    const uint2 ch = L.chains[blockIdx.x];
+    fixup_phase1<false>(base + off[blockIdx.y], label_space ? k : 1u, ch.x, ch.y, threadIdx.x,
+                        blockDim.x);
+}
+
+__global__ void k_batch_fix2(ListPtrs L, uint64_t *base, const uint64_t *__restrict__ off,
+                             const QueryDesc *__restrict__ descs, int label_space)
+{
+    if (blockIdx.x >= L.nfix2) return;
+    const uint32_t k = descs[blockIdx.y].k;
+    if (label_space && k < 5) return;
+    const uint2 t = L.fix2[blockIdx.x];
+    const uint2 ch = L.chains[t.x];
+    fixup_phase2<false>(base + off[blockIdx.y], label_space ? k : 1u, ch.x, ch.y, t.y, threadIdx.x,
+                        blockDim.x);
+}
+
+static rr_status batch_fixup(const ListPtrs &L, uint64_t *base, const uint64_t *off,
+                             const QueryDesc *descs, uint32_t nq, int label_space, cudaStream_t st)
+{
+    if (!L.nchains) return RR_OK;
+    k_batch_fix1<<<dim3(L.nchains, nq), 128, 0, st>>>(L, base, off, descs, label_space);
+    RR_LAUNCHED();
+    if (L.nfix2) {
+        k_batch_fix2<<<dim3(L.nfix2, nq), 256, 0, st>>>(L, base, off, descs, label_space);
+        RR_LAUNCHED();
+    }
+    return RR_OK;
 }
 
 // Tasks of layer l of a unit with (k, ppl, chunk).
@@ -461,22 +534,37 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         nslots = std::max<uint32_t>(1, nslots);
         for (size_t i = 0; i < units.size(); ++i) units[i].slot = (uint32_t)(i % nslots);
 
-        // segments in task order: wave, layer, unit
-        std::vector<uint32_t> unit_total(units.size(), 0);
-        std::vector<std::vector<uint32_t>> per_layer(units.size());
-        for (size_t i = 0; i < units.size(); ++i) {
-            const BatchUnit &u = units[i];
-            const uint32_t ngroups = u.chunk / (32u * u.ppl);
-            per_layer[i].assign(u.k + 1, 0);
-            for (uint32_t l = 2; l <= u.k - 1; ++l) {
-                uint32_t kind;
-                per_layer[i][l] = layer_tasks(g, u.k, l, ngroups, &kind);
-                unit_total[i] += per_layer[i][l];
-            }
-        }
+        // segments in task order: wave, layer, unit; after a layer that writes
+        // prefix state, the unit's carry fix-up segments (phase 1, phase 2)
         std::vector<BatchSeg> segs;
         std::vector<char> started(units.size(), 0);
+        std::vector<uint32_t> emitted(units.size(), 0);  // tasks emitted so far per unit
         uint64_t total = 0;
+        auto emit = [&](size_t i, uint32_t l, uint32_t kind, uint32_t nt, uint32_t ngroups,
+                        uint32_t fixed_kind) {
+            BatchSeg sg{};
+            sg.begin = (uint32_t)total;
+            sg.ntasks = nt;
+            sg.unit = (uint32_t)i;
+            sg.layer = l;
+            sg.kind = kind;
+            sg.ngroups = ngroups;
+            sg.fixed_kind = fixed_kind;
+            if (!started[i]) {
+                // the unit's first layer reuses the slot: wait for the unit that
+                // held it before to finish
+                started[i] = 1;
+                const long prev = (long)i - (long)nslots;
+                sg.wait_unit = prev >= 0 ? (int32_t)prev : -1;
+                sg.wait_count = prev >= 0 ? emitted[prev] : 0;
+            } else {
+                sg.wait_unit = (int32_t)i;
+                sg.wait_count = emitted[i];
+            }
+            segs.push_back(sg);
+            total += nt;
+            emitted[i] += nt;
+        };
         for (size_t w0 = 0; w0 < units.size(); w0 += nslots) {
             const size_t w1 = std::min(units.size(), w0 + nslots);
             uint32_t maxl = 0;
@@ -489,28 +577,12 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                     uint32_t kind;
                     const uint32_t nt = layer_tasks(g, u.k, l, ngroups, &kind);
                     if (nt == 0) continue;
-                    BatchSeg sg{};
-                    sg.begin = (uint32_t)total;
-                    sg.ntasks = nt;
-                    sg.unit = (uint32_t)i;
-                    sg.layer = l;
-                    sg.kind = kind;
-                    sg.ngroups = ngroups;
-                    if (!started[i]) {
-                        // the unit's first layer reuses the slot: wait for the
-                        // unit that held it before to finish
-                        started[i] = 1;
-                        const long prev = (long)i - (long)nslots;
-                        sg.wait_unit = prev >= 0 ? (int32_t)prev : -1;
-                        sg.wait_count = prev >= 0 ? unit_total[prev] : 0;
-                    } else {
-                        uint32_t before = 0;
-                        for (uint32_t l2 = 2; l2 < l; ++l2) before += per_layer[i][l2];
-                        sg.wait_unit = (int32_t)i;
-                        sg.wait_count = before;
+                    emit(i, l, kind, nt, ngroups, 0);
+                    if (writes_state(kind)) {
+                        const RowList &L = kind == kSecondTail ? g.state_list : g.deep_list;
+                        if (L.nchains) emit(i, l, kFix1, L.nchains, ngroups, kind);
+                        if (L.nfix2) emit(i, l, kFix2, L.nfix2, ngroups, kind);
                     }
-                    segs.push_back(sg);
-                    total += nt;
                 }
         }
         if (total >= (1ull << 32)) return fail(RR_EINVAL, "rr_reach_batch_device: batch too large");
@@ -572,6 +644,11 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                                            d_pyoff.as<uint64_t>());
         timing_end(tslot, kTimeFirst, st);
         RR_LAUNCHED();
+        {
+            rr_status fs = batch_fixup(prod, d_py.as<uint64_t>(), d_pyoff.as<uint64_t>(),
+                                       d_descs.as<QueryDesc>(), (uint32_t)grp.size(), 0, st);
+            if (fs != RR_OK) return fs;
+        }
         tslot = timing_begin(st);
         k_batch_second<<<dim3(std::max<uint32_t>(1, (g.state_list.nitems + kW2 - 1) / kW2),
                               (unsigned)grp.size()),
@@ -581,6 +658,12 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                                             B.pr2.as<uint64_t>(), B.pr2off.as<uint64_t>(), g.n);
         timing_end(tslot, kTimeSecond, st);
         RR_LAUNCHED();
+        {
+            rr_status fs = batch_fixup(list_ptrs(g.state_list, false), B.pr2.as<uint64_t>(),
+                                       B.pr2off.as<uint64_t>(), d_descs.as<QueryDesc>(),
+                                       (uint32_t)grp.size(), 1, st);
+            if (fs != RR_OK) return fs;
+        }
         k_batch_zero_rows<<<nslots, 256, 0, st>>>(d_slots.as<uint64_t>(), slot_bytes / 8,
                                                   (g.deep_list.count + 1) * max_chunk, nslots,
                                                   max_chunk);

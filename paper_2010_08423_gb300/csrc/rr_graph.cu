@@ -326,11 +326,14 @@ static void build_items(const std::vector<uint32_t> &off, uint32_t n,
 }
 
 // Head-aligned scheduling ranges over a row list: consecutive head runs are
-// packed until `target` entries; a longer run forms its own range. Largest first.
+// packed until `target` entries; a run of `target` entries or more forms its
+// own range(s), cut into pieces of at most RowList::kMaxRun entries (the cut
+// runs are returned in `chains`). Ranges are ordered largest first.
 static void build_entry_items(const std::vector<uint32_t> &head, uint32_t target,
-                              std::vector<uint2> &items)
+                              std::vector<uint2> &items, std::vector<uint2> *chains)
 {
     std::vector<uint2> tmp;
+    const uint32_t maxrun = RowList::kMaxRun;
     const uint64_t cnt = head.size();
     uint64_t start = 0, i = 0;
     while (i < cnt) {
@@ -338,7 +341,9 @@ static void build_entry_items(const std::vector<uint32_t> &head, uint32_t target
         while (j < cnt && head[j] == head[i]) ++j;  // run [i, j)
         if (j - i >= target) {
             if (i > start) tmp.push_back(make_uint2((uint32_t)start, (uint32_t)i));
-            tmp.push_back(make_uint2((uint32_t)i, (uint32_t)j));
+            for (uint64_t b = i; b < j; b += maxrun)
+                tmp.push_back(make_uint2((uint32_t)b, (uint32_t)std::min<uint64_t>(j, b + maxrun)));
+            if (chains && j - i > maxrun) chains->push_back(make_uint2((uint32_t)i, (uint32_t)j));
             start = j;
         } else if (j - start >= target) {
             tmp.push_back(make_uint2((uint32_t)start, (uint32_t)j));
@@ -480,9 +485,28 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         // comes from many queries at once
         const uint32_t target =
             (uint32_t)std::min<uint64_t>(128, std::max<uint64_t>(1, R.count / (152 * 64)));
-        std::vector<uint2> items, coarse;
-        build_entry_items(heads, target, items);
-        build_entry_items(heads, 32, coarse);
+        // runs longer than kMaxRun are cut at the same places in both range
+        // sets, so one chain table serves both
+        std::vector<uint2> items, coarse, chains;
+        build_entry_items(heads, std::min<uint32_t>(target, RowList::kMaxRun), items, &chains);
+        build_entry_items(heads, 32, coarse, nullptr);
+        R.nchains = (uint32_t)chains.size();
+        RR_CUDA(R.chains.reserve(std::max<size_t>(1, chains.size()) * sizeof(uint2)));
+        if (!chains.empty())
+            RR_CUDA(cudaMemcpyAsync(R.chains.p, chains.data(), chains.size() * sizeof(uint2),
+                                    cudaMemcpyHostToDevice, st));
+        std::vector<uint2> fix2;
+        for (size_t c = 0; c < chains.size(); ++c) {
+            const uint32_t R_ = RowList::kMaxRun;
+            const uint32_t len = chains[c].y - chains[c].x;
+            const uint32_t slots = ((len + R_ - 1) / R_ - 1) * (R_ - 1);
+            for (uint32_t s0 = 0; s0 < slots; s0 += 64) fix2.push_back(make_uint2((uint32_t)c, s0));
+        }
+        R.nfix2 = (uint32_t)fix2.size();
+        RR_CUDA(R.fix2.reserve(std::max<size_t>(1, fix2.size()) * sizeof(uint2)));
+        if (!fix2.empty())
+            RR_CUDA(cudaMemcpyAsync(R.fix2.p, fix2.data(), fix2.size() * sizeof(uint2),
+                                    cudaMemcpyHostToDevice, st));
         R.nitems = (uint32_t)items.size();
         R.nitems_coarse = (uint32_t)coarse.size();
         RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));

@@ -137,10 +137,19 @@ struct RowList {
     uint32_t nitems = 0;
     DevBuf items_coarse;    // uint2 ranges of about 32 entries (persistent batch)
     uint32_t nitems_coarse = 0;
+    // Head segments longer than kMaxRun entries are cut into pieces of kMaxRun
+    // that run in parallel, each computing a prefix from zero; `chains` lists
+    // every cut segment as (first entry, end entry) so that a fix-up pass can
+    // XOR the running carry into the later pieces.
+    static constexpr uint32_t kMaxRun = 128;
+    DevBuf chains;          // uint2 (begin, end) of every cut segment
+    uint32_t nchains = 0;
+    DevBuf fix2;            // uint2 (chain, first row slot) of every phase-2 fix-up task
+    uint32_t nfix2 = 0;
     size_t bytes() const
     {
         return head.bytes + eid.bytes + src.bytes + a0.bytes + b0.bytes + a1.bytes + b1.bytes +
-               a3.bytes + b3.bytes + items.bytes + items_coarse.bytes;
+               a3.bytes + b3.bytes + items.bytes + items_coarse.bytes + chains.bytes + fix2.bytes;
     }
 };
 

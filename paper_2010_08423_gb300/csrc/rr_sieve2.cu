@@ -41,6 +41,40 @@ __global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
     layer_warp<PPL, FROM_Y, OUT, false, FROM_R2>(p, item, task - item * p.ngroups);
 }
 
+// Carry fix-up of cut head segments (rr_v2_device.cuh): phase 1 one block
+// per cut segment, phase 2 one block per task of kFixRows row slots.
+__global__ void k_fix1(const uint2 *__restrict__ chains, uint32_t nchains, uint64_t *buf,
+                       uint32_t width)
+{
+    if (blockIdx.x >= nchains) return;
+    const uint2 ch = chains[blockIdx.x];
+    fixup_phase1<false>(buf, width, ch.x, ch.y, threadIdx.x, blockDim.x);
+}
+
+__global__ void k_fix2(const uint2 *__restrict__ chains, const uint2 *__restrict__ tasks,
+                       uint32_t ntasks, uint64_t *buf, uint32_t width)
+{
+    if (blockIdx.x >= ntasks) return;
+    const uint2 t = tasks[blockIdx.x];
+    const uint2 ch = chains[t.x];
+    fixup_phase2<false>(buf, width, ch.x, ch.y, t.y, threadIdx.x, blockDim.x);
+}
+
+static rr_status launch_fixup(const RowList &L, uint64_t *buf, uint32_t width, cudaStream_t st,
+                              uint64_t *nk)
+{
+    if (L.nchains == 0) return RR_OK;
+    k_fix1<<<L.nchains, 128, 0, st>>>(L.chains.as<uint2>(), L.nchains, buf, width);
+    RR_LAUNCHED();
+    ++*nk;
+    if (L.nfix2) {
+        k_fix2<<<L.nfix2, 256, 0, st>>>(L.chains.as<uint2>(), L.fix2.as<uint2>(), L.nfix2, buf, width);
+        RR_LAUNCHED();
+        ++*nk;
+    }
+    return RR_OK;
+}
+
 __global__ void __launch_bounds__(kW2 * 32) k_second_label(const V2Params p, uint64_t *__restrict__ pr2)
 {
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
@@ -232,6 +266,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
         timing_end(tslot, kTimeFirst, st);
         RR_LAUNCHED();
         ++nk;
+        rr_status fs = launch_fixup(g.prod_list, py, 1, st, &nk);
+        if (fs != RR_OK) return fs;
     }
     vp.py = py;
     vp.pr2 = pr2;
@@ -246,6 +282,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
             timing_end(tslot, kTimeSecond, st);
             RR_LAUNCHED();
             ++nk;
+            rr_status fs = launch_fixup(g.state_list, pr2, k, st, &nk);
+            if (fs != RR_OK) return fs;
         }
     }
 
@@ -277,6 +315,9 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
             s = ppl == 4 ? launch_v2<4>(vp, src, out, st) : launch_v2<2>(vp, src, out, st);
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;
+            s = launch_fixup(src == 1 ? g.state_list : g.deep_list, vp.st_out,
+                             out == 1 ? rstride : chunk, st, &nk);
+            if (s != RR_OK) return s;
         }
         // layer k-1 from the transformed state (state-row indices when k = 4)
         if (k == 4) set_list(vp, g.tail_list, 1);

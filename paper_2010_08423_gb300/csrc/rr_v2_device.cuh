@@ -349,6 +349,68 @@ __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t it
 }
 
 // ---------------------------------------------------------------------------
+// Carry fix-up of a cut head segment [b, e) of a row list whose prefix rows
+// (entry + 1) hold `width` words each (1: scalar layer-1 prefix, k: label
+// space, chunk: per-point, groups*(lg+1): transformed). Every piece of
+// RowList::kMaxRun entries was computed from zero; the stored forms are all
+// XOR-linear, so adding the full prefix at the previous piece's last row fixes
+// a piece. Phase 1 walks the pieces' last rows in order (one thread per
+// column); phase 2 (after phase 1 of the segment has finished) fixes the other
+// rows, cut into tasks of kFixRows row slots. COHERENT reads state through L2
+// when it was written earlier in the same launch.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kFixRows = 64;
+
+template <bool COHERENT>
+__device__ __forceinline__ uint64_t ld_state(const uint64_t *q)
+{
+    return COHERENT ? __ldcg(q) : *q;
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ void fixup_phase1(uint64_t *__restrict__ buf, uint32_t width, uint32_t b,
+                                             uint32_t e, uint32_t tid, uint32_t nthreads)
+{
+    constexpr uint32_t R = RowList::kMaxRun;
+    for (uint32_t c = tid; c < width; c += nthreads) {
+        uint64_t carry = ld_state<COHERENT>(buf + (size_t)(b + R) * width + c);  // piece 0's last row
+        for (uint32_t ps = b + R; ps < e; ps += R) {
+            const uint32_t pe = min(e, ps + R);  // piece [ps, pe): rows ps+1 .. pe
+            uint64_t *last = buf + (size_t)pe * width + c;
+            const uint64_t fixed = ld_state<COHERENT>(last) ^ carry;
+            *last = fixed;
+            carry = fixed;
+        }
+    }
+}
+
+// Row slots of a cut segment: piece p >= 1 contributes slots for its rows
+// ps+1 .. ps+R-1 (its last row is handled by phase 1), R-1 slots per piece.
+__device__ __forceinline__ uint32_t fixup_slots(uint32_t b, uint32_t e)
+{
+    constexpr uint32_t R = RowList::kMaxRun;
+    return ((e - b + R - 1) / R - 1) * (R - 1);
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ void fixup_phase2(uint64_t *__restrict__ buf, uint32_t width, uint32_t b,
+                                             uint32_t e, uint32_t slot0, uint32_t tid, uint32_t nthreads)
+{
+    constexpr uint32_t R = RowList::kMaxRun;
+    const uint32_t slots = min(kFixRows, fixup_slots(b, e) - slot0);
+    const uint64_t total = (uint64_t)slots * width;
+    for (uint64_t idx = tid; idx < total; idx += nthreads) {
+        const uint32_t c = (uint32_t)(idx % width);
+        const uint32_t slot = slot0 + (uint32_t)(idx / width);
+        const uint32_t piece = 1 + slot / (R - 1);
+        const uint32_t ps = b + piece * R;
+        const uint32_t row = ps + 1 + slot % (R - 1);
+        if (row >= min(e, ps + R)) continue;  // past a short last piece, or its last row
+        buf[(size_t)row * width + c] ^= ld_state<COHERENT>(buf + (size_t)ps * width + c);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Last layer from the transformed state: lane (g, j) accumulates
 // sum_e y_{e,k-1} T_{g,j}(W_e) over the rows e of one head vertex v, then
 // multiplies once by z_{v,j} (j < lg) or by the XOR of z_{v,j'} over the
