@@ -192,7 +192,9 @@ def batched_metrics(capi, torch, gc, nq=256, seed=GRAPH_SEED):
             "launches": "1 persistent kernel (+ z-table, first-layer and bitmap prologue/epilogue)"}
 
 
-def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E):
+def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
+                   workload="plain queries, k~U{6..12}, s~U, on the n=100000 m=1000000 graph",
+                   warm=8):
     """Serving: Poisson arrivals of plain queries (s ~ U, k ~ U{6..12}) at 0.5x,
     0.8x and 1.1x of the server's measured capacity; latency = submit -> done."""
     import threading
@@ -200,12 +202,11 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E):
     n = g["n"]
     qs = [(int(rng.integers(0, n)), int(rng.integers(6, 13)), int(rng.integers(1, 2**62)))
           for _ in range(nq)]
-    out = {"workload": "plain queries, k~U{6..12}, s~U, on the n=100000 m=1000000 graph",
-           "slots": 4}
+    out = {"workload": workload, "slots": 4, "queries_per_level": nq}
     with capi.Graph(g) as G:
         srv = capi.rr_server_create(G.handle, 0, 4)
         try:
-            for s_, k_, sd in qs[:8]:  # warm-up: capture each slot's graphs
+            for s_, k_, sd in qs[:warm]:  # warm-up: capture each slot's graphs
                 capi.rr_query_poll(srv, capi.rr_query_submit(srv, s_, k_, sd), n, -1)
             t0 = time.perf_counter()
             ts = [capi.rr_query_submit(srv, s_, k_, sd) for s_, k_, sd in qs]
@@ -251,6 +252,76 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E):
         finally:
             capi.rr_server_destroy(srv)
     return out
+
+
+def motif_metrics(capi, torch, steps=5):
+    """Chung-Lu exponent 2.5, n=1e6, m=1e7, bursty t in [1,10000], delta ~
+    U{5..50}, 8 colours; k-RestlessMotifReach with k=10 from the first vertex
+    with an out-edge, motif = its colour + 9 uniform colours (seeded)."""
+    g = W.motif_powerlaw()
+    s = W.first_source(g)
+    motif = W.motif_for(g, s, 10, W.GRAPH_SEED_BASE + 3)
+    n, m = g["n"], len(g["src"])
+    t0 = time.perf_counter()
+    with capi.Graph(g) as G:
+        load_s = time.perf_counter() - t0
+        info = G.info()
+        st = torch.cuda.Stream()
+        d_w = torch.zeros(n, dtype=torch.int64, device="cuda")
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+        for i in range(2):
+            capi.rr_reach_device(G.handle, s, 10, i + 1, d_w, None, st.cuda_stream, motif=motif)
+        st.synchronize()
+        tot = 0.0
+        with torch.cuda.stream(st):
+            for i in range(steps):
+                flush.fill_(i)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                capi.rr_reach_device(G.handle, s, 10, 100 + i, d_w, None, st.cuda_stream, motif=motif)
+                e1.record(st)
+                st.synchronize()
+                tot += e0.elapsed_time(e1)
+        reach = int((d_w != 0).sum().item())
+    units = float(2 ** 10) * 10 * m
+    return {"workload": "Chung-Lu exponent 2.5, n=1e6, m=1e7, bursty t in [1,10000], delta~U{5..50}, "
+                        "8 colours; k-RestlessMotifReach k=10, motif = source colour + 9 uniform colours",
+            "value": units * steps / (tot / 1e3), "unit": UNIT, "ms_per_query": tot / steps,
+            "reachable_vertices": reach, "graph_load_s": round(load_s, 3),
+            "state_rows": info["producer_window_rows"] + 1, "deep_rows": info["state_compute_rows"],
+            "max_in_degree": info["max_in_degree"], "l2": "flushed between queries"}
+
+
+def atmost_metrics(capi, torch, g, k=10, reps=5):
+    """at-most-k (the exact-k' queries for k' = 2..k, run concurrently) against
+    the exact-k query on the benchmark graph. The paper's experiments report the
+    ratio of the two runtimes (column 4 of its scalability tables; below 2 on
+    most graphs), which the nominal work sum_{k'} k' 2^k' / (k 2^k) predicts."""
+    n, m = g["n"], len(g["src"])
+    with capi.Graph(g) as G:
+        st = torch.cuda.Stream()
+        d_w = torch.zeros((k - 1, n), dtype=torch.int64, device="cuda")
+        d_bm = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        capi.rr_reach_atmost_device(G.handle, SOURCE, k, 1, d_w, d_bm, st.cuda_stream)
+        capi.rr_reach_device(G.handle, SOURCE, k, 1, d_w[0], None, st.cuda_stream)
+        st.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(st):
+            e[0].record(st)
+            for i in range(reps):
+                capi.rr_reach_atmost_device(G.handle, SOURCE, k, 2 + i, d_w, d_bm, st.cuda_stream)
+            e[1].record(st)
+            e[2].record(st)
+            for i in range(reps):
+                capi.rr_reach_device(G.handle, SOURCE, k, 2 + i, d_w[0], None, st.cuda_stream)
+            e[3].record(st)
+            st.synchronize()
+        t_atm = e[0].elapsed_time(e[1]) / reps
+        t_exact = e[2].elapsed_time(e[3]) / reps
+    nominal_ratio = sum(kk * 2 ** kk for kk in range(2, k + 1)) / (k * 2 ** k)
+    return {"k": k, "atmost_ms": t_atm, "exact_ms": t_exact, "time_ratio": t_atm / t_exact,
+            "nominal_work_ratio": nominal_ratio,
+            "value": sum(2 ** kk * kk * m for kk in range(2, k + 1)) / (t_atm / 1e3), "unit": UNIT}
 
 
 def run_reference(args):
@@ -448,6 +519,14 @@ def main():
         gc = W.scale_uniform(ncolors=8)
         line["batched"] = batched_metrics(capi, torch, gc)
         line["served"] = served_metrics(capi, g)
+        line["atmost_k"] = atmost_metrics(capi, torch, g)
+        line["motif_powerlaw"] = motif_metrics(capi, torch)
+        g5 = W.served_powerlaw()
+        line["served_powerlaw"] = served_metrics(
+            capi, g5, nq=16, seed=W.GRAPH_SEED_BASE + 5, warm=4,
+            workload="plain queries, k~U{6..12}, s~U, on the Chung-Lu exponent 2.3 graph "
+                     "n=1e7 m=1e8 t~U[1,1e5] delta~U{10..200}")
+        del g5
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, K)
     if rank == 0:

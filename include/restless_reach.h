@@ -158,6 +158,19 @@ rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t 
                                 uint8_t *d_bitmaps, uint64_t *d_witness, int32_t *d_status,
                                 void *stream);
 
+/* rr_reach_atmost_device: at-most-k-RestlessReach (Sec. "Discussion"; Algorithm 2
+ * with its loop over k' stopped at k): the plain queries (source, k', seed) for
+ * k' = 2..k. d_witness ((k-1) * n uint64, device) gets the witness of k' in row
+ * k'-2; d_bitmap (ceil(n/8) bytes, device, may be NULL) gets the union of the
+ * reach sets: vertices reached by a restless path of at most k vertices.
+ * Ordered on `stream`: the k-1 queries run concurrently on streams of the
+ * library's own that start after the work already on `stream` and that
+ * `stream` waits for; when their scratch does not fit 60% of free device memory
+ * together they run one after another on `stream`. Scratch stays allocated
+ * with the graph. Errors as rr_reach_device. */
+rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,
+                                 uint8_t *d_bitmap, uint64_t *d_witness, void *stream);
+
 /* ---- serving: continuous batching over a resident graph --------------------
  * rr_server_create: starts a server thread that admits queries while device
  * memory (device_mem_budget bytes of scratch, 0 = 60% of free memory) and

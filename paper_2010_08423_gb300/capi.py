@@ -56,7 +56,7 @@ EXPORTED = [
     "rr_query_submit", "rr_query_poll", "rr_query_cancel", "rr_query_times", "rr_autotune",
     "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
-    "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc",
+    "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
 ]
 
 _lib = None
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_device": [vp, pq, vp, vp, vp],
         "rr_reach_device_noalloc": [vp, pq, vp, vp, vp],
         "rr_reach_batch_device": [vp, pq, u32, vp, vp, vp, vp],
+        "rr_reach_atmost_device": [vp, u32, u32, u64, vp, vp, vp],
         "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
         "rr_server_destroy": [vp],
         "rr_query_submit": [vp, pq, ctypes.POINTER(u64)],
@@ -210,6 +211,12 @@ def rr_reach_batch_device(g, queries, d_witness, d_bitmaps=None, d_status=None, 
     _check(load().rr_reach_batch_device(g, arr, len(queries), _dp(d_bitmaps), _dp(d_witness),
                                         _dp(d_status), _dp(stream)))
     del keep
+
+
+def rr_reach_atmost_device(g, source, k, seed, d_witness, d_bitmap=None, stream=None):
+    """At most k vertices: d_witness is (k-1) x n (row k'-2 = witness of k')."""
+    _check(load().rr_reach_atmost_device(g, int(source), int(k), int(seed) & ((1 << 64) - 1),
+                                         _dp(d_bitmap), _dp(d_witness), _dp(stream)))
 
 
 def rr_server_create(g, budget: int = 0, max_slots: int = 0):

@@ -28,7 +28,7 @@ namespace {
 enum BatchKind : uint32_t {
     kSecondFull = 0,   // layer 2, window sums from the scalar prefix, full state out
     kSecondTail = 1,   // layer 2 when k = 4, transformed state out
-    kSecondFinal = 2,  // layer 2 when k = 3, per-vertex sums out
+    // 2: unused (k <= 3 queries finish in the prologue: k_batch_first2, k_batch_last3)
     kMidFull = 3,      // layers 3..k-3
     kMidTail = 4,      // layer k-2 (k >= 6), transformed state out
     kLast = 5,         // layer k-1 from the transformed state
@@ -71,7 +71,7 @@ struct ListPtrs {
 };
 
 struct BatchArgs {
-    ListPtrs prod, state, win, tail, deep, tail3;
+    ListPtrs prod, state, tail, deep, tail3;
     uint32_t n;
     const BatchUnit *units;
     const BatchSeg *segs;
@@ -169,10 +169,6 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
         vp.st_out = red;
         layer_warp<PPL, true, 1, true>(vp, item, group);
         break;
-    case kSecondFinal:
-        set_list(vp, a.win, 0);
-        layer_warp<PPL, true, 2, true>(vp, item, group);
-        break;
     case kThirdFull:
         set_list(vp, a.deep, 1);
         vp.st_out = bufs[l & 1u];
@@ -226,7 +222,12 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
     }
 }
 
-__global__ void __launch_bounds__(kW2 * 32, 4) k_batch(const BatchArgs a)
+// MINB = blocks per SM the register budget is set for: 4 (128 registers, some
+// spilled) for large batches, where more resident warps hide the tasks'
+// latencies; 2 (no spills) for small batches, whose critical path is the
+// per-task time.
+template <int MINB>
+__global__ void __launch_bounds__(kW2 * 32, MINB) k_batch(const BatchArgs a)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -334,6 +335,47 @@ k_batch_second(ListPtrs state, const QueryDesc *__restrict__ descs, const uint64
     second_label_warp(vp, task, pr2);
 }
 
+// the batch's k = 2 queries in closed form (blockIdx.y = query)
+__global__ void k_batch_first2(const QueryDesc *__restrict__ descs, const uint64_t *__restrict__ z_all,
+                               const uint64_t *__restrict__ z_off, const uint32_t *__restrict__ off,
+                               const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ row_eid,
+                               uint32_t n, uint32_t m)
+{
+    const QueryDesc *qd = descs + blockIdx.y;
+    if (qd->k != 2) return;
+    V2Params vp{};
+    vp.qd = qd;
+    vp.z = qd->colored ? z_all + z_off[blockIdx.y] : nullptr;
+    vp.n = n;
+    vp.k = 2;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
+        first2_closed(vp, off, row_src, row_eid, r);
+}
+
+// the last layer of the batch's k = 3 queries in closed form (blockIdx.y = query)
+__global__ void k_batch_last3(ListPtrs win, uint32_t count, const QueryDesc *__restrict__ descs,
+                              const uint64_t *__restrict__ z_all, const uint64_t *__restrict__ z_off,
+                              const uint64_t *__restrict__ py_all, const uint64_t *__restrict__ py_off,
+                              uint32_t n)
+{
+    const QueryDesc *qd = descs + blockIdx.y;
+    if (qd->k != 3) return;
+    V2Params vp{};
+    vp.qd = qd;
+    vp.z = qd->colored ? z_all + z_off[blockIdx.y] : nullptr;
+    vp.py = py_all + py_off[blockIdx.y];
+    vp.n = n;
+    vp.k = 3;
+    vp.layer = 2;
+    vp.head = win.head;
+    vp.eid = win.eid;
+    vp.src = win.src;
+    vp.ia = win.a0;
+    vp.ib = win.b0;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+        last3_closed(vp, e);
+}
+
 __global__ void k_batch_bitmap(uint32_t n, const QueryDesc *__restrict__ descs)
 {
     const QueryDesc *qd = descs + blockIdx.y;
@@ -414,24 +456,24 @@ static rr_status batch_fixup(const ListPtrs &L, uint64_t *base, const uint64_t *
     return RR_OK;
 }
 
-// Tasks of layer l of a unit with (k, ppl, chunk).
-uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, uint32_t *kind)
+// Tasks of layer l of a unit with (k, ppl, chunk), over the coarse or the fine
+// scheduling ranges of the layer's row list.
+uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, bool coarse,
+                     uint32_t *kind)
 {
-    if (k == 3) {
-        *kind = kSecondFinal;
-        return g.win_list.nitems_coarse * ngroups;
-    }
+    auto items = [coarse](const RowList &L) { return coarse ? L.nitems_coarse : L.nitems; };
+    if (k <= 3) return 0;  // closed forms in the prologue
     if (l == k - 1) {
         *kind = k == 4 ? kLast : kLastDeep;
-        return k == 4 ? g.tail_list.nitems_coarse : g.tail3_list.nitems_coarse;
+        return k == 4 ? items(g.tail_list) : items(g.tail3_list);
     }
     if (l == 2) {
         if (k >= 5) return 0;  // label-space layer 2 runs in the prologue
         *kind = kSecondTail;   // k = 4
-        return g.state_list.nitems_coarse * ngroups;
+        return items(g.state_list) * ngroups;
     }
     *kind = l == 3 ? ((k == 5) ? kThirdTail : kThirdFull) : ((l == k - 2) ? kMidTail : kMidFull);
-    return g.deep_list.nitems_coarse * ngroups;
+    return items(g.deep_list) * ngroups;
 }
 
 }  // namespace
@@ -449,7 +491,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
     if (nq == 0) return RR_OK;
     const size_t nb = (g.n + 7) / 8;
     if (d_status) RR_CUDA(cudaMemsetAsync(d_status, 0, (size_t)nq * 4, st));
-    // k = 2 queries and per-point-engine graphs run one query at a time
+    // graphs on the per-point engine run one query at a time
     std::vector<uint32_t> bq;
     for (uint32_t i = 0; i < nq; ++i) {
         if (uses_v2(g, qs[i].k)) {
@@ -462,6 +504,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
     }
     if (bq.empty()) return RR_OK;
 
+    BatchBuffers &B = g.batch;
     size_t free_b = 0, total_b = 0;
     RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
     uint64_t budget = (uint64_t)(0.6 * (double)free_b);
@@ -521,11 +564,26 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             const uint32_t ppl = npts >= 128 ? 4u : 2u;
             uint32_t chunk = (uint32_t)std::max<uint64_t>(32ull * ppl, std::min<uint64_t>(npts, max_chunk));
             chunk = std::max<uint32_t>(chunk, 32u * ppl);
-            const uint64_t nch = (npts + chunk - 1) / chunk;
+            const uint64_t nch = q.k <= 3 ? 0 : (npts + chunk - 1) / chunk;  // k <= 3: prologue
             for (uint64_t c = 0; c < nch; ++c)
                 units.push_back(BatchUnit{(uint32_t)j, q.k, (uint32_t)(c * chunk), chunk, ppl, 0,
                                           grp[j]});
         }
+        // Coarse ranges (about 32 entries) keep the task count of large batches
+        // low; a batch whose first wave would leave resident warps without a
+        // task even at the deepest layers takes the fine ranges (one head run
+        // each), which shorten each layer's critical path.
+        if (!B.blocks_per_sm) {
+            int dev = 0;
+            RR_CUDA(cudaGetDevice(&dev));
+            RR_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, dev));
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.blocks_per_sm, k_batch<2>, kW2 * 32, 0));
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.blocks_per_sm_wide, k_batch<4>,
+                                                                  kW2 * 32, 0));
+            B.blocks_per_sm = std::max(1, B.blocks_per_sm);
+            B.blocks_per_sm_wide = std::max(1, B.blocks_per_sm_wide);
+        }
+        const uint64_t resident_warps = (uint64_t)B.sms * B.blocks_per_sm * kW2;
         const uint64_t slot_bytes = slot_words_for(g, max_chunk) * 8;
         // as many slots as memory allows (up to every unit at once): units in
         // flight together hide each other's layer-to-layer dependencies
@@ -533,6 +591,10 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             {(uint64_t)units.size(), 4096ull, (budget - qbytes) / slot_bytes});
         nslots = std::max<uint32_t>(1, nslots);
         for (size_t i = 0; i < units.size(); ++i) units[i].slot = (uint32_t)(i % nslots);
+        uint64_t wave_tasks = 0;
+        for (size_t i = 0; i < std::min<size_t>(units.size(), nslots); ++i)
+            wave_tasks += (uint64_t)g.deep_list.nitems_coarse * (units[i].chunk / (32u * units[i].ppl));
+        const bool coarse = 2 * wave_tasks >= resident_warps;
 
         // segments in task order: wave, layer, unit; after a layer that writes
         // prefix state, the unit's carry fix-up segments (phase 1, phase 2)
@@ -575,7 +637,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                     if (l > u.k - 1) continue;
                     const uint32_t ngroups = u.chunk / (32u * u.ppl);
                     uint32_t kind;
-                    const uint32_t nt = layer_tasks(g, u.k, l, ngroups, &kind);
+                    const uint32_t nt = layer_tasks(g, u.k, l, ngroups, coarse, &kind);
                     if (nt == 0) continue;
                     emit(i, l, kind, nt, ngroups, 0);
                     if (writes_state(kind)) {
@@ -592,7 +654,6 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                       (uint32_t)si);
 
         // device buffers (kept by the graph and grown as needed)
-        BatchBuffers &B = g.batch;
         RR_CUDA(B.units.reserve(units.size() * sizeof(BatchUnit)));
         RR_CUDA(B.segs.reserve(std::max<size_t>(1, segs.size()) * sizeof(BatchSeg)));
         RR_CUDA(B.descs.reserve(descs.size() * sizeof(QueryDesc)));
@@ -602,30 +663,56 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         RR_CUDA(B.py.reserve(grp.size() * py_words * 8));
         RR_CUDA(B.pr2.reserve(std::max<uint64_t>(1, pr2w) * 8));
         RR_CUDA(B.pr2off.reserve(grp.size() * 8));
-        RR_CUDA(cudaMemcpyAsync(B.pr2off.p, pr2_off.data(), grp.size() * 8, cudaMemcpyHostToDevice, st));
         RR_CUDA(B.slots.reserve((size_t)nslots * slot_bytes));
         RR_CUDA(B.done.reserve(units.size() * 4));
         RR_CUDA(B.ctl.reserve(8));
         RR_CUDA(B.task_seg.reserve(std::max<size_t>(1, task_seg.size()) * 4));
-        if (!task_seg.empty())
-            RR_CUDA(cudaMemcpyAsync(B.task_seg.p, task_seg.data(), task_seg.size() * 4,
-                                    cudaMemcpyHostToDevice, st));
         if (!d_status) RR_CUDA(B.status.reserve((size_t)nq * 4));
         int32_t *status = d_status ? d_status : B.status.as<int32_t>();
         if (!d_status) RR_CUDA(cudaMemsetAsync(status, 0, (size_t)nq * 4, st));
         DevBuf &d_units = B.units, &d_segs = B.segs, &d_descs = B.descs, &d_zoff = B.zoff,
                &d_pyoff = B.pyoff, &d_z = B.z, &d_py = B.py, &d_slots = B.slots, &d_done = B.done,
                &d_ctl = B.ctl;
-        // pageable sources: each copy is staged before the call returns
-        RR_CUDA(cudaMemcpyAsync(d_units.p, units.data(), units.size() * sizeof(BatchUnit),
-                                cudaMemcpyHostToDevice, st));
-        if (!segs.empty())
-            RR_CUDA(cudaMemcpyAsync(d_segs.p, segs.data(), segs.size() * sizeof(BatchSeg),
-                                    cudaMemcpyHostToDevice, st));
-        RR_CUDA(cudaMemcpyAsync(d_descs.p, descs.data(), descs.size() * sizeof(QueryDesc),
-                                cudaMemcpyHostToDevice, st));
-        RR_CUDA(cudaMemcpyAsync(d_zoff.p, z_off.data(), grp.size() * 8, cudaMemcpyHostToDevice, st));
-        RR_CUDA(cudaMemcpyAsync(d_pyoff.p, py_off.data(), grp.size() * 8, cudaMemcpyHostToDevice, st));
+        {
+            // pack the plan into pinned staging memory and upload it asynchronously
+            struct Part {
+                const void *src;
+                size_t bytes;
+                void *dst;
+            } parts[] = {
+                {units.data(), units.size() * sizeof(BatchUnit), d_units.p},
+                {segs.data(), segs.size() * sizeof(BatchSeg), d_segs.p},
+                {descs.data(), descs.size() * sizeof(QueryDesc), d_descs.p},
+                {z_off.data(), grp.size() * 8, d_zoff.p},
+                {py_off.data(), grp.size() * 8, d_pyoff.p},
+                {pr2_off.data(), grp.size() * 8, B.pr2off.p},
+                {task_seg.data(), task_seg.size() * 4, B.task_seg.p},
+            };
+            size_t need = 0;
+            for (const Part &pt : parts) need += (pt.bytes + 255) / 256 * 256;
+            if (B.stage_pending) {
+                RR_CUDA(cudaEventSynchronize(B.stage_ev));
+                B.stage_pending = false;
+            }
+            if (need > B.h_cap) {
+                if (B.h_stage) cudaFreeHost(B.h_stage);
+                B.h_stage = nullptr;
+                B.h_cap = 0;
+                RR_CUDA(cudaMallocHost(&B.h_stage, need));
+                B.h_cap = need;
+            }
+            if (!B.stage_ev) RR_CUDA(cudaEventCreateWithFlags(&B.stage_ev, cudaEventDisableTiming));
+            size_t off = 0;
+            for (const Part &pt : parts) {
+                if (pt.bytes) {
+                    std::memcpy(B.h_stage + off, pt.src, pt.bytes);
+                    RR_CUDA(cudaMemcpyAsync(pt.dst, B.h_stage + off, pt.bytes, cudaMemcpyHostToDevice, st));
+                }
+                off += (pt.bytes + 255) / 256 * 256;
+            }
+            RR_CUDA(cudaEventRecord(B.stage_ev, st));
+            B.stage_pending = true;
+        }
         RR_CUDA(cudaMemsetAsync(d_done.p, 0, units.size() * 4, st));
         RR_CUDA(cudaMemsetAsync(d_ctl.p, 0, 8, st));
         for (uint32_t j : grp) RR_CUDA(cudaMemsetAsync(d_witness + (size_t)j * g.n, 0, (size_t)g.n * 8, st));
@@ -664,6 +751,31 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                                        (uint32_t)grp.size(), 1, st);
             if (fs != RR_OK) return fs;
         }
+        bool any2 = false, any3 = false;
+        for (uint32_t j : grp) {
+            any2 |= qs[j].k == 2;
+            any3 |= qs[j].k == 3;
+        }
+        if (any2 && g.m) {
+            const uint32_t m32 = (uint32_t)g.m;
+            const int t2 = timing_begin(st);
+            k_batch_first2<<<dim3(std::min<uint32_t>(2048, (m32 + 255) / 256), (unsigned)grp.size()), 256, 0,
+                             st>>>(d_descs.as<QueryDesc>(), d_z.as<uint64_t>(), d_zoff.as<uint64_t>(),
+                                   g.off.as<uint32_t>(), g.row_src.as<uint32_t>(), g.row_eid.as<uint32_t>(),
+                                   g.n, m32);
+            timing_end(t2, kTimeFirst, st);
+            RR_LAUNCHED();
+        }
+        if (any3 && g.win_list.count) {
+            const uint32_t cnt = (uint32_t)g.win_list.count;
+            const int t3 = timing_begin(st);
+            k_batch_last3<<<dim3(std::min<uint32_t>(2048, (cnt + 255) / 256), (unsigned)grp.size()), 256, 0,
+                            st>>>(list_ptrs(g.win_list, false), cnt, d_descs.as<QueryDesc>(),
+                                  d_z.as<uint64_t>(), d_zoff.as<uint64_t>(), d_py.as<uint64_t>(),
+                                  d_pyoff.as<uint64_t>(), g.n);
+            timing_end(t3, kTimeLast, st);
+            RR_LAUNCHED();
+        }
         k_batch_zero_rows<<<nslots, 256, 0, st>>>(d_slots.as<uint64_t>(), slot_bytes / 8,
                                                   (g.deep_list.count + 1) * max_chunk, nslots,
                                                   max_chunk);
@@ -671,11 +783,10 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
 
         BatchArgs a{};
         a.prod = prod;
-        a.state = list_ptrs(g.state_list, true);
-        a.win = list_ptrs(g.win_list, true);
-        a.tail = list_ptrs(g.tail_list, true);
-        a.deep = list_ptrs(g.deep_list, true);
-        a.tail3 = list_ptrs(g.tail3_list, true);
+        a.state = list_ptrs(g.state_list, coarse);
+        a.tail = list_ptrs(g.tail_list, coarse);
+        a.deep = list_ptrs(g.deep_list, coarse);
+        a.tail3 = list_ptrs(g.tail3_list, coarse);
         a.n = g.n;
         a.units = d_units.as<BatchUnit>();
         a.segs = d_segs.as<BatchSeg>();
@@ -698,13 +809,11 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         a.status = status;
         a.timeout_ns = 2000000000ull;
         if (total) {
-            int per_sm = 0, dev = 0, sms = 0;
-            RR_CUDA(cudaGetDevice(&dev));
-            RR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kW2 * 32, 0));
-            const unsigned blocks = (unsigned)std::max(1, sms * std::max(1, per_sm));
+            const unsigned blocks =
+                (unsigned)std::max(1, B.sms * (coarse ? B.blocks_per_sm_wide : B.blocks_per_sm));
             const int bslot = timing_begin(st);
-            k_batch<<<blocks, kW2 * 32, 0, st>>>(a);
+            if (coarse) k_batch<4><<<blocks, kW2 * 32, 0, st>>>(a);
+            else k_batch<2><<<blocks, kW2 * 32, 0, st>>>(a);
             timing_end(bslot, kTimeBatch, st);
             RR_LAUNCHED();
         }
@@ -713,6 +822,87 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                              256, 0, st>>>(g.n, d_descs.as<QueryDesc>());
             RR_LAUNCHED();
         }
+    }
+    return RR_OK;
+}
+
+// bitmap of the union of `rows` witness rows (row-major, n each)
+__global__ void k_union_bitmap(const uint64_t *__restrict__ W, uint32_t rows, uint32_t n,
+                               uint8_t *__restrict__ bm)
+{
+    const uint32_t nb = (n + 7) / 8;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        for (uint32_t i = 0; i < 8; ++i) {
+            const uint32_t v = b * 8 + i;
+            if (v >= n) break;
+            for (uint32_t r = 0; r < rows; ++r)
+                if (W[(size_t)r * n + v]) {
+                    bits |= 1u << i;
+                    break;
+                }
+        }
+        bm[b] = (uint8_t)bits;
+    }
+}
+
+// at-most-k (Algorithm 2 stopped at k): the exact-k' queries for k' = 2..k,
+// row k'-2 of d_witness each. They run concurrently, one lane (workspace and
+// stream) each, largest k' first and on the stream of highest priority, forked
+// from and joined back to `st`; if the
+// scratch of all of them does not fit 60% of free device memory they run in
+// order on the graph's own workspace instead.
+rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
+                        uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st)
+{
+    const uint32_t lanes = k - 1;
+    size_t free_b = 0, total_b = 0;
+    RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const uint64_t per_lane = (uint64_t)(0.6 * (double)(free_b + g.fan.bytes())) / lanes;
+    uint64_t need = 0;
+    for (uint32_t kk = 2; kk <= k; ++kk) {
+        const uint64_t b = query_scratch_bytes(g, kk, per_lane);
+        need = (b == UINT64_MAX || need == UINT64_MAX) ? UINT64_MAX : need + b;
+    }
+    if (need == UINT64_MAX) {
+        for (uint32_t kk = 2; kk <= k; ++kk) {
+            const rr_query q{source, kk, seed, nullptr};
+            rr_status s = reach_on_stream(g, g.ws, &q, nullptr, d_witness + (size_t)(kk - 2) * g.n, 0, st);
+            if (s != RR_OK) return s;
+        }
+    } else {
+        FanOut &F = g.fan;
+        if (!F.fork) RR_CUDA(cudaEventCreateWithFlags(&F.fork, cudaEventDisableTiming));
+        int prio_least = 0, prio_greatest = 0;
+        RR_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+        while (F.ws.size() < lanes) {
+            // lane j runs k' = k - j: the longest chain gets the highest priority
+            const int prio = std::min(prio_least, prio_greatest + (int)F.ws.size());
+            cudaStream_t s2 = nullptr;
+            cudaEvent_t e2 = nullptr;
+            RR_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio));
+            F.st.push_back(s2);
+            RR_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+            F.done.push_back(e2);
+            F.ws.emplace_back(new Workspace());
+        }
+        RR_CUDA(cudaEventRecord(F.fork, st));
+        for (uint32_t kk = k; kk >= 2; --kk) {
+            const uint32_t j = k - kk;  // lane
+            const rr_query q{source, kk, seed, nullptr};
+            RR_CUDA(cudaStreamWaitEvent(F.st[j], F.fork, 0));
+            rr_status s = reach_on_stream(g, *F.ws[j], &q, nullptr, d_witness + (size_t)(kk - 2) * g.n,
+                                          per_lane, F.st[j]);
+            RR_CUDA(cudaEventRecord(F.done[j], F.st[j]));
+            RR_CUDA(cudaStreamWaitEvent(st, F.done[j], 0));
+            if (s != RR_OK) return s;
+        }
+    }
+    if (d_bitmap) {
+        const uint32_t nb = (g.n + 7) / 8;
+        k_union_bitmap<<<std::max<uint32_t>(1, std::min<uint32_t>(1024, (nb + 255) / 256)), 256, 0, st>>>(
+            d_witness, k - 1, g.n, d_bitmap);
+        RR_LAUNCHED();
     }
     return RR_OK;
 }

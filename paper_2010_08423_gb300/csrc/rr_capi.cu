@@ -85,6 +85,8 @@ rr_status debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out
 rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
                        uint64_t *d_witness, int32_t *d_status, cudaStream_t st);
 rr_status autotune(Graph &g, uint32_t k, uint32_t *ppl, uint32_t *chunk);
+rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
+                        uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st);
 
 }  // namespace rr
 
@@ -184,6 +186,18 @@ rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t 
     }
     std::lock_guard<std::mutex> lk(g->mu);
     return batch_device(*g, qs, nq, d_bitmaps, d_witness, d_status, (cudaStream_t)stream);
+}
+
+rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,
+                                 uint8_t *d_bitmap, uint64_t *d_witness, void *stream)
+{
+    clear_error();
+    if (!g || !d_witness) return fail(RR_EINVAL, "rr_reach_atmost_device: NULL argument");
+    rr_query q{source, k, seed, nullptr};
+    rr_status s = validate_query(*g, &q);
+    if (s != RR_OK) return s;
+    std::lock_guard<std::mutex> lk(g->mu);
+    return atmost_device(*g, source, k, seed, d_bitmap, d_witness, (cudaStream_t)stream);
 }
 
 rr_status rr_autotune(rr_graph *g, uint32_t k, uint32_t *best_ppl, uint32_t *best_chunk)

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -153,9 +154,48 @@ struct RowList {
     }
 };
 
-// Device buffers of the persistent batched launch, kept per graph.
+// Device buffers of the persistent batched launch, kept per graph, and a
+// pinned staging area for the batch plan (reused once the event recorded
+// after its last upload has completed, so uploads never wait on the stream).
 struct BatchBuffers {
     DevBuf units, segs, descs, zoff, pyoff, z, py, slots, done, ctl, status, task_seg, pr2, pr2off;
+    char *h_stage = nullptr;
+    size_t h_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
+    bool stage_pending = false;
+    int blocks_per_sm = 0;       // occupancy of the persistent kernel (0 = not queried yet)
+    int blocks_per_sm_wide = 0;  // the same for its large-batch variant
+    int sms = 0;
+    ~BatchBuffers()
+    {
+        if (stage_ev) cudaEventDestroy(stage_ev);
+        if (h_stage) cudaFreeHost(h_stage);
+    }
+};
+
+// Lanes for single queries that run concurrently (the k' = 2..k queries of
+// at-most-k): a workspace and a stream per lane, forked from and joined back
+// to the caller's stream with events.
+struct FanOut {
+    std::vector<std::unique_ptr<Workspace>> ws;
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    size_t bytes() const
+    {
+        size_t b = 0;
+        for (const auto &w : ws) b += w->bytes();
+        return b;
+    }
+    ~FanOut()
+    {
+        for (cudaStream_t s : st) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        for (cudaEvent_t e : done) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+    }
 };
 
 // -------- graph ------------------------------------------------------------
@@ -206,6 +246,7 @@ struct Graph {
     mutable std::mutex mu;
     mutable Workspace ws;
     mutable BatchBuffers batch;
+    mutable FanOut fan;
     mutable cudaStream_t stream = nullptr;
 
     // tuning per k (index k): 0 = automatic; tune_gen changes on every update

@@ -195,7 +195,7 @@ rr_status rr_server_create(const rr_graph *g, uint64_t device_mem_budget, uint32
     // would serialise the device and stop queries from overlapping).
     const uint64_t share = s->budget / max_slots;
     uint64_t state_bytes = 0;
-    for (uint32_t k = 3; k <= 20; ++k) {
+    for (uint32_t k = 2; k <= 20; ++k) {
         const uint64_t b = query_scratch_bytes(*g, k, share);
         if (b == UINT64_MAX)
             return fail(RR_ENOMEM, "rr_server_create: budget too small for one point chunk per slot");

@@ -410,7 +410,7 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
 
 bool uses_v2(const Graph &g, uint32_t k)
 {
-    return g.compact && k >= 3;
+    return g.compact && k >= 2;
 }
 
 bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl_out,

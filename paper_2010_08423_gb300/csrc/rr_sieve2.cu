@@ -82,6 +82,20 @@ __global__ void __launch_bounds__(kW2 * 32) k_second_label(const V2Params p, uin
     second_label_warp(p, task, pr2);
 }
 
+__global__ void k_first2(const V2Params p, const uint32_t *__restrict__ off,
+                         const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ row_eid,
+                         uint32_t m)
+{
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
+        first2_closed(p, off, row_src, row_eid, r);
+}
+
+__global__ void k_last3(const V2Params p, uint32_t count)
+{
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+        last3_closed(p, e);
+}
+
 template <int LG>
 __global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
 {
@@ -119,8 +133,7 @@ static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st
     const unsigned blocks = blocks_for(tasks);
     if (src == 1) {
         if (out == 0) k_layer_v2<PPL, true, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
-        else if (out == 1) k_layer_v2<PPL, true, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
-        else k_layer_v2<PPL, true, 2><<<blocks, kW2 * 32, 0, st>>>(vp);
+        else k_layer_v2<PPL, true, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
     } else if (src == 2) {
         if (out == 0) k_layer_v2<PPL, false, 0, true><<<blocks, kW2 * 32, 0, st>>>(vp);
         else k_layer_v2<PPL, false, 1, true><<<blocks, kW2 * 32, 0, st>>>(vp);
@@ -128,7 +141,7 @@ static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st
         if (out == 0) k_layer_v2<PPL, false, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
         else k_layer_v2<PPL, false, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
     }
-    timing_end(tslot, out == 2 ? kTimeLast : (src == 1 ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid)), st);
+    timing_end(tslot, src == 1 ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid), st);
     RR_LAUNCHED();
     return RR_OK;
 }
@@ -150,10 +163,11 @@ static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, 
 {
     const uint64_t srows = g.state_list.count + 1;  // layer 2 (label space; k = 4 transformed)
     const uint64_t drows = g.deep_list.count + 1;   // layers >= 3
-    *py_w = (g.prod_list.count + 1 + 31) / 32 * 32;
-    *pr2_w = (srows * k + 31) / 32 * 32;
-    *full_w = drows * chunk;
-    *red_w = std::max(srows, drows) * v2_reduced_stride(ppl, chunk);
+    // k = 2 and k = 3 are closed forms: no per-point state
+    *py_w = k >= 3 ? (g.prod_list.count + 1 + 31) / 32 * 32 : 0;
+    *pr2_w = k >= 5 ? (srows * k + 31) / 32 * 32 : 0;
+    *full_w = k >= 4 ? drows * chunk : 0;
+    *red_w = k >= 4 ? std::max(srows, drows) * v2_reduced_stride(ppl, chunk) : 0;
 }
 
 uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
@@ -253,11 +267,32 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
     vp.ngroups = chunk / (32u * ppl);
     vp.npoints = 1u << k;
 
+    if (k == 2) {
+        // the only layer, in closed form
+        if (g.m) {
+            const int tslot = timing_begin(st);
+            k_first2<<<grid_cap(g.m, 256), 256, 0, st>>>(vp, g.off.as<uint32_t>(), g.row_src.as<uint32_t>(),
+                                                         g.row_eid.as<uint32_t>(), (uint32_t)g.m);
+            timing_end(tslot, kTimeFirst, st);
+            RR_LAUNCHED();
+            ++nk;
+        }
+        if (bitmap) {
+            k_bitmap_q<<<grid_cap((g.n + 7) / 8, 256), 256, 0, st>>>(g.n, d_desc);
+            RR_LAUNCHED();
+            ++nk;
+        }
+        if (kernels) *kernels = nk;
+        return RR_OK;
+    }
+
     // layer 1: scalar prefix (independent of the point chunk); zero rows
     RR_CUDA(cudaMemsetAsync(py, 0, 8, st));
-    RR_CUDA(cudaMemsetAsync(full0, 0, (size_t)chunk * 8, st));
-    RR_CUDA(cudaMemsetAsync(full1, 0, (size_t)chunk * 8, st));
-    RR_CUDA(cudaMemsetAsync(red, 0, (size_t)rstride * 8, st));
+    if (k >= 4) {
+        RR_CUDA(cudaMemsetAsync(full0, 0, (size_t)chunk * 8, st));
+        RR_CUDA(cudaMemsetAsync(full1, 0, (size_t)chunk * 8, st));
+        RR_CUDA(cudaMemsetAsync(red, 0, (size_t)rstride * 8, st));
+    }
     set_list(vp, g.prod_list, 0);
     vp.layer = 1;
     if (vp.nitems) {
@@ -287,18 +322,20 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
         }
     }
 
-    const uint64_t nchunks = ((1ull << k) + chunk - 1) / chunk;
+    if (k == 3 && g.win_list.count) {
+        // last layer in closed form (no sieve points)
+        set_list(vp, g.win_list, 0);
+        vp.layer = 2;
+        const int tslot = timing_begin(st);
+        k_last3<<<grid_cap(g.win_list.count, 256), 256, 0, st>>>(vp, (uint32_t)g.win_list.count);
+        timing_end(tslot, kTimeLast, st);
+        RR_LAUNCHED();
+        ++nk;
+    }
+    const uint64_t nchunks = k == 3 ? 0 : ((1ull << k) + chunk - 1) / chunk;
     for (uint64_t c = 0; c < nchunks; ++c) {
         vp.chunk_base = (uint32_t)(c * chunk);
         rr_status s = RR_OK;
-        if (k == 3) {
-            set_list(vp, g.win_list, 0);
-            vp.layer = 2;
-            s = ppl == 4 ? launch_v2<4>(vp, 1, 2, st) : launch_v2<2>(vp, 1, 2, st);
-            if (s != RR_OK) return s;
-            nk += vp.nitems ? 1 : 0;
-            continue;
-        }
         // layers 2 (k = 4) or 3 (k >= 5) .. k-2; the last of them writes the
         // transformed state
         uint64_t *bufs[2] = {full0, full1};

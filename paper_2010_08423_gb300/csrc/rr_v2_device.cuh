@@ -107,12 +107,69 @@ __device__ __forceinline__ void first_scalar_warp(const V2Params &p, uint32_t ta
 }
 
 // ---------------------------------------------------------------------------
-// Layers 2..k-2 (and the last layer when k = 3).
+// k = 2 without sieve points: layer 1 is the last layer, and summing
+// y_{e,1} x_s^L x_v^L over all L leaves the 2x2 permanent, so every edge
+// e = (s, v) adds y_{e,1} (z_{s,1} z_{v,2} + z_{s,2} z_{v,1}) to S[v]. One
+// thread per CSR row r; only rows leaving the source look up their head v
+// (the vertex with off[v] <= r < off[v+1], by bisection).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void first2_closed(const V2Params &p, const uint32_t *__restrict__ off,
+                                              const uint32_t *__restrict__ row_src,
+                                              const uint32_t *__restrict__ row_eid, uint32_t r)
+{
+    const uint32_t s = p.qd->source;
+    if (row_src[r] != s) return;
+    uint32_t lo = 0, hi = p.n;  // off[lo] <= r < off[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (off[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t v = lo;
+    const uint64_t perm = gf64_mul(zval(p, s, 0), zval(p, v, 1)) ^ gf64_mul(zval(p, s, 1), zval(p, v, 0));
+    const uint64_t val = gf64_mul(sm_draw(p.qd->key_y, (uint64_t)row_eid[r] * 32u), perm);  // y_{e,1}
+    if (val) atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + v), (unsigned long long)val);
+}
+
+// ---------------------------------------------------------------------------
+// The last layer when k = 3, without sieve points. With the scalar layer-1
+// prefix the layer-2 value of entry e (tail u, head v) at point L is
+// y_{e,2} Y_e x_s^L x_u^L x_v^L, Y_e = PY[a0] ^ PY[b0]. Summed over all L, a
+// product of k linear forms x_i^L = sum_{j in L} Z[i][j] gives the permanent
+// of Z: each map i -> j_i is counted once for every L holding its image, i.e.
+// 2^{k - |image|} times, which is odd only for the bijections. So entry e adds
+//     y_{e,2} Y_e perm(z_s; z_u; z_v)
+// to S[v], and only entries with Y_e != 0 (a source edge inside the window)
+// do any multiplication. One thread per entry.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void last3_closed(const V2Params &p, uint32_t ent)
+{
+    const uint64_t Y = p.py[p.ia[ent]] ^ p.py[p.ib[ent]];
+    if (!Y) return;
+    const uint32_t s = p.qd->source, u = p.src[ent], v = p.head[ent];
+    uint64_t a[3], b[3], c[3];
+#pragma unroll
+    for (uint32_t j = 0; j < 3; ++j) {
+        a[j] = zval(p, s, j);
+        b[j] = zval(p, u, j);
+        c[j] = zval(p, v, j);
+    }
+    // expansion along z_s: 2x2 permanents of (z_u, z_v) without column j
+    const uint64_t m0 = gf64_mul(b[1], c[2]) ^ gf64_mul(b[2], c[1]);
+    const uint64_t m1 = gf64_mul(b[0], c[2]) ^ gf64_mul(b[2], c[0]);
+    const uint64_t m2 = gf64_mul(b[0], c[1]) ^ gf64_mul(b[1], c[0]);
+    const uint64_t perm = gf64_mul(a[0], m0) ^ gf64_mul(a[1], m1) ^ gf64_mul(a[2], m2);
+    const uint64_t y = sm_draw(p.qd->key_y, (uint64_t)p.eid[ent] * 32u + 1u);  // y_{e,2}
+    const uint64_t val = gf64_mul(gf64_mul(y, Y), perm);
+    if (val) atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + v), (unsigned long long)val);
+}
+
+// ---------------------------------------------------------------------------
+// Layers 2..k-2.
 //   FROM_Y: window sum W^L = Y_e x_s^L x_u^L (layer 2), Y_e = PY[a0] ^ PY[b0];
 //   else  : W^L = state[a1] ^ state[b1] (layers >= 3).
 //   OUT 0: write the per-point prefix to the state row of the entry;
-//   OUT 1: write the group's transformed prefix (T_0..T_{lg-1}, V);
-//   OUT 2: XOR the per-vertex totals into S (last layer, k = 3).
+//   OUT 1: write the group's transformed prefix (T_0..T_{lg-1}, V).
 // One warp per (scheduling range, point group); lanes own PPL points each.
 // ---------------------------------------------------------------------------
 // COHERENT: state written earlier in the same launch is read through L2
@@ -129,7 +186,6 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     const uint32_t k = p.k;
     const uint32_t source = p.qd->source;
     const uint64_t key_y = p.qd->key_y;
-    uint64_t *const S = p.qd->S;
     const uint32_t col = group * (32u * PPL) + (uint32_t)lane * PPL;
     const uint32_t gbase = p.chunk_base + group * (32u * PPL);
     const uint32_t hi_bits = gbase >> LG;
@@ -162,23 +218,6 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         }
     };
     enter_head(cur);
-    bool any = false;
-
-    auto flush = [&](uint32_t v) {
-        if constexpr (OUT == 2) {
-            if constexpr (FROM_Y) {
-#pragma unroll
-                for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
-            }
-            uint64_t t = 0;
-#pragma unroll
-            for (int i = 0; i < PPL; ++i) t ^= acc[i];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) t ^= shfl64x(t, off);
-            if (lane == 0 && t) atomicXor(reinterpret_cast<unsigned long long *>(S + v),
-                                          (unsigned long long)t);
-        }
-    };
 
     for (uint32_t base = it.x; base < it.y; base += 32) {
         const uint32_t ent = base + lane;
@@ -199,10 +238,8 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         for (uint32_t t = 0; t < nb; ++t) {
             const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
             if (h != cur) {
-                if (any) flush(cur);
 #pragma unroll
                 for (int i = 0; i < PPL; ++i) acc[i] = R[i] = 0;
-                any = false;
                 cur = h;
                 enter_head(cur);
             }
@@ -216,11 +253,8 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 combine_labels<PPL>(gf64_mul(coef, zu), k, lane, hi_bits, r);
 #pragma unroll
                 for (int i = 0; i < PPL; ++i) R[i] ^= r[i];
-                if constexpr (OUT != 2) {
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
-                }
-                any = true;
+                for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
             } else if (a != b) {
                 const uint64_t coef = shfl64b(m_coef, (int)t);
                 uint64_t c[PPL], w[PPL];
@@ -256,7 +290,6 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 #pragma unroll
                 for (int i = 0; i < PPL; ++i)
                     acc[i] ^= valid[i] ? gf64_mul(c[i], w[i]) : 0ull;
-                any = true;
             }
             const size_t row = (size_t)base + t + 1;  // state row of this entry
             if constexpr (OUT == 0) {
@@ -304,7 +337,6 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
             }
         }
     }
-    if (any) flush(cur);
 }
 
 // ---------------------------------------------------------------------------

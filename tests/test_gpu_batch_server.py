@@ -143,3 +143,72 @@ def test_server_cancel_and_admission():
         with pytest.raises(capi.RRError) as ei:
             capi.rr_server_create(G.handle, 1 << 10, 1)
         assert ei.value.status == capi.RR_ENOMEM
+
+
+def test_atmost_k_union_and_rows():
+    """at-most-k (Algorithm 2 stopped at k): union of the exact-k' reach sets for
+    k' = 2..k, each row equal to the single query's witness and the oracle's."""
+    torch = _torch()
+    g = W.uniform(1500, 20_000, 20, 0, 5, 66)
+    n = g["n"]
+    k = 6
+    with capi.Graph(g) as G:
+        d_w = torch.zeros((k - 1, n), dtype=torch.int64, device="cuda")
+        d_bm = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        capi.rr_reach_atmost_device(G.handle, 3, k, 99, d_w, d_bm)
+        torch.cuda.synchronize()
+        w = d_w.cpu().numpy().view(np.uint64)
+        bm = d_bm.cpu().numpy()
+        union = np.zeros(n, dtype=bool)
+        for kk in range(2, k + 1):
+            ref = oracle.sieve(g, 3, kk, 99)
+            assert np.array_equal(w[kk - 2], ref), kk
+            reach, _, _ = oracle.dfs_paths(g, 3, kk)
+            assert np.array_equal(ref != 0, reach.astype(bool))
+            union |= reach.astype(bool)
+        got = np.array([(bm[v >> 3] >> (v & 7)) & 1 for v in range(n)], dtype=bool)
+        assert union.any() and np.array_equal(got, union)
+
+
+def test_atmost_lanes_reused_across_k():
+    """Successive at-most calls with different k reuse the concurrent lanes
+    (lane j runs k' = k - j), so each lane meets several query sizes; every row
+    must equal the single query's witness."""
+    torch = _torch()
+    g = W.uniform(2500, 30_000, 25, 0, 6, 67, ncolors=2)
+    n = g["n"]
+    with capi.Graph(g) as G:
+        st = torch.cuda.Stream()
+        for k, s, seed in ((8, 2, 5), (3, 7, 6), (10, 1, 7), (5, 2, 8)):
+            d_w = torch.full((k - 1, n), -1, dtype=torch.int64, device="cuda")
+            d_bm = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
+            capi.rr_reach_atmost_device(G.handle, s, k, seed, d_w, d_bm, st.cuda_stream)
+            st.synchronize()
+            w = d_w.cpu().numpy().view(np.uint64)
+            union = np.zeros(n, dtype=bool)
+            for kk in range(2, k + 1):
+                _, ref = G.reach(s, kk, seed)
+                assert np.array_equal(w[kk - 2], ref), (k, kk)
+                union |= ref != 0
+            bm = d_bm.cpu().numpy()
+            got = np.unpackbits(bm, bitorder="little")[:n].astype(bool)
+            assert np.array_equal(got, union), k
+            assert union.sum() > 10
+
+
+def test_large_batch_coarse_ranges_equal_single_queries():
+    """A batch large enough to run on the coarse scheduling ranges (about 32
+    entries a task) and the high-occupancy kernel variant: 64 mixed queries on
+    the n = 1e5, m = 1e6 graph, every row equal to the single query's."""
+    torch = _torch()
+    g = W.scale_uniform(ncolors=8)
+    qs = W.query_set(g, 64, 7, 11, 0x5EED0004, colored_every_other=True)
+    n = g["n"]
+    with capi.Graph(g) as G:
+        d_w = torch.zeros((len(qs), n), dtype=torch.int64, device="cuda")
+        capi.rr_reach_batch_device(G.handle, qs, d_w)
+        torch.cuda.synchronize()
+        w = d_w.cpu().numpy().view(np.uint64)
+        for i, q in enumerate(qs):
+            _, ref = G.reach(q["source"], q["k"], q["seed"], motif=q["motif"])
+            assert np.array_equal(w[i], ref), (i, q["k"])

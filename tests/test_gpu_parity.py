@@ -262,9 +262,9 @@ def test_full_size_dense_windows_full_witness():
         assert np.array_equal(w, ref)
 
 
-@pytest.mark.parametrize("k", [3, 4, 5, 9, 11])
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 9, 11])
 def test_engines_agree_across_k(k):
-    # compact graphs run the reduced-state engine for k >= 3, dense-flag graphs
+    # compact graphs run the reduced-state engine for k >= 2, dense-flag graphs
     # the per-point engine; both must equal the oracle (multi-chunk for k >= 10)
     g = _dense_uniform(800, 9_000, 12, 4, 70 + k, ncolors=2)
     ref = oracle.sieve(g, 1, k, 1000 + k)
@@ -357,3 +357,30 @@ def test_cut_hub_segments_carry_fixup():
     with _graph(g, capi.FLAG_DENSE_STATE) as G:
         _, w = G.reach(9, 6, 76)
         assert np.array_equal(w, oracle.sieve(g, 9, 6, 76))
+
+
+def test_k3_closed_form_cycles_and_parallel_edges():
+    """k = 3 sums its last layer in closed form (a 3x3 permanent per edge).
+    Walks s -> a -> s repeat z_s and must cancel; parallel edges carry distinct
+    y and must not; colored queries take z from the shade table."""
+    rng = np.random.default_rng(33)
+    n = 40
+    src, dst, t = [], [], []
+    for a in range(1, 12):
+        for rep in range(3):                      # parallel s -> a edges
+            src.append(0); dst.append(a); t.append(5 + rep)
+        src.append(a); dst.append(0); t.append(7)  # back to the source
+        for b in rng.integers(12, n, 4):
+            src.append(a); dst.append(int(b)); t.append(int(rng.integers(5, 10)))
+    g = {"n": n, "src": np.array(src, np.uint32), "dst": np.array(dst, np.uint32),
+         "t": np.array(t, np.uint32), "delta": np.full(n, 3, np.uint32),
+         "color": rng.integers(0, 2, n).astype(np.uint8)}
+    with _graph(g) as G:
+        for seed in (1, 2, 3):
+            _, w = G.reach(0, 3, seed)
+            ref = oracle.sieve(g, 0, 3, seed)
+            assert np.array_equal(w, ref)
+            assert w[0] == 0 and np.count_nonzero(ref) > 5
+            motif = [int(g["color"][0]), 0, 1]
+            _, w = G.reach(0, 3, seed, motif=motif)
+            assert np.array_equal(w, oracle.sieve(g, 0, 3, seed, motif=motif))
