@@ -67,12 +67,12 @@ def _load():
         lib.orc_ztable.argtypes = [u32, u32, u64, vp, vp, vp]
         lib.orc_sieve.restype = i32
         lib.orc_sieve.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, u32, u32, u64,
-                                  vp, u32, vp, vp, i32]
+                                  vp, u32, vp, vp, vp, i32]
         lib.orc_gf_det.restype = u64
         lib.orc_gf_det.argtypes = [u32, vp]
         lib.orc_dfs_paths.restype = u64
         lib.orc_dfs_paths.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, u32, u32, u64,
-                                      vp, vp]
+                                      vp, vp, vp, vp]
         lib.orc_max_threads.restype = i32
         lib.orc_max_threads.argtypes = []
         _lib = lib
@@ -151,11 +151,14 @@ def ztable(n: int, k: int, seed: int, color=None, motif=None) -> np.ndarray:
 # -- sieve and brute force -------------------------------------------------
 
 def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
-          per_mask: bool = False, threads: int = 0):
+          per_mask: bool = False, threads: int = 0, edges: bool = False):
     """Per-vertex sieve sums S (n uint64) over all 2^k points or ``masks``.
 
     ``graph`` is a mapping with n, src, dst, t, delta and optionally color.
-    Returns S, or (S, per_mask_sums[nmasks, n]) when per_mask is True.
+    Returns S, or (S, per_mask_sums[nmasks, n]) when per_mask is True, or
+    (S, E) when edges is True: E[e] (m uint64) is the sum over the points of
+    the last layer's value of input edge e (Algorithm 1's fine-grained output
+    before grouping by arrival time).
     """
     n = int(graph["n"])
     src, dst, t, delta = (_u32(graph[x]) for x in ("src", "dst", "t", "delta"))
@@ -169,22 +172,49 @@ def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
         nm = 1 << k
     S = np.zeros(n, dtype=np.uint64)
     pm = np.zeros((nm, n), dtype=np.uint64) if per_mask else None
+    E = np.zeros(m, dtype=np.uint64) if edges else None
     rc = _load().orc_sieve(n, m, _ptr(src), _ptr(dst), _ptr(t), _ptr(delta),
                            _ptr(color), _ptr(motif), source, k, seed,
                            _ptr(masks), 0 if masks is None else nm, _ptr(S),
-                           _ptr(pm), int(threads))
+                           _ptr(pm), _ptr(E), int(threads))
     if rc == 1:
         raise ValueError("orc_sieve: invalid input")
     if rc:
         raise MemoryError("orc_sieve: allocation failed")
+    if edges:
+        return S, E
     return (S, pm) if per_mask else S
 
 
+NO_ARRIVAL = 0xFFFFFFFF
+
+
+def arrival_times(graph, E) -> np.ndarray:
+    """R[v] (n uint32): the smallest time i such that the polynomial of the
+    walks ending at v at time i -- the XOR of E[e] over the edges e into v with
+    t_e = i -- is non-zero; NO_ARRIVAL if there is none (Algorithm 1's R)."""
+    n = int(graph["n"])
+    dst = np.asarray(graph["dst"], dtype=np.int64)
+    t = np.asarray(graph["t"], dtype=np.int64)
+    groups = {}
+    for e in range(dst.shape[0]):
+        key = (int(dst[e]), int(t[e]))
+        groups[key] = groups.get(key, 0) ^ int(E[e])
+    R = np.full(n, NO_ARRIVAL, dtype=np.uint32)
+    for (v, ti), val in groups.items():
+        if val and ti < R[v]:
+            R[v] = ti
+    return R
+
+
 def dfs_paths(graph, source: int, k: int, seed: int = 0, motif=None,
-              with_det: bool = False):
+              with_det: bool = False, with_edges: bool = False):
     """Exhaustive temporal DFS over restless k-vertex paths from ``source``.
 
-    Returns (reach[n] uint8, Sdet[n] uint64 or None, number_of_paths).
+    Returns (reach[n] uint8, Sdet[n] uint64 or None, number_of_paths), and
+    with_edges=True appends Edet[m] (the determinant sums split by the path's
+    last edge) and arrive[n] uint32 (earliest last-edge time of a path ending at
+    v, NO_ARRIVAL if none).
     """
     n = int(graph["n"])
     src, dst, t, delta = (_u32(graph[x]) for x in ("src", "dst", "t", "delta"))
@@ -193,9 +223,13 @@ def dfs_paths(graph, source: int, k: int, seed: int = 0, motif=None,
     motif = _u8(motif)
     reach = np.zeros(n, dtype=np.uint8)
     sdet = np.zeros(n, dtype=np.uint64) if with_det else None
+    edet = np.zeros(m, dtype=np.uint64) if with_edges else None
+    arrive = np.zeros(n, dtype=np.uint32) if with_edges else None
     cnt = _load().orc_dfs_paths(n, m, _ptr(src), _ptr(dst), _ptr(t), _ptr(delta),
                                 _ptr(color), _ptr(motif), source, k, seed,
-                                _ptr(reach), _ptr(sdet))
+                                _ptr(reach), _ptr(sdet), _ptr(edet), _ptr(arrive))
     if cnt == (1 << 64) - 1:
         raise ValueError("orc_dfs_paths: invalid input")
+    if with_edges:
+        return reach, sdet, int(cnt), edet, arrive
     return reach, sdet, int(cnt)

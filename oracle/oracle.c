@@ -246,6 +246,7 @@ static void orc_free_inlists(orc_inlists *L)
  *   P_l^L[e]   = y_{e,l} * x_{v_e}^L * sum_{f : v_f = u_e, t_f <= t_e <= t_f + delta(u_e)} P_{l-1}^L[f]
  *                                                                  (Eq. (1), l = 2..k-1)
  *   out[v]    ^= sum_{e : v_e = v} P_{k-1}^L[e]
+ *   eout[e]   ^= P_{k-1}^L[e]            (if eout is not NULL)
  * P_l^L[e] is the evaluation of all restless walks with l edges whose last
  * edge is e, i.e. Eq. (1)'s chi_{v_e, l+1, t_e} restricted to edge e.
  */
@@ -253,7 +254,7 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
                           const uint32_t *t, const uint32_t *delta, const orc_inlists *IN,
                           uint32_t s, uint32_t k, uint64_t seed, const uint64_t *z,
                           uint32_t mask, uint64_t *x, uint64_t *prev, uint64_t *cur,
-                          uint64_t *out)
+                          uint64_t *out, uint64_t *eout)
 {
     for (uint64_t u = 0; u < n; ++u) {
         uint64_t acc = 0;
@@ -287,6 +288,9 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
     }
     for (uint64_t e = 0; e < m; ++e)
         out[dst[e]] ^= prev[e];
+    if (eout)
+        for (uint64_t e = 0; e < m; ++e)
+            eout[e] ^= prev[e];
 }
 
 /*
@@ -301,6 +305,11 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
  *                              2^k points 0..2^k-1
  *   S                          out, n values: XOR over the evaluated points
  *   per_mask                   optional out, nmasks*n values (row p = point masks[p])
+ *   E                          optional out, m values: for every edge e the XOR over
+ *                              the evaluated points of P_{k-1}^L[e] (the walks of k
+ *                              vertices whose last edge is e; Algorithm 1's
+ *                              per-time polynomials are the sums of E over the
+ *                              edges into u at time i)
  *   nthreads                   OpenMP threads over sieve points (0 = default)
  *
  * Returns 0 on success, 1 on invalid input, 2 on allocation failure.
@@ -309,7 +318,7 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
               const uint32_t *t, const uint32_t *delta, const uint8_t *color,
               const uint8_t *motif, uint32_t s, uint32_t k, uint64_t seed,
               const uint32_t *masks, uint32_t nmasks, uint64_t *S, uint64_t *per_mask,
-              int nthreads)
+              uint64_t *E, int nthreads)
 {
     if (k < 2 || k > 20 || s >= n)
         return 1;
@@ -330,6 +339,8 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
         return 2;
     }
     memset(S, 0, (size_t)n * sizeof(uint64_t));
+    if (E)
+        memset(E, 0, (size_t)m * sizeof(uint64_t));
     int fail = 0;
 #ifdef _OPENMP
     if (nthreads > 0)
@@ -344,7 +355,8 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
         uint64_t *cur = (uint64_t *)malloc((size_t)m * sizeof(uint64_t) + 8);
         uint64_t *acc = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
         uint64_t *one = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
-        if (!x || !prev || !cur || !acc || !one) {
+        uint64_t *eacc = E ? (uint64_t *)calloc((size_t)m + 1, sizeof(uint64_t)) : NULL;
+        if (!x || !prev || !cur || !acc || !one || (E && !eacc)) {
 #pragma omp atomic write
             fail = 1;
         } else {
@@ -353,21 +365,27 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                 uint32_t mask = masks ? masks[p] : (uint32_t)p;
                 memset(one, 0, (size_t)n * sizeof(uint64_t));
                 orc_one_point(n, m, src, dst, t, delta, &IN, s, k, seed, z, mask, x, prev,
-                              cur, one);
+                              cur, one, eacc);
                 for (uint32_t v = 0; v < n; ++v)
                     acc[v] ^= one[v];
                 if (per_mask)
                     memcpy(per_mask + (size_t)p * n, one, (size_t)n * sizeof(uint64_t));
             }
 #pragma omp critical
-            for (uint32_t v = 0; v < n; ++v)
-                S[v] ^= acc[v];
+            {
+                for (uint32_t v = 0; v < n; ++v)
+                    S[v] ^= acc[v];
+                if (E)
+                    for (uint64_t e = 0; e < m; ++e)
+                        E[e] ^= eacc[e];
+            }
         }
         free(x);
         free(prev);
         free(cur);
         free(acc);
         free(one);
+        free(eacc);
     }
     orc_free_inlists(&IN);
     free(z);
@@ -441,6 +459,8 @@ typedef struct {
     uint32_t need[256];/* remaining colour counts (motif) */
     uint8_t *reach;    /* out: n */
     uint64_t *Sdet;    /* out: n (may be NULL) */
+    uint64_t *Edet;    /* out: m, by last edge (may be NULL) */
+    uint32_t *arrive;  /* out: n, earliest last-edge time (may be NULL) */
     uint64_t *mat;     /* k*k scratch */
     uint64_t npaths;
 } orc_dfs;
@@ -450,9 +470,12 @@ static void orc_dfs_emit(orc_dfs *D)
 {
     uint32_t k = D->k;
     uint32_t end = D->pathv[k - 1];
+    uint64_t last = D->pathe[k - 2];
     D->reach[end] = 1;
     D->npaths++;
-    if (!D->Sdet)
+    if (D->arrive && D->t[last] < D->arrive[end])
+        D->arrive[end] = D->t[last];
+    if (!D->Sdet && !D->Edet)
         return;
     /* weight = prod_l y_{e_l, l} * det(Z_P), Z_P[i][j] = z_{u_i, j} */
     uint64_t w = 1;
@@ -462,7 +485,10 @@ static void orc_dfs_emit(orc_dfs *D)
         for (uint32_t j = 0; j < k; ++j)
             D->mat[i * k + j] = D->z[(uint64_t)D->pathv[i] * k + j];
     w = orc_gf_mul(w, orc_gf_det(k, D->mat));
-    D->Sdet[end] ^= w;
+    if (D->Sdet)
+        D->Sdet[end] ^= w;
+    if (D->Edet)
+        D->Edet[last] ^= w;
 }
 
 static void orc_dfs_rec(orc_dfs *D, uint32_t depth /* vertices so far */)
@@ -508,13 +534,18 @@ static void orc_dfs_rec(orc_dfs *D, uint32_t depth /* vertices so far */)
  *   (non-surjective label maps are counted an even number of times), which
  *   equals det(Z_P); walks that repeat a vertex give equal rows and vanish.
  *   So Sdet must equal orc_sieve's S bit for bit.
+ *   Edet (optional, m) = the same sum split by the path's last edge, which
+ *   must equal orc_sieve's E bit for bit.
+ *   arrive (optional, n) = the earliest time of a path's last edge among the
+ *   paths ending at v (UINT32_MAX if none): the minimum reachability time R_v
+ *   of Algorithm 1, found without any sieve.
  *
  * Returns the number of paths found (saturating), or (uint64)-1 on bad input.
  */
 uint64_t orc_dfs_paths(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                        const uint32_t *t, const uint32_t *delta, const uint8_t *color,
                        const uint8_t *motif, uint32_t s, uint32_t k, uint64_t seed,
-                       uint8_t *reach, uint64_t *Sdet)
+                       uint8_t *reach, uint64_t *Sdet, uint64_t *Edet, uint32_t *arrive)
 {
     if (k < 2 || k > 31 || s >= n)
         return (uint64_t)-1;
@@ -543,13 +574,21 @@ uint64_t orc_dfs_paths(uint32_t n, uint64_t m, const uint32_t *src, const uint32
     D.ostart = ostart;
     D.oedge = oedge;
     uint64_t *z = NULL;
-    if (Sdet) {
+    if (Sdet || Edet) {
         z = (uint64_t *)malloc((size_t)n * k * sizeof(uint64_t) + 8);
         orc_ztable(n, k, seed, color, motif, z);
-        memset(Sdet, 0, (size_t)n * sizeof(uint64_t));
     }
+    if (Sdet)
+        memset(Sdet, 0, (size_t)n * sizeof(uint64_t));
+    if (Edet)
+        memset(Edet, 0, (size_t)m * sizeof(uint64_t));
+    if (arrive)
+        for (uint32_t v = 0; v < n; ++v)
+            arrive[v] = UINT32_MAX;
     D.z = z;
     D.Sdet = Sdet;
+    D.Edet = Edet;
+    D.arrive = arrive;
     D.pathv = (uint32_t *)malloc(k * sizeof(uint32_t));
     D.pathe = (uint64_t *)malloc(k * sizeof(uint64_t));
     D.onpath = (uint8_t *)calloc(n, 1);

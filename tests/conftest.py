@@ -16,6 +16,17 @@ def pytest_configure(config):
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
+def read_arrivals(name):
+    """The 'arrival k v t' lines of a fixture: {k: {v: t}}."""
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            f = line.split("#", 1)[0].split()
+            if f and f[0] == "arrival":
+                out.setdefault(int(f[1]), {})[int(f[2])] = int(f[3])
+    return out
+
+
 def read_fixture(name):
     """Graph plus the 'source', 'expect k v...' and 'motif' lines of a fixture."""
     from paper_2010_08423_gb300.workloads import load_edge_fixture

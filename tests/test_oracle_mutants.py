@@ -3,7 +3,8 @@
 Each case plants one mistake in a temporary copy of oracle/oracle.c (the
 committed oracle is never modified), builds it, and checks that at least one
 of the pins -- the field's closed forms, the paper's figures, the
-determinant identity -- fails on it, while the unmodified copy passes them all.
+determinant identity and its split by last edge -- fails on it, while the
+unmodified copy passes them all.
 """
 import ctypes
 import os
@@ -37,6 +38,7 @@ MUTANTS = {
     "label bit shifted": ("if ((mask >> (j - 1)) & 1U)\n                acc ^= z[u * k + (j - 1)];",
                           "if ((mask >> j) & 1U)\n                acc ^= z[u * k + (j - 1)];"),
     "wrong reduction constant": ("#define ORC_POLY_LOW 0x1BULL", "#define ORC_POLY_LOW 0x1DULL"),
+    "edge sums overwritten per point": ("            eout[e] ^= prev[e];", "            eout[e] = prev[e];"),
 }
 
 
@@ -83,6 +85,19 @@ def _pins_fail(libpath) -> list:
             _, sdet, _ = oracle.dfs_paths(g, s, k, seed, with_det=True)
             if not np.array_equal(S, sdet):
                 failures.append("determinant identity")
+                break
+        # the same identity split by last edge (fine-grained outputs)
+        rng = random.Random(19)
+        for gi in range(30):
+            g = W.tiny_random(3100 + gi, n=rng.randint(3, 7), m=rng.randint(4, 16),
+                              tau=rng.randint(1, 5), dmax=rng.randint(0, 3))
+            s = rng.randrange(g["n"])
+            k = rng.randint(2, min(5, g["n"]))
+            seed = rng.getrandbits(64)
+            _, E = oracle.sieve(g, s, k, seed, edges=True)
+            _, _, _, edet, _ = oracle.dfs_paths(g, s, k, seed, with_det=True, with_edges=True)
+            if not np.array_equal(E, edet):
+                failures.append("edge determinant identity")
                 break
     finally:
         oracle._lib = saved
