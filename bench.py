@@ -324,6 +324,44 @@ def atmost_metrics(capi, torch, g, k=10, reps=5):
             "value": sum(2 ** kk * kk * m for kk in range(2, k + 1)) / (t_atm / 1e3), "unit": UNIT}
 
 
+def fine_metrics(capi, torch, g, k=K, reps=10):
+    """Fine-grained oracle (Algorithm 1 with per-time outputs: per-edge sums,
+    minimum arrival time R, set D) against the plain query on the benchmark
+    graph and query."""
+    n, m = g["n"], len(g["src"])
+    with capi.Graph(g) as G:
+        st = torch.cuda.Stream()
+        d_w = torch.zeros(n, dtype=torch.int64, device="cuda")
+        d_e = torch.zeros(m, dtype=torch.int64, device="cuda")
+        d_r = torch.zeros(n, dtype=torch.int32, device="cuda")
+        d_b = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        for i in range(3):
+            capi.rr_reach_arrival_device(G.handle, SOURCE, k, 1 + i, d_w, d_r, d_e, d_b, st.cuda_stream)
+            capi.rr_reach_device(G.handle, SOURCE, k, 1 + i, d_w, None, st.cuda_stream)
+        st.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(st):
+            e[0].record(st)
+            for i in range(reps):
+                capi.rr_reach_arrival_device(G.handle, SOURCE, k, 7 + i, d_w, d_r, d_e, d_b,
+                                             st.cuda_stream)
+            e[1].record(st)
+            e[2].record(st)
+            for i in range(reps):
+                capi.rr_reach_device(G.handle, SOURCE, k, 7 + i, d_w, None, st.cuda_stream)
+            e[3].record(st)
+            st.synchronize()
+        t_fine = e[0].elapsed_time(e[1]) / reps
+        t_plain = e[2].elapsed_time(e[3]) / reps
+        R = d_r.cpu().numpy().view(np.uint32)
+    reached = R != 0xFFFFFFFF
+    return {"k": k, "fine_ms": t_fine, "plain_ms": t_plain, "time_ratio": t_fine / t_plain,
+            "vertices_with_arrival": int(reached.sum()),
+            "median_arrival": float(np.median(R[reached])) if reached.any() else None,
+            "value": units_per_query(k, m) / (t_fine / 1e3), "unit": UNIT,
+            "outputs": "witness S, per-edge sums E (m), minimum arrival R (n), set D"}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -520,6 +558,7 @@ def main():
         line["batched"] = batched_metrics(capi, torch, gc)
         line["served"] = served_metrics(capi, g)
         line["atmost_k"] = atmost_metrics(capi, torch, g)
+        line["fine_grained"] = fine_metrics(capi, torch, g)
         line["motif_powerlaw"] = motif_metrics(capi, torch)
         g5 = W.served_powerlaw()
         line["served_powerlaw"] = served_metrics(

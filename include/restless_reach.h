@@ -158,6 +158,27 @@ rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t 
                                 uint8_t *d_bitmaps, uint64_t *d_witness, int32_t *d_status,
                                 void *stream);
 
+/* rr_reach_arrival_device: the fine-grained decision oracle (Algorithm 1; Sec.
+ * "A fine-grained decision oracle") for one query. Algorithm 1 keeps a
+ * polynomial per (vertex u, time i) for the walks of k vertices ending at u
+ * with a last edge at time i; here that polynomial is the XOR of the per-edge
+ * sums over the edges into u at time i.
+ *   d_witness   (n uint64, device, required) per-vertex sums, as rr_reach_device;
+ *   d_edge_sums (m uint64, device, may be NULL) for every input edge e, the sum
+ *               over all 2^k sieve points of e's last-layer value (the walks of
+ *               k vertices whose last edge is e);
+ *   d_arrival   (n uint32, device, required) R_u = the smallest i whose
+ *               polynomial is non-zero, UINT32_MAX if there is none (the minimum
+ *               reachability time of Algorithm 1);
+ *   d_bitmap    (ceil(n/8) bytes, device, may be NULL) Algorithm 1's D: bit u set
+ *               iff R_u < UINT32_MAX.
+ * Enqueued on `stream`. Without d_edge_sums the library keeps an m * 8-byte
+ * buffer with the graph. Errors: RR_EINVAL for a NULL required argument or an
+ * invalid query (as rr_reach_device); RR_ENOMEM, RR_ECUDA as rr_reach_device. */
+rr_status rr_reach_arrival_device(const rr_graph *g, const rr_query *q, uint64_t *d_witness,
+                                  uint64_t *d_edge_sums, uint32_t *d_arrival, uint8_t *d_bitmap,
+                                  void *stream);
+
 /* rr_reach_atmost_device: at-most-k-RestlessReach (Sec. "Discussion"; Algorithm 2
  * with its loop over k' stopped at k): the plain queries (source, k', seed) for
  * k' = 2..k. d_witness ((k-1) * n uint64, device) gets the witness of k' in row

@@ -57,6 +57,7 @@ EXPORTED = [
     "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
+    "rr_reach_arrival_device",
 ]
 
 _lib = None
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_device_noalloc": [vp, pq, vp, vp, vp],
         "rr_reach_batch_device": [vp, pq, u32, vp, vp, vp, vp],
         "rr_reach_atmost_device": [vp, u32, u32, u64, vp, vp, vp],
+        "rr_reach_arrival_device": [vp, pq, vp, vp, vp, vp, vp],
         "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
         "rr_server_destroy": [vp],
         "rr_query_submit": [vp, pq, ctypes.POINTER(u64)],
@@ -210,6 +212,19 @@ def rr_reach_batch_device(g, queries, d_witness, d_bitmaps=None, d_status=None, 
     arr, keep = _query_array(queries)
     _check(load().rr_reach_batch_device(g, arr, len(queries), _dp(d_bitmaps), _dp(d_witness),
                                         _dp(d_status), _dp(stream)))
+    del keep
+
+
+NO_ARRIVAL = 0xFFFFFFFF
+
+
+def rr_reach_arrival_device(g, source, k, seed, d_witness, d_arrival, d_edge_sums=None,
+                            d_bitmap=None, stream=None, motif=None):
+    """Fine-grained oracle: witness (n), minimum arrival time R (n uint32,
+    NO_ARRIVAL if none), optional per-edge sums (m) and bitmap of R < NO_ARRIVAL."""
+    q, keep = make_query(source, k, seed, motif)
+    _check(load().rr_reach_arrival_device(g, ctypes.byref(q), _dp(d_witness), _dp(d_edge_sums),
+                                          _dp(d_arrival), _dp(d_bitmap), _dp(stream)))
     del keep
 
 
@@ -343,6 +358,22 @@ class Graph:
 
     def point_sums(self, source, k, seed, masks, motif=None):
         return rr_debug_point_sums(self.handle, self.n, source, k, seed, masks, motif)
+
+    def arrival(self, source, k, seed, motif=None):
+        """Fine-grained oracle on the current CUDA device: returns host arrays
+        (witness[n] uint64, edge_sums[m] uint64, arrival[n] uint32, bitmap)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        d_w = torch.empty(self.n, dtype=torch.int64, device=dev)
+        d_e = torch.empty(max(1, self.m), dtype=torch.int64, device=dev)
+        d_r = torch.empty(self.n, dtype=torch.int32, device=dev)
+        d_b = torch.empty((self.n + 7) // 8, dtype=torch.uint8, device=dev)
+        st = torch.cuda.current_stream(dev)
+        rr_reach_arrival_device(self.handle, source, k, seed, d_w, d_r, d_e, d_b,
+                                st.cuda_stream, motif)
+        st.synchronize()
+        return (d_w.cpu().numpy().view(np.uint64), d_e.cpu().numpy().view(np.uint64)[:self.m],
+                d_r.cpu().numpy().view(np.uint32), d_b.cpu().numpy())
 
     def close(self):
         if self.handle:

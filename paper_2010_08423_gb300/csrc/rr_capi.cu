@@ -87,6 +87,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
 rr_status autotune(Graph &g, uint32_t k, uint32_t *ppl, uint32_t *chunk);
 rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st);
+rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness, uint64_t *d_E,
+                         uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st);
 
 }  // namespace rr
 
@@ -186,6 +188,20 @@ rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t 
     }
     std::lock_guard<std::mutex> lk(g->mu);
     return batch_device(*g, qs, nq, d_bitmaps, d_witness, d_status, (cudaStream_t)stream);
+}
+
+rr_status rr_reach_arrival_device(const rr_graph *g, const rr_query *q, uint64_t *d_witness,
+                                  uint64_t *d_edge_sums, uint32_t *d_arrival, uint8_t *d_bitmap,
+                                  void *stream)
+{
+    clear_error();
+    if (!g || !q) return fail(RR_EINVAL, "rr_reach_arrival_device: NULL graph or query");
+    if (!d_witness || !d_arrival)
+        return fail(RR_EINVAL, "rr_reach_arrival_device: d_witness and d_arrival are required");
+    rr_status s = validate_query(*g, q);
+    if (s != RR_OK) return s;
+    std::lock_guard<std::mutex> lk(g->mu);
+    return arrival_device(*g, q, d_witness, d_edge_sums, d_arrival, d_bitmap, (cudaStream_t)stream);
 }
 
 rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,

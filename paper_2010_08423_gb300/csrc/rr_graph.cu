@@ -566,7 +566,7 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     if (m == 0) {
         RR_CUDA(cudaMemsetAsync(g->off.p, 0, (size_t)(n + 1) * 4, st));
     } else {
-        DevBuf d_src, d_dst, d_t, key_in, key_out, val_in, row_t, row_dst, tmp;
+        DevBuf d_src, d_dst, d_t, key_in, key_out, val_in, tmp;
         RR_CUDA(d_src.reserve(mb * 4));
         RR_CUDA(d_dst.reserve(mb * 4));
         RR_CUDA(d_t.reserve(mb * 4));
@@ -595,15 +595,15 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
         val_in.release();
         d_dst.release();
         d_t.release();
-        RR_CUDA(row_t.reserve(mb * 4));
-        RR_CUDA(row_dst.reserve(mb * 4));
+        RR_CUDA(g->row_t.reserve(mb * 4));
+        RR_CUDA(g->row_head.reserve(mb * 4));
         k_unpack_rows<<<grid_for(m, 256), 256, 0, st>>>(
             key_out.as<uint64_t>(), g->row_eid.as<uint32_t>(), d_src.as<uint32_t>(), m,
-            row_t.as<uint32_t>(), row_dst.as<uint32_t>(), g->row_src.as<uint32_t>());
+            g->row_t.as<uint32_t>(), g->row_head.as<uint32_t>(), g->row_src.as<uint32_t>());
         RR_LAUNCHED();
         key_out.release();
         d_src.release();
-        k_offsets<<<grid_for(m + 1, 256), 256, 0, st>>>(row_dst.as<uint32_t>(), m, n,
+        k_offsets<<<grid_for(m + 1, 256), 256, 0, st>>>(g->row_head.as<uint32_t>(), m, n,
                                                         g->off.as<uint32_t>());
         RR_LAUNCHED();
 
@@ -613,7 +613,7 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
         RR_CUDA(diff.reserve((mb + 1) * 4));
         RR_CUDA(cudaMemsetAsync(diff.p, 0, (mb + 1) * 4, st));
         k_windows<<<grid_for(m, 256), 256, 0, st>>>(
-            row_t.as<uint32_t>(), g->row_src.as<uint32_t>(), g->off.as<uint32_t>(),
+            g->row_t.as<uint32_t>(), g->row_src.as<uint32_t>(), g->off.as<uint32_t>(),
             d_delta.as<uint32_t>(), m, g->row_lo.as<uint32_t>(), g->row_hi.as<uint32_t>(),
             diff.as<int32_t>(), counter.as<unsigned long long>());
         RR_LAUNCHED();
@@ -659,7 +659,7 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
         g->state_rows = 1ull + last_rank;
         g->window_rows = nonempty;
         g->producer_window_rows = prod_window;
-        rr_status ls = build_lists_v2(*g, row_dst.as<uint32_t>(), tprod.as<uint32_t>(), st);
+        rr_status ls = build_lists_v2(*g, g->row_head.as<uint32_t>(), tprod.as<uint32_t>(), st);
         if (ls != RR_OK) return ls;
     }
 

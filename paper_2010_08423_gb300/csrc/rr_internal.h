@@ -76,6 +76,7 @@ struct QueryDesc {
     uint64_t key_y, key_z, key_g, key_o;
     uint64_t *S;        // witness output (n)
     uint8_t *bitmap;    // bitmap output or null
+    uint64_t *E;        // per-edge last-layer sums (m, by input edge index) or null
     uint32_t shades[512];  // first shade [0..255], multiplicity [256..511]
 };
 
@@ -89,6 +90,7 @@ struct Workspace {
     DevBuf shade;   // 512 uint32
     DevBuf bitmap;  // ceil(n/8)
     DevBuf desc;    // QueryDesc
+    DevBuf edges;   // m * 8: per-edge sums (fine-grained output) when the caller gives none
     cudaStream_t capture = nullptr;           // stream used only to capture graphs
     std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs;
     std::vector<uint64_t> graph_kernels;      // kernel nodes per cached graph
@@ -106,7 +108,7 @@ struct Workspace {
     uint64_t shape_gen[32] = {0};
     size_t bytes() const
     {
-        return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes + desc.bytes;
+        return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes + desc.bytes + edges.bytes;
     }
     void drop_graphs()
     {
@@ -228,6 +230,8 @@ struct Graph {
     DevBuf row_src;  // m uint32
     DevBuf row_lo;   // m uint32 (debug / tests)
     DevBuf row_hi;   // m uint32
+    DevBuf row_t;    // m uint32: time of the row's edge
+    DevBuf row_head; // m uint32: head v of the row (the row lies in v's segment)
     DevBuf color;    // n uint8 (if coloured)
     DevBuf items;    // uint2 (v0, v1) vertex ranges, largest first
     uint32_t nitems = 0;
@@ -257,7 +261,8 @@ struct Graph {
     size_t device_bytes() const
     {
         return off.bytes + row_a.bytes + row_b.bytes + row_s.bytes + row_eid.bytes +
-               row_src.bytes + row_lo.bytes + row_hi.bytes + color.bytes + items.bytes +
+               row_src.bytes + row_lo.bytes + row_hi.bytes + row_t.bytes + row_head.bytes +
+               color.bytes + items.bytes +
                prod_list.bytes() + state_list.bytes() + win_list.bytes() + tail_list.bytes() +
                deep_list.bytes() + tail3_list.bytes();
     }
@@ -292,14 +297,18 @@ rr_status launch_bitmap(const uint64_t *d_S, uint32_t n, uint8_t *d_bitmap, cuda
 
 // Runs all chunks and layers of one query; d_S must be zeroed by the caller
 // unless debug masks are given (then d_out = nmasks*n, zeroed by the caller).
+// d_E (m, zeroed by the caller, or null) gets the per-edge sums of the last layer.
 rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_z,
                            uint64_t *d_state, uint32_t ppl, uint32_t chunk, uint64_t *d_S,
                            const uint32_t *d_masks, uint32_t nmasks, uint64_t *d_debug_out,
-                           cudaStream_t st);
+                           cudaStream_t st, uint64_t *d_E = nullptr);
 // Runs one query on `st` with scratch `ws`; d_witness (n) required. `budget`
-// bounds the state buffers (0 = 60% of free device memory).
+// bounds the state buffers (0 = 60% of free device memory). d_E (m, zeroed by
+// the caller, or null) gets for every input edge the sum over all sieve points
+// of its last-layer value.
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
-                          uint64_t *d_witness, uint64_t budget, cudaStream_t st);
+                          uint64_t *d_witness, uint64_t budget, cudaStream_t st,
+                          uint64_t *d_E = nullptr);
 // Bytes of scratch one query of size k needs with the shape chosen for budget.
 uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
 
@@ -315,7 +324,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels);
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
-                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st);
+                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st,
+                   uint64_t *d_E = nullptr);
 
 }  // namespace rr
 

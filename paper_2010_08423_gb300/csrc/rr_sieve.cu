@@ -39,6 +39,7 @@ struct LayerParams {
     const uint64_t *st_in;
     uint64_t *st_out;
     uint64_t *S;                // last layer: per-vertex XOR target
+    uint64_t *E;                // last layer: per-edge XOR target (m, by input edge) or null
     const uint32_t *masks;      // mask-list mode: point p is masks[p]
     uint64_t *dbg_out;          // mask-list mode, last layer: out[p * n + v]
 };
@@ -176,10 +177,24 @@ k_layer(const LayerParams p)
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) w[i] = wa[i] ^ wb[i];
                 }
+                uint64_t dsum = 0;  // this row's own sum over the lane's points
 #pragma unroll
-                for (int i = 0; i < PPL; ++i)
-                    acc[i] ^= valid[i] ? gf64_mul(w[i], c[i]) : 0ull;
+                for (int i = 0; i < PPL; ++i) {
+                    const uint64_t inc = valid[i] ? gf64_mul(w[i], c[i]) : 0ull;
+                    acc[i] ^= inc;
+                    dsum ^= inc;
+                }
                 any = true;
+                if constexpr ((MODE & kLast) != 0 && !MASKLIST) {
+                    if (p.E) {
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1)
+                            dsum ^= __shfl_xor_sync(0xffffffffu, (unsigned long long)dsum, off);
+                        if (lane == 0 && dsum)
+                            atomicXor(reinterpret_cast<unsigned long long *>(p.E + eid),
+                                      (unsigned long long)dsum);
+                    }
+                }
             }
             if constexpr ((MODE & kLast) == 0) store_pts<PPL>(p.st_out + (size_t)rs * p.chunk + col, acc);
         }
@@ -361,7 +376,7 @@ static rr_status launch_layer_ppl(const LayerParams &lp, int mode, bool masklist
 rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_z,
                            uint64_t *d_state, uint32_t ppl, uint32_t chunk, uint64_t *d_S,
                            const uint32_t *d_masks, uint32_t nmasks, uint64_t *d_debug_out,
-                           cudaStream_t st)
+                           cudaStream_t st, uint64_t *d_E)
 {
     const uint32_t k = q->k;
     const bool masklist = d_masks != nullptr;
@@ -390,6 +405,7 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
     lp.ngroups = chunk / (32u * ppl);
     lp.npoints = (uint32_t)npoints;
     lp.S = d_S;
+    lp.E = d_E;
     lp.masks = d_masks;
     lp.dbg_out = d_debug_out;
     for (uint64_t c = 0; c < nchunks; ++c) {
@@ -442,7 +458,7 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget)
 }
 
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
-                          uint64_t *d_witness, uint64_t budget, cudaStream_t st)
+                          uint64_t *d_witness, uint64_t budget, cudaStream_t st, uint64_t *d_E)
 {
     rr_status vs = validate_query(g, q);
     if (vs != RR_OK) return vs;
@@ -472,7 +488,7 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk, k)
                                 : 2ull * g.state_rows * chunk * 8ull));
     RR_CUDA(ws.z.reserve((size_t)g.n * k * 8));
-    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st);
+    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st, d_E);
     const QueryKeys keys = make_keys(q->seed);
     const uint32_t *d_shades = nullptr;
     if (q->motif) {
@@ -486,7 +502,7 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     if (s != RR_OK) return s;
     RR_CUDA(cudaMemsetAsync(d_witness, 0, (size_t)g.n * 8, st));
     s = run_query_layers(g, q, ws.z.as<uint64_t>(), ws.state.as<uint64_t>(), ppl, chunk, d_witness,
-                         nullptr, 0, nullptr, st);
+                         nullptr, 0, nullptr, st, d_E);
     if (s != RR_OK) return s;
     if (d_bitmap) return launch_bitmap(d_witness, g.n, d_bitmap, st);
     return RR_OK;

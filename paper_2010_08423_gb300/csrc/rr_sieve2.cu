@@ -384,7 +384,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
 // or, while kernel timing is enabled, enqueues the launches directly so each
 // can be timed.
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
-                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st)
+                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st, uint64_t *d_E)
 {
     const uint32_t k = q->k;
     RR_CUDA(ws.desc.reserve(sizeof(QueryDesc)));
@@ -399,6 +399,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     hd.key_o = keys.key_omega;
     hd.S = d_witness;
     hd.bitmap = d_bitmap;
+    hd.E = d_E;
     if (q->motif) {
         ShadeTable sh;
         make_shades(q->motif, k, &sh);

@@ -127,8 +127,10 @@ __device__ __forceinline__ void first2_closed(const V2Params &p, const uint32_t 
     }
     const uint32_t v = lo;
     const uint64_t perm = gf64_mul(zval(p, s, 0), zval(p, v, 1)) ^ gf64_mul(zval(p, s, 1), zval(p, v, 0));
-    const uint64_t val = gf64_mul(sm_draw(p.qd->key_y, (uint64_t)row_eid[r] * 32u), perm);  // y_{e,1}
+    const uint32_t e = row_eid[r];
+    const uint64_t val = gf64_mul(sm_draw(p.qd->key_y, (uint64_t)e * 32u), perm);  // y_{e,1}
     if (val) atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + v), (unsigned long long)val);
+    if (p.qd->E) p.qd->E[e] = val;  // one row per edge
 }
 
 // ---------------------------------------------------------------------------
@@ -159,9 +161,11 @@ __device__ __forceinline__ void last3_closed(const V2Params &p, uint32_t ent)
     const uint64_t m1 = gf64_mul(b[0], c[2]) ^ gf64_mul(b[2], c[0]);
     const uint64_t m2 = gf64_mul(b[0], c[1]) ^ gf64_mul(b[1], c[0]);
     const uint64_t perm = gf64_mul(a[0], m0) ^ gf64_mul(a[1], m1) ^ gf64_mul(a[2], m2);
-    const uint64_t y = sm_draw(p.qd->key_y, (uint64_t)p.eid[ent] * 32u + 1u);  // y_{e,2}
+    const uint32_t e = p.eid[ent];
+    const uint64_t y = sm_draw(p.qd->key_y, (uint64_t)e * 32u + 1u);  // y_{e,2}
     const uint64_t val = gf64_mul(gf64_mul(y, Y), perm);
     if (val) atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + v), (unsigned long long)val);
+    if (p.qd->E) p.qd->E[e] = val;  // one entry per edge
 }
 
 // ---------------------------------------------------------------------------
@@ -456,6 +460,7 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
     const uint32_t k = p.k;
     const uint64_t key_y = p.qd->key_y;
     uint64_t *const S = p.qd->S;
+    uint64_t *const E = p.qd->E;  // per-edge sums wanted (fine-grained output)
     const uint32_t slots = p.ngroups * (LG + 1);
     const bool active = (uint32_t)lane < slots;
     const uint32_t g = (uint32_t)lane / (LG + 1);
@@ -487,7 +492,8 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
         const uint32_t m_head = has ? p.head[ent] : 0u;
         const uint32_t m_a = has ? p.ia[ent] : 0u;
         const uint32_t m_b = has ? p.ib[ent] : 0u;
-        const uint64_t m_y = has ? sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u)) : 0ull;
+        const uint32_t m_eid = has ? p.eid[ent] : 0u;
+        const uint64_t m_y = has ? sm_draw(key_y, (uint64_t)m_eid * 32u + (p.layer - 1u)) : 0ull;
         const uint32_t nb = min(32u, it.y - base);
         for (uint32_t t = 0; t < nb; ++t) {
             const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
@@ -500,11 +506,23 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
             const uint32_t a = __shfl_sync(0xffffffffu, m_a, (int)t);
             const uint32_t b = __shfl_sync(0xffffffffu, m_b, (int)t);
             const uint64_t y = shfl64b(m_y, (int)t);
+            uint64_t yt = 0;
             if (active) {
                 const uint64_t *sa = p.st_in + (size_t)a * slots + lane;
                 const uint64_t *sb = p.st_in + (size_t)b * slots + lane;
                 const uint64_t tv = COHERENT ? (__ldcg(sa) ^ __ldcg(sb)) : (*sa ^ *sb);
-                acc ^= gf64_mul(y, tv);
+                yt = gf64_mul(y, tv);
+                acc ^= yt;
+            }
+            if (E) {
+                // this entry's own sum over the chunk's points: the flush's
+                // product taken per entry instead of per head
+                uint64_t c = active ? gf64_mul(zsel, yt) : 0ull;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) c ^= shfl64x(c, off);
+                const uint32_t e = __shfl_sync(0xffffffffu, m_eid, (int)t);
+                if (lane == 0 && c) atomicXor(reinterpret_cast<unsigned long long *>(E + e),
+                                              (unsigned long long)c);
             }
         }
     }
