@@ -67,12 +67,12 @@ def _load():
         lib.orc_ztable.argtypes = [u32, u32, u64, vp, vp, vp]
         lib.orc_sieve.restype = i32
         lib.orc_sieve.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, u32, u32, u64,
-                                  vp, u32, vp, vp, vp, i32]
+                                  vp, u32, vp, vp, vp, vp, i32]
         lib.orc_gf_det.restype = u64
         lib.orc_gf_det.argtypes = [u32, vp]
         lib.orc_dfs_paths.restype = u64
         lib.orc_dfs_paths.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, u32, u32, u64,
-                                      vp, vp, vp, vp]
+                                      vp, vp, vp, vp, vp]
         lib.orc_max_threads.restype = i32
         lib.orc_max_threads.argtypes = []
         _lib = lib
@@ -151,14 +151,15 @@ def ztable(n: int, k: int, seed: int, color=None, motif=None) -> np.ndarray:
 # -- sieve and brute force -------------------------------------------------
 
 def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
-          per_mask: bool = False, threads: int = 0, edges: bool = False):
+          per_mask: bool = False, threads: int = 0, edges: bool = False, deleted=None):
     """Per-vertex sieve sums S (n uint64) over all 2^k points or ``masks``.
 
     ``graph`` is a mapping with n, src, dst, t, delta and optionally color.
     Returns S, or (S, per_mask_sums[nmasks, n]) when per_mask is True, or
     (S, E) when edges is True: E[e] (m uint64) is the sum over the points of
     the last layer's value of input edge e (Algorithm 1's fine-grained output
-    before grouping by arrival time).
+    before grouping by arrival time). ``deleted`` (n flags, optional) removes
+    vertices from the graph (their z rows are zero).
     """
     n = int(graph["n"])
     src, dst, t, delta = (_u32(graph[x]) for x in ("src", "dst", "t", "delta"))
@@ -176,7 +177,7 @@ def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
     rc = _load().orc_sieve(n, m, _ptr(src), _ptr(dst), _ptr(t), _ptr(delta),
                            _ptr(color), _ptr(motif), source, k, seed,
                            _ptr(masks), 0 if masks is None else nm, _ptr(S),
-                           _ptr(pm), _ptr(E), int(threads))
+                           _ptr(pm), _ptr(E), _ptr(_u8(deleted)), int(threads))
     if rc == 1:
         raise ValueError("orc_sieve: invalid input")
     if rc:
@@ -194,27 +195,97 @@ def arrival_times(graph, E) -> np.ndarray:
     walks ending at v at time i -- the XOR of E[e] over the edges e into v with
     t_e = i -- is non-zero; NO_ARRIVAL if there is none (Algorithm 1's R)."""
     n = int(graph["n"])
+    R = np.full(n, NO_ARRIVAL, dtype=np.uint32)
+    for (v, ti), val in _group_sums(graph, E).items():
+        if val and ti < R[v]:
+            R[v] = ti
+    return R
+
+
+def _group_sums(graph, E) -> dict:
+    """{(v, t): XOR of E[e] over the edges e into v at time t}."""
     dst = np.asarray(graph["dst"], dtype=np.int64)
     t = np.asarray(graph["t"], dtype=np.int64)
     groups = {}
     for e in range(dst.shape[0]):
         key = (int(dst[e]), int(t[e]))
         groups[key] = groups.get(key, 0) ^ int(E[e])
-    R = np.full(n, NO_ARRIVAL, dtype=np.uint32)
-    for (v, ti), val in groups.items():
-        if val and ti < R[v]:
-            R[v] = ti
-    return R
+    return groups
+
+
+def extract_path(graph, source: int, k: int, seed: int, target: int, motif=None):
+    """One optimal restless path of k vertices from source to target (Sec.
+    "Extracting an optimal solution using k queries"): the last time of the path
+    is the target's minimum arrival time R_target. Step l = k..2 queries the
+    fine-grained oracle for l vertices on the graph without the vertices chosen
+    so far (and, for motif queries, without their colours in M); the next vertex
+    u is the tail of an edge (u, cur, t_cur) whose window t_cur - delta(u) <= i
+    <= t_cur holds a time i with a non-zero (u, i) polynomial. Ties go to the
+    earliest i, then the smallest edge index. The first edge is the smallest-
+    index edge from the source at the chosen time.
+
+    Returns (vertices[k], edges[k-1], times[k-1]) as lists, or None when the
+    target has no arrival (or, with probability <= (3k-1)/2^64 per step, a
+    polynomial vanished)."""
+    n = int(graph["n"])
+    src = np.asarray(graph["src"], dtype=np.int64)
+    dst = np.asarray(graph["dst"], dtype=np.int64)
+    t = np.asarray(graph["t"], dtype=np.int64)
+    delta = np.asarray(graph["delta"], dtype=np.int64)
+    color = graph.get("color")
+    M = list(motif) if motif is not None else None
+    deleted = np.zeros(n, dtype=np.uint8)
+    _, E = sieve(graph, source, k, seed, motif=M, edges=True)
+    R = arrival_times(graph, E)
+    if R[target] == NO_ARRIVAL:
+        return None
+    path, times, edges = [int(target)], [int(R[target])], []
+    deleted[target] = 1
+    if M is not None:
+        M.remove(int(color[target]))
+    for ell in range(k - 1, 1, -1):
+        _, E = sieve(graph, source, ell, seed, motif=M, edges=True, deleted=deleted)
+        groups = _group_sums(graph, E)
+        cur, tc = path[-1], times[-1]
+        best = None
+        for e in range(src.shape[0]):
+            u = int(src[e])
+            if dst[e] != cur or t[e] != tc or deleted[u]:
+                continue
+            for i in range(max(0, tc - int(delta[u])), tc + 1):
+                if groups.get((u, i), 0):
+                    if best is None or (i, e) < best:
+                        best = (i, e)
+                    break
+        if best is None:
+            return None
+        i, e = best
+        u = int(src[e])
+        path.append(u)
+        times.append(i)
+        edges.append(e)
+        deleted[u] = 1
+        if M is not None:
+            M.remove(int(color[u]))
+    cur, tc = path[-1], times[-1]
+    first = [e for e in range(src.shape[0]) if src[e] == source and dst[e] == cur and t[e] == tc]
+    if not first:
+        return None
+    edges.append(min(first))
+    path.append(int(source))
+    path.reverse()
+    edges.reverse()
+    return path, [int(e) for e in edges], [int(t[e]) for e in edges]
 
 
 def dfs_paths(graph, source: int, k: int, seed: int = 0, motif=None,
-              with_det: bool = False, with_edges: bool = False):
+              with_det: bool = False, with_edges: bool = False, deleted=None):
     """Exhaustive temporal DFS over restless k-vertex paths from ``source``.
 
     Returns (reach[n] uint8, Sdet[n] uint64 or None, number_of_paths), and
     with_edges=True appends Edet[m] (the determinant sums split by the path's
     last edge) and arrive[n] uint32 (earliest last-edge time of a path ending at
-    v, NO_ARRIVAL if none).
+    v, NO_ARRIVAL if none). ``deleted`` (n flags) bars vertices from every path.
     """
     n = int(graph["n"])
     src, dst, t, delta = (_u32(graph[x]) for x in ("src", "dst", "t", "delta"))
@@ -227,7 +298,8 @@ def dfs_paths(graph, source: int, k: int, seed: int = 0, motif=None,
     arrive = np.zeros(n, dtype=np.uint32) if with_edges else None
     cnt = _load().orc_dfs_paths(n, m, _ptr(src), _ptr(dst), _ptr(t), _ptr(delta),
                                 _ptr(color), _ptr(motif), source, k, seed,
-                                _ptr(reach), _ptr(sdet), _ptr(edet), _ptr(arrive))
+                                _ptr(reach), _ptr(sdet), _ptr(edet), _ptr(arrive),
+                                _ptr(_u8(deleted)))
     if cnt == (1 << 64) - 1:
         raise ValueError("orc_dfs_paths: invalid input")
     if with_edges:

@@ -305,6 +305,11 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
  *                              2^k points 0..2^k-1
  *   S                          out, n values: XOR over the evaluated points
  *   per_mask                   optional out, nmasks*n values (row p = point masks[p])
+ *   deleted                    optional, n flags: vertices removed from the graph
+ *                              (the extraction's G^{l-1} = G^l minus u_l, Sec.
+ *                              "Extracting an optimal solution using k queries"),
+ *                              realised as z_u = 0, which makes every walk through
+ *                              u vanish and leaves all other terms unchanged
  *   E                          optional out, m values: for every edge e the XOR over
  *                              the evaluated points of P_{k-1}^L[e] (the walks of k
  *                              vertices whose last edge is e; Algorithm 1's
@@ -318,7 +323,7 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
               const uint32_t *t, const uint32_t *delta, const uint8_t *color,
               const uint8_t *motif, uint32_t s, uint32_t k, uint64_t seed,
               const uint32_t *masks, uint32_t nmasks, uint64_t *S, uint64_t *per_mask,
-              uint64_t *E, int nthreads)
+              uint64_t *E, const uint8_t *deleted, int nthreads)
 {
     if (k < 2 || k > 20 || s >= n)
         return 1;
@@ -333,6 +338,11 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
         free(z);
         return 1;
     }
+    if (deleted)
+        for (uint64_t u = 0; u < n; ++u)
+            if (deleted[u])
+                for (uint32_t j = 0; j < k; ++j)
+                    z[u * k + j] = 0;
     orc_inlists IN;
     if (orc_build_inlists(n, m, dst, &IN)) {
         free(z);
@@ -461,6 +471,7 @@ typedef struct {
     uint64_t *Sdet;    /* out: n (may be NULL) */
     uint64_t *Edet;    /* out: m, by last edge (may be NULL) */
     uint32_t *arrive;  /* out: n, earliest last-edge time (may be NULL) */
+    const uint8_t *deleted; /* n flags: vertices no path may use (may be NULL) */
     uint64_t *mat;     /* k*k scratch */
     uint64_t npaths;
 } orc_dfs;
@@ -501,7 +512,7 @@ static void orc_dfs_rec(orc_dfs *D, uint32_t depth /* vertices so far */)
     for (uint64_t q = D->ostart[u]; q < D->ostart[u + 1]; ++q) {
         uint64_t e = D->oedge[q];
         uint32_t v = D->dst[e];
-        if (D->onpath[v])
+        if (D->onpath[v] || (D->deleted && D->deleted[v]))
             continue;
         if (depth >= 2 && !orc_continues(D->t[D->pathe[depth - 2]], D->t[e], D->delta[u]))
             continue;
@@ -539,13 +550,16 @@ static void orc_dfs_rec(orc_dfs *D, uint32_t depth /* vertices so far */)
  *   arrive (optional, n) = the earliest time of a path's last edge among the
  *   paths ending at v (UINT32_MAX if none): the minimum reachability time R_v
  *   of Algorithm 1, found without any sieve.
+ *   deleted (optional, n flags) = vertices that no path may visit (the graph
+ *   without them).
  *
  * Returns the number of paths found (saturating), or (uint64)-1 on bad input.
  */
 uint64_t orc_dfs_paths(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                        const uint32_t *t, const uint32_t *delta, const uint8_t *color,
                        const uint8_t *motif, uint32_t s, uint32_t k, uint64_t seed,
-                       uint8_t *reach, uint64_t *Sdet, uint64_t *Edet, uint32_t *arrive)
+                       uint8_t *reach, uint64_t *Sdet, uint64_t *Edet, uint32_t *arrive,
+                       const uint8_t *deleted)
 {
     if (k < 2 || k > 31 || s >= n)
         return (uint64_t)-1;
@@ -589,6 +603,7 @@ uint64_t orc_dfs_paths(uint32_t n, uint64_t m, const uint32_t *src, const uint32
     D.Sdet = Sdet;
     D.Edet = Edet;
     D.arrive = arrive;
+    D.deleted = deleted;
     D.pathv = (uint32_t *)malloc(k * sizeof(uint32_t));
     D.pathe = (uint64_t *)malloc(k * sizeof(uint64_t));
     D.onpath = (uint8_t *)calloc(n, 1);

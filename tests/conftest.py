@@ -27,6 +27,19 @@ def read_arrivals(name):
     return out
 
 
+def read_paths(name):
+    """The 'path k v..' and 'path_times k t..' lines: {k: (vertices, times)}."""
+    verts, times = {}, {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            f = line.split("#", 1)[0].split()
+            if f and f[0] == "path":
+                verts[int(f[1])] = [int(x) for x in f[2:]]
+            elif f and f[0] == "path_times":
+                times[int(f[1])] = [int(x) for x in f[2:]]
+    return {k: (verts[k], times.get(k)) for k in verts}
+
+
 def read_fixture(name):
     """Graph plus the 'source', 'expect k v...' and 'motif' lines of a fixture."""
     from paper_2010_08423_gb300.workloads import load_edge_fixture
