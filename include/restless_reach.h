@@ -59,7 +59,8 @@ typedef enum {
     RR_EAGAIN = 3,    /* query queued or still running */
     RR_ETIMEDOUT = 4, /* a bounded device wait gave up; results of that query are invalid */
     RR_ECANCELED = 5, /* query was cancelled */
-    RR_ECUDA = 6      /* a CUDA runtime call failed */
+    RR_ECUDA = 6,     /* a CUDA runtime call failed */
+    RR_ENOPATH = 7    /* rr_extract_path: no path of k vertices reaches the target */
 } rr_status;
 
 typedef struct rr_graph rr_graph;
@@ -178,6 +179,29 @@ rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t 
 rr_status rr_reach_arrival_device(const rr_graph *g, const rr_query *q, uint64_t *d_witness,
                                   uint64_t *d_edge_sums, uint32_t *d_arrival, uint8_t *d_bitmap,
                                   void *stream);
+
+/* rr_extract_path: one optimal restless path (Sec. "Extracting an optimal
+ * solution using k queries"; the k-RestlessPath / k-RestlessMotif problems):
+ * k vertices from q->source to `target`, their colours equal to q->motif's
+ * multiset when given, whose last edge time is the target's minimum arrival
+ * time (the smallest possible largest timestamp). It takes k-1 fine-grained
+ * queries: for k vertices, then for l = k-1 .. 2 vertices on the graph without
+ * the vertices already chosen (deleted vertices have zero z rows) and without
+ * their colours in the motif. The next vertex back is the tail u of an edge
+ * (u, cur, t_cur) whose restless window t_cur - delta(u) <= i <= t_cur holds a
+ * time i with a non-zero (u, i) polynomial; ties go to the earliest i, then to
+ * the smallest input edge index, and the first edge is the smallest-index edge
+ * from the source at the chosen time. Every step is certified by a non-zero
+ * polynomial, so the path returned is always a valid restless path.
+ *   vertices (k uint32, host) u_1 = source .. u_k = target;
+ *   edges    (k-1 uint32, host) input edge index of (u_j, u_{j+1});
+ *   times    (k-1 uint32, host) that edge's time.
+ * Synchronous; uses the graph's own stream and scratch. Errors: RR_EINVAL for
+ * NULL outputs, target >= n, target == source or an invalid query; RR_ENOPATH
+ * if the target has no arrival (or, with probability <= (3k-1)/2^64 per step, a
+ * step's polynomials vanished); RR_ENOMEM / RR_ECUDA on device failure. */
+rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target, uint32_t *vertices,
+                          uint32_t *edges, uint32_t *times);
 
 /* rr_reach_atmost_device: at-most-k-RestlessReach (Sec. "Discussion"; Algorithm 2
  * with its loop over k' stopped at k): the plain queries (source, k', seed) for

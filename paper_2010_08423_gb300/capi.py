@@ -15,9 +15,9 @@ import numpy as np
 
 from . import build as _build
 
-RR_OK, RR_EINVAL, RR_ENOMEM, RR_EAGAIN, RR_ETIMEDOUT, RR_ECANCELED, RR_ECUDA = range(7)
+RR_OK, RR_EINVAL, RR_ENOMEM, RR_EAGAIN, RR_ETIMEDOUT, RR_ECANCELED, RR_ECUDA, RR_ENOPATH = range(8)
 STATUS_NAMES = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_EAGAIN",
-                4: "RR_ETIMEDOUT", 5: "RR_ECANCELED", 6: "RR_ECUDA"}
+                4: "RR_ETIMEDOUT", 5: "RR_ECANCELED", 6: "RR_ECUDA", 7: "RR_ENOPATH"}
 FLAG_DENSE_STATE = 1
 
 
@@ -57,7 +57,7 @@ EXPORTED = [
     "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
-    "rr_reach_arrival_device",
+    "rr_reach_arrival_device", "rr_extract_path",
 ]
 
 _lib = None
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_batch_device": [vp, pq, u32, vp, vp, vp, vp],
         "rr_reach_atmost_device": [vp, u32, u32, u64, vp, vp, vp],
         "rr_reach_arrival_device": [vp, pq, vp, vp, vp, vp, vp],
+        "rr_extract_path": [vp, pq, u32, vp, vp, vp],
         "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
         "rr_server_destroy": [vp],
         "rr_query_submit": [vp, pq, ctypes.POINTER(u64)],
@@ -228,6 +229,22 @@ def rr_reach_arrival_device(g, source, k, seed, d_witness, d_arrival, d_edge_sum
     del keep
 
 
+def rr_extract_path(g, source, k, seed, target, motif=None):
+    """One optimal restless path: (vertices[k], edges[k-1], times[k-1]) as lists,
+    or None if the target has no path of k vertices (RR_ENOPATH)."""
+    q, keep = make_query(source, k, seed, motif)
+    verts = np.zeros(k, dtype=np.uint32)
+    edges = np.zeros(max(1, k - 1), dtype=np.uint32)
+    times = np.zeros(max(1, k - 1), dtype=np.uint32)
+    st = load().rr_extract_path(g, ctypes.byref(q), int(target), verts.ctypes.data,
+                                edges.ctypes.data, times.ctypes.data)
+    del keep
+    if st == RR_ENOPATH:
+        return None
+    _check(st)
+    return verts.tolist(), edges[:k - 1].tolist(), times[:k - 1].tolist()
+
+
 def rr_reach_atmost_device(g, source, k, seed, d_witness, d_bitmap=None, stream=None):
     """At most k vertices: d_witness is (k-1) x n (row k'-2 = witness of k')."""
     _check(load().rr_reach_atmost_device(g, int(source), int(k), int(seed) & ((1 << 64) - 1),
@@ -355,6 +372,9 @@ class Graph:
 
     def reach(self, source, k, seed, motif=None):
         return rr_reach_sync(self.handle, self.n, source, k, seed, motif)
+
+    def extract_path(self, source, k, seed, target, motif=None):
+        return rr_extract_path(self.handle, source, k, seed, target, motif)
 
     def point_sums(self, source, k, seed, masks, motif=None):
         return rr_debug_point_sums(self.handle, self.n, source, k, seed, masks, motif)

@@ -87,8 +87,6 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
 rr_status autotune(Graph &g, uint32_t k, uint32_t *ppl, uint32_t *chunk);
 rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st);
-rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness, uint64_t *d_E,
-                         uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st);
 
 }  // namespace rr
 
@@ -202,6 +200,20 @@ rr_status rr_reach_arrival_device(const rr_graph *g, const rr_query *q, uint64_t
     if (s != RR_OK) return s;
     std::lock_guard<std::mutex> lk(g->mu);
     return arrival_device(*g, q, d_witness, d_edge_sums, d_arrival, d_bitmap, (cudaStream_t)stream);
+}
+
+rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target, uint32_t *vertices,
+                          uint32_t *edges, uint32_t *times)
+{
+    clear_error();
+    if (!g || !q || !vertices || !edges || !times)
+        return fail(RR_EINVAL, "rr_extract_path: NULL argument");
+    rr_status s = validate_query(*g, q);
+    if (s != RR_OK) return s;
+    if (target >= g->n || target == q->source)
+        return fail(RR_EINVAL, "rr_extract_path: target must be a vertex other than the source");
+    std::lock_guard<std::mutex> lk(g->mu);
+    return extract_path(*g, q, target, vertices, edges, times);
 }
 
 rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,

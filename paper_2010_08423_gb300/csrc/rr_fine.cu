@@ -46,6 +46,44 @@ __global__ void k_arrival_bitmap(uint32_t n, const uint32_t *__restrict__ R, uin
     }
 }
 
+// One extraction step (Sec. "Extracting an optimal solution using k queries").
+// Among the rows r of `cur`'s segment with time tc whose tail u is not
+// deleted, find the earliest time i inside r's restless window at which u's
+// (u, i) polynomial -- the XOR of E over u's rows at time i -- is non-zero;
+// best = min over such rows of (i << 32 | r). Rows of one (head, time) run are
+// in input-edge order, so the smallest r is the smallest edge index. With
+// `first` set, the candidates are instead the rows from `source` (the path's
+// first edge) and best = min r.
+__global__ void k_extract_step(uint32_t cur, uint32_t tc, const uint32_t *__restrict__ off,
+                               const uint32_t *__restrict__ row_t, const uint32_t *__restrict__ row_src,
+                               const uint32_t *__restrict__ row_lo, const uint32_t *__restrict__ row_hi,
+                               const uint32_t *__restrict__ row_eid, const uint64_t *__restrict__ E,
+                               const uint8_t *__restrict__ vmask, uint32_t source, int first,
+                               unsigned long long *best)
+{
+    const uint32_t r0 = off[cur], r1 = off[cur + 1];
+    for (uint32_t r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < r1; r += gridDim.x * blockDim.x) {
+        if (row_t[r] != tc) continue;
+        const uint32_t u = row_src[r];
+        if (first) {
+            if (u == source) atomicMin(best, (unsigned long long)r);
+            continue;
+        }
+        if (vmask[u]) continue;
+        uint32_t f = row_lo[r];
+        const uint32_t hi = row_hi[r];
+        while (f < hi) {  // the window's rows, one time group at a time
+            const uint32_t t = row_t[f];
+            uint64_t x = 0;
+            for (; f < hi && row_t[f] == t; ++f) x ^= E[row_eid[f]];
+            if (x) {
+                atomicMin(best, ((unsigned long long)t << 32) | r);
+                break;
+            }
+        }
+    }
+}
+
 unsigned grid_for(uint64_t count, unsigned block)
 {
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(152ull * 32, (count + block - 1) / block));
@@ -54,7 +92,7 @@ unsigned grid_for(uint64_t count, unsigned block)
 }  // namespace
 
 rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness, uint64_t *d_E,
-                         uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st)
+                         uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st, const uint8_t *d_vmask)
 {
     Workspace &ws = g.ws;
     if (!d_E) {
@@ -63,7 +101,7 @@ rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness,
     }
     if (g.m) RR_CUDA(cudaMemsetAsync(d_E, 0, (size_t)g.m * 8, st));
     RR_CUDA(cudaMemsetAsync(d_R, 0xFF, (size_t)g.n * 4, st));
-    rr_status s = reach_on_stream(g, ws, q, nullptr, d_witness, 0, st, d_E);
+    rr_status s = reach_on_stream(g, ws, q, nullptr, d_witness, 0, st, d_E, d_vmask);
     if (s != RR_OK) return s;
     if (g.m) {
         k_arrival<<<grid_for(g.m, 256), 256, 0, st>>>((uint32_t)g.m, g.row_head.as<uint32_t>(),
@@ -75,6 +113,98 @@ rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness,
         k_arrival_bitmap<<<grid_for((g.n + 7) / 8, 256), 256, 0, st>>>(g.n, d_R, d_bitmap);
         RR_LAUNCHED();
     }
+    return RR_OK;
+}
+
+// One optimal restless path (Sec. "Extracting an optimal solution using k
+// queries"): the fine-grained query for k vertices gives the target's minimum
+// arrival time; each further query, for one vertex fewer on the graph without
+// the chosen vertices (and, for motif queries, without their colours in M),
+// certifies the next vertex back. Synchronous on the graph's stream.
+rr_status extract_path(const Graph &g, const rr_query *q, uint32_t target, uint32_t *vertices,
+                       uint32_t *edges, uint32_t *times)
+{
+    const uint32_t k = q->k;
+    cudaStream_t st = g.stream;
+    Workspace &ws = g.ws;
+    RR_CUDA(ws.S.reserve((size_t)g.n * 8));
+    RR_CUDA(ws.arrival.reserve((size_t)g.n * 4));
+    RR_CUDA(ws.vmask.reserve(g.n));
+    RR_CUDA(ws.pick.reserve(8));
+    RR_CUDA(ws.edges.reserve((size_t)std::max<uint64_t>(1, g.m) * 8));
+    uint8_t *vm = ws.vmask.as<uint8_t>();
+    RR_CUDA(cudaMemsetAsync(vm, 0, g.n, st));
+    std::vector<uint8_t> M;
+    if (q->motif) M.assign(q->motif, q->motif + k);
+    auto drop_colour = [&](uint32_t v) -> rr_status {
+        if (!q->motif) return RR_OK;
+        uint8_t c = 0;
+        RR_CUDA(cudaMemcpyAsync(&c, g.color.as<uint8_t>() + v, 1, cudaMemcpyDeviceToHost, st));
+        RR_CUDA(cudaStreamSynchronize(st));
+        auto it = std::find(M.begin(), M.end(), c);
+        if (it == M.end()) return fail(RR_ECUDA, "rr_extract_path: chosen vertex colour not in M");
+        M.erase(it);
+        return RR_OK;
+    };
+    auto run = [&](uint32_t kk, const uint8_t *mask) -> rr_status {
+        rr_query qq{q->source, kk, q->seed, q->motif ? M.data() : nullptr};
+        return arrival_device(g, &qq, ws.S.as<uint64_t>(), ws.edges.as<uint64_t>(),
+                              ws.arrival.as<uint32_t>(), nullptr, st, mask);
+    };
+    auto pick = [&](uint32_t cur, uint32_t tc, int first, uint64_t *out) -> rr_status {
+        RR_CUDA(cudaMemsetAsync(ws.pick.p, 0xFF, 8, st));
+        k_extract_step<<<152, 256, 0, st>>>(cur, tc, g.off.as<uint32_t>(), g.row_t.as<uint32_t>(),
+                                            g.row_src.as<uint32_t>(), g.row_lo.as<uint32_t>(),
+                                            g.row_hi.as<uint32_t>(), g.row_eid.as<uint32_t>(),
+                                            ws.edges.as<uint64_t>(), vm, q->source, first,
+                                            ws.pick.as<unsigned long long>());
+        RR_LAUNCHED();
+        RR_CUDA(cudaMemcpyAsync(out, ws.pick.p, 8, cudaMemcpyDeviceToHost, st));
+        RR_CUDA(cudaStreamSynchronize(st));
+        return RR_OK;
+    };
+    auto row_field = [&](const DevBuf &b, uint32_t r, uint32_t *out) -> rr_status {
+        RR_CUDA(cudaMemcpyAsync(out, b.as<uint32_t>() + r, 4, cudaMemcpyDeviceToHost, st));
+        RR_CUDA(cudaStreamSynchronize(st));
+        return RR_OK;
+    };
+
+    // the target's minimum arrival time
+    rr_status s = run(k, nullptr);
+    if (s != RR_OK) return s;
+    uint32_t tc = 0;
+    RR_CUDA(cudaMemcpyAsync(&tc, ws.arrival.as<uint32_t>() + target, 4, cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    if (tc == 0xFFFFFFFFu) return fail(RR_ENOPATH, "rr_extract_path: the target has no arrival");
+    uint32_t cur = target;
+    vertices[k - 1] = target;
+    times[k - 2] = tc;
+    for (uint32_t ell = k - 1; ell >= 2; --ell) {
+        RR_CUDA(cudaMemsetAsync(vm + cur, 1, 1, st));  // delete the vertex chosen last
+        if ((s = drop_colour(cur)) != RR_OK) return s;
+        if ((s = run(ell, vm)) != RR_OK) return s;
+        uint64_t best = 0;
+        if ((s = pick(cur, tc, 0, &best)) != RR_OK) return s;
+        if (best == ~0ull)
+            return fail(RR_ENOPATH, "rr_extract_path: a step's polynomials vanished (probability <= (3k-1)/2^64)");
+        const uint32_t r = (uint32_t)best, i = (uint32_t)(best >> 32);
+        uint32_t u = 0, e = 0;
+        if ((s = row_field(g.row_src, r, &u)) != RR_OK) return s;
+        if ((s = row_field(g.row_eid, r, &e)) != RR_OK) return s;
+        vertices[ell - 1] = u;
+        edges[ell - 1] = e;
+        times[ell - 2] = i;
+        cur = u;
+        tc = i;
+    }
+    // the first edge: from the source into vertices[1] at its chosen time
+    uint64_t best = 0;
+    if ((s = pick(cur, tc, 1, &best)) != RR_OK) return s;
+    if (best == ~0ull) return fail(RR_ECUDA, "rr_extract_path: no source edge at the chosen time");
+    uint32_t e0 = 0;
+    if ((s = row_field(g.row_eid, (uint32_t)best, &e0)) != RR_OK) return s;
+    vertices[0] = q->source;
+    edges[0] = e0;
     return RR_OK;
 }
 

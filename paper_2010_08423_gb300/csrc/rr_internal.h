@@ -77,6 +77,7 @@ struct QueryDesc {
     uint64_t *S;        // witness output (n)
     uint8_t *bitmap;    // bitmap output or null
     uint64_t *E;        // per-edge last-layer sums (m, by input edge index) or null
+    const uint8_t *vmask;  // deleted vertices (n flags: z rows are zero) or null
     uint32_t shades[512];  // first shade [0..255], multiplicity [256..511]
 };
 
@@ -91,6 +92,9 @@ struct Workspace {
     DevBuf bitmap;  // ceil(n/8)
     DevBuf desc;    // QueryDesc
     DevBuf edges;   // m * 8: per-edge sums (fine-grained output) when the caller gives none
+    DevBuf arrival; // n * 4: minimum arrival times (path extraction)
+    DevBuf vmask;   // n: deleted vertices (path extraction)
+    DevBuf pick;    // 8: the extraction step's choice
     cudaStream_t capture = nullptr;           // stream used only to capture graphs
     std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs;
     std::vector<uint64_t> graph_kernels;      // kernel nodes per cached graph
@@ -108,7 +112,8 @@ struct Workspace {
     uint64_t shape_gen[32] = {0};
     size_t bytes() const
     {
-        return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes + desc.bytes + edges.bytes;
+        return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes + desc.bytes + edges.bytes +
+               arrival.bytes + vmask.bytes + pick.bytes;
     }
     void drop_graphs()
     {
@@ -292,7 +297,7 @@ bool choose_shape(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl, ui
 struct LayerParams;
 rr_status launch_ztable(const Graph &g, uint32_t k, const QueryKeys &keys, bool colored,
                         const uint32_t *d_shades /* 512 or null */, uint64_t *d_z,
-                        cudaStream_t st);
+                        cudaStream_t st, const uint8_t *d_vmask = nullptr);
 rr_status launch_bitmap(const uint64_t *d_S, uint32_t n, uint8_t *d_bitmap, cudaStream_t st);
 
 // Runs all chunks and layers of one query; d_S must be zeroed by the caller
@@ -306,9 +311,11 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
 // bounds the state buffers (0 = 60% of free device memory). d_E (m, zeroed by
 // the caller, or null) gets for every input edge the sum over all sieve points
 // of its last-layer value.
+// d_vmask (n flags, device, or null) deletes vertices: their z rows are zero,
+// so no walk through them contributes.
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st,
-                          uint64_t *d_E = nullptr);
+                          uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr);
 // Bytes of scratch one query of size k needs with the shape chosen for budget.
 uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
 
@@ -320,12 +327,24 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 // Enqueues the whole launch sequence of one k >= 3 query (z-table, witness
 // clear, all layers, bitmap) reading per-query values from d_desc; returns
 // the number of kernels enqueued in *kernels.
-rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap, uint32_t ppl,
+// table: z is read from a z-table built from the descriptor (motif queries and
+// queries with deleted vertices); otherwise plain z is drawn on the fly.
+rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels);
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                    uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st,
-                   uint64_t *d_E = nullptr);
+                   uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr);
+
+// Fine-grained outputs (rr_fine.cu): the query with per-edge sums d_E (m, or
+// null for the workspace's buffer), minimum arrival times d_R (n) and the set
+// D as a bitmap (or null); d_vmask deletes vertices.
+rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness, uint64_t *d_E,
+                         uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
+                         const uint8_t *d_vmask = nullptr);
+// One optimal restless path to `target` by k-1 fine-grained queries (host outputs).
+rr_status extract_path(const Graph &g, const rr_query *q, uint32_t target, uint32_t *vertices,
+                       uint32_t *edges, uint32_t *times);
 
 }  // namespace rr
 

@@ -222,7 +222,7 @@ k_layer(const LayerParams p)
 // z_{u,j} (j = 0..k-1 stored at u*k + j): plain iid draws or Eq. (3).
 __global__ void k_ztable(uint32_t n, uint32_t k, uint64_t key_z, uint64_t key_g, uint64_t key_o,
                          const uint8_t *__restrict__ color, const uint32_t *__restrict__ shades,
-                         uint64_t *__restrict__ z)
+                         uint64_t *__restrict__ z, const uint8_t *__restrict__ vmask)
 {
     const uint64_t total = (uint64_t)n * k;
     for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
@@ -239,6 +239,7 @@ __global__ void k_ztable(uint32_t n, uint32_t k, uint64_t key_z, uint64_t key_g,
             for (uint32_t d = d0; d < d0 + mu; ++d)
                 val ^= gf64_mul(sm_draw(key_g, u * 32u + d), sm_draw(key_o, (uint64_t)d * 32u + j));
         }
+        if (vmask && vmask[u]) val = 0;  // deleted vertex
         z[idx] = val;
     }
 }
@@ -325,12 +326,13 @@ bool choose_shape(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl_out
 }
 
 rr_status launch_ztable(const Graph &g, uint32_t k, const QueryKeys &keys, bool colored,
-                        const uint32_t *d_shades, uint64_t *d_z, cudaStream_t st)
+                        const uint32_t *d_shades, uint64_t *d_z, cudaStream_t st,
+                        const uint8_t *d_vmask)
 {
     const int tslot = timing_begin(st);
     k_ztable<<<grid_1d((uint64_t)g.n * k, 256), 256, 0, st>>>(
         g.n, k, keys.key_z, keys.key_gamma, keys.key_omega,
-        colored ? g.color.as<uint8_t>() : nullptr, colored ? d_shades : nullptr, d_z);
+        colored ? g.color.as<uint8_t>() : nullptr, colored ? d_shades : nullptr, d_z, d_vmask);
     timing_end(tslot, kTimeZ, st);
     RR_LAUNCHED();
     return RR_OK;
@@ -458,7 +460,8 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget)
 }
 
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
-                          uint64_t *d_witness, uint64_t budget, cudaStream_t st, uint64_t *d_E)
+                          uint64_t *d_witness, uint64_t budget, cudaStream_t st, uint64_t *d_E,
+                          const uint8_t *d_vmask)
 {
     rr_status vs = validate_query(g, q);
     if (vs != RR_OK) return vs;
@@ -488,7 +491,7 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk, k)
                                 : 2ull * g.state_rows * chunk * 8ull));
     RR_CUDA(ws.z.reserve((size_t)g.n * k * 8));
-    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st, d_E);
+    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st, d_E, d_vmask);
     const QueryKeys keys = make_keys(q->seed);
     const uint32_t *d_shades = nullptr;
     if (q->motif) {
@@ -498,7 +501,8 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
         RR_CUDA(cudaMemcpyAsync(ws.shade.p, &sh, sizeof sh, cudaMemcpyHostToDevice, st));
         d_shades = ws.shade.as<uint32_t>();
     }
-    rr_status s = launch_ztable(g, k, keys, q->motif != nullptr, d_shades, ws.z.as<uint64_t>(), st);
+    rr_status s = launch_ztable(g, k, keys, q->motif != nullptr, d_shades, ws.z.as<uint64_t>(), st,
+                                d_vmask);
     if (s != RR_OK) return s;
     RR_CUDA(cudaMemsetAsync(d_witness, 0, (size_t)g.n * 8, st));
     s = run_query_layers(g, q, ws.z.as<uint64_t>(), ws.state.as<uint64_t>(), ppl, chunk, d_witness,

@@ -177,7 +177,8 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
     return (py_w + pr2_w + 2 * full_w + red_w) * 8ull + 4096;
 }
 
-// z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades).
+// z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades); rows
+// of deleted vertices are zero.
 __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__ qd,
                            const uint8_t *__restrict__ color, uint64_t *__restrict__ z)
 {
@@ -197,6 +198,7 @@ __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__
             for (uint32_t d = d0; d < d0 + mu; ++d)
                 val ^= gf64_mul(sm_draw(kg, u * 32u + d), sm_draw(ko, (uint64_t)d * 32u + j));
         }
+        if (qd->vmask && qd->vmask[u]) val = 0;
         z[idx] = val;
     }
 }
@@ -231,7 +233,7 @@ static unsigned grid_cap(uint64_t count, unsigned block)
     return (unsigned)g;
 }
 
-rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap, uint32_t ppl,
+rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels)
 {
@@ -246,7 +248,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
 
     {
-        if (colored) {  // plain queries draw z on the fly
+        if (table) {  // plain queries without deletions draw z on the fly
             const int tslot = timing_begin(st);
             k_ztable_q<<<grid_cap((uint64_t)g.n * k, 256), 256, 0, st>>>(g.n, k, d_desc,
                                                                         g.color.as<uint8_t>(), d_z);
@@ -260,7 +262,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
     }
     V2Params vp{};
     vp.qd = d_desc;
-    vp.z = colored ? d_z : nullptr;
+    vp.z = table ? d_z : nullptr;
     vp.n = g.n;
     vp.k = k;
     vp.chunk = chunk;
@@ -384,7 +386,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool colored, bool bitmap
 // or, while kernel timing is enabled, enqueues the launches directly so each
 // can be timed.
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
-                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st, uint64_t *d_E)
+                   uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st, uint64_t *d_E,
+                   const uint8_t *d_vmask)
 {
     const uint32_t k = q->k;
     RR_CUDA(ws.desc.reserve(sizeof(QueryDesc)));
@@ -400,6 +403,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     hd.S = d_witness;
     hd.bitmap = d_bitmap;
     hd.E = d_E;
+    hd.vmask = d_vmask;
     if (q->motif) {
         ShadeTable sh;
         make_shades(q->motif, k, &sh);
@@ -419,10 +423,10 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     ws.h_ring[slot] = hd;
     RR_CUDA(cudaMemcpyAsync(ws.desc.p, &ws.h_ring[slot], sizeof hd, cudaMemcpyHostToDevice, st));
     ws.ring_used[slot] = true;
-    const bool colored = q->motif != nullptr;
+    const bool table = q->motif != nullptr || d_vmask != nullptr;
     const bool bitmap = d_bitmap != nullptr;
     if (g_timing.load(std::memory_order_relaxed)) {
-        rr_status s = enqueue_query_v2(g, k, colored, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
+        rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
                                        ws.state.as<uint64_t>(), dd, st, nullptr);
         RR_CUDA(cudaEventRecord(ws.ring_ev[slot], st));
         return s;
@@ -433,7 +437,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
         ws.graph_z = ws.z.p;
     }
     const uint64_t key = (uint64_t)k | ((uint64_t)ppl << 8) | ((uint64_t)chunk << 16) |
-                         ((uint64_t)colored << 40) | ((uint64_t)bitmap << 41);
+                         ((uint64_t)table << 40) | ((uint64_t)bitmap << 41);
     cudaGraphExec_t exec = nullptr;
     uint64_t nkern = 0;
     for (size_t i = 0; i < ws.graphs.size(); ++i)
@@ -444,7 +448,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     if (!exec) {
         if (!ws.capture) RR_CUDA(cudaStreamCreateWithFlags(&ws.capture, cudaStreamNonBlocking));
         RR_CUDA(cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeThreadLocal));
-        rr_status s = enqueue_query_v2(g, k, colored, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
+        rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
                                        ws.state.as<uint64_t>(), dd, ws.capture, &nkern);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(ws.capture, &graph);
