@@ -67,7 +67,7 @@ def _load():
         lib.orc_ztable.argtypes = [u32, u32, u64, vp, vp, vp]
         lib.orc_sieve.restype = i32
         lib.orc_sieve.argtypes = [u32, u64, vp, vp, vp, vp, vp, vp, u32, u32, u64,
-                                  vp, u32, vp, vp, vp, vp, i32]
+                                  vp, u32, vp, vp, vp, vp, vp, i32]
         lib.orc_gf_det.restype = u64
         lib.orc_gf_det.argtypes = [u32, vp]
         lib.orc_dfs_paths.restype = u64
@@ -151,7 +151,8 @@ def ztable(n: int, k: int, seed: int, color=None, motif=None) -> np.ndarray:
 # -- sieve and brute force -------------------------------------------------
 
 def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
-          per_mask: bool = False, threads: int = 0, edges: bool = False, deleted=None):
+          per_mask: bool = False, threads: int = 0, edges: bool = False, deleted=None,
+          sources=None):
     """Per-vertex sieve sums S (n uint64) over all 2^k points or ``masks``.
 
     ``graph`` is a mapping with n, src, dst, t, delta and optionally color.
@@ -159,7 +160,9 @@ def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
     (S, E) when edges is True: E[e] (m uint64) is the sum over the points of
     the last layer's value of input edge e (Algorithm 1's fine-grained output
     before grouping by arrival time). ``deleted`` (n flags, optional) removes
-    vertices from the graph (their z rows are zero).
+    vertices from the graph (their z rows are zero). ``sources`` (a list of
+    vertices, optional) starts walks at every one of them; ``source`` is then
+    ignored.
     """
     n = int(graph["n"])
     src, dst, t, delta = (_u32(graph[x]) for x in ("src", "dst", "t", "delta"))
@@ -174,10 +177,15 @@ def sieve(graph, source: int, k: int, seed: int, motif=None, masks=None,
     S = np.zeros(n, dtype=np.uint64)
     pm = np.zeros((nm, n), dtype=np.uint64) if per_mask else None
     E = np.zeros(m, dtype=np.uint64) if edges else None
+    flags = None
+    if sources is not None:
+        flags = np.zeros(n, dtype=np.uint8)
+        flags[np.asarray(list(sources), dtype=np.int64)] = 1
+        source = 0
     rc = _load().orc_sieve(n, m, _ptr(src), _ptr(dst), _ptr(t), _ptr(delta),
                            _ptr(color), _ptr(motif), source, k, seed,
                            _ptr(masks), 0 if masks is None else nm, _ptr(S),
-                           _ptr(pm), _ptr(E), _ptr(_u8(deleted)), int(threads))
+                           _ptr(pm), _ptr(E), _ptr(_u8(deleted)), _ptr(flags), int(threads))
     if rc == 1:
         raise ValueError("orc_sieve: invalid input")
     if rc:

@@ -254,7 +254,7 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
                           const uint32_t *t, const uint32_t *delta, const orc_inlists *IN,
                           uint32_t s, uint32_t k, uint64_t seed, const uint64_t *z,
                           uint32_t mask, uint64_t *x, uint64_t *prev, uint64_t *cur,
-                          uint64_t *out, uint64_t *eout)
+                          uint64_t *out, uint64_t *eout, const uint8_t *sources)
 {
     for (uint64_t u = 0; u < n; ++u) {
         uint64_t acc = 0;
@@ -265,6 +265,13 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
     }
     /* layer 1 */
     for (uint64_t e = 0; e < m; ++e) {
+        if (sources) {
+            /* a set of sources: every edge leaving one of them starts a walk */
+            prev[e] = sources[src[e]]
+                          ? orc_gf_mul(orc_gf_mul(orc_y(seed, e, 1), x[src[e]]), x[dst[e]])
+                          : 0;
+            continue;
+        }
         if (src[e] == s)
             prev[e] = orc_gf_mul(orc_gf_mul(orc_y(seed, e, 1), x[s]), x[dst[e]]);
         else
@@ -305,6 +312,10 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
  *                              2^k points 0..2^k-1
  *   S                          out, n values: XOR over the evaluated points
  *   per_mask                   optional out, nmasks*n values (row p = point masks[p])
+ *   sources                    optional, n flags: a set of sources (Sec. "Discussion":
+ *                              the multi-source variant); layer 1 then starts at
+ *                              every edge leaving a flagged vertex u, with x_u in
+ *                              place of x_s, and s is ignored
  *   deleted                    optional, n flags: vertices removed from the graph
  *                              (the extraction's G^{l-1} = G^l minus u_l, Sec.
  *                              "Extracting an optimal solution using k queries"),
@@ -323,7 +334,7 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
               const uint32_t *t, const uint32_t *delta, const uint8_t *color,
               const uint8_t *motif, uint32_t s, uint32_t k, uint64_t seed,
               const uint32_t *masks, uint32_t nmasks, uint64_t *S, uint64_t *per_mask,
-              uint64_t *E, const uint8_t *deleted, int nthreads)
+              uint64_t *E, const uint8_t *deleted, const uint8_t *sources, int nthreads)
 {
     if (k < 2 || k > 20 || s >= n)
         return 1;
@@ -375,7 +386,7 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                 uint32_t mask = masks ? masks[p] : (uint32_t)p;
                 memset(one, 0, (size_t)n * sizeof(uint64_t));
                 orc_one_point(n, m, src, dst, t, delta, &IN, s, k, seed, z, mask, x, prev,
-                              cur, one, eacc);
+                              cur, one, eacc, sources);
                 for (uint32_t v = 0; v < n; ++v)
                     acc[v] ^= one[v];
                 if (per_mask)
