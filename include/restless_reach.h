@@ -180,6 +180,24 @@ rr_status rr_reach_arrival_device(const rr_graph *g, const rr_query *q, uint64_t
                                   uint64_t *d_edge_sums, uint32_t *d_arrival, uint8_t *d_bitmap,
                                   void *stream);
 
+/* rr_reach_sources_device: k-RestlessReach (or MotifReach) from a set of
+ * sources, optionally avoiding separators (Sec. "Discussion": the set-of-sources
+ * variant; Sec. on separators in the case study). Walks start at every edge
+ * leaving any of the nsources vertices in `sources` (host array), so the
+ * witness is the XOR of the single-source witnesses with the same seed, and a
+ * vertex is reached iff some restless path of k vertices from some source
+ * (with colours M when `motif` is given) ends at it. d_separators (n flags,
+ * device, may be NULL): vertices no path may use (their z rows are zero).
+ * One source runs the same engine as rr_reach_device; several run the
+ * per-point engine. d_witness (n uint64, device, required) and d_bitmap
+ * (ceil(n/8), device, may be NULL) as rr_reach_device. Enqueued on `stream`.
+ * Errors: RR_EINVAL for NULL sources/d_witness, nsources == 0 or an invalid
+ * query for any source; RR_ENOMEM, RR_ECUDA as rr_reach_device. */
+rr_status rr_reach_sources_device(const rr_graph *g, const uint32_t *sources, uint32_t nsources,
+                                  uint32_t k, uint64_t seed, const uint8_t *motif,
+                                  const uint8_t *d_separators, uint8_t *d_bitmap, uint64_t *d_witness,
+                                  void *stream);
+
 /* rr_extract_path: one optimal restless path (Sec. "Extracting an optimal
  * solution using k queries"; the k-RestlessPath / k-RestlessMotif problems):
  * k vertices from q->source to `target`, their colours equal to q->motif's

@@ -57,7 +57,7 @@ EXPORTED = [
     "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
-    "rr_reach_arrival_device", "rr_extract_path",
+    "rr_reach_arrival_device", "rr_extract_path", "rr_reach_sources_device",
 ]
 
 _lib = None
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_atmost_device": [vp, u32, u32, u64, vp, vp, vp],
         "rr_reach_arrival_device": [vp, pq, vp, vp, vp, vp, vp],
         "rr_extract_path": [vp, pq, u32, vp, vp, vp],
+        "rr_reach_sources_device": [vp, vp, u32, u32, u64, vp, vp, vp, vp, vp],
         "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
         "rr_server_destroy": [vp],
         "rr_query_submit": [vp, pq, ctypes.POINTER(u64)],
@@ -227,6 +228,18 @@ def rr_reach_arrival_device(g, source, k, seed, d_witness, d_arrival, d_edge_sum
     _check(load().rr_reach_arrival_device(g, ctypes.byref(q), _dp(d_witness), _dp(d_edge_sums),
                                           _dp(d_arrival), _dp(d_bitmap), _dp(stream)))
     del keep
+
+
+def rr_reach_sources_device(g, sources, k, seed, d_witness, d_bitmap=None, d_separators=None,
+                            stream=None, motif=None):
+    """k-RestlessReach from a set of sources, avoiding optional separators."""
+    srcs = np.ascontiguousarray(sources, dtype=np.uint32)
+    mo = None if motif is None else np.ascontiguousarray(motif, dtype=np.uint8)
+    _check(load().rr_reach_sources_device(g, srcs.ctypes.data, int(srcs.shape[0]), int(k),
+                                          int(seed) & ((1 << 64) - 1),
+                                          None if mo is None else mo.ctypes.data,
+                                          _dp(d_separators), _dp(d_bitmap), _dp(d_witness),
+                                          _dp(stream)))
 
 
 def rr_extract_path(g, source, k, seed, target, motif=None):

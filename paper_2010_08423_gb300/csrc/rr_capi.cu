@@ -202,6 +202,24 @@ rr_status rr_reach_arrival_device(const rr_graph *g, const rr_query *q, uint64_t
     return arrival_device(*g, q, d_witness, d_edge_sums, d_arrival, d_bitmap, (cudaStream_t)stream);
 }
 
+rr_status rr_reach_sources_device(const rr_graph *g, const uint32_t *sources, uint32_t nsources,
+                                  uint32_t k, uint64_t seed, const uint8_t *motif,
+                                  const uint8_t *d_separators, uint8_t *d_bitmap, uint64_t *d_witness,
+                                  void *stream)
+{
+    clear_error();
+    if (!g || !sources || nsources == 0 || !d_witness)
+        return fail(RR_EINVAL, "rr_reach_sources_device: NULL argument or empty source set");
+    for (uint32_t i = 0; i < nsources; ++i) {
+        const rr_query q{sources[i], k, seed, motif};
+        rr_status s = validate_query(*g, &q);
+        if (s != RR_OK) return s;
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    return sources_device(*g, sources, nsources, k, seed, motif, d_separators, d_bitmap, d_witness,
+                          (cudaStream_t)stream);
+}
+
 rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target, uint32_t *vertices,
                           uint32_t *edges, uint32_t *times)
 {

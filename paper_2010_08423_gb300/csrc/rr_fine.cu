@@ -208,4 +208,26 @@ rr_status extract_path(const Graph &g, const rr_query *q, uint32_t target, uint3
     return RR_OK;
 }
 
+// k-RestlessReach from a set of sources, optionally avoiding separators (Sec.
+// "Discussion": the multi-source variant; the case study's separators). Walks
+// start at every edge leaving a source; the sums are the XOR of the
+// single-source sums. One source runs the reduced-state engine, a larger set
+// the per-point engine with a source mask.
+rr_status sources_device(const Graph &g, const uint32_t *sources, uint32_t nsources, uint32_t k,
+                         uint64_t seed, const uint8_t *motif, const uint8_t *d_separators,
+                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st)
+{
+    const rr_query q{sources[0], k, seed, motif};
+    if (nsources == 1)
+        return reach_on_stream(g, g.ws, &q, d_bitmap, d_witness, 0, st, nullptr, d_separators);
+    std::vector<uint8_t> flags(g.n, 0);
+    for (uint32_t i = 0; i < nsources; ++i) flags[sources[i]] = 1;
+    Workspace &ws = g.ws;
+    RR_CUDA(ws.srcmask.reserve(g.n));
+    // pageable source: the copy is staged before the call returns
+    RR_CUDA(cudaMemcpyAsync(ws.srcmask.p, flags.data(), g.n, cudaMemcpyHostToDevice, st));
+    return reach_on_stream(g, ws, &q, d_bitmap, d_witness, 0, st, nullptr, d_separators,
+                           ws.srcmask.as<uint8_t>());
+}
+
 }  // namespace rr

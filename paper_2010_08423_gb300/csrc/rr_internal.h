@@ -95,6 +95,7 @@ struct Workspace {
     DevBuf arrival; // n * 4: minimum arrival times (path extraction)
     DevBuf vmask;   // n: deleted vertices (path extraction)
     DevBuf pick;    // 8: the extraction step's choice
+    DevBuf srcmask; // n: a set of sources (rr_reach_sources_device)
     cudaStream_t capture = nullptr;           // stream used only to capture graphs
     std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs;
     std::vector<uint64_t> graph_kernels;      // kernel nodes per cached graph
@@ -113,7 +114,7 @@ struct Workspace {
     size_t bytes() const
     {
         return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes + desc.bytes + edges.bytes +
-               arrival.bytes + vmask.bytes + pick.bytes;
+               arrival.bytes + vmask.bytes + pick.bytes + srcmask.bytes;
     }
     void drop_graphs()
     {
@@ -306,16 +307,19 @@ rr_status launch_bitmap(const uint64_t *d_S, uint32_t n, uint8_t *d_bitmap, cuda
 rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_z,
                            uint64_t *d_state, uint32_t ppl, uint32_t chunk, uint64_t *d_S,
                            const uint32_t *d_masks, uint32_t nmasks, uint64_t *d_debug_out,
-                           cudaStream_t st, uint64_t *d_E = nullptr);
+                           cudaStream_t st, uint64_t *d_E = nullptr,
+                           const uint8_t *d_srcmask = nullptr);
 // Runs one query on `st` with scratch `ws`; d_witness (n) required. `budget`
 // bounds the state buffers (0 = 60% of free device memory). d_E (m, zeroed by
 // the caller, or null) gets for every input edge the sum over all sieve points
 // of its last-layer value.
 // d_vmask (n flags, device, or null) deletes vertices: their z rows are zero,
-// so no walk through them contributes.
+// so no walk through them contributes. d_srcmask (n flags, device, or null)
+// starts walks at every flagged vertex instead of q->source.
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st,
-                          uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr);
+                          uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr,
+                          const uint8_t *d_srcmask = nullptr);
 // Bytes of scratch one query of size k needs with the shape chosen for budget.
 uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
 
@@ -342,6 +346,10 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
 rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness, uint64_t *d_E,
                          uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
                          const uint8_t *d_vmask = nullptr);
+// A set of sources and optional separators (n flags, device).
+rr_status sources_device(const Graph &g, const uint32_t *sources, uint32_t nsources, uint32_t k,
+                         uint64_t seed, const uint8_t *motif, const uint8_t *d_separators,
+                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st);
 // One optimal restless path to `target` by k-1 fine-grained queries (host outputs).
 rr_status extract_path(const Graph &g, const rr_query *q, uint32_t target, uint32_t *vertices,
                        uint32_t *edges, uint32_t *times);

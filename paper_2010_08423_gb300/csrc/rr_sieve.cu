@@ -40,6 +40,7 @@ struct LayerParams {
     uint64_t *st_out;
     uint64_t *S;                // last layer: per-vertex XOR target
     uint64_t *E;                // last layer: per-edge XOR target (m, by input edge) or null
+    const uint8_t *src_mask;    // layer 1: a set of sources (n flags) instead of `source`
     const uint32_t *masks;      // mask-list mode: point p is masks[p]
     uint64_t *dbg_out;          // mask-list mode, last layer: out[p * n + v]
 };
@@ -126,7 +127,9 @@ k_layer(const LayerParams p)
         for (uint32_t r = r0; r < r1; ++r) {
             const uint32_t ra = p.row_a[r];
             const uint32_t rs = ((MODE & kLast) != 0) ? 0u : p.row_s[r];
-            const bool compute = ((MODE & kFirst) != 0) ? (p.row_src[r] == p.source) : (ra != 0u);
+            const bool compute = ((MODE & kFirst) != 0)
+                                     ? (p.src_mask ? p.src_mask[p.row_src[r]] != 0 : p.row_src[r] == p.source)
+                                     : (ra != 0u);
             if constexpr ((MODE & kLast) != 0) {
                 if (!compute) continue;
             } else {
@@ -167,8 +170,21 @@ k_layer(const LayerParams p)
                 }
                 uint64_t w[PPL];
                 if constexpr ((MODE & kFirst) != 0) {
+                    if (p.src_mask) {
+                        // x_u of this row's tail u (one of the sources)
+                        const size_t u = p.row_src[r];
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) w[i] = xs[i];
+                        for (int i = 0; i < PPL; ++i) w[i] = 0;
+                        for (uint32_t j = 0; j < k; ++j) {
+                            const uint64_t zuj = p.z[u * k + j];
+#pragma unroll
+                            for (int i = 0; i < PPL; ++i)
+                                if ((L[i] >> j) & 1u) w[i] ^= zuj;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < PPL; ++i) w[i] = xs[i];
+                    }
                 } else {
                     const uint32_t rb = p.row_b[r];
                     uint64_t wa[PPL], wb[PPL];
@@ -378,7 +394,7 @@ static rr_status launch_layer_ppl(const LayerParams &lp, int mode, bool masklist
 rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_z,
                            uint64_t *d_state, uint32_t ppl, uint32_t chunk, uint64_t *d_S,
                            const uint32_t *d_masks, uint32_t nmasks, uint64_t *d_debug_out,
-                           cudaStream_t st, uint64_t *d_E)
+                           cudaStream_t st, uint64_t *d_E, const uint8_t *d_srcmask)
 {
     const uint32_t k = q->k;
     const bool masklist = d_masks != nullptr;
@@ -408,6 +424,7 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
     lp.npoints = (uint32_t)npoints;
     lp.S = d_S;
     lp.E = d_E;
+    lp.src_mask = d_srcmask;
     lp.masks = d_masks;
     lp.dbg_out = d_debug_out;
     for (uint64_t c = 0; c < nchunks; ++c) {
@@ -461,12 +478,19 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget)
 
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st, uint64_t *d_E,
-                          const uint8_t *d_vmask)
+                          const uint8_t *d_vmask, const uint8_t *d_srcmask)
 {
     rr_status vs = validate_query(g, q);
     if (vs != RR_OK) return vs;
     const uint32_t k = q->k;
-    const bool v2 = uses_v2(g, k);
+    // a set of sources runs on the per-point engine (the reduced-state engine
+    // factors x_s out of layer 1); its shape is never cached per k
+    const bool v2 = uses_v2(g, k) && !d_srcmask;
+    if (d_srcmask && budget == 0) {
+        size_t free_b = 0, total_b = 0;
+        RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        budget = (uint64_t)(0.6 * (double)(free_b + ws.state.bytes));
+    }
     uint32_t ppl = 0, chunk = 0;
     if (budget == 0 && ws.shape_ppl[k] && ws.shape_gen[k] == g.tune_gen) {
         // shape already chosen for this k on this workspace: no device query
@@ -506,7 +530,7 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     if (s != RR_OK) return s;
     RR_CUDA(cudaMemsetAsync(d_witness, 0, (size_t)g.n * 8, st));
     s = run_query_layers(g, q, ws.z.as<uint64_t>(), ws.state.as<uint64_t>(), ppl, chunk, d_witness,
-                         nullptr, 0, nullptr, st, d_E);
+                         nullptr, 0, nullptr, st, d_E, d_srcmask);
     if (s != RR_OK) return s;
     if (d_bitmap) return launch_bitmap(d_witness, g.n, d_bitmap, st);
     return RR_OK;
