@@ -885,6 +885,7 @@ rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t se
             RR_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
             F.done.push_back(e2);
             F.ws.emplace_back(new Workspace());
+            F.ws.back()->pdl = false;
         }
         RR_CUDA(cudaEventRecord(F.fork, st));
         for (uint32_t kk = k; kk >= 2; --kk) {

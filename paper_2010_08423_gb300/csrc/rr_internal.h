@@ -108,6 +108,9 @@ struct Workspace {
     cudaEvent_t ring_ev[kRing] = {};
     bool ring_used[kRing] = {};
     uint32_t ring_pos = 0;
+    // launch the query's kernels with programmatic dependent launch (off for
+    // workspaces whose queries run concurrently with others)
+    bool pdl = true;
     // shape chosen per k (0 = not chosen yet) and the tuning generation it used
     uint32_t shape_ppl[32] = {0}, shape_chunk[32] = {0};
     uint64_t shape_gen[32] = {0};
@@ -335,7 +338,8 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 // queries with deleted vertices); otherwise plain z is drawn on the fly.
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
-                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels);
+                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels,
+                           bool pdl = true);
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                    uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st,
                    uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr);

@@ -25,8 +25,35 @@
 
 namespace rr {
 
+// Launches a kernel of the single-query sequence with programmatic stream
+// serialisation: it may be scheduled while the previous kernel of the stream
+// still runs, and waits for it in pdl_enter() before touching memory. Captured
+// into the per-shape CUDA graph as a programmatic dependency.
+// Off for workspaces whose queries run beside others on concurrent streams:
+// there a grid waiting for its predecessor holds SM slots the other streams'
+// kernels could use.
+static thread_local bool t_pdl = true;
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = t_pdl ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 __global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uint64_t *__restrict__ py)
 {
+    pdl_enter();
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
     first_scalar_warp(p, task, py);
@@ -35,6 +62,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uin
 template <int PPL, bool FROM_Y, int OUT, bool FROM_R2 = false>
 __global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
 {
+    pdl_enter();
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems * p.ngroups) return;
     const uint32_t item = task / p.ngroups;
@@ -46,6 +74,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
 __global__ void k_fix1(const uint2 *__restrict__ chains, uint32_t nchains, uint64_t *buf,
                        uint32_t width)
 {
+    pdl_enter();
     if (blockIdx.x >= nchains) return;
     const uint2 ch = chains[blockIdx.x];
     fixup_phase1<false>(buf, width, ch.x, ch.y, threadIdx.x, blockDim.x);
@@ -54,6 +83,7 @@ __global__ void k_fix1(const uint2 *__restrict__ chains, uint32_t nchains, uint6
 __global__ void k_fix2(const uint2 *__restrict__ chains, const uint2 *__restrict__ tasks,
                        uint32_t ntasks, uint64_t *buf, uint32_t width)
 {
+    pdl_enter();
     if (blockIdx.x >= ntasks) return;
     const uint2 t = tasks[blockIdx.x];
     const uint2 ch = chains[t.x];
@@ -64,11 +94,13 @@ static rr_status launch_fixup(const RowList &L, uint64_t *buf, uint32_t width, c
                               uint64_t *nk)
 {
     if (L.nchains == 0) return RR_OK;
-    k_fix1<<<L.nchains, 128, 0, st>>>(L.chains.as<uint2>(), L.nchains, buf, width);
+    RR_CUDA(launch_pdl(k_fix1, dim3(L.nchains), dim3(128), st, L.chains.as<uint2>(), L.nchains, buf,
+                       width));
     RR_LAUNCHED();
     ++*nk;
     if (L.nfix2) {
-        k_fix2<<<L.nfix2, 256, 0, st>>>(L.chains.as<uint2>(), L.fix2.as<uint2>(), L.nfix2, buf, width);
+        RR_CUDA(launch_pdl(k_fix2, dim3(L.nfix2), dim3(256), st, L.chains.as<uint2>(),
+                           L.fix2.as<uint2>(), L.nfix2, buf, width));
         RR_LAUNCHED();
         ++*nk;
     }
@@ -77,6 +109,7 @@ static rr_status launch_fixup(const RowList &L, uint64_t *buf, uint32_t width, c
 
 __global__ void __launch_bounds__(kW2 * 32) k_second_label(const V2Params p, uint64_t *__restrict__ pr2)
 {
+    pdl_enter();
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
     second_label_warp(p, task, pr2);
@@ -86,12 +119,14 @@ __global__ void k_first2(const V2Params p, const uint32_t *__restrict__ off,
                          const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ row_eid,
                          uint32_t m)
 {
+    pdl_enter();
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
         first2_closed(p, off, row_src, row_eid, r);
 }
 
 __global__ void k_last3(const V2Params p, uint32_t count)
 {
+    pdl_enter();
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
         last3_closed(p, e);
 }
@@ -99,6 +134,7 @@ __global__ void k_last3(const V2Params p, uint32_t count)
 template <int LG>
 __global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
 {
+    pdl_enter();
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
     last_warp<LG, false>(p, task);
@@ -132,14 +168,14 @@ static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st
     const int tslot = timing_begin(st);
     const unsigned blocks = blocks_for(tasks);
     if (src == 1) {
-        if (out == 0) k_layer_v2<PPL, true, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
-        else k_layer_v2<PPL, true, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
+        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 0>, dim3(blocks), dim3(kW2 * 32), st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 1>, dim3(blocks), dim3(kW2 * 32), st, vp));
     } else if (src == 2) {
-        if (out == 0) k_layer_v2<PPL, false, 0, true><<<blocks, kW2 * 32, 0, st>>>(vp);
-        else k_layer_v2<PPL, false, 1, true><<<blocks, kW2 * 32, 0, st>>>(vp);
+        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true>, dim3(blocks), dim3(kW2 * 32), st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, true>, dim3(blocks), dim3(kW2 * 32), st, vp));
     } else {
-        if (out == 0) k_layer_v2<PPL, false, 0><<<blocks, kW2 * 32, 0, st>>>(vp);
-        else k_layer_v2<PPL, false, 1><<<blocks, kW2 * 32, 0, st>>>(vp);
+        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0>, dim3(blocks), dim3(kW2 * 32), st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1>, dim3(blocks), dim3(kW2 * 32), st, vp));
     }
     timing_end(tslot, src == 1 ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid), st);
     RR_LAUNCHED();
@@ -182,6 +218,7 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__ qd,
                            const uint8_t *__restrict__ color, uint64_t *__restrict__ z)
 {
+    pdl_enter();
     const uint64_t total = (uint64_t)n * k;
     const bool colored = qd->colored != 0;
     const uint64_t kz = qd->key_z, kg = qd->key_g, ko = qd->key_o;
@@ -203,15 +240,33 @@ __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__
     }
 }
 
-__global__ void k_zero_q(uint32_t n, const QueryDesc *__restrict__ qd)
+// Clears the witness and the zero rows of the scratch: the scalar prefix's
+// row 0, row 0 of both full state buffers (chunk values each), of the
+// transformed buffer (rstride values) and of the label-space prefix (k values).
+__global__ void k_zero_q(uint32_t n, const QueryDesc *__restrict__ qd, uint64_t *py, uint64_t *full0,
+                         uint64_t *full1, uint32_t chunk, uint64_t *red, uint32_t rstride,
+                         uint64_t *pr2, uint32_t kpr2)
 {
+    pdl_enter();
     uint64_t *S = qd->S;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        S[v] = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t v = tid; v < n; v += stride) S[v] = 0;
+    if (py && tid == 0) py[0] = 0;
+    if (full0)
+        for (uint32_t i = tid; i < chunk; i += stride) {
+            full0[i] = 0;
+            full1[i] = 0;
+        }
+    if (red)
+        for (uint32_t i = tid; i < rstride; i += stride) red[i] = 0;
+    if (pr2)
+        for (uint32_t i = tid; i < kpr2; i += stride) pr2[i] = 0;
 }
 
 __global__ void k_bitmap_q(uint32_t n, const QueryDesc *__restrict__ qd)
 {
+    pdl_enter();
     const uint64_t *S = qd->S;
     uint8_t *bm = qd->bitmap;
     const uint32_t nb = (n + 7) / 8;
@@ -235,8 +290,13 @@ static unsigned grid_cap(uint64_t count, unsigned block)
 
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
-                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels)
+                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels, bool pdl)
 {
+    struct PdlScope {
+        bool saved;
+        explicit PdlScope(bool on) : saved(t_pdl) { t_pdl = on; }
+        ~PdlScope() { t_pdl = saved; }
+    } pdl_scope(pdl);
     uint64_t nk = 0;
     uint64_t py_w, pr2_w, full_w, red_w;
     v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &full_w, &red_w);
@@ -250,13 +310,16 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     {
         if (table) {  // plain queries without deletions draw z on the fly
             const int tslot = timing_begin(st);
-            k_ztable_q<<<grid_cap((uint64_t)g.n * k, 256), 256, 0, st>>>(g.n, k, d_desc,
-                                                                        g.color.as<uint8_t>(), d_z);
+            RR_CUDA(launch_pdl(k_ztable_q, dim3(grid_cap((uint64_t)g.n * k, 256)), dim3(256), st, g.n, k,
+                               d_desc, g.color.as<uint8_t>(), d_z));
             timing_end(tslot, kTimeZ, st);
             RR_LAUNCHED();
             ++nk;
         }
-        k_zero_q<<<grid_cap(g.n, 256), 256, 0, st>>>(g.n, d_desc);
+        // witness and the scratch's zero rows (k = 2 has no scratch)
+        RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, g.n, d_desc,
+                           k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
+                           chunk, k >= 4 ? red : nullptr, rstride, k >= 5 ? pr2 : nullptr, k));
         RR_LAUNCHED();
         ++nk;
     }
@@ -273,14 +336,14 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         // the only layer, in closed form
         if (g.m) {
             const int tslot = timing_begin(st);
-            k_first2<<<grid_cap(g.m, 256), 256, 0, st>>>(vp, g.off.as<uint32_t>(), g.row_src.as<uint32_t>(),
-                                                         g.row_eid.as<uint32_t>(), (uint32_t)g.m);
+            RR_CUDA(launch_pdl(k_first2, dim3(grid_cap(g.m, 256)), dim3(256), st, vp, g.off.as<uint32_t>(),
+                               g.row_src.as<uint32_t>(), g.row_eid.as<uint32_t>(), (uint32_t)g.m));
             timing_end(tslot, kTimeFirst, st);
             RR_LAUNCHED();
             ++nk;
         }
         if (bitmap) {
-            k_bitmap_q<<<grid_cap((g.n + 7) / 8, 256), 256, 0, st>>>(g.n, d_desc);
+            RR_CUDA(launch_pdl(k_bitmap_q, dim3(grid_cap((g.n + 7) / 8, 256)), dim3(256), st, g.n, d_desc));
             RR_LAUNCHED();
             ++nk;
         }
@@ -288,18 +351,12 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         return RR_OK;
     }
 
-    // layer 1: scalar prefix (independent of the point chunk); zero rows
-    RR_CUDA(cudaMemsetAsync(py, 0, 8, st));
-    if (k >= 4) {
-        RR_CUDA(cudaMemsetAsync(full0, 0, (size_t)chunk * 8, st));
-        RR_CUDA(cudaMemsetAsync(full1, 0, (size_t)chunk * 8, st));
-        RR_CUDA(cudaMemsetAsync(red, 0, (size_t)rstride * 8, st));
-    }
+    // layer 1: scalar prefix (independent of the point chunk)
     set_list(vp, g.prod_list, 0);
     vp.layer = 1;
     if (vp.nitems) {
         const int tslot = timing_begin(st);
-        k_first_scalar<<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp, py);
+        RR_CUDA(launch_pdl(k_first_scalar, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, py));
         timing_end(tslot, kTimeFirst, st);
         RR_LAUNCHED();
         ++nk;
@@ -310,12 +367,11 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     vp.pr2 = pr2;
     if (k >= 5) {
         // layer 2 in label space (independent of the point chunk)
-        RR_CUDA(cudaMemsetAsync(pr2, 0, (size_t)k * 8, st));
         set_list(vp, g.state_list, 0);
         vp.layer = 2;
         if (vp.nitems) {
             const int tslot = timing_begin(st);
-            k_second_label<<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp, pr2);
+            RR_CUDA(launch_pdl(k_second_label, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, pr2));
             timing_end(tslot, kTimeSecond, st);
             RR_LAUNCHED();
             ++nk;
@@ -329,7 +385,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         set_list(vp, g.win_list, 0);
         vp.layer = 2;
         const int tslot = timing_begin(st);
-        k_last3<<<grid_cap(g.win_list.count, 256), 256, 0, st>>>(vp, (uint32_t)g.win_list.count);
+        RR_CUDA(launch_pdl(k_last3, dim3(grid_cap(g.win_list.count, 256)), dim3(256), st, vp,
+                           (uint32_t)g.win_list.count));
         timing_end(tslot, kTimeLast, st);
         RR_LAUNCHED();
         ++nk;
@@ -365,15 +422,15 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         vp.st_in = red;
         if (vp.nitems) {
             const int tslot = timing_begin(st);
-            if (ppl == 4) k_last_v2<7><<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp);
-            else k_last_v2<6><<<blocks_for(vp.nitems), kW2 * 32, 0, st>>>(vp);
+            if (ppl == 4) RR_CUDA(launch_pdl(k_last_v2<7>, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp));
+            else RR_CUDA(launch_pdl(k_last_v2<6>, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp));
             timing_end(tslot, kTimeLast, st);
             RR_LAUNCHED();
             ++nk;
         }
     }
     if (bitmap) {
-        k_bitmap_q<<<grid_cap((g.n + 7) / 8, 256), 256, 0, st>>>(g.n, d_desc);
+        RR_CUDA(launch_pdl(k_bitmap_q, dim3(grid_cap((g.n + 7) / 8, 256)), dim3(256), st, g.n, d_desc));
         RR_LAUNCHED();
         ++nk;
     }
@@ -427,7 +484,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     const bool bitmap = d_bitmap != nullptr;
     if (g_timing.load(std::memory_order_relaxed)) {
         rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
-                                       ws.state.as<uint64_t>(), dd, st, nullptr);
+                                       ws.state.as<uint64_t>(), dd, st, nullptr, ws.pdl);
         RR_CUDA(cudaEventRecord(ws.ring_ev[slot], st));
         return s;
     }
@@ -449,7 +506,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
         if (!ws.capture) RR_CUDA(cudaStreamCreateWithFlags(&ws.capture, cudaStreamNonBlocking));
         RR_CUDA(cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeThreadLocal));
         rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
-                                       ws.state.as<uint64_t>(), dd, ws.capture, &nkern);
+                                       ws.state.as<uint64_t>(), dd, ws.capture, &nkern, ws.pdl);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(ws.capture, &graph);
         if (s != RR_OK) {

@@ -36,6 +36,18 @@ __device__ __forceinline__ uint64_t zval(const V2Params &p, uint64_t u, uint32_t
     return p.z ? p.z[u * p.k + j] : sm_draw(p.qd->key_z, u * 32u + j);
 }
 
+// Programmatic dependent launch (sm_90 and later): wait until the previous
+// kernel of the stream has completed and its writes are visible, then let the
+// next kernel be scheduled once every block of this one has got here, so its
+// launch overlaps this kernel's work while at most one waiting grid per stream
+// holds SM slots. Called before a kernel touches memory; without a
+// programmatic dependency both are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint64_t shfl64b(uint64_t v, int src)
 {
     return __shfl_sync(0xffffffffu, (unsigned long long)v, src);
