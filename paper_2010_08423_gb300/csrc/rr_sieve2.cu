@@ -51,9 +51,39 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cud
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-__global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uint64_t *__restrict__ py)
+// What a query clears before its layers: the witness (n values; n = 0 skips
+// it) and the zero rows of the scratch -- row 0 of the scalar prefix, of both
+// full state buffers (chunk values each), of the transformed buffer (rstride
+// values) and of the label-space prefix (kpr2 values). Null pointers skip.
+struct ZeroRows {
+    uint64_t *py, *full0, *full1, *red, *pr2;
+    uint32_t n, chunk, rstride, kpr2;
+};
+
+__device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, const ZeroRows &z)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t *S = qd->S;
+    for (uint32_t v = tid; v < z.n; v += stride) S[v] = 0;
+    if (z.py && tid == 0) z.py[0] = 0;
+    if (z.full0)
+        for (uint32_t i = tid; i < z.chunk; i += stride) {
+            z.full0[i] = 0;
+            z.full1[i] = 0;
+        }
+    if (z.red)
+        for (uint32_t i = tid; i < z.rstride; i += stride) z.red[i] = 0;
+    if (z.pr2)
+        for (uint32_t i = tid; i < z.kpr2; i += stride) z.pr2[i] = 0;
+}
+
+// Layer 1; its grid also clears what zero_rows lists (saving a launch).
+__global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uint64_t *__restrict__ py,
+                                                           const ZeroRows zr)
 {
     pdl_enter();
+    zero_rows(p.qd, zr);
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
     first_scalar_warp(p, task, py);
@@ -240,28 +270,10 @@ __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__
     }
 }
 
-// Clears the witness and the zero rows of the scratch: the scalar prefix's
-// row 0, row 0 of both full state buffers (chunk values each), of the
-// transformed buffer (rstride values) and of the label-space prefix (k values).
-__global__ void k_zero_q(uint32_t n, const QueryDesc *__restrict__ qd, uint64_t *py, uint64_t *full0,
-                         uint64_t *full1, uint32_t chunk, uint64_t *red, uint32_t rstride,
-                         uint64_t *pr2, uint32_t kpr2)
+__global__ void k_zero_q(const QueryDesc *__restrict__ qd, const ZeroRows zr)
 {
     pdl_enter();
-    uint64_t *S = qd->S;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    for (uint32_t v = tid; v < n; v += stride) S[v] = 0;
-    if (py && tid == 0) py[0] = 0;
-    if (full0)
-        for (uint32_t i = tid; i < chunk; i += stride) {
-            full0[i] = 0;
-            full1[i] = 0;
-        }
-    if (red)
-        for (uint32_t i = tid; i < rstride; i += stride) red[i] = 0;
-    if (pr2)
-        for (uint32_t i = tid; i < kpr2; i += stride) pr2[i] = 0;
+    zero_rows(qd, zr);
 }
 
 __global__ void k_bitmap_q(uint32_t n, const QueryDesc *__restrict__ qd)
@@ -316,10 +328,14 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             RR_LAUNCHED();
             ++nk;
         }
-        // witness and the scratch's zero rows (k = 2 has no scratch)
-        RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, g.n, d_desc,
-                           k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
-                           chunk, k >= 4 ? red : nullptr, rstride, k >= 5 ? pr2 : nullptr, k));
+    }
+    // the witness and the scratch's zero rows (k = 2 has no scratch); cleared by
+    // the first layer's grid when it runs
+    const ZeroRows zr{k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
+                      k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, rstride, k};
+    const bool zero_in_first = k >= 3 && g.prod_list.nitems > 0;
+    if (!zero_in_first) {
+        RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, d_desc, zr));
         RR_LAUNCHED();
         ++nk;
     }
@@ -356,7 +372,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     vp.layer = 1;
     if (vp.nitems) {
         const int tslot = timing_begin(st);
-        RR_CUDA(launch_pdl(k_first_scalar, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, py));
+        RR_CUDA(launch_pdl(k_first_scalar, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, py, zr));
         timing_end(tslot, kTimeFirst, st);
         RR_LAUNCHED();
         ++nk;

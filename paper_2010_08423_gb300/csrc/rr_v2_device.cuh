@@ -226,7 +226,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     uint64_t zv = 0;
     auto enter_head = [&](uint32_t v) {
         zv = (uint32_t)lane < k ? zval(p, v, lane) : 0ull;
-        if constexpr (FROM_Y) {
+        if constexpr (FROM_Y || FROM_R2) {
             uint64_t xv[PPL];
             combine_labels<PPL>(zv, k, lane, hi_bits, xv);
 #pragma unroll
@@ -271,22 +271,30 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 for (int i = 0; i < PPL; ++i) R[i] ^= r[i];
 #pragma unroll
                 for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
-            } else if (a != b) {
-                const uint64_t coef = shfl64b(m_coef, (int)t);
-                uint64_t c[PPL], w[PPL];
-                combine_labels<PPL>(gf64_mul(coef, zv), k, lane, hi_bits, c);
-                if constexpr (FROM_R2) {
+            } else if constexpr (FROM_R2) {
+                // the same factoring one layer later: acc^L = (x_v^L x_s^L) * R^L with
+                // R^L = sum_e x_{u_e}^L (y_{e,3} rho_e)^L; y is folded into the label
+                // values lane-parallel, so each entry costs two products per point
+                if (a != b) {
+                    const uint64_t coef = shfl64b(m_coef, (int)t);
                     const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
                     const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
                     const uint64_t rj = (uint32_t)lane < k
                                             ? (p.pr2[(size_t)a * k + lane] ^ p.pr2[(size_t)b * k + lane])
                                             : 0ull;
-                    uint64_t xu[PPL], rho[PPL];
+                    uint64_t xu[PPL], yrho[PPL];
                     combine_labels<PPL>(zu, k, lane, hi_bits, xu);
-                    combine_labels<PPL>(rj, k, lane, hi_bits, rho);
+                    combine_labels<PPL>(gf64_mul(coef, rj), k, lane, hi_bits, yrho);
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) w[i] = gf64_mul(gf64_mul(xs[i], xu[i]), rho[i]);
-                } else {
+                    for (int i = 0; i < PPL; ++i) R[i] ^= gf64_mul(xu[i], yrho[i]);
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
+                }
+            } else if (a != b) {
+                const uint64_t coef = shfl64b(m_coef, (int)t);
+                uint64_t c[PPL], w[PPL];
+                combine_labels<PPL>(gf64_mul(coef, zv), k, lane, hi_bits, c);
+                {
                     const uint64_t *pa = p.st_in + (size_t)a * p.chunk + col;
                     const uint64_t *pb = p.st_in + (size_t)b * p.chunk + col;
                     const ulonglong2 *va = reinterpret_cast<const ulonglong2 *>(pa);
