@@ -249,7 +249,10 @@ __global__ void __launch_bounds__(kW2 * 32, MINB) k_batch(const BatchArgs a)
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (ok) {
             __threadfence();  // acquire side: see the predecessors' state writes
-            if (u.ppl == 4) run_task<4>(a, sg, u, t - sg.begin);
+            // layer 3 writing full state takes 2 points per lane whatever the
+            // unit's shape: the stored rows do not depend on the lane-to-point
+            // map, and this multiply-heavy layer needs half the registers so
+            if (u.ppl == 4 && sg.kind != kThirdFull) run_task<4>(a, sg, u, t - sg.begin);
             else run_task<2>(a, sg, u, t - sg.begin);
         }
         __threadfence();  // release side: publish this task's writes
@@ -635,10 +638,15 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                 for (size_t i = w0; i < w1; ++i) {
                     const BatchUnit &u = units[i];
                     if (l > u.k - 1) continue;
-                    const uint32_t ngroups = u.chunk / (32u * u.ppl);
+                    uint32_t ngroups = u.chunk / (32u * u.ppl);
                     uint32_t kind;
-                    const uint32_t nt = layer_tasks(g, u.k, l, ngroups, coarse, &kind);
+                    uint32_t nt = layer_tasks(g, u.k, l, ngroups, coarse, &kind);
                     if (nt == 0) continue;
+                    if (kind == kThirdFull && u.ppl == 4) {
+                        // layer 3 runs with 2 points per lane (see run_task)
+                        ngroups *= 2;
+                        nt *= 2;
+                    }
                     emit(i, l, kind, nt, ngroups, 0);
                     if (writes_state(kind)) {
                         const RowList &L = kind == kSecondTail ? g.state_list : g.deep_list;

@@ -424,7 +424,16 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             vp.layer = l;
             vp.st_in = bufs[(l - 1) & 1u];
             vp.st_out = out == 1 ? red : bufs[l & 1u];
-            s = ppl == 4 ? launch_v2<4>(vp, src, out, st) : launch_v2<2>(vp, src, out, st);
+            if (src == 2 && out == 0 && ppl == 4) {
+                // layer 3 writing full state: the lane-to-point map does not
+                // change the stored rows, and 2 points per lane halve the
+                // registers of this multiply-heavy layer (twice the warps in flight)
+                vp.ngroups = chunk / 64u;
+                s = launch_v2<2>(vp, src, out, st);
+                vp.ngroups = chunk / (32u * ppl);
+            } else {
+                s = ppl == 4 ? launch_v2<4>(vp, src, out, st) : launch_v2<2>(vp, src, out, st);
+            }
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;
             s = launch_fixup(src == 1 ? g.state_list : g.deep_list, vp.st_out,

@@ -57,17 +57,19 @@ __device__ __forceinline__ uint64_t shfl64x(uint64_t v, int mask)
     return __shfl_xor_sync(0xffffffffu, (unsigned long long)v, mask);
 }
 
-// Sum over j in L of the per-label values held by lanes 0..k-1 (lane j holds
-// label j+1's value), for the lane's PPL consecutive points of a group whose
-// first point has high bits `hi_bits` (bits >= LOGP+5 of the point index).
+// Sum over j in L of the per-label values held by lanes first..first+k-1 (lane
+// first+j holds label j+1's value), for the lane's PPL consecutive points of a
+// group whose first point has high bits `hi_bits` (bits >= LOGP+5 of the point
+// index).
 template <int PPL>
 __device__ __forceinline__ void combine_labels(uint64_t lane_val, uint32_t k, int lane,
-                                               uint32_t hi_bits, uint64_t (&out)[PPL])
+                                               uint32_t hi_bits, uint64_t (&out)[PPL],
+                                               uint32_t first = 0)
 {
     constexpr int LOGP = PPL == 4 ? 2 : 1;
     uint64_t base = 0, low0 = 0, low1 = 0;
     for (uint32_t j = 0; j < k; ++j) {
-        const uint64_t bj = shfl64b(lane_val, (int)j);
+        const uint64_t bj = shfl64b(lane_val, (int)(first + j));
         if (j == 0) low0 = bj;
         else if (LOGP == 2 && j == 1) low1 = bj;
         else if (j < (uint32_t)LOGP + 5u) {
@@ -225,8 +227,8 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     uint32_t cur = p.head[it.x];
     uint64_t zv = 0;
     auto enter_head = [&](uint32_t v) {
-        zv = (uint32_t)lane < k ? zval(p, v, lane) : 0ull;
         if constexpr (FROM_Y || FROM_R2) {
+            zv = (uint32_t)lane < k ? zval(p, v, lane) : 0ull;
             uint64_t xv[PPL];
             combine_labels<PPL>(zv, k, lane, hi_bits, xv);
 #pragma unroll
@@ -234,6 +236,12 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         }
     };
     enter_head(cur);
+    // middle layers: the label products y_e z_{v_e,j} of E = floor(32/k)
+    // consecutive entries are formed by one multiplication per lane (lane
+    // e'*k + j holds entry e''s label j), not one per entry
+    const uint32_t E = k <= 16 ? 32u / k : 1u;
+    const uint32_t lane_e = (uint32_t)lane / k, lane_j = (uint32_t)lane % k;
+    uint64_t lab = 0;
 
     for (uint32_t base = it.x; base < it.y; base += 32) {
         const uint32_t ent = base + lane;
@@ -290,10 +298,16 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
                 }
-            } else if (a != b) {
-                const uint64_t coef = shfl64b(m_coef, (int)t);
+            } else {
+              if (t % E == 0) {
+                  const uint32_t src_lane = min(t + lane_e, 31u);
+                  const uint32_t hv = __shfl_sync(0xffffffffu, m_head, (int)src_lane);
+                  const uint64_t yv = shfl64b(m_coef, (int)src_lane);
+                  lab = (lane_e < E && t + lane_e < nb) ? gf64_mul(yv, zval(p, hv, lane_j)) : 0ull;
+              }
+              if (a != b) {
                 uint64_t c[PPL], w[PPL];
-                combine_labels<PPL>(gf64_mul(coef, zv), k, lane, hi_bits, c);
+                combine_labels<PPL>(lab, k, lane, hi_bits, c, (t % E) * k);
                 {
                     const uint64_t *pa = p.st_in + (size_t)a * p.chunk + col;
                     const uint64_t *pb = p.st_in + (size_t)b * p.chunk + col;
@@ -314,6 +328,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 #pragma unroll
                 for (int i = 0; i < PPL; ++i)
                     acc[i] ^= valid[i] ? gf64_mul(c[i], w[i]) : 0ull;
+              }
             }
             const size_t row = (size_t)base + t + 1;  // state row of this entry
             if constexpr (OUT == 0) {
