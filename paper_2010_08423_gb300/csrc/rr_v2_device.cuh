@@ -236,9 +236,10 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         }
     };
     enter_head(cur);
-    // middle layers: the label products y_e z_{v_e,j} of E = floor(32/k)
-    // consecutive entries are formed by one multiplication per lane (lane
-    // e'*k + j holds entry e''s label j), not one per entry
+    // middle layers and layer 3: the label products of E = floor(32/k)
+    // consecutive entries (y_e z_{v_e,j}, resp. y_e rho_{e,j}) are formed by
+    // one multiplication per lane (lane i*k + j holds label j of the block's
+    // i-th entry), not one per entry
     const uint32_t E = k <= 16 ? 32u / k : 1u;
     const uint32_t lane_e = (uint32_t)lane / k, lane_j = (uint32_t)lane % k;
     uint64_t lab = 0;
@@ -283,16 +284,22 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 // the same factoring one layer later: acc^L = (x_v^L x_s^L) * R^L with
                 // R^L = sum_e x_{u_e}^L (y_{e,3} rho_e)^L; y is folded into the label
                 // values lane-parallel, so each entry costs two products per point
+                if (t % E == 0) {
+                    // y rho_j of E consecutive entries, one multiplication per lane
+                    const uint32_t src_lane = min(t + lane_e, 31u);
+                    const uint32_t ae = __shfl_sync(0xffffffffu, m_a, (int)src_lane);
+                    const uint32_t be = __shfl_sync(0xffffffffu, m_b, (int)src_lane);
+                    const uint64_t ye = shfl64b(m_coef, (int)src_lane);
+                    lab = 0;
+                    if (lane_e < E && t + lane_e < nb && ae != be)
+                        lab = gf64_mul(ye, p.pr2[(size_t)ae * k + lane_j] ^ p.pr2[(size_t)be * k + lane_j]);
+                }
                 if (a != b) {
-                    const uint64_t coef = shfl64b(m_coef, (int)t);
                     const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
                     const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
-                    const uint64_t rj = (uint32_t)lane < k
-                                            ? (p.pr2[(size_t)a * k + lane] ^ p.pr2[(size_t)b * k + lane])
-                                            : 0ull;
                     uint64_t xu[PPL], yrho[PPL];
                     combine_labels<PPL>(zu, k, lane, hi_bits, xu);
-                    combine_labels<PPL>(gf64_mul(coef, rj), k, lane, hi_bits, yrho);
+                    combine_labels<PPL>(lab, k, lane, hi_bits, yrho, (t % E) * k);
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) R[i] ^= gf64_mul(xu[i], yrho[i]);
 #pragma unroll
