@@ -51,21 +51,32 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
-    workload, or None if the kernel sources changed since that capture."""
-    import glob
+# the sources whose change invalidates a recorded ncu capture of the query
+# kernels (their code, the device arithmetic and the row lists they read)
+KERNEL_SOURCES = ("rr_device.cuh", "rr_v2_device.cuh", "rr_sieve2.cu", "rr_graph.cu", "rr_internal.h")
+
+
+def kernel_sources_sha1() -> str:
     import hashlib
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_08423_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str, ppl: int, chunk: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
+    workload, or None if the kernel sources or the query shape differ from that
+    capture's."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic_k8_uniform_n1e5_m1e6.json")) as fh:
             rec = json.load(fh)
     except OSError:
         return None
-    h = hashlib.sha1()
-    for path in sorted(glob.glob(os.path.join(ROOT, "paper_2010_08423_gb300", "csrc", "*"))):
-        with open(path, "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest() != rec.get("source_sha1"):
+    if kernel_sources_sha1() != rec.get("source_sha1"):
+        return None
+    if rec.get("shape") != [ppl, chunk]:
         return None
     return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
@@ -254,7 +265,76 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
     return out
 
 
-def motif_metrics(capi, torch, steps=5):
+def gf_mul_peak(capi, torch):
+    """Measured peak rate of the device GF(2^64) multiply (multiplications/s):
+    the rr_bench_gf_mul microbenchmark (register-only dependent chains, both
+    operands changing every step) over the whole GPU, timed with CUDA events."""
+    st = torch.cuda.Stream()
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    capi.rr_bench_gf_mul(sms * 8, 256, 64, sink, st.cuda_stream)
+    st.synchronize()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        mults = capi.rr_bench_gf_mul(sms * 8, 256, 2048, sink, st.cuda_stream)
+        e1.record(st)
+        st.synchronize()
+        best = max(best, mults / (e0.elapsed_time(e1) / 1e3))
+    return best
+
+
+def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, ztable_mults=0):
+    """Per kernel kind of the reduced-state engine: average launch time (from
+    the library's CUDA-event timing of `queries` queries), algorithmic bytes and
+    GF(2^64) multiplications per launch, and the fractions of the measured HBM
+    copy bandwidth and of the measured multiply rate; `bound` is the larger."""
+    S = info["producer_window_rows"]   # state rows (label-space layer 2)
+    D = info["state_compute_rows"]     # deep rows: per-point state of layers >= 3
+    DC = info["deep_compute_rows"]     # deep rows that multiply at layers >= 4
+    T3 = info["deep_tail_rows"]        # last-layer rows
+    P = info["state_rows"]             # rows of the scalar layer-1 prefix
+    c = chunk
+    lg = 7 if ppl == 4 else 6
+    rstride = c // (32 * ppl) * (lg + 1)
+    # layer 3 reads the label-space prefix (2k values) and multiplies twice per point;
+    # layers 4..k-3 read two state rows and multiply once per point
+    l3 = (D * c * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c))
+    mid = (D * c * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k))
+    nmid = max(0, k - 5)
+    if nmid:
+        mid_avg = ((l3[0] + (nmid - 1) * mid[0]) / nmid, (l3[1] + (nmid - 1) * mid[1]) / nmid)
+    else:
+        mid_avg = mid
+    tail = ((D * rstride * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c)) if k == 5 else
+            (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
+    alg = {
+        "first_layer": (P * 8 + P * 12, 0),
+        "second_layer": (S * k * 8 + S * 20 + 2 * S * 8, S * (1 + k)),
+        "mid_layer": mid_avg,
+        "tail_layer": tail,
+        "last_layer": (2 * T3 * rstride * 8 + T3 * 16 + n * 8, T3 * rstride),
+        "ztable": (n * k * 8, ztable_mults),
+    }
+    out = {}
+    for name, (kms, kn) in kt.items():
+        if not kn or name not in alg:
+            continue
+        avg_s = kms / kn / 1e3
+        b, mu = alg[name]
+        gbs = b / avg_s / 1e9
+        gms = mu / avg_s / 1e9
+        fh, fa = gbs / hbm_peak, gms / (mul_peak / 1e9)
+        out[name] = {"avg_launch_us": round(avg_s * 1e6, 2), "launches_per_query": kn / queries,
+                     "alg_bytes_per_launch": int(b), "achieved_gbs": round(gbs, 1),
+                     "hbm_frac": round(fh, 4), "alg_gf_mults_per_launch": int(mu),
+                     "achieved_gmul_s": round(gms, 2), "alu_frac": round(fa, 4),
+                     "bound": "alu" if fa >= fh else "hbm", "time_ms_per_query": round(kms / queries, 4)}
+    return out
+
+
+def motif_metrics(capi, torch, mul_peak, hbm_peak, steps=5):
     """Chung-Lu exponent 2.5, n=1e6, m=1e7, bursty t in [1,10000], delta ~
     U{5..50}, 8 colours; k-RestlessMotifReach with k=10 from the first vertex
     with an out-edge, motif = its colour + 9 uniform colours (seeded)."""
@@ -283,10 +363,28 @@ def motif_metrics(capi, torch, steps=5):
                 st.synchronize()
                 tot += e0.elapsed_time(e1)
         reach = int((d_w != 0).sum().item())
+        # per-kernel roofline from one more query launched kernel by kernel
+        capi.rr_timing_enable(True)
+        capi.rr_timing_read(reset=True)
+        try:
+            capi.rr_reach_device(G.handle, s, 10, 999, d_w, None, st.cuda_stream, motif=motif)
+            st.synchronize()
+            kt = capi.rr_timing_read(reset=True)
+        finally:
+            capi.rr_timing_enable(False)
     units = float(2 ** 10) * 10 * m
+    ppl = 4
+    chunk = min(2 ** 10, 4 * 32 * ppl)  # the engine's default shape for k = 10
+    # a coloured z entry multiplies once per shade of its vertex's colour (Eq. 3)
+    mu = np.bincount(np.asarray(motif, dtype=np.int64), minlength=256)
+    zt = 10 * int((np.bincount(np.asarray(g["color"], dtype=np.int64), minlength=256) * mu).sum())
+    by_kernel = kernel_rooflines(info, 10, chunk, ppl, n, kt, 1, hbm_peak, mul_peak, ztable_mults=zt)
+    dom = max(by_kernel, key=lambda k_: by_kernel[k_]["time_ms_per_query"]) if by_kernel else None
     return {"workload": "Chung-Lu exponent 2.5, n=1e6, m=1e7, bursty t in [1,10000], delta~U{5..50}, "
                         "8 colours; k-RestlessMotifReach k=10, motif = source colour + 9 uniform colours",
             "value": units * steps / (tot / 1e3), "unit": UNIT, "ms_per_query": tot / steps,
+            "dominant_kernel": dom, "roofline_by_kernel": by_kernel,
+            "shape": {"points_per_lane": ppl, "points_per_chunk": chunk},
             "reachable_vertices": reach, "graph_load_s": round(load_s, 3),
             "state_rows": info["producer_window_rows"] + 1, "deep_rows": info["state_compute_rows"],
             "max_in_degree": info["max_in_degree"], "l2": "flushed between queries"}
@@ -410,6 +508,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--dense", action="store_true", help="dense state layout (every row stored)")
+    ap.add_argument("--shape", default=None,
+                    help="points per lane x points per chunk (e.g. 2x256) instead of the autotuner; "
+                         "profiling runs pin the shape the autotuner picks without a profiler")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -432,7 +533,11 @@ def main():
     G = capi.Graph(g, capi.FLAG_DENSE_STATE if args.dense else 0)
     load_s = time.perf_counter() - t0
     info = G.info()
-    ppl, chunk = capi.rr_autotune(G.handle, K)
+    if args.shape:
+        ppl, chunk = (int(x) for x in args.shape.lower().split("x"))
+        capi.rr_set_tuning(G.handle, K, ppl, chunk)
+    else:
+        ppl, chunk = capi.rr_autotune(G.handle, K)
 
     stream = torch.cuda.Stream()
     d_w = torch.empty(n, dtype=torch.int64, device="cuda")
@@ -502,42 +607,32 @@ def main():
         e2e_s = float(t.item())
     e2e_value = world * args.steps * units / e2e_s
 
-    # roofline: algorithmic bytes per launch of each kernel kind of the
-    # reduced-state engine, over its measured average launch duration
+    # roofline: algorithmic bytes and GF(2^64) multiplications per launch of
+    # each kernel kind, against the measured copy bandwidth and the measured
+    # multiply rate; the dominant kernel reports the binding one
     peaks, peak_kind = measured_peaks()
-    srows = info["producer_window_rows"]      # state rows (layer 2, label space)
-    drows = info["state_compute_rows"]        # deep rows: per-point state of layers >= 3
-    dc = info["deep_compute_rows"]            # deep rows that multiply at layers >= 4
-    t3 = info["deep_tail_rows"]               # last-layer rows
-    lg = 7 if ppl == 4 else 6
-    rstride = chunk // (32 * ppl) * (lg + 1)
-    alg = {
-        "second_layer": srows * K * 8 + srows * 20 + 2 * srows * 8 + srows * K * 8,
-        "mid_layer": drows * chunk * 8 + 2 * dc * chunk * 8 + drows * 20,
-        "tail_layer": drows * rstride * 8 + 2 * dc * chunk * 8 + drows * 20,
-        "last_layer": 2 * t3 * rstride * 8 + t3 * 16 + n * 8,
-        "first_layer": info["state_rows"] * 8 * 2,
-        "ztable": n * K * 8,
-    }
+    mul_peak = gf_mul_peak(capi, torch)
+    by_kernel = kernel_rooflines(info, K, chunk, ppl, n, kt, 5, peaks["hbm_gbs"], mul_peak)
     if args.dense:
-        alg = {"mid_layer": (m + 2 * info["window_rows"]) * chunk * 8 + m * 16 + n * K * 8}
-    by_kernel = {}
-    for name, (kms, kn) in kt.items():
-        if kn and name in alg:
-            avg_s = kms / kn / 1e3
-            gbs = alg[name] / avg_s / 1e9
-            by_kernel[name] = {"avg_launch_us": round(avg_s * 1e6, 2), "launches_per_query": kn / 5,
-                               "alg_bytes_per_launch": alg[name], "achieved_gbs": round(gbs, 1),
-                               "frac": round(gbs / peaks["hbm_gbs"], 4)}
+        by_kernel = {}
     dom = max(by_kernel, key=lambda k_: kt[k_][0]) if by_kernel else None
     roofline = None
     if dom:
         d = by_kernel[dom]
-        roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": d["frac"],
-                    "traffic": None if args.dense else recorded_traffic(dom), "kernel": dom,
-                    "peak_kind": peak_kind, "avg_launch_us": d["avg_launch_us"],
-                    "alg_bytes_per_launch": d["alg_bytes_per_launch"]}
+        traffic = recorded_traffic(dom, ppl, chunk)
+        common = {"traffic": traffic, "kernel": dom, "avg_launch_us": d["avg_launch_us"],
+                  "alg_bytes_per_launch": d["alg_bytes_per_launch"],
+                  "alg_gf_mults_per_launch": d["alg_gf_mults_per_launch"],
+                  "hbm_frac": d["hbm_frac"], "alu_frac": d["alu_frac"]}
+        if d["bound"] == "alu":
+            roofline = {"bound": "alu", "achieved": d["achieved_gmul_s"],
+                        "peak": round(mul_peak / 1e9, 2), "unit": "GF(2^64) Gmul/s",
+                        "frac": d["alu_frac"],
+                        "peak_kind": "measured live: rr_bench_gf_mul, register-only multiply chains "
+                                     "on all SMs (integer issue bound)", **common}
+        else:
+            roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": d["hbm_frac"], "peak_kind": peak_kind, **common}
     tot_k = max(1e-9, sum(v[0] for v in kt.values()))
     kernel_share = {k_: round(v[0] / tot_k, 4) for k_, v in kt.items() if v[1]}
 
@@ -548,8 +643,10 @@ def main():
             "config": {"workload": WORKLOAD, "graph_seed": GRAPH_SEED, "l2": "flushed between steps",
                        "state_layout": "dense" if args.dense else "compact",
                        "points_per_lane": ppl, "points_per_chunk": chunk,
-                       "state_rows": srows + 1, "deep_rows": drows, "deep_compute_rows": dc,
-                       "last_layer_rows": t3,
+                       "state_rows": info["producer_window_rows"] + 1,
+                       "deep_rows": info["state_compute_rows"],
+                       "deep_compute_rows": info["deep_compute_rows"],
+                       "last_layer_rows": info["deep_tail_rows"],
                        "producer_rows": info["state_rows"] - 1, "window_rows": info["window_rows"],
                        "graph_load_s": round(load_s, 3)},
             "roofline": roofline,
@@ -566,7 +663,7 @@ def main():
         line["served"] = served_metrics(capi, g)
         line["atmost_k"] = atmost_metrics(capi, torch, g)
         line["fine_grained"] = fine_metrics(capi, torch, g)
-        line["motif_powerlaw"] = motif_metrics(capi, torch)
+        line["motif_powerlaw"] = motif_metrics(capi, torch, mul_peak, peaks["hbm_gbs"])
         g5 = W.served_powerlaw()
         line["served_powerlaw"] = served_metrics(
             capi, g5, nq=16, seed=W.GRAPH_SEED_BASE + 5, warm=4,

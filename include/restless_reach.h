@@ -277,6 +277,16 @@ rr_status rr_debug_graph(const rr_graph *g, uint32_t *off, uint32_t *row_eid, ui
 rr_status rr_debug_ztable(const rr_graph *g, const rr_query *q, uint64_t *out);
 /* rr_debug_gf_mul: out[i] = a[i]*b[i] in GF(2^64) on the device, HOST arrays. */
 rr_status rr_debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count);
+/* rr_bench_gf_mul: the device GF(2^64) multiply at its peak rate, for the
+ * arithmetic roofline of the sieve kernels (not part of the paper's method).
+ * Enqueues blocks x threads threads on `stream`, each running four dependent
+ * multiply chains of `iters` steps in registers (both operands change every
+ * step); *mults (host) receives the number of multiplications enqueued;
+ * d_sink (one uint64, device) keeps the results live and is practically never
+ * written. Errors: RR_EINVAL for threads == 0 or > 1024, blocks == 0 or a NULL
+ * pointer; RR_ECUDA if the launch fails. */
+rr_status rr_bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *d_sink,
+                          uint64_t *mults, void *stream);
 /* rr_debug_draw: out[i] = draw(key, first + i) on the device, HOST out. */
 rr_status rr_debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out);
 

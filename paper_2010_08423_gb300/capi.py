@@ -57,7 +57,7 @@ EXPORTED = [
     "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
-    "rr_reach_arrival_device", "rr_extract_path", "rr_reach_sources_device",
+    "rr_reach_arrival_device", "rr_extract_path", "rr_reach_sources_device", "rr_bench_gf_mul",
 ]
 
 _lib = None
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_atmost_device": [vp, u32, u32, u64, vp, vp, vp],
         "rr_reach_arrival_device": [vp, pq, vp, vp, vp, vp, vp],
         "rr_extract_path": [vp, pq, u32, vp, vp, vp],
+        "rr_bench_gf_mul": [u32, u32, u32, vp, ctypes.POINTER(u64), vp],
         "rr_reach_sources_device": [vp, vp, u32, u32, u64, vp, vp, vp, vp, vp],
         "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
         "rr_server_destroy": [vp],
@@ -240,6 +241,14 @@ def rr_reach_sources_device(g, sources, k, seed, d_witness, d_bitmap=None, d_sep
                                           None if mo is None else mo.ctypes.data,
                                           _dp(d_separators), _dp(d_bitmap), _dp(d_witness),
                                           _dp(stream)))
+
+
+def rr_bench_gf_mul(blocks, threads, iters, d_sink, stream=None) -> int:
+    """Enqueues the multiply-rate microbenchmark; returns the multiplications."""
+    n = ctypes.c_uint64()
+    _check(load().rr_bench_gf_mul(int(blocks), int(threads), int(iters), _dp(d_sink),
+                                  ctypes.byref(n), _dp(stream)))
+    return n.value
 
 
 def rr_extract_path(g, source, k, seed, target, motif=None):

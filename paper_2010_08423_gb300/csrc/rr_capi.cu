@@ -81,6 +81,8 @@ rr_status debug_point_sums(const Graph &g, const rr_query *q, const uint32_t *ma
                            uint32_t nmasks, uint64_t *out);
 rr_status debug_ztable(const Graph &g, const rr_query *q, uint64_t *out);
 rr_status debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count);
+rr_status bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *d_sink,
+                       uint64_t *mults, cudaStream_t st);
 rr_status debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out);
 rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
                        uint64_t *d_witness, int32_t *d_status, cudaStream_t st);
@@ -300,6 +302,13 @@ rr_status rr_debug_ztable(const rr_graph *g, const rr_query *q, uint64_t *out)
     clear_error();
     if (!g || !out) return fail(RR_EINVAL, "rr_debug_ztable: NULL argument");
     return debug_ztable(*g, q, out);
+}
+
+rr_status rr_bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *d_sink,
+                          uint64_t *mults, void *stream)
+{
+    clear_error();
+    return bench_gf_mul(blocks, threads, iters, d_sink, mults, (cudaStream_t)stream);
 }
 
 rr_status rr_debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count)

@@ -598,6 +598,34 @@ rr_status debug_ztable(const Graph &g, const rr_query *q, uint64_t *out)
     return RR_OK;
 }
 
+// Multiply-rate microbenchmark: four dependent chains per thread, each step
+// multiplying two values that both change every iteration (so nothing about an
+// operand can be hoisted out of the loop), and nothing read from memory.
+__global__ void k_gf_mul_rate(uint32_t iters, uint64_t *sink)
+{
+    const uint64_t id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t a = sm_mix(id + 1), b = sm_mix(id + 2), c = sm_mix(id + 3), d = sm_mix(id + 4);
+    for (uint32_t i = 0; i < iters; ++i) {
+        const uint64_t a2 = gf64_mul(a, b), b2 = gf64_mul(b, c), c2 = gf64_mul(c, d), d2 = gf64_mul(d, a);
+        a = a2;
+        b = b2;
+        c = c2;
+        d = d2;
+    }
+    if ((a ^ b ^ c ^ d) == 0x5EEDull) sink[0] = a;  // keeps the chains live; practically never taken
+}
+
+rr_status bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *d_sink,
+                       uint64_t *mults, cudaStream_t st)
+{
+    if (!blocks || !threads || threads > 1024 || !d_sink || !mults)
+        return fail(RR_EINVAL, "rr_bench_gf_mul: bad launch shape or NULL argument");
+    k_gf_mul_rate<<<blocks, threads, 0, st>>>(iters, d_sink);
+    RR_LAUNCHED();
+    *mults = (uint64_t)blocks * threads * iters * 4ull;
+    return RR_OK;
+}
+
 rr_status debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count)
 {
     if (count == 0) return RR_OK;
