@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstring>
 
+#define RR_OUTLINED_MUL 1  // one out-of-line multiply for the many task kinds of k_batch
 #include "rr_v2_device.cuh"
 
 namespace rr {
@@ -222,7 +223,7 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
     }
 }
 
-// MINB = blocks per SM the register budget is set for: 4 (128 registers, some
+// MINB = blocks per SM the register budget is set for: 6 (80 registers, a few
 // spilled) for large batches, where more resident warps hide the tasks'
 // latencies; 2 (no spills) for small batches, whose critical path is the
 // per-task time.
@@ -581,7 +582,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             RR_CUDA(cudaGetDevice(&dev));
             RR_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, dev));
             RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.blocks_per_sm, k_batch<2>, kW2 * 32, 0));
-            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.blocks_per_sm_wide, k_batch<4>,
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.blocks_per_sm_wide, k_batch<6>,
                                                                   kW2 * 32, 0));
             B.blocks_per_sm = std::max(1, B.blocks_per_sm);
             B.blocks_per_sm_wide = std::max(1, B.blocks_per_sm_wide);
@@ -820,7 +821,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             const unsigned blocks =
                 (unsigned)std::max(1, B.sms * (coarse ? B.blocks_per_sm_wide : B.blocks_per_sm));
             const int bslot = timing_begin(st);
-            if (coarse) k_batch<4><<<blocks, kW2 * 32, 0, st>>>(a);
+            if (coarse) k_batch<6><<<blocks, kW2 * 32, 0, st>>>(a);
             else k_batch<2><<<blocks, kW2 * 32, 0, st>>>(a);
             timing_end(bslot, kTimeBatch, st);
             RR_LAUNCHED();

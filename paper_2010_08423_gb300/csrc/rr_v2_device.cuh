@@ -9,6 +9,23 @@
 
 namespace rr {
 
+// The multiply used by the per-warp layer code. Kernels that inline many task
+// kinds (the persistent batch) define RR_OUTLINED_MUL before including this
+// header and call one out-of-line copy: inlining ~300 integer instructions at
+// every call site of every kind overflowed the instruction cache there. The
+// one-query kernels, each a single variant, keep it inline.
+#ifdef RR_OUTLINED_MUL
+__device__ __noinline__ static uint64_t rr_mul(uint64_t a, uint64_t b)
+{
+    return gf64_mul(a, b);
+}
+#else
+__device__ __forceinline__ static uint64_t rr_mul(uint64_t a, uint64_t b)
+{
+    return gf64_mul(a, b);
+}
+#endif
+
 constexpr int kW2 = 4;  // warps per block
 
 struct V2Params {
@@ -140,9 +157,9 @@ __device__ __forceinline__ void first2_closed(const V2Params &p, const uint32_t 
         else hi = mid;
     }
     const uint32_t v = lo;
-    const uint64_t perm = gf64_mul(zval(p, s, 0), zval(p, v, 1)) ^ gf64_mul(zval(p, s, 1), zval(p, v, 0));
+    const uint64_t perm = rr_mul(zval(p, s, 0), zval(p, v, 1)) ^ rr_mul(zval(p, s, 1), zval(p, v, 0));
     const uint32_t e = row_eid[r];
-    const uint64_t val = gf64_mul(sm_draw(p.qd->key_y, (uint64_t)e * 32u), perm);  // y_{e,1}
+    const uint64_t val = rr_mul(sm_draw(p.qd->key_y, (uint64_t)e * 32u), perm);  // y_{e,1}
     if (val) atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + v), (unsigned long long)val);
     if (p.qd->E) p.qd->E[e] = val;  // one row per edge
 }
@@ -171,13 +188,13 @@ __device__ __forceinline__ void last3_closed(const V2Params &p, uint32_t ent)
         c[j] = zval(p, v, j);
     }
     // expansion along z_s: 2x2 permanents of (z_u, z_v) without column j
-    const uint64_t m0 = gf64_mul(b[1], c[2]) ^ gf64_mul(b[2], c[1]);
-    const uint64_t m1 = gf64_mul(b[0], c[2]) ^ gf64_mul(b[2], c[0]);
-    const uint64_t m2 = gf64_mul(b[0], c[1]) ^ gf64_mul(b[1], c[0]);
-    const uint64_t perm = gf64_mul(a[0], m0) ^ gf64_mul(a[1], m1) ^ gf64_mul(a[2], m2);
+    const uint64_t m0 = rr_mul(b[1], c[2]) ^ rr_mul(b[2], c[1]);
+    const uint64_t m1 = rr_mul(b[0], c[2]) ^ rr_mul(b[2], c[0]);
+    const uint64_t m2 = rr_mul(b[0], c[1]) ^ rr_mul(b[1], c[0]);
+    const uint64_t perm = rr_mul(a[0], m0) ^ rr_mul(a[1], m1) ^ rr_mul(a[2], m2);
     const uint32_t e = p.eid[ent];
     const uint64_t y = sm_draw(p.qd->key_y, (uint64_t)e * 32u + 1u);  // y_{e,2}
-    const uint64_t val = gf64_mul(gf64_mul(y, Y), perm);
+    const uint64_t val = rr_mul(rr_mul(y, Y), perm);
     if (val) atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + v), (unsigned long long)val);
     if (p.qd->E) p.qd->E[e] = val;  // one entry per edge
 }
@@ -232,7 +249,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
             uint64_t xv[PPL];
             combine_labels<PPL>(zv, k, lane, hi_bits, xv);
 #pragma unroll
-            for (int i = 0; i < PPL; ++i) xvxs[i] = gf64_mul(xv[i], xs[i]);
+            for (int i = 0; i < PPL; ++i) xvxs[i] = rr_mul(xv[i], xs[i]);
         }
     };
     enter_head(cur);
@@ -255,7 +272,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         if (has) {
             m_coef = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u));
             if constexpr (FROM_Y) {
-                m_coef = gf64_mul(m_coef, p.py[m_a] ^ p.py[m_b]);  // y_{e,2} * Y_e
+                m_coef = rr_mul(m_coef, p.py[m_a] ^ p.py[m_b]);  // y_{e,2} * Y_e
             }
             if constexpr (FROM_Y || FROM_R2) m_src = p.src[ent];
         }
@@ -275,11 +292,11 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
                 const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
                 uint64_t r[PPL];
-                combine_labels<PPL>(gf64_mul(coef, zu), k, lane, hi_bits, r);
+                combine_labels<PPL>(rr_mul(coef, zu), k, lane, hi_bits, r);
 #pragma unroll
                 for (int i = 0; i < PPL; ++i) R[i] ^= r[i];
 #pragma unroll
-                for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
+                for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? rr_mul(xvxs[i], R[i]) : 0ull;
             } else if constexpr (FROM_R2) {
                 // the same factoring one layer later: acc^L = (x_v^L x_s^L) * R^L with
                 // R^L = sum_e x_{u_e}^L (y_{e,3} rho_e)^L; y is folded into the label
@@ -292,7 +309,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     const uint64_t ye = shfl64b(m_coef, (int)src_lane);
                     lab = 0;
                     if (lane_e < E && t + lane_e < nb && ae != be)
-                        lab = gf64_mul(ye, p.pr2[(size_t)ae * k + lane_j] ^ p.pr2[(size_t)be * k + lane_j]);
+                        lab = rr_mul(ye, p.pr2[(size_t)ae * k + lane_j] ^ p.pr2[(size_t)be * k + lane_j]);
                 }
                 if (a != b) {
                     const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
@@ -301,16 +318,16 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     combine_labels<PPL>(zu, k, lane, hi_bits, xu);
                     combine_labels<PPL>(lab, k, lane, hi_bits, yrho, (t % E) * k);
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) R[i] ^= gf64_mul(xu[i], yrho[i]);
+                    for (int i = 0; i < PPL; ++i) R[i] ^= rr_mul(xu[i], yrho[i]);
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? gf64_mul(xvxs[i], R[i]) : 0ull;
+                    for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? rr_mul(xvxs[i], R[i]) : 0ull;
                 }
             } else {
               if (t % E == 0) {
                   const uint32_t src_lane = min(t + lane_e, 31u);
                   const uint32_t hv = __shfl_sync(0xffffffffu, m_head, (int)src_lane);
                   const uint64_t yv = shfl64b(m_coef, (int)src_lane);
-                  lab = (lane_e < E && t + lane_e < nb) ? gf64_mul(yv, zval(p, hv, lane_j)) : 0ull;
+                  lab = (lane_e < E && t + lane_e < nb) ? rr_mul(yv, zval(p, hv, lane_j)) : 0ull;
               }
               if (a != b) {
                 uint64_t c[PPL], w[PPL];
@@ -334,7 +351,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 }
 #pragma unroll
                 for (int i = 0; i < PPL; ++i)
-                    acc[i] ^= valid[i] ? gf64_mul(c[i], w[i]) : 0ull;
+                    acc[i] ^= valid[i] ? rr_mul(c[i], w[i]) : 0ull;
               }
             }
             const size_t row = (size_t)base + t + 1;  // state row of this entry
@@ -407,7 +424,7 @@ __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t it
         const uint32_t m_src = has ? p.src[ent] : 0u;
         uint64_t m_coef = 0;
         if (has)
-            m_coef = gf64_mul(sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + 1u),  // y_{e,2}
+            m_coef = rr_mul(sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + 1u),  // y_{e,2}
                               p.py[p.ia[ent]] ^ p.py[p.ib[ent]]);               // Y_e
         const uint32_t nb = min(32u, it.y - base);
         for (uint32_t t = 0; t < nb; ++t) {
@@ -419,7 +436,7 @@ __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t it
             const uint64_t coef = shfl64b(m_coef, (int)t);
             const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
             if ((uint32_t)lane < k) {
-                acc ^= gf64_mul(coef, zval(p, u, lane));
+                acc ^= rr_mul(coef, zval(p, u, lane));
                 pr2[((size_t)base + t + 1) * k + lane] = acc;
             }
         }
@@ -522,7 +539,7 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
     uint64_t zsel = zsel_of(cur);
     uint64_t acc = 0;
     auto flush = [&](uint32_t v) {
-        uint64_t t = active ? gf64_mul(zsel, acc) : 0ull;
+        uint64_t t = active ? rr_mul(zsel, acc) : 0ull;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t ^= shfl64x(t, off);
         if (lane == 0 && t) atomicXor(reinterpret_cast<unsigned long long *>(S + v),
@@ -553,13 +570,13 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
                 const uint64_t *sa = p.st_in + (size_t)a * slots + lane;
                 const uint64_t *sb = p.st_in + (size_t)b * slots + lane;
                 const uint64_t tv = COHERENT ? (__ldcg(sa) ^ __ldcg(sb)) : (*sa ^ *sb);
-                yt = gf64_mul(y, tv);
+                yt = rr_mul(y, tv);
                 acc ^= yt;
             }
             if (E) {
                 // this entry's own sum over the chunk's points: the flush's
                 // product taken per entry instead of per head
-                uint64_t c = active ? gf64_mul(zsel, yt) : 0ull;
+                uint64_t c = active ? rr_mul(zsel, yt) : 0ull;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) c ^= shfl64x(c, off);
                 const uint32_t e = __shfl_sync(0xffffffffu, m_eid, (int)t);

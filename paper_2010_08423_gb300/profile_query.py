@@ -1,7 +1,8 @@
 """Runs warm-up queries and then one query of a named synthetic workload, for
 a profiler to capture (e.g. ``ncu ... python -m paper_2010_08423_gb300.profile_query
 --workload powerlaw-2e5 --k 10``). Prints the query's time and its number of
-reached vertices. Inputs come from ``workloads`` (seeded, synthetic).
+reached vertices (or, with --batch N, times one persistent batched launch of N
+mixed queries). Inputs come from ``workloads`` (seeded, synthetic).
 
 Workloads:
   uniform-1e5    n = 1e5, m = 1e6 uniform multigraph, t ~ U[1,1000], delta ~ U{1..20}
@@ -25,6 +26,9 @@ def main(argv=None) -> int:
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--motif", action="store_true", help="a motif query (source colour + k-1 colours)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead: one persistent batched launch of this many queries, "
+                         "k ~ U{4..12}, odd ones coloured")
     args = ap.parse_args(argv)
 
     if args.workload == "uniform-1e5":
@@ -36,6 +40,21 @@ def main(argv=None) -> int:
         s = W.first_source(g)
     motif = W.motif_for(g, s, args.k, W.GRAPH_SEED_BASE + 3) if args.motif else None
     torch.cuda.set_device(0)
+    if args.batch:
+        qs = W.query_set(g, args.batch, 4, 12, W.GRAPH_SEED_BASE + 4)
+        with capi.Graph(g) as G:
+            d_w = torch.zeros((len(qs), g["n"]), dtype=torch.int64, device="cuda")
+            st = torch.cuda.Stream()
+            for _ in range(args.warmup):
+                capi.rr_reach_batch_device(G.handle, qs, d_w, None, None, st.cuda_stream)
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            capi.rr_reach_batch_device(G.handle, qs, d_w, None, None, st.cuda_stream)
+            e1.record(st)
+            st.synchronize()
+            print(f"{args.workload} batch of {len(qs)} ms {e0.elapsed_time(e1):.3f}")
+        return 0
     with capi.Graph(g) as G:
         d_w = torch.zeros(g["n"], dtype=torch.int64, device="cuda")
         st = torch.cuda.Stream()
