@@ -287,6 +287,16 @@ rr_status rr_debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, u
  * pointer; RR_ECUDA if the launch fails. */
 rr_status rr_bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *d_sink,
                           uint64_t *mults, void *stream);
+/* rr_debug_wait_probe: runs the bounded wait of the persistent batched kernel
+ * (the wait a task does for the tasks it depends on) on a counter that nothing
+ * increments, so that its failure path can be tested without a fault: the wait
+ * must give up after timeout_ns of device time (or at once when abort_preset is
+ * non-zero: the batch's abort flag is set), report RR_ETIMEDOUT in *status (host)
+ * and leave the context usable. *elapsed_ns (host) = the wait's duration.
+ * Synchronous, default stream. Errors: RR_EINVAL for NULL outputs or a timeout
+ * above 10 s. Not part of the paper's method. */
+rr_status rr_debug_wait_probe(uint64_t timeout_ns, int32_t abort_preset, int32_t *status,
+                              uint64_t *elapsed_ns);
 /* rr_debug_draw: out[i] = draw(key, first + i) on the device, HOST out. */
 rr_status rr_debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out);
 

@@ -58,6 +58,7 @@ EXPORTED = [
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
     "rr_reach_arrival_device", "rr_extract_path", "rr_reach_sources_device", "rr_bench_gf_mul",
+    "rr_debug_wait_probe",
 ]
 
 _lib = None
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_arrival_device": [vp, pq, vp, vp, vp, vp, vp],
         "rr_extract_path": [vp, pq, u32, vp, vp, vp],
         "rr_bench_gf_mul": [u32, u32, u32, vp, ctypes.POINTER(u64), vp],
+        "rr_debug_wait_probe": [u64, i32, ctypes.POINTER(i32), ctypes.POINTER(u64)],
         "rr_reach_sources_device": [vp, vp, u32, u32, u64, vp, vp, vp, vp, vp],
         "rr_server_create": [vp, u64, u32, ctypes.POINTER(vp)],
         "rr_server_destroy": [vp],
@@ -241,6 +243,15 @@ def rr_reach_sources_device(g, sources, k, seed, d_witness, d_bitmap=None, d_sep
                                           None if mo is None else mo.ctypes.data,
                                           _dp(d_separators), _dp(d_bitmap), _dp(d_witness),
                                           _dp(stream)))
+
+
+def rr_debug_wait_probe(timeout_ns: int, abort_preset: bool = False):
+    """(status, elapsed_ns) of the batch kernel's bounded wait on a counter that
+    nothing increments."""
+    st, ns = ctypes.c_int32(), ctypes.c_uint64()
+    _check(load().rr_debug_wait_probe(int(timeout_ns), 1 if abort_preset else 0, ctypes.byref(st),
+                                      ctypes.byref(ns)))
+    return st.value, ns.value
 
 
 def rr_bench_gf_mul(blocks, threads, iters, d_sink, stream=None) -> int:

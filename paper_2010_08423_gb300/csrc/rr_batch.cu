@@ -262,6 +262,19 @@ __global__ void __launch_bounds__(kW2 * 32, MINB) k_batch(const BatchArgs a)
     }
 }
 
+// Exercises wait_for on a counter that nothing increments (out[0] = 1 if the
+// wait ended without the counter, out[1] = nanoseconds it took): the bounded
+// wait must give up after timeout_ns, or at once when the abort flag is set,
+// and leave the context usable.
+__global__ void k_wait_probe(BatchArgs a, const uint32_t *ctr, uint64_t *out)
+{
+    if (threadIdx.x != 0) return;
+    const uint64_t t0 = global_ns();
+    const bool ok = wait_for(a, ctr, 1u);
+    out[0] = ok ? 0ull : 1ull;
+    out[1] = global_ns() - t0;
+}
+
 // Prologue / epilogue over all queries of the batch (blockIdx.y = query).
 __global__ void k_batch_ztable(uint32_t n, const QueryDesc *__restrict__ descs,
                                const uint8_t *__restrict__ color, uint64_t *__restrict__ z_all,
@@ -861,6 +874,34 @@ __global__ void k_union_bitmap(const uint64_t *__restrict__ W, uint32_t rows, ui
 // from and joined back to `st`; if the
 // scratch of all of them does not fit 60% of free device memory they run in
 // order on the graph's own workspace instead.
+// Runs the persistent kernel's bounded wait on a counter that is never
+// incremented (see k_wait_probe); synchronous.
+rr_status debug_wait_probe(uint64_t timeout_ns, int abort_preset, int32_t *status,
+                           uint64_t *elapsed_ns)
+{
+    if (!status || !elapsed_ns) return fail(RR_EINVAL, "rr_debug_wait_probe: NULL argument");
+    if (timeout_ns > 10000000000ull) return fail(RR_EINVAL, "rr_debug_wait_probe: timeout above 10 s");
+    DevBuf buf;
+    RR_CUDA(buf.reserve(32));  // [0] counter, [1] next task, [2] abort flag, [4..7] out
+    uint32_t *w = buf.as<uint32_t>();
+    RR_CUDA(cudaMemset(buf.p, 0, 32));
+    if (abort_preset) {
+        const uint32_t one = 1;
+        RR_CUDA(cudaMemcpy(w + 2, &one, 4, cudaMemcpyHostToDevice));
+    }
+    BatchArgs a{};
+    a.ctl = w + 1;  // ctl[1] is the abort flag
+    a.timeout_ns = timeout_ns;
+    uint64_t *out = reinterpret_cast<uint64_t *>(w + 4);
+    k_wait_probe<<<1, 32>>>(a, w, out);
+    RR_LAUNCHED();
+    uint64_t h[2] = {0, 0};
+    RR_CUDA(cudaMemcpy(h, out, 16, cudaMemcpyDeviceToHost));
+    *status = h[0] ? (int32_t)RR_ETIMEDOUT : (int32_t)RR_OK;
+    *elapsed_ns = h[1];
+    return RR_OK;
+}
+
 rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st)
 {

@@ -83,6 +83,8 @@ rr_status debug_ztable(const Graph &g, const rr_query *q, uint64_t *out);
 rr_status debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count);
 rr_status bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *d_sink,
                        uint64_t *mults, cudaStream_t st);
+rr_status debug_wait_probe(uint64_t timeout_ns, int abort_preset, int32_t *status,
+                           uint64_t *elapsed_ns);
 rr_status debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out);
 rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
                        uint64_t *d_witness, int32_t *d_status, cudaStream_t st);
@@ -302,6 +304,13 @@ rr_status rr_debug_ztable(const rr_graph *g, const rr_query *q, uint64_t *out)
     clear_error();
     if (!g || !out) return fail(RR_EINVAL, "rr_debug_ztable: NULL argument");
     return debug_ztable(*g, q, out);
+}
+
+rr_status rr_debug_wait_probe(uint64_t timeout_ns, int32_t abort_preset, int32_t *status,
+                              uint64_t *elapsed_ns)
+{
+    clear_error();
+    return debug_wait_probe(timeout_ns, abort_preset, status, elapsed_ns);
 }
 
 rr_status rr_bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *d_sink,
