@@ -349,7 +349,7 @@ k_batch_second(ListPtrs state, const QueryDesc *__restrict__ descs, const uint64
     vp.ib = state.b0;
     vp.items = state.items;
     vp.nitems = state.nitems;
-    second_label_warp(vp, task, pr2);
+    second_label_warp<false>(vp, task, pr2);
 }
 
 // the batch's k = 2 queries in closed form (blockIdx.y = query)

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uin
 template <int PPL, bool FROM_Y, int OUT, bool FROM_R2 = false>
 __global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
 {
-    pdl_enter();
+    // pdl_enter() inside layer_warp, after the graph- and query-only loads
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems * p.ngroups) return;
     const uint32_t item = task / p.ngroups;
@@ -139,10 +139,10 @@ static rr_status launch_fixup(const RowList &L, uint64_t *buf, uint32_t width, c
 
 __global__ void __launch_bounds__(kW2 * 32) k_second_label(const V2Params p, uint64_t *__restrict__ pr2)
 {
-    pdl_enter();
+    // pdl_enter() inside second_label_warp, after the graph- and query-only loads
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
-    second_label_warp(p, task, pr2);
+    second_label_warp<true>(p, task, pr2);
 }
 
 __global__ void k_first2(const V2Params p, const uint32_t *__restrict__ off,
@@ -164,7 +164,7 @@ __global__ void k_last3(const V2Params p, uint32_t count)
 template <int LG>
 __global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
 {
-    pdl_enter();
+    // pdl_enter() inside last_warp, after the graph- and query-only loads
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
     last_warp<LG, false>(p, task);

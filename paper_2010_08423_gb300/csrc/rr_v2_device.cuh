@@ -64,6 +64,12 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// The layer bodies of the one-query kernels call pdl_enter() late: after the
+// loads and hashes that read only graph and query data (row metadata, y and z
+// draws, per-head factors), before their first read of a previous kernel's
+// results and before any write. When a kernel of the chain starts, the kernel
+// two places before it has completed (its predecessor let it launch only after
+// its own wait), so the query's z-table is ready; all writes wait.
 
 __device__ __forceinline__ uint64_t shfl64b(uint64_t v, int src)
 {
@@ -271,10 +277,13 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         uint32_t m_src = 0;
         if (has) {
             m_coef = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u));
-            if constexpr (FROM_Y) {
-                m_coef = rr_mul(m_coef, p.py[m_a] ^ p.py[m_b]);  // y_{e,2} * Y_e
-            }
             if constexpr (FROM_Y || FROM_R2) m_src = p.src[ent];
+        }
+        if constexpr (!COHERENT) {
+            if (base == it.x) pdl_enter();  // the previous layer's results are read from here on
+        }
+        if constexpr (FROM_Y) {
+            if (has) m_coef = rr_mul(m_coef, p.py[m_a] ^ p.py[m_b]);  // y_{e,2} * Y_e
         }
         const uint32_t nb = min(32u, it.y - base);
         for (uint32_t t = 0; t < nb; ++t) {
@@ -408,6 +417,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 // so that P_2^L[f'] = x_v^L x_s^L sum_{j in L} (y Y)_{f'} z_{u_{f'},j}. Independent of
 // the point chunk; lane j owns label j (one multiplication per lane and row).
 // ---------------------------------------------------------------------------
+template <bool LATE_WAIT>
 __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t item,
                                                   uint64_t *__restrict__ pr2)
 {
@@ -422,10 +432,12 @@ __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t it
         const bool has = ent < it.y;
         const uint32_t m_head = has ? p.head[ent] : 0u;
         const uint32_t m_src = has ? p.src[ent] : 0u;
+        const uint64_t m_y = has ? sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + 1u) : 0ull;  // y_{e,2}
+        if constexpr (LATE_WAIT) {
+            if (base == it.x) pdl_enter();  // the layer-1 prefix is read from here on
+        }
         uint64_t m_coef = 0;
-        if (has)
-            m_coef = rr_mul(sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + 1u),  // y_{e,2}
-                              p.py[p.ia[ent]] ^ p.py[p.ib[ent]]);               // Y_e
+        if (has) m_coef = rr_mul(m_y, p.py[p.ia[ent]] ^ p.py[p.ib[ent]]);  // y_{e,2} Y_e
         const uint32_t nb = min(32u, it.y - base);
         for (uint32_t t = 0; t < nb; ++t) {
             const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
@@ -553,6 +565,9 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
         const uint32_t m_b = has ? p.ib[ent] : 0u;
         const uint32_t m_eid = has ? p.eid[ent] : 0u;
         const uint64_t m_y = has ? sm_draw(key_y, (uint64_t)m_eid * 32u + (p.layer - 1u)) : 0ull;
+        if constexpr (!COHERENT) {
+            if (base == it.x) pdl_enter();  // the transformed state is read from here on
+        }
         const uint32_t nb = min(32u, it.y - base);
         for (uint32_t t = 0; t < nb; ++t) {
             const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
