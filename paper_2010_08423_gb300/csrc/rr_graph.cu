@@ -480,11 +480,14 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         if (R.count)
             RR_CUDA(cudaMemcpyAsync(heads.data(), R.head.p, R.count * 4, cudaMemcpyDeviceToHost, st));
         RR_CUDA(cudaStreamSynchronize(st));
-        // fine ranges: enough warps for about 64 per SM even with one point
-        // group; coarse ranges for the persistent batch, whose parallelism
-        // comes from many queries at once
+        // fine ranges: enough warps for about 32 per SM even with one point
+        // group -- about what the layer kernels keep resident, so that one
+        // wave covers a small list (under programmatic dependent launch a
+        // kernel's successor can start only once its last wave runs); coarse
+        // ranges for the persistent batch, whose parallelism comes from many
+        // queries at once
         const uint32_t target =
-            (uint32_t)std::min<uint64_t>(128, std::max<uint64_t>(1, R.count / (152 * 64)));
+            (uint32_t)std::min<uint64_t>(128, std::max<uint64_t>(1, R.count / (152 * 32)));
         // runs longer than kMaxRun are cut at the same places in both range
         // sets, so one chain table serves both
         std::vector<uint2> items, coarse, chains;
