@@ -384,3 +384,13 @@ def test_k3_closed_form_cycles_and_parallel_edges():
             motif = [int(g["color"][0]), 0, 1]
             _, w = G.reach(0, 3, seed, motif=motif)
             assert np.array_equal(w, oracle.sieve(g, 0, 3, seed, motif=motif))
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_results():
+    g = _dense_uniform(1500, 20_000, 30, 5, 13)
+    ref = oracle.sieve(g, 7, 6, 41)
+    with _graph(g) as G:
+        ppl, chunk = capi.rr_autotune(G.handle, 6)
+        assert ppl in (2, 4) and chunk % (32 * ppl) == 0 and chunk <= max(64, 32 * ppl)
+        _, w = G.reach(7, 6, 41)
+        assert np.array_equal(w, ref)
