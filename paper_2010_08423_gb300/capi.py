@@ -176,11 +176,19 @@ def rr_graph_get_info(g) -> dict:
     return {f: getattr(info, f) for f, _ in rr_graph_info._fields_}
 
 
-def rr_reach_sync(g, n, source, k, seed, motif=None):
-    """Returns (bitmap uint8[ceil(n/8)], witness uint64[n])."""
+def rr_reach_sync(g, n, source, k, seed, motif=None, out=None):
+    """Returns (bitmap uint8[ceil(n/8)], witness uint64[n]); `out` = a
+    preallocated (bitmap, witness) pair of C-contiguous host arrays (pinned
+    memory, e.g. views of pinned torch tensors, makes the copies plain DMA)."""
     q, keep = make_query(source, k, seed, motif)
-    bm = np.zeros((n + 7) // 8, dtype=np.uint8)
-    w = np.zeros(n, dtype=np.uint64)
+    if out is None:
+        bm = np.zeros((n + 7) // 8, dtype=np.uint8)
+        w = np.zeros(n, dtype=np.uint64)
+    else:
+        bm, w = out
+        if (bm.dtype != np.uint8 or w.dtype != np.uint64 or bm.shape[0] < (n + 7) // 8
+                or w.shape[0] < n or not bm.flags.c_contiguous or not w.flags.c_contiguous):
+            raise ValueError("rr_reach_sync: out must be (uint8[ceil(n/8)], uint64[n]) C-contiguous")
     _check(load().rr_reach_sync(g, ctypes.byref(q), _hp(bm), _hp(w)))
     del keep
     return bm, w
@@ -403,8 +411,8 @@ class Graph:
     def info(self):
         return rr_graph_get_info(self.handle)
 
-    def reach(self, source, k, seed, motif=None):
-        return rr_reach_sync(self.handle, self.n, source, k, seed, motif)
+    def reach(self, source, k, seed, motif=None, out=None):
+        return rr_reach_sync(self.handle, self.n, source, k, seed, motif, out)
 
     def extract_path(self, source, k, seed, target, motif=None):
         return rr_extract_path(self.handle, source, k, seed, target, motif)

@@ -394,3 +394,19 @@ def test_autotune_picks_a_valid_shape_and_keeps_results():
         assert ppl in (2, 4) and chunk % (32 * ppl) == 0 and chunk <= max(64, 32 * ppl)
         _, w = G.reach(7, 6, 41)
         assert np.array_equal(w, ref)
+
+
+def test_sync_into_preallocated_pinned_buffers():
+    import torch
+    g = _dense_uniform(1200, 15_000, 25, 5, 14)
+    n = g["n"]
+    h_bm = torch.full(((n + 7) // 8,), 255, dtype=torch.uint8, pin_memory=True).numpy()
+    h_w = torch.full((n,), -1, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    with _graph(g) as G:
+        bm, w = G.reach(5, 6, 21)
+        bm2, w2 = G.reach(5, 6, 21, out=(h_bm, h_w))
+        assert bm2 is h_bm and w2 is h_w
+        assert np.array_equal(w, h_w) and np.array_equal(bm, h_bm)
+        assert np.array_equal(w, oracle.sieve(g, 5, 6, 21))
+        with pytest.raises(ValueError):
+            G.reach(5, 6, 21, out=(h_bm, h_w[:10]))
