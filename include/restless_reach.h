@@ -120,8 +120,11 @@ rr_status rr_reach_sync(const rr_graph *g, const rr_query *q, uint8_t *bitmap,
 /* rr_reach_device: same computation, enqueued on `stream` (a cudaStream_t,
  * NULL = legacy default stream) with DEVICE outputs d_bitmap (ceil(n/8)
  * bytes, may be NULL) and d_witness (n uint64, required). Returns once the
- * work is enqueued; the graph's scratch state is reused by the next call, so
- * calls on one graph must be ordered on one stream. */
+ * work is enqueued. The graph's scratch is reused by the next call: calls on
+ * one graph that use it (this one, rr_reach_sync, the batched, at-most-k,
+ * fine-grained, set-of-sources and extraction calls, rr_autotune) may be
+ * issued on different streams -- each call's stream first waits, on the
+ * device, for the previous such call's work. */
 rr_status rr_reach_device(const rr_graph *g, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, void *stream);
 

@@ -96,6 +96,30 @@ rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t se
 
 using namespace rr;
 
+namespace {
+
+// Held (under the graph's lock) by every entry point that uses the graph's
+// scratch: the call's stream first waits for the previous such call's work,
+// and the call's own last work is marked for the next one.
+struct ScratchOrder {
+    const Graph &g;
+    cudaStream_t st;
+    ScratchOrder(const Graph &g_, cudaStream_t st_) : g(g_), st(st_)
+    {
+        if (g.scratch_pending) cudaStreamWaitEvent(st, g.scratch_ev, 0);
+    }
+    ~ScratchOrder()
+    {
+        if (!g.scratch_ev && cudaEventCreateWithFlags(&g.scratch_ev, cudaEventDisableTiming) != cudaSuccess) {
+            g.scratch_ev = nullptr;
+            return;
+        }
+        g.scratch_pending = cudaEventRecord(g.scratch_ev, st) == cudaSuccess;
+    }
+};
+
+}  // namespace
+
 extern "C" {
 
 rr_status rr_graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
@@ -117,6 +141,10 @@ rr_status rr_graph_free(rr_graph *g)
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(g->dev);
+    if (g->scratch_ev) {
+        cudaEventSynchronize(g->scratch_ev);  // the last call's work, on whatever stream
+        cudaEventDestroy(g->scratch_ev);
+    }
     if (g->stream) {
         cudaStreamSynchronize(g->stream);
         cudaStreamDestroy(g->stream);
@@ -152,6 +180,7 @@ rr_status rr_reach_sync(const rr_graph *g, const rr_query *q, uint8_t *bitmap, u
     clear_error();
     if (!g) return fail(RR_EINVAL, "rr_reach_sync: NULL graph");
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, g->stream);
     const size_t nb = (g->n + 7) / 8;
     RR_CUDA(g->ws.S.reserve((size_t)g->n * 8));
     RR_CUDA(g->ws.bitmap.reserve(nb));
@@ -174,6 +203,7 @@ rr_status rr_reach_device(const rr_graph *g, const rr_query *q, uint8_t *d_bitma
     if (!g) return fail(RR_EINVAL, "rr_reach_device: NULL graph");
     if (!d_witness) return fail(RR_EINVAL, "rr_reach_device: d_witness is required");
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, (cudaStream_t)stream);
     return reach_on_stream(*g, g->ws, q, d_bitmap, d_witness, 0, (cudaStream_t)stream);
 }
 
@@ -189,6 +219,7 @@ rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t 
         if (s != RR_OK) return fail(s, "query " + std::to_string(i) + ": " + rr_last_error());
     }
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, (cudaStream_t)stream);
     return batch_device(*g, qs, nq, d_bitmaps, d_witness, d_status, (cudaStream_t)stream);
 }
 
@@ -203,6 +234,7 @@ rr_status rr_reach_arrival_device(const rr_graph *g, const rr_query *q, uint64_t
     rr_status s = validate_query(*g, q);
     if (s != RR_OK) return s;
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, (cudaStream_t)stream);
     return arrival_device(*g, q, d_witness, d_edge_sums, d_arrival, d_bitmap, (cudaStream_t)stream);
 }
 
@@ -220,6 +252,7 @@ rr_status rr_reach_sources_device(const rr_graph *g, const uint32_t *sources, ui
         if (s != RR_OK) return s;
     }
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, (cudaStream_t)stream);
     return sources_device(*g, sources, nsources, k, seed, motif, d_separators, d_bitmap, d_witness,
                           (cudaStream_t)stream);
 }
@@ -235,6 +268,7 @@ rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target,
     if (target >= g->n || target == q->source)
         return fail(RR_EINVAL, "rr_extract_path: target must be a vertex other than the source");
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, g->stream);
     return extract_path(*g, q, target, vertices, edges, times);
 }
 
@@ -247,6 +281,7 @@ rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k,
     rr_status s = validate_query(*g, &q);
     if (s != RR_OK) return s;
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, (cudaStream_t)stream);
     return atmost_device(*g, source, k, seed, d_bitmap, d_witness, (cudaStream_t)stream);
 }
 
@@ -256,6 +291,7 @@ rr_status rr_autotune(rr_graph *g, uint32_t k, uint32_t *best_ppl, uint32_t *bes
     if (!g) return fail(RR_EINVAL, "rr_autotune: NULL graph");
     if (k < 2 || k > 20) return fail(RR_EINVAL, "rr_autotune: k must be in [2, 20]");
     std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, g->stream);
     return autotune(*g, k, best_ppl, best_chunk);
 }
 

@@ -260,6 +260,11 @@ struct Graph {
     mutable Workspace ws;
     mutable BatchBuffers batch;
     mutable FanOut fan;
+    // device-side order of calls that use the scratch above: each such call's
+    // stream waits for this event (recorded after the previous call's last
+    // work), so calls issued on different streams never overlap on it
+    mutable cudaEvent_t scratch_ev = nullptr;
+    mutable bool scratch_pending = false;
     mutable cudaStream_t stream = nullptr;
 
     // tuning per k (index k): 0 = automatic; tune_gen changes on every update

@@ -212,3 +212,35 @@ def test_large_batch_coarse_ranges_equal_single_queries():
         for i, q in enumerate(qs):
             _, ref = G.reach(q["source"], q["k"], q["seed"], motif=q["motif"])
             assert np.array_equal(w[i], ref), (i, q["k"])
+
+
+def test_calls_on_different_streams_are_ordered_on_the_graphs_scratch():
+    """Calls that reuse the graph's scratch may be issued on different streams:
+    each waits on the device for the previous one. Batches and single queries
+    alternate over two streams without host synchronisation in between; every
+    result must equal the single query's."""
+    torch = _torch()
+    g = W.uniform(3000, 40_000, 40, 0, 6, 31, ncolors=2)
+    n = g["n"]
+    qa = W.query_set(g, 24, 5, 10, 0x5EED0031, colored_every_other=True)
+    qb = W.query_set(g, 24, 5, 10, 0x5EED0032, colored_every_other=True)
+    with capi.Graph(g) as G:
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        wa = torch.zeros((len(qa), n), dtype=torch.int64, device="cuda")
+        wb = torch.zeros((len(qb), n), dtype=torch.int64, device="cuda")
+        w1 = torch.zeros(n, dtype=torch.int64, device="cuda")
+        w2 = torch.zeros(n, dtype=torch.int64, device="cuda")
+        capi.rr_reach_batch_device(G.handle, qa, wa, None, None, s1.cuda_stream)
+        capi.rr_reach_device(G.handle, 3, 9, 77, w1, None, s2.cuda_stream)
+        capi.rr_reach_batch_device(G.handle, qb, wb, None, None, s2.cuda_stream)
+        capi.rr_reach_device(G.handle, 5, 8, 78, w2, None, s1.cuda_stream)
+        torch.cuda.synchronize()
+        for rows, qs in ((wa, qa), (wb, qb)):
+            got = rows.cpu().numpy().view(np.uint64)
+            for i, q in enumerate(qs):
+                _, ref = G.reach(q["source"], q["k"], q["seed"], motif=q["motif"])
+                assert np.array_equal(got[i], ref), i
+        _, r1 = G.reach(3, 9, 77)
+        _, r2 = G.reach(5, 8, 78)
+        assert np.array_equal(w1.cpu().numpy().view(np.uint64), r1)
+        assert np.array_equal(w2.cpu().numpy().view(np.uint64), r2)
