@@ -8,6 +8,7 @@
 // retires queries whose completion event has fired. Results are bit-identical
 // to rr_reach_sync: every query runs the same kernels on its own scratch.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <condition_variable>
@@ -30,15 +31,23 @@ struct Ticket {
     rr_status status = RR_OK;
     std::string error;
     Clock::time_point t_submit, t_admit, t_done;
-    std::vector<uint64_t> witness;  // filled when Done
+    int result = -1;  // index of the result buffer holding witness and bitmap (Done)
     int slot = -1;
+};
+
+// Pinned host buffers a query's witness and bitmap are copied into. A slot
+// holds one while its query runs; on completion it passes to the ticket (no
+// copy) and the slot takes a free one from the pool.
+struct ResultBuf {
+    uint64_t *w = nullptr;  // n entries
+    uint8_t *bm = nullptr;  // ceil(n/8) bytes
 };
 
 struct Slot {
     Workspace ws;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    uint64_t *h_witness = nullptr;  // pinned, n entries
+    int result = -1;                // result buffer of the running query
     uint64_t reserved = 0;          // bytes of budget this slot holds
     uint64_t ticket = 0;
     bool busy = false;
@@ -49,8 +58,11 @@ struct Server {
     uint64_t budget = 0;
     uint64_t used = 0;
     std::deque<Slot> slots;  // deque: slots are never relocated
+    std::vector<ResultBuf> results;    // all result buffers (index = id)
+    std::vector<int> free_results;     // ids of unused ones
+    std::atomic<bool> woken{false};    // a query's copies finished (host callback)
     std::mutex mu;
-    std::condition_variable cv_work;   // server thread wakes on submit / stop
+    std::condition_variable cv_work;   // server thread wakes on submit / stop / completion
     std::condition_variable cv_done;   // pollers wake on completion
     std::deque<uint64_t> queue;
     std::map<uint64_t, std::shared_ptr<Ticket>> tickets;
@@ -68,8 +80,39 @@ struct Server {
         return query_scratch_bytes(*g, k, share);
     }
 
+    // a free result buffer (a new pinned one when the pool is empty), or -1
+    int take_result()
+    {
+        if (!free_results.empty()) {
+            const int id = free_results.back();
+            free_results.pop_back();
+            return id;
+        }
+        ResultBuf b;
+        if (cudaMallocHost(&b.w, (size_t)g->n * 8) != cudaSuccess) return -1;
+        if (cudaMallocHost(&b.bm, ((size_t)g->n + 7) / 8 + 1) != cudaSuccess) {
+            cudaFreeHost(b.w);
+            return -1;
+        }
+        results.push_back(b);
+        return (int)results.size() - 1;
+    }
+
     void run();
 };
+
+// Runs on a driver thread once a query's result copies have finished: wakes
+// the server thread. It makes no CUDA call and never blocks on the server's
+// lock (the server thread makes CUDA calls while holding it); when the lock
+// is busy it notifies without it, and the server thread's bounded wait covers
+// a wake-up lost in between.
+static void CUDART_CB on_query_copied(void *arg)
+{
+    Server *s = static_cast<Server *>(arg);
+    s->woken.store(true);
+    std::unique_lock<std::mutex> lk(s->mu, std::try_to_lock);
+    s->cv_work.notify_one();
+}
 
 void Server::run()
 {
@@ -99,9 +142,14 @@ void Server::run()
                     t.state = Ticket::Canceled;
                     t.status = RR_ECANCELED;
                 } else {
-                    t.witness.assign(sl.h_witness, sl.h_witness + g->n);
+                    t.result = sl.result;  // hand the pinned buffers over
+                    sl.result = -1;
                     t.state = Ticket::Done;
                 }
+            }
+            if (sl.result >= 0) {  // failed or cancelled: buffers back to the pool
+                free_results.push_back(sl.result);
+                sl.result = -1;
             }
             sl.busy = false;
             used -= sl.reserved;
@@ -130,14 +178,26 @@ void Server::run()
             t.state = Ticket::Running;
             t.slot = free_slot;
             rr_status st = RR_OK;
-            if (sl.ws.S.reserve((size_t)g->n * 8) != cudaSuccess) st = RR_ENOMEM;
-            if (st == RR_OK) st = reach_on_stream(*g, sl.ws, &t.q, nullptr, sl.ws.S.as<uint64_t>(),
-                                                  share, sl.stream);
-            if (st == RR_OK &&
-                cudaMemcpyAsync(sl.h_witness, sl.ws.S.p, (size_t)g->n * 8, cudaMemcpyDeviceToHost,
-                                sl.stream) != cudaSuccess)
-                st = RR_ECUDA;
+            const size_t nb = ((size_t)g->n + 7) / 8;
+            if (sl.result < 0) sl.result = take_result();
+            if (sl.result < 0) st = RR_ENOMEM;
+            if (st == RR_OK && (sl.ws.S.reserve((size_t)g->n * 8) != cudaSuccess ||
+                                sl.ws.bitmap.reserve(nb) != cudaSuccess))
+                st = RR_ENOMEM;
+            if (st == RR_OK)
+                st = reach_on_stream(*g, sl.ws, &t.q, sl.ws.bitmap.as<uint8_t>(), sl.ws.S.as<uint64_t>(),
+                                     share, sl.stream);
+            if (st == RR_OK) {
+                const ResultBuf &rb = results[sl.result];
+                if (cudaMemcpyAsync(rb.w, sl.ws.S.p, (size_t)g->n * 8, cudaMemcpyDeviceToHost,
+                                    sl.stream) != cudaSuccess ||
+                    cudaMemcpyAsync(rb.bm, sl.ws.bitmap.p, nb, cudaMemcpyDeviceToHost, sl.stream) !=
+                        cudaSuccess)
+                    st = RR_ECUDA;
+            }
             if (st == RR_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = RR_ECUDA;
+            if (st == RR_OK && cudaLaunchHostFunc(sl.stream, on_query_copied, this) != cudaSuccess)
+                st = RR_ECUDA;
             if (st != RR_OK) {
                 t.state = Ticket::Failed;
                 t.status = st;
@@ -153,13 +213,18 @@ void Server::run()
             any_busy = true;
         }
         if (stop && !any_busy) break;
-        if (any_busy) {
-            lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(50));
-            lk.lock();
-        } else {
-            cv_work.wait(lk, [&] { return stop || !queue.empty(); });
-        }
+        // sleep until a query's copies finish (host callback), a query
+        // arrives while a slot is free, or the server stops; the 2 ms bound
+        // only guards against a missed wake-up
+        auto can_admit = [&] {
+            if (queue.empty()) return false;
+            for (const Slot &sl : slots)
+                if (!sl.busy) return true;
+            return false;
+        };
+        cv_work.wait_for(lk, std::chrono::milliseconds(2),
+                         [&] { return stop || woken.load() || can_admit(); });
+        woken.store(false);
     }
 }
 
@@ -204,12 +269,23 @@ rr_status rr_server_create(const rr_graph *g, uint64_t device_mem_budget, uint32
     for (auto &sl : s->slots) {
         RR_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
         RR_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
-        RR_CUDA(cudaMallocHost(&sl.h_witness, (size_t)g->n * 8));
+        sl.result = s->take_result();
+        if (sl.result < 0) return fail(RR_ENOMEM, "rr_server_create: pinned result buffers");
         RR_CUDA(sl.ws.state.reserve(state_bytes));
+        RR_CUDA(sl.ws.bitmap.reserve(((size_t)g->n + 7) / 8));
         RR_CUDA(sl.ws.z.reserve((size_t)g->n * 20 * 8));
         RR_CUDA(sl.ws.S.reserve((size_t)g->n * 8));
         RR_CUDA(sl.ws.shade.reserve(sizeof(ShadeTable)));
     }
+    // one spare result buffer per slot: completed queries keep theirs until
+    // polled, and serving allocates only when more than that are waiting
+    std::vector<int> spares;
+    for (size_t i = 0; i < s->slots.size(); ++i) {
+        const int id = s->take_result();
+        if (id < 0) return fail(RR_ENOMEM, "rr_server_create: pinned result buffers");
+        spares.push_back(id);
+    }
+    s->free_results = spares;
     s->th = std::thread([p = s.get()] { p->run(); });
     *out = s.release();
     return RR_OK;
@@ -236,7 +312,11 @@ rr_status rr_server_destroy(rr_server *s)
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
-        if (sl.h_witness) cudaFreeHost(sl.h_witness);
+
+    }
+    for (ResultBuf &b : s->results) {
+        if (b.w) cudaFreeHost(b.w);
+        if (b.bm) cudaFreeHost(b.bm);
     }
     delete s;
     return RR_OK;
@@ -289,13 +369,14 @@ rr_status rr_query_poll(rr_server *s, uint64_t ticket, int32_t timeout_ms, uint8
     s->collected[ticket] = {t->t_submit, t->t_admit, t->t_done};
     if (t->state != Ticket::Done)
         return fail(t->status, t->error.empty() ? "query did not complete" : t->error);
+    // the ticket owns its result buffer now: copy out without holding the lock
+    const ResultBuf rb = s->results[t->result];
+    lk.unlock();
     const uint32_t n = s->g->n;
-    if (witness) std::memcpy(witness, t->witness.data(), (size_t)n * 8);
-    if (bitmap) {
-        std::memset(bitmap, 0, (n + 7) / 8);
-        for (uint32_t v = 0; v < n; ++v)
-            if (t->witness[v]) bitmap[v >> 3] |= (uint8_t)(1u << (v & 7));
-    }
+    if (witness) std::memcpy(witness, rb.w, (size_t)n * 8);
+    if (bitmap) std::memcpy(bitmap, rb.bm, ((size_t)n + 7) / 8);
+    lk.lock();
+    s->free_results.push_back(t->result);
     return RR_OK;
 }
 
