@@ -210,6 +210,24 @@ def arrival_times(graph, E) -> np.ndarray:
     return R
 
 
+def atmost_arrival(graph, source: int, k: int, seed: int):
+    """RestlessReach bounded by k (Algorithm 2 with its loop over k' stopped at
+    k, R and D accumulated over the loop): R[v] (n uint32) = the minimum over
+    k' = 2..k of Algorithm 1's minimum arrival time for k' vertices
+    (NO_ARRIVAL if none), and L[v] (n uint8) = the smallest such k' with an
+    arrival (0 if none) -- the vertex count of a shortest restless path."""
+    n = int(graph["n"])
+    R = np.full(n, NO_ARRIVAL, dtype=np.uint32)
+    L = np.zeros(n, dtype=np.uint8)
+    for kk in range(2, k + 1):
+        _, E = sieve(graph, source, kk, seed, edges=True)
+        Rk = arrival_times(graph, E)
+        hit = Rk != NO_ARRIVAL
+        L[(L == 0) & hit] = kk
+        R = np.minimum(R, Rk)
+    return R, L
+
+
 def _group_sums(graph, E) -> dict:
     """{(v, t): XOR of E[e] over the edges e into v at time t}."""
     dst = np.asarray(graph["dst"], dtype=np.int64)

@@ -107,3 +107,20 @@ def test_arrival_times_definition_on_hand_made_sums():
     E = np.array([5, 5, 9, 0], dtype=np.uint64)
     R = oracle.arrival_times(g, E)
     assert R.tolist() == [oracle.NO_ARRIVAL, 7, oracle.NO_ARRIVAL]
+
+
+def test_bounded_restless_reach_equals_dfs_over_lengths():
+    # R = min over k' <= k of the DFS earliest arrival with k' vertices; L = the
+    # smallest k' that reaches v (shortest restless path, in vertices)
+    checked = 0
+    for g, s, k, seed, _ in _random_graphs(50, 53):
+        R, L = oracle.atmost_arrival(g, s, k, seed)
+        want_R = np.full(g["n"], oracle.NO_ARRIVAL, dtype=np.uint32)
+        want_L = np.zeros(g["n"], dtype=np.uint8)
+        for kk in range(2, k + 1):
+            _, _, _, _, arrive = oracle.dfs_paths(g, s, kk, with_edges=True)
+            want_L[(want_L == 0) & (arrive != oracle.NO_ARRIVAL)] = kk
+            want_R = np.minimum(want_R, arrive)
+        assert np.array_equal(R, want_R) and np.array_equal(L, want_L), (s, k)
+        checked += int((L > 0).any())
+    assert checked >= 20
