@@ -416,8 +416,21 @@ def atmost_metrics(capi, torch, g, k=10, reps=5):
             st.synchronize()
         t_atm = e[0].elapsed_time(e[1]) / reps
         t_exact = e[2].elapsed_time(e[3]) / reps
+        # bounded RestlessReach (minimum arrival and shortest length over k' <= k)
+        d_r = torch.zeros(n, dtype=torch.int32, device="cuda")
+        d_l = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        capi.rr_reach_bounded_device(G.handle, SOURCE, k, 1, d_r, d_l, d_bm, st.cuda_stream)
+        st.synchronize()
+        with torch.cuda.stream(st):
+            e[0].record(st)
+            for i in range(reps):
+                capi.rr_reach_bounded_device(G.handle, SOURCE, k, 2 + i, d_r, d_l, d_bm, st.cuda_stream)
+            e[1].record(st)
+            st.synchronize()
+        t_bounded = e[0].elapsed_time(e[1]) / reps
     nominal_ratio = sum(kk * 2 ** kk for kk in range(2, k + 1)) / (k * 2 ** k)
     return {"k": k, "atmost_ms": t_atm, "exact_ms": t_exact, "time_ratio": t_atm / t_exact,
+            "bounded_ms": t_bounded, "bounded_time_ratio": t_bounded / t_exact,
             "nominal_work_ratio": nominal_ratio,
             "value": sum(2 ** kk * kk * m for kk in range(2, k + 1)) / (t_atm / 1e3), "unit": UNIT}
 

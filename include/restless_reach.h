@@ -237,6 +237,25 @@ rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target,
 rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,
                                  uint8_t *d_bitmap, uint64_t *d_witness, void *stream);
 
+/* rr_reach_bounded_device: RestlessReach bounded by k (Algorithm 2 with its
+ * loop over k' stopped at k, its outputs R and D accumulated over the loop):
+ * the fine-grained query (rr_reach_arrival_device) for every k' = 2..k from
+ * `source`, plain colours.
+ *   d_arrival (n uint32, device, required): R_v = the smallest time at which a
+ *             restless path of at most k vertices from the source can end at
+ *             v (the minimum over k' of the k'-vertex minimum arrival), or
+ *             UINT32_MAX if none;
+ *   d_length  (n uint8, device, may be NULL): the vertex count of a shortest
+ *             restless path from the source to v (2..k), 0 if none;
+ *   d_bitmap  (ceil(n/8) bytes, device, may be NULL): D = {v : R_v defined}.
+ * The k-1 queries run concurrently on the library's lanes (as
+ * rr_reach_atmost_device) when their scratch (including m*8 bytes of per-edge
+ * sums each) fits 60% of free device memory, else one after another. Ordered on
+ * `stream`. Errors as rr_reach_device. */
+rr_status rr_reach_bounded_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,
+                                  uint32_t *d_arrival, uint8_t *d_length, uint8_t *d_bitmap,
+                                  void *stream);
+
 /* ---- serving: continuous batching over a resident graph --------------------
  * rr_server_create: starts a server thread that admits queries while device
  * memory (device_mem_budget bytes of scratch, 0 = 60% of free memory) and

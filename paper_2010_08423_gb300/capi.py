@@ -58,7 +58,7 @@ EXPORTED = [
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
     "rr_reach_arrival_device", "rr_extract_path", "rr_reach_sources_device", "rr_bench_gf_mul",
-    "rr_debug_wait_probe",
+    "rr_debug_wait_probe", "rr_reach_bounded_device",
 ]
 
 _lib = None
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_device_noalloc": [vp, pq, vp, vp, vp],
         "rr_reach_batch_device": [vp, pq, u32, vp, vp, vp, vp],
         "rr_reach_atmost_device": [vp, u32, u32, u64, vp, vp, vp],
+        "rr_reach_bounded_device": [vp, u32, u32, u64, vp, vp, vp, vp],
         "rr_reach_arrival_device": [vp, pq, vp, vp, vp, vp, vp],
         "rr_extract_path": [vp, pq, u32, vp, vp, vp],
         "rr_bench_gf_mul": [u32, u32, u32, vp, ctypes.POINTER(u64), vp],
@@ -284,6 +285,15 @@ def rr_extract_path(g, source, k, seed, target, motif=None):
         return None
     _check(st)
     return verts.tolist(), edges[:k - 1].tolist(), times[:k - 1].tolist()
+
+
+def rr_reach_bounded_device(g, source, k, seed, d_arrival, d_length=None, d_bitmap=None,
+                            stream=None):
+    """Bounded RestlessReach: minimum arrival over paths of at most k vertices
+    (n uint32), shortest path length in vertices (n uint8) and D."""
+    _check(load().rr_reach_bounded_device(g, int(source), int(k), int(seed) & ((1 << 64) - 1),
+                                          _dp(d_arrival), _dp(d_length), _dp(d_bitmap),
+                                          _dp(stream)))
 
 
 def rr_reach_atmost_device(g, source, k, seed, d_witness, d_bitmap=None, stream=None):

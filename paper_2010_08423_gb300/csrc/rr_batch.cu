@@ -868,6 +868,30 @@ __global__ void k_union_bitmap(const uint64_t *__restrict__ W, uint32_t rows, ui
     }
 }
 
+// Lane j of the fan-out runs the query with k' = k - j of a call: the longest
+// chain gets the highest stream priority. Lanes launch without programmatic
+// dependencies (with several concurrent streams a waiting grid would hold SM
+// slots the other lanes could use).
+rr_status ensure_fan_lanes(const Graph &g, uint32_t lanes)
+{
+    FanOut &F = g.fan;
+    if (!F.fork) RR_CUDA(cudaEventCreateWithFlags(&F.fork, cudaEventDisableTiming));
+    int prio_least = 0, prio_greatest = 0;
+    RR_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    while (F.ws.size() < lanes) {
+        const int prio = std::min(prio_least, prio_greatest + (int)F.ws.size());
+        cudaStream_t s2 = nullptr;
+        cudaEvent_t e2 = nullptr;
+        RR_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio));
+        F.st.push_back(s2);
+        RR_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+        F.done.push_back(e2);
+        F.ws.emplace_back(new Workspace());
+        F.ws.back()->pdl = false;
+    }
+    return RR_OK;
+}
+
 // at-most-k (Algorithm 2 stopped at k): the exact-k' queries for k' = 2..k,
 // row k'-2 of d_witness each. They run concurrently, one lane (workspace and
 // stream) each, largest k' first and on the stream of highest priority, forked
@@ -922,21 +946,8 @@ rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t se
         }
     } else {
         FanOut &F = g.fan;
-        if (!F.fork) RR_CUDA(cudaEventCreateWithFlags(&F.fork, cudaEventDisableTiming));
-        int prio_least = 0, prio_greatest = 0;
-        RR_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
-        while (F.ws.size() < lanes) {
-            // lane j runs k' = k - j: the longest chain gets the highest priority
-            const int prio = std::min(prio_least, prio_greatest + (int)F.ws.size());
-            cudaStream_t s2 = nullptr;
-            cudaEvent_t e2 = nullptr;
-            RR_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, prio));
-            F.st.push_back(s2);
-            RR_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
-            F.done.push_back(e2);
-            F.ws.emplace_back(new Workspace());
-            F.ws.back()->pdl = false;
-        }
+        rr_status ls = ensure_fan_lanes(g, lanes);
+        if (ls != RR_OK) return ls;
         RR_CUDA(cudaEventRecord(F.fork, st));
         for (uint32_t kk = k; kk >= 2; --kk) {
             const uint32_t j = k - kk;  // lane

@@ -272,6 +272,21 @@ rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target,
     return extract_path(*g, q, target, vertices, edges, times);
 }
 
+rr_status rr_reach_bounded_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,
+                                  uint32_t *d_arrival, uint8_t *d_length, uint8_t *d_bitmap,
+                                  void *stream)
+{
+    clear_error();
+    if (!g || !d_arrival) return fail(RR_EINVAL, "rr_reach_bounded_device: NULL argument");
+    rr_query q{source, k, seed, nullptr};
+    rr_status s = validate_query(*g, &q);
+    if (s != RR_OK) return s;
+    std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, (cudaStream_t)stream);
+    return atmost_arrival_device(*g, source, k, seed, d_arrival, d_length, d_bitmap,
+                                 (cudaStream_t)stream);
+}
+
 rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,
                                  uint8_t *d_bitmap, uint64_t *d_witness, void *stream)
 {

@@ -91,17 +91,37 @@ unsigned grid_for(uint64_t count, unsigned block)
 
 }  // namespace
 
+// Folds one k' into the bounded-reach outputs (callers go through k' in
+// increasing order): R = min(R, R_k'), L = k' where L is still 0 and k'
+// reaches the vertex.
+__global__ void k_merge_arrival(uint32_t n, const uint32_t *__restrict__ Rk, uint32_t kk,
+                                uint32_t *__restrict__ R, uint8_t *__restrict__ L)
+{
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint32_t r = Rk[v];
+        if (r == 0xFFFFFFFFu) continue;
+        if (r < R[v]) R[v] = r;
+        if (L && L[v] == 0) L[v] = (uint8_t)kk;
+    }
+}
+
 rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness, uint64_t *d_E,
                          uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st, const uint8_t *d_vmask)
 {
-    Workspace &ws = g.ws;
+    return arrival_on(g, g.ws, q, d_witness, d_E, d_R, d_bitmap, st, d_vmask, 0);
+}
+
+rr_status arrival_on(const Graph &g, Workspace &ws, const rr_query *q, uint64_t *d_witness,
+                     uint64_t *d_E, uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
+                     const uint8_t *d_vmask, uint64_t budget)
+{
     if (!d_E) {
         RR_CUDA(ws.edges.reserve((size_t)std::max<uint64_t>(1, g.m) * 8));
         d_E = ws.edges.as<uint64_t>();
     }
     if (g.m) RR_CUDA(cudaMemsetAsync(d_E, 0, (size_t)g.m * 8, st));
     RR_CUDA(cudaMemsetAsync(d_R, 0xFF, (size_t)g.n * 4, st));
-    rr_status s = reach_on_stream(g, ws, q, nullptr, d_witness, 0, st, d_E, d_vmask);
+    rr_status s = reach_on_stream(g, ws, q, nullptr, d_witness, budget, st, d_E, d_vmask);
     if (s != RR_OK) return s;
     if (g.m) {
         k_arrival<<<grid_for(g.m, 256), 256, 0, st>>>((uint32_t)g.m, g.row_head.as<uint32_t>(),
@@ -228,6 +248,73 @@ rr_status sources_device(const Graph &g, const uint32_t *sources, uint32_t nsour
     RR_CUDA(cudaMemcpyAsync(ws.srcmask.p, flags.data(), g.n, cudaMemcpyHostToDevice, st));
     return reach_on_stream(g, ws, &q, d_bitmap, d_witness, 0, st, nullptr, d_separators,
                            ws.srcmask.as<uint8_t>());
+}
+
+// Bounded RestlessReach (Algorithm 2 with its loop over k' stopped at k):
+// the fine-grained query for every k' = 2..k, concurrently on the graph's
+// lanes (largest k' first) when their scratch fits 60% of free device memory
+// together, else one after another on the graph's workspace; then R = the
+// minimum arrival over k', L = the smallest k' reaching each vertex, and the
+// bitmap of D = {v : R_v defined}.
+rr_status atmost_arrival_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
+                                uint32_t *d_R, uint8_t *d_L, uint8_t *d_bitmap, cudaStream_t st)
+{
+    const uint32_t lanes = k - 1;
+    const size_t mb = (size_t)std::max<uint64_t>(1, g.m) * 8;
+    size_t free_b = 0, total_b = 0;
+    RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const uint64_t per_lane = (uint64_t)(0.6 * (double)(free_b + g.fan.bytes())) / lanes;
+    const uint64_t extra = mb + (uint64_t)g.n * 12;  // per-edge sums, arrival, witness
+    uint64_t need = 0;
+    for (uint32_t kk = 2; kk <= k; ++kk) {
+        const uint64_t b = per_lane > extra ? query_scratch_bytes(g, kk, per_lane - extra) : UINT64_MAX;
+        need = (b == UINT64_MAX || need == UINT64_MAX) ? UINT64_MAX : need + b + extra;
+    }
+    RR_CUDA(cudaMemsetAsync(d_R, 0xFF, (size_t)g.n * 4, st));
+    if (d_L) RR_CUDA(cudaMemsetAsync(d_L, 0, g.n, st));
+    const unsigned grid = grid_for(g.n, 256);
+    if (need == UINT64_MAX) {
+        Workspace &ws = g.ws;
+        RR_CUDA(ws.S.reserve((size_t)g.n * 8));
+        RR_CUDA(ws.arrival.reserve((size_t)g.n * 4));
+        RR_CUDA(ws.edges.reserve(mb));
+        for (uint32_t kk = 2; kk <= k; ++kk) {
+            const rr_query q{source, kk, seed, nullptr};
+            rr_status s = arrival_on(g, ws, &q, ws.S.as<uint64_t>(), ws.edges.as<uint64_t>(),
+                                     ws.arrival.as<uint32_t>(), nullptr, st, nullptr, 0);
+            if (s != RR_OK) return s;
+            k_merge_arrival<<<grid, 256, 0, st>>>(g.n, ws.arrival.as<uint32_t>(), kk, d_R, d_L);
+            RR_LAUNCHED();
+        }
+    } else {
+        rr_status s = ensure_fan_lanes(g, lanes);
+        if (s != RR_OK) return s;
+        FanOut &F = g.fan;
+        RR_CUDA(cudaEventRecord(F.fork, st));
+        for (uint32_t kk = k; kk >= 2; --kk) {
+            const uint32_t j = k - kk;  // lane
+            Workspace &ws = *F.ws[j];
+            RR_CUDA(ws.S.reserve((size_t)g.n * 8));
+            RR_CUDA(ws.arrival.reserve((size_t)g.n * 4));
+            RR_CUDA(ws.edges.reserve(mb));
+            const rr_query q{source, kk, seed, nullptr};
+            RR_CUDA(cudaStreamWaitEvent(F.st[j], F.fork, 0));
+            s = arrival_on(g, ws, &q, ws.S.as<uint64_t>(), ws.edges.as<uint64_t>(),
+                           ws.arrival.as<uint32_t>(), nullptr, F.st[j], nullptr, per_lane - extra);
+            RR_CUDA(cudaEventRecord(F.done[j], F.st[j]));
+            RR_CUDA(cudaStreamWaitEvent(st, F.done[j], 0));
+            if (s != RR_OK) return s;
+        }
+        for (uint32_t kk = 2; kk <= k; ++kk) {
+            k_merge_arrival<<<grid, 256, 0, st>>>(g.n, F.ws[k - kk]->arrival.as<uint32_t>(), kk, d_R, d_L);
+            RR_LAUNCHED();
+        }
+    }
+    if (d_bitmap) {
+        k_arrival_bitmap<<<grid_for((g.n + 7) / 8, 256), 256, 0, st>>>(g.n, d_R, d_bitmap);
+        RR_LAUNCHED();
+    }
+    return RR_OK;
 }
 
 }  // namespace rr

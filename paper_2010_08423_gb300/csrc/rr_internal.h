@@ -355,6 +355,15 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
 rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness, uint64_t *d_E,
                          uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
                          const uint8_t *d_vmask = nullptr);
+// The fine-grained query on workspace `ws` (budget as reach_on_stream).
+rr_status arrival_on(const Graph &g, Workspace &ws, const rr_query *q, uint64_t *d_witness,
+                     uint64_t *d_E, uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
+                     const uint8_t *d_vmask, uint64_t budget);
+// Bounded RestlessReach: minimum arrival over k' = 2..k, shortest length, D.
+rr_status atmost_arrival_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
+                                uint32_t *d_R, uint8_t *d_L, uint8_t *d_bitmap, cudaStream_t st);
+// Makes sure the graph has at least `lanes` concurrent-query lanes (rr_batch.cu).
+rr_status ensure_fan_lanes(const Graph &g, uint32_t lanes);
 // A set of sources and optional separators (n flags, device).
 rr_status sources_device(const Graph &g, const uint32_t *sources, uint32_t nsources, uint32_t k,
                          uint64_t seed, const uint8_t *motif, const uint8_t *d_separators,

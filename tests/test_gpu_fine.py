@@ -108,3 +108,24 @@ def test_without_edge_buffer_and_on_an_edgeless_graph():
     with capi.Graph(empty) as G:
         S, E, R, bm = G.arrival(0, 3, 1)
         assert not S.any() and E.size == 0 and (R == capi.NO_ARRIVAL).all() and not bm.any()
+
+
+@pytest.mark.parametrize("k", [2, 5, 8])
+def test_bounded_reach_min_arrival_and_shortest_length(k):
+    import torch
+    g = W.uniform(1500, 20_000, 30, 0, 5, 60 + k)
+    n = g["n"]
+    R_ref, L_ref = oracle.atmost_arrival(g, 4, k, 13)
+    with capi.Graph(g) as G:
+        d_r = torch.zeros(n, dtype=torch.int32, device="cuda")
+        d_l = torch.full((n,), 99, dtype=torch.uint8, device="cuda")
+        d_b = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        for rep in range(2):  # lanes reused on the second call
+            capi.rr_reach_bounded_device(G.handle, 4, k, 13, d_r, d_l, d_b)
+            torch.cuda.synchronize()
+            R = d_r.cpu().numpy().view(np.uint32)
+            assert np.array_equal(R, R_ref)
+            assert np.array_equal(d_l.cpu().numpy(), L_ref)
+            D = np.unpackbits(d_b.cpu().numpy(), bitorder="little")[:n].astype(bool)
+            assert np.array_equal(D, R_ref != oracle.NO_ARRIVAL)
+        assert (L_ref > 0).sum() > 3
