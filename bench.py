@@ -10,7 +10,11 @@ Workload (one step = one complete query: z-table, k-1 edge layers over all
 Metric: GF(2^64) edge-updates/s counted as the nominal 2^k * k * m per query.
 `value` is device-timed (CUDA events on the launching stream, L2 flushed
 between steps, graph resident in HBM); `e2e` is the same metric through the
-host-buffer C-ABI call rr_reach_sync (result copied back every step).
+host-buffer C-ABI call rr_reach_sync (descriptor uploaded and results copied
+back into pinned host buffers every step). `roofline` reports the dominant
+kernel against the measured copy bandwidth or the measured GF(2^64) multiply
+rate, whichever binds. Extra lines: batched, served, at-most-k / bounded,
+fine-grained, a Chung-Lu motif workload and serving on an n = 1e7 graph.
 
 --impl reference times the CPU oracle (oracle/) on a bounded sample of the
 same workload: the only other place this file runs oracle code.

@@ -1,23 +1,30 @@
 // rr_sieve2.cu -- the reduced-state engine: same per-vertex sums as the
-// per-point engine (rr_sieve.cu), with three exact rewrites of the work.
+// per-point engine (rr_sieve.cu), with exact rewrites of the work.
 //
 // 1. Layer 1 as a scalar. P_1^L[f] = [u_f = s] y_{f,1} x_s^L x_{v_f}^L, so
 //    the layer-2 window sum of edge e = (u, v) is W_2^L[e] = Y_e x_s^L x_u^L with
 //    the scalar Y_e = sum of y_{f,1} over the source's edges f inside e's window.
 //    Layer 1 therefore stores one GF(2^64) prefix per producer row (PY), not one
 //    per sieve point.
-// 2. State rows only where the prefix changes. For l >= 2, P_l[f] can be
-//    non-zero only for rows f whose own window is non-empty, so the per-point
-//    prefix state of layers 2..k-3 keeps just those rows ("state rows").
-// 3. The last layer as a linear form. x_v^L = sum_{j in L} z_{v,j}, hence
+// 2. Layer 2 in label space (k >= 5): P_2^L[f] = x_v^L x_s^L sum_{j in L}
+//    (y Y)_f z_{u_f,j}, so layer 2 keeps k values per state row (rows whose
+//    own window is non-empty), independent of the point chunk.
+// 3. Layer 3 from that label-space prefix, factored per head:
+//    acc^L = (x_v x_s)^L sum_e x_{u_e}^L (y rho_e)^L.
+// 4. Deep rows only from layer 3 on: state rows whose window holds a state row
+//    are the only rows that can be non-zero there.
+// 5. The last layer as a linear form. x_v^L = sum_{j in L} z_{v,j}, hence
 //        sum_L y_e x_v^L W^L = y_e sum_j z_{v,j} T_j(W),  T_j(W) = sum_{L ni j} W^L,
-//    and T_j is XOR-linear, so layer k-2 stores for every state row and point
-//    group only the lg+1 sums T_j (j below lg = log2 of the group size) and
-//    V = sum over the group (the high labels of a group are fixed, so their
-//    T_j is V or 0), and layer k-1 needs one multiplication per stored value
-//    instead of one per sieve point.
-// Only the sieve points' order of summation changes; every result is
-// bit-identical to the per-point engine and the oracle.
+//    and T_j is XOR-linear, so layer k-2 stores for every row and point group
+//    only the lg+1 sums T_j (j below lg = log2 of the group size) and V = the
+//    sum over the group (the high labels of a group are fixed, so their T_j is
+//    V or 0), and layer k-1 needs one multiplication per stored value instead
+//    of one per sieve point.
+// 6. k = 2 and k = 3 in closed form (a 2x2 / 3x3 permanent per edge).
+// Only the order of summation changes; every result is bit-identical to the
+// per-point engine and the oracle. One query's launch sequence is captured
+// once per shape as a CUDA graph and its kernels use programmatic dependent
+// launch.
 #include <algorithm>
 #include <cstring>
 
