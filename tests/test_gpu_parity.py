@@ -410,3 +410,21 @@ def test_sync_into_preallocated_pinned_buffers():
         assert np.array_equal(w, oracle.sieve(g, 5, 6, 21))
         with pytest.raises(ValueError):
             G.reach(5, 6, 21, out=(h_bm, h_w[:10]))
+
+
+def test_largest_k_on_a_restless_chain():
+    """k = 20, the largest k accepted (2^20 sieve points, 2,048 point chunks of
+    512): a 21-vertex chain 0 -> 1 -> ... -> 20 with times 1..20 and waits of at
+    most 1, plus a few edges that break restlessness. The witness must equal
+    the determinant identity computed by DFS (the sieve oracle would take too
+    long at this k): non-zero exactly at vertex 19."""
+    src = list(range(20)) + [3, 7, 12]
+    dst = list(range(1, 21)) + [9, 15, 2]
+    t = list(range(1, 21)) + [40, 2, 1]
+    g = {"n": 21, "src": np.array(src, np.uint32), "dst": np.array(dst, np.uint32),
+         "t": np.array(t, np.uint32), "delta": np.ones(21, np.uint32)}
+    with _graph(g) as G:
+        _, w = G.reach(0, 20, 2024)
+    reach, sdet, npaths = oracle.dfs_paths(g, 0, 20, 2024, with_det=True)
+    assert npaths == 1 and np.nonzero(reach)[0].tolist() == [19]
+    assert np.array_equal(w, sdet)
