@@ -211,7 +211,9 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
                    workload="plain queries, k~U{6..12}, s~U, on the n=100000 m=1000000 graph",
                    warm=8):
     """Serving: Poisson arrivals of plain queries (s ~ U, k ~ U{6..12}) at 0.5x,
-    0.8x and 1.1x of the server's measured capacity; latency = submit -> done."""
+    0.8x and 1.1x of the server's measured capacity; latency = submit -> done.
+    Warm-up: `warm` queries one at a time, then one untimed burst (the batch
+    lanes' first use grows the batch kernel's buffers)."""
     import threading
     rng = np.random.default_rng(seed)
     n = g["n"]
@@ -223,12 +225,18 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
         try:
             for s_, k_, sd in qs[:warm]:  # warm-up: capture each slot's graphs
                 capi.rr_query_poll(srv, capi.rr_query_submit(srv, s_, k_, sd), n, -1)
+            for t in [capi.rr_query_submit(srv, s_, k_, sd) for s_, k_, sd in qs[:64]]:
+                capi.rr_query_poll(srv, t, n, -1)
+            a0 = capi.rr_server_stats(srv)
             t0 = time.perf_counter()
             ts = [capi.rr_query_submit(srv, s_, k_, sd) for s_, k_, sd in qs]
             for t in ts:
                 capi.rr_query_poll(srv, t, n, -1)
             cap = nq / (time.perf_counter() - t0)
             out["capacity_queries_per_s"] = cap
+            a1 = capi.rr_server_stats(srv)
+            out["capacity_admission"] = {"single": a1[0] - a0[0], "batched": a1[1] - a0[1],
+                                         "batches": a1[2] - a0[2]}
             loads = []
             for frac in (0.5, 0.8, 1.1):
                 rate = frac * cap
@@ -264,6 +272,9 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
                               "queries_per_s": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
                               "p99_ms": float(np.percentile(lat, 99))})
             out["loads"] = loads
+            a2 = capi.rr_server_stats(srv)
+            out["loads_admission"] = {"single": a2[0] - a1[0], "batched": a2[1] - a1[1],
+                                      "batches": a2[2] - a1[2]}
         finally:
             capi.rr_server_destroy(srv)
     return out

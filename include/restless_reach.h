@@ -262,7 +262,12 @@ rr_status rr_reach_bounded_device(const rr_graph *g, uint32_t source, uint32_t k
  * max_slots (concurrent point chunks, 0 = automatic) allow, runs every
  * admitted chunk's layers as they become ready, and retires queries as their
  * last chunk finishes, so that queries arriving while others run share the
- * GPU with them. Results are identical to rr_reach_sync's. */
+ * GPU with them. On graphs of at most 2^24 edges, under a backlog (8 or more
+ * queued queries on the reduced-state engine) queued queries are admitted
+ * instead in batches of up to 64 to the persistent batch kernel
+ * (rr_reach_batch_device), on one of two batch lanes whose outputs take at
+ * most a quarter of the budget; rr_server_set_batching changes or turns off
+ * that policy. Results are identical to rr_reach_sync's either way. */
 rr_status rr_server_create(const rr_graph *g, uint64_t device_mem_budget, uint32_t max_slots,
                            rr_server **out);
 rr_status rr_server_destroy(rr_server *s);
@@ -277,6 +282,16 @@ rr_status rr_query_poll(rr_server *s, uint64_t ticket, int32_t timeout_ms, uint8
 rr_status rr_query_cancel(rr_server *s, uint64_t ticket);
 /* Per-ticket timing in microseconds: submit->admit, submit->done. */
 rr_status rr_query_times(rr_server *s, uint64_t ticket, double *queue_us, double *total_us);
+/* Counts since creation: queries admitted one at a time to a slot, queries
+ * admitted in batches, and batches launched. Any pointer may be NULL. */
+rr_status rr_server_stats(rr_server *s, uint64_t *single, uint64_t *batched, uint64_t *batches);
+/* Batch admission: a backlog of min_batch queued queries starts a batch of up
+ * to max_batch (2 <= min_batch <= max_batch <= the lanes' capacity: 256, or
+ * fewer where a quarter of the budget holds fewer); min_batch = 0 turns
+ * batching off. The lanes' buffers are allocated on the first call that
+ * turns batching on (RR_ENOMEM / RR_ECUDA if that fails). RR_EINVAL on other
+ * values or on a server without lanes (per-point engine graphs). */
+rr_status rr_server_set_batching(rr_server *s, uint32_t min_batch, uint32_t max_batch);
 
 /* ---- tuning ----------------------------------------------------------------
  * Kernel shape used for a (graph, k): points per lane (2 or 4) and points per

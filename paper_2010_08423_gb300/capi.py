@@ -53,7 +53,9 @@ TIMING_KINDS = ["first_layer", "mid_layer", "last_layer", "ztable", "batch", "se
 EXPORTED = [
     "rr_graph_load", "rr_graph_free", "rr_graph_get_info", "rr_reach_sync",
     "rr_reach_device", "rr_reach_batch_device", "rr_server_create", "rr_server_destroy",
-    "rr_query_submit", "rr_query_poll", "rr_query_cancel", "rr_query_times", "rr_autotune",
+    "rr_query_submit", "rr_query_poll", "rr_query_cancel", "rr_query_times", "rr_server_stats",
+    "rr_server_set_batching",
+    "rr_autotune",
     "rr_set_tuning", "rr_debug_point_sums", "rr_debug_graph", "rr_debug_ztable",
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
@@ -101,6 +103,8 @@ def load(build_if_missing: bool = True):
         "rr_query_submit": [vp, pq, ctypes.POINTER(u64)],
         "rr_query_poll": [vp, u64, i32, vp, vp],
         "rr_query_cancel": [vp, u64],
+        "rr_server_stats": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)],
+        "rr_server_set_batching": [vp, u32, u32],
         "rr_query_times": [vp, u64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)],
         "rr_autotune": [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)],
@@ -339,6 +343,17 @@ def rr_query_times(s, ticket):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().rr_query_times(s, int(ticket), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def rr_server_stats(s):
+    """(queries admitted singly, queries admitted in batches, batches)."""
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().rr_server_stats(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def rr_server_set_batching(s, min_batch, max_batch):
+    _check(load().rr_server_set_batching(s, int(min_batch), int(max_batch)))
 
 
 def rr_autotune(g, k):

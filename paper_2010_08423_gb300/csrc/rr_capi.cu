@@ -86,8 +86,6 @@ rr_status bench_gf_mul(uint32_t blocks, uint32_t threads, uint32_t iters, uint64
 rr_status debug_wait_probe(uint64_t timeout_ns, int abort_preset, int32_t *status,
                            uint64_t *elapsed_ns);
 rr_status debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out);
-rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
-                       uint64_t *d_witness, int32_t *d_status, cudaStream_t st);
 rr_status autotune(Graph &g, uint32_t k, uint32_t *ppl, uint32_t *chunk);
 rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st);
@@ -95,30 +93,6 @@ rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t se
 }  // namespace rr
 
 using namespace rr;
-
-namespace {
-
-// Held (under the graph's lock) by every entry point that uses the graph's
-// scratch: the call's stream first waits for the previous such call's work,
-// and the call's own last work is marked for the next one.
-struct ScratchOrder {
-    const Graph &g;
-    cudaStream_t st;
-    ScratchOrder(const Graph &g_, cudaStream_t st_) : g(g_), st(st_)
-    {
-        if (g.scratch_pending) cudaStreamWaitEvent(st, g.scratch_ev, 0);
-    }
-    ~ScratchOrder()
-    {
-        if (!g.scratch_ev && cudaEventCreateWithFlags(&g.scratch_ev, cudaEventDisableTiming) != cudaSuccess) {
-            g.scratch_ev = nullptr;
-            return;
-        }
-        g.scratch_pending = cudaEventRecord(g.scratch_ev, st) == cudaSuccess;
-    }
-};
-
-}  // namespace
 
 extern "C" {
 

@@ -333,6 +333,11 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
 
 // Reduced-state engine (rr_sieve2.cu), used for k >= 3 on compact graphs.
 bool uses_v2(const Graph &g, uint32_t k);
+// Queries qs[0..nq) through the persistent batch kernel (rr_batch.cu);
+// query i's witness at d_witness + i*n, bitmap at d_bitmaps + i*ceil(n/8),
+// abort status at d_status[i]. Uses the graph's scratch: hold its lock.
+rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
+                       uint64_t *d_witness, int32_t *d_status, cudaStream_t st);
 bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl, uint32_t *chunk);
 uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk);
 uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k);
@@ -348,6 +353,26 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                    uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st,
                    uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr);
+
+// Held (under the graph's lock) by every call that uses the graph's scratch:
+// the call's stream first waits for the previous such call's work, and the
+// call's own last work is marked for the next one.
+struct ScratchOrder {
+    const Graph &g;
+    cudaStream_t st;
+    ScratchOrder(const Graph &g_, cudaStream_t st_) : g(g_), st(st_)
+    {
+        if (g.scratch_pending) cudaStreamWaitEvent(st, g.scratch_ev, 0);
+    }
+    ~ScratchOrder()
+    {
+        if (!g.scratch_ev && cudaEventCreateWithFlags(&g.scratch_ev, cudaEventDisableTiming) != cudaSuccess) {
+            g.scratch_ev = nullptr;
+            return;
+        }
+        g.scratch_pending = cudaEventRecord(g.scratch_ev, st) == cudaSuccess;
+    }
+};
 
 // Fine-grained outputs (rr_fine.cu): the query with per-edge sums d_E (m, or
 // null for the workspace's buffer), minimum arrival times d_R (n) and the set

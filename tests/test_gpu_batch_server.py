@@ -122,6 +122,63 @@ def test_server_result_alone_equals_result_in_mix(mixed):
             capi.rr_server_destroy(srv)
 
 
+def test_server_backlog_goes_through_batch_lanes(mixed):
+    """A burst of queued queries is admitted in batches (persistent kernel) and
+    every result still equals the single-query result; a query cancelled in
+    the middle of the burst ends cancelled, the others are unaffected."""
+    g, qs = mixed
+    n = g["n"]
+    burst = (qs * 6)[:90]
+    with capi.Graph(g) as G:
+        srv = capi.rr_server_create(G.handle, 0, 2)
+        try:
+            ts = [capi.rr_query_submit(srv, q["source"], q["k"], q["seed"], q["motif"])
+                  for q in burst]
+            capi.rr_query_cancel(srv, ts[45])
+            for i, (q, t) in enumerate(zip(burst, ts)):
+                if i == 45:
+                    with pytest.raises(capi.RRError) as ei:
+                        capi.rr_query_poll(srv, t, n, -1)
+                    assert ei.value.status == capi.RR_ECANCELED
+                    continue
+                st, bm, w = capi.rr_query_poll(srv, t, n, -1)
+                assert st == capi.RR_OK
+                bm_ref, w_ref = G.reach(q["source"], q["k"], q["seed"], motif=q["motif"])
+                assert np.array_equal(w, w_ref) and np.array_equal(bm, bm_ref), i
+            single, batched, batches = capi.rr_server_stats(srv)
+            assert batched >= 8 and batches >= 1 and single + batched <= len(burst)
+            # a lone query afterwards takes a slot again
+            st, _, w = capi.rr_query_poll(srv, capi.rr_query_submit(srv, 3, 7, 77), n, -1)
+            assert np.array_equal(w, G.reach(3, 7, 77)[1])
+            assert capi.rr_server_stats(srv)[0] == single + 1
+        finally:
+            capi.rr_server_destroy(srv)
+
+
+def test_server_batching_switch():
+    g = W.uniform(2000, 20_000, 30, 0, 5, 8)
+    n = g["n"]
+    with capi.Graph(g) as G:
+        srv = capi.rr_server_create(G.handle, 0, 2)
+        try:
+            for bad in ((1, 4), (9, 8), (8, 100_000)):
+                with pytest.raises(capi.RRError) as ei:
+                    capi.rr_server_set_batching(srv, *bad)
+                assert ei.value.status == capi.RR_EINVAL
+            capi.rr_server_set_batching(srv, 0, 0)  # off: every query takes a slot
+            ts = [capi.rr_query_submit(srv, i % 50, 5 + i % 4, i) for i in range(40)]
+            ws = [capi.rr_query_poll(srv, t, n, -1)[2] for t in ts]
+            assert capi.rr_server_stats(srv) == (40, 0, 0)
+            capi.rr_server_set_batching(srv, 2, 256)  # on again, every backlog of 2
+            ts = [capi.rr_query_submit(srv, i % 50, 5 + i % 4, i) for i in range(40)]
+            for w, t in zip(ws, ts):
+                assert np.array_equal(capi.rr_query_poll(srv, t, n, -1)[2], w)
+            single, batched, batches = capi.rr_server_stats(srv)
+            assert single + batched == 80 and batched >= 2 and batches >= 1
+        finally:
+            capi.rr_server_destroy(srv)
+
+
 def test_server_cancel_and_admission():
     g = W.uniform(2000, 20_000, 30, 0, 5, 5)
     with capi.Graph(g) as G:
