@@ -91,6 +91,10 @@ typedef struct {
     uint64_t tail_rows;            /* rows whose window holds a producer row with a window */
     uint64_t deep_compute_rows;    /* deep rows whose window holds a deep row */
     uint64_t deep_tail_rows;       /* rows whose window holds a deep row */
+    uint64_t deep_head_runs;       /* head runs over the deep rows' scheduling ranges */
+    int factored_layer3;           /* 1: queries with k >= 8 (6 if forced) store layer
+                                      3's sums without the head's factor x_v x_s and
+                                      layer 4 restores it per window */
 } rr_graph_info;
 
 /* ---- graph ----------------------------------------------------------------
@@ -100,7 +104,12 @@ typedef struct {
  * t_e - delta(u_e) <= t_f <= t_e) and the scheduling ranges. Host arrays are
  * read only; src/dst/t have m entries, delta n, color n (or NULL).
  * flags: bit 0 set = keep the dense state layout (one state row per edge)
- * instead of storing only rows that lie in some window.
+ * instead of storing only rows that lie in some window. Bits 1 / 2 force the
+ * factored layer-3 state on (queries with k >= 6) / off; by default it is
+ * used for k >= 8 when it takes fewer multiplications per sieve point: layer
+ * 3 then saves one product per deep row and one per head run, layer 4 spends
+ * two per deep row with a non-empty window (deep_rows + deep_head_runs >
+ * 2 deep_compute_rows). Results are bit-identical either way.
  * Errors: RR_EINVAL for n == 0, m >= 2^31, an endpoint >= n or a self-loop;
  * RR_ENOMEM / RR_ECUDA on device failure (nothing is leaked). */
 rr_status rr_graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,

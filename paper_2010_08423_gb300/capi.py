@@ -19,6 +19,8 @@ RR_OK, RR_EINVAL, RR_ENOMEM, RR_EAGAIN, RR_ETIMEDOUT, RR_ECANCELED, RR_ECUDA, RR
 STATUS_NAMES = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_EAGAIN",
                 4: "RR_ETIMEDOUT", 5: "RR_ECANCELED", 6: "RR_ECUDA", 7: "RR_ENOPATH"}
 FLAG_DENSE_STATE = 1
+FLAG_FACTOR_L3_ON = 2
+FLAG_FACTOR_L3_OFF = 4
 
 
 class RRError(RuntimeError):
@@ -39,7 +41,8 @@ class rr_graph_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("has_colors", ctypes.c_int),
                 ("compact", ctypes.c_int), ("producer_window_rows", ctypes.c_uint64),
                 ("state_compute_rows", ctypes.c_uint64), ("tail_rows", ctypes.c_uint64),
-                ("deep_compute_rows", ctypes.c_uint64), ("deep_tail_rows", ctypes.c_uint64)]
+                ("deep_compute_rows", ctypes.c_uint64), ("deep_tail_rows", ctypes.c_uint64),
+                ("deep_head_runs", ctypes.c_uint64), ("factored_layer3", ctypes.c_int)]
 
 
 class rr_kernel_times(ctypes.Structure):

@@ -146,6 +146,8 @@ rr_status rr_graph_get_info(const rr_graph *g, rr_graph_info *out)
     out->tail_rows = g->tail_list.count;
     out->deep_compute_rows = g->deep_compute_rows;
     out->deep_tail_rows = g->tail3_list.count;
+    out->deep_head_runs = g->deep_head_runs;
+    out->factored_layer3 = g->factor_l3 ? 1 : 0;
     return RR_OK;
 }
 

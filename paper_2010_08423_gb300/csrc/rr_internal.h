@@ -229,6 +229,9 @@ struct Graph {
     uint64_t producer_window_rows = 0;  // producer rows with a non-empty window
     uint64_t state_compute_rows = 0;    // state rows whose window holds a state row
     uint64_t deep_compute_rows = 0;     // deep rows whose window holds a deep row
+    uint64_t deep_head_runs = 0;        // head runs over the deep list's fine ranges
+    uint32_t factor_mode = 0;           // 0 = cost model, 1 = on, 2 = off
+    bool factor_l3 = false;             // factored layer-3 state (k >= 6)
     uint32_t max_in_degree = 0;
 
     DevBuf off;      // n+1 uint32

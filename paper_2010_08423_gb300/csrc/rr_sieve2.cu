@@ -96,14 +96,14 @@ __global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uin
     first_scalar_warp(p, task, py);
 }
 
-template <int PPL, bool FROM_Y, int OUT, bool FROM_R2 = false>
+template <int PPL, bool FROM_Y, int OUT, bool FROM_R2 = false, int XF = 0>
 __global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
 {
     // pdl_enter() inside layer_warp, after the graph- and query-only loads
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems * p.ngroups) return;
     const uint32_t item = task / p.ngroups;
-    layer_warp<PPL, FROM_Y, OUT, false, FROM_R2>(p, item, task - item * p.ngroups);
+    layer_warp<PPL, FROM_Y, OUT, false, FROM_R2, XF>(p, item, task - item * p.ngroups);
 }
 
 // Carry fix-up of cut head segments (rr_v2_device.cuh): phase 1 one block
@@ -197,22 +197,29 @@ static void set_list(V2Params &vp, const RowList &L, int win)
 
 // src: 0 = window sums from the per-point state, 1 = from the scalar layer-1
 // prefix (layer 2), 2 = from the label-space layer-2 prefix (layer 3).
+// xf: factored layer-3 state (layer_warp's XF): 1 on layer 3 (out 0 only),
+// 2 on layer 4.
 template <int PPL>
-static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st)
+static rr_status launch_v2(const V2Params &vp, int src, int out, int xf, cudaStream_t st)
 {
     const uint64_t tasks = (uint64_t)vp.nitems * vp.ngroups;
     if (tasks == 0) return RR_OK;
     const int tslot = timing_begin(st);
     const unsigned blocks = blocks_for(tasks);
+    const dim3 B(kW2 * 32);
     if (src == 1) {
-        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 0>, dim3(blocks), dim3(kW2 * 32), st, vp));
-        else RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 1>, dim3(blocks), dim3(kW2 * 32), st, vp));
+        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 0>, dim3(blocks), B, st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 1>, dim3(blocks), B, st, vp));
     } else if (src == 2) {
-        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true>, dim3(blocks), dim3(kW2 * 32), st, vp));
-        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, true>, dim3(blocks), dim3(kW2 * 32), st, vp));
+        if (out == 1) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, true>, dim3(blocks), B, st, vp));
+        else if (xf == 1) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true, 1>, dim3(blocks), B, st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true>, dim3(blocks), B, st, vp));
+    } else if (xf == 2) {
+        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, false, 2>, dim3(blocks), B, st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, false, 2>, dim3(blocks), B, st, vp));
     } else {
-        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0>, dim3(blocks), dim3(kW2 * 32), st, vp));
-        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1>, dim3(blocks), dim3(kW2 * 32), st, vp));
+        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0>, dim3(blocks), B, st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1>, dim3(blocks), B, st, vp));
     }
     timing_end(tslot, src == 1 ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid), st);
     RR_LAUNCHED();
@@ -421,9 +428,14 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         // layers 2 (k = 4) or 3 (k >= 5) .. k-2; the last of them writes the
         // transformed state
         uint64_t *bufs[2] = {full0, full1};
+        // factored layer-3 state: forced, from k = 6 (layer 4 a middle or tail
+        // layer); by the graph's cost model, from k = 8 -- with 64 or 128
+        // points layer 4's extra registers cost more than layer 3 saves
+        const bool fact = g.factor_l3 && k >= (g.factor_mode == 1 ? 6u : 8u);
         for (uint32_t l = (k >= 5 ? 3u : 2u); l <= k - 2; ++l) {
             const int src = (l == 2) ? 1 : (l == 3 ? 2 : 0);
             const int out = (l == k - 2) ? 1 : 0;
+            const int xf = !fact ? 0 : (l == 3 ? 1 : (l == 4 ? 2 : 0));
             // layer 2 (k = 4) runs over the state rows; layers >= 3 over the deep rows,
             // layer 3 reading the label-space prefix at state-row indices
             if (src == 1) set_list(vp, g.state_list, 0);
@@ -436,10 +448,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
                 // change the stored rows, and 2 points per lane halve the
                 // registers of this multiply-heavy layer (twice the warps in flight)
                 vp.ngroups = chunk / 64u;
-                s = launch_v2<2>(vp, src, out, st);
+                s = launch_v2<2>(vp, src, out, xf, st);
                 vp.ngroups = chunk / (32u * ppl);
             } else {
-                s = ppl == 4 ? launch_v2<4>(vp, src, out, st) : launch_v2<2>(vp, src, out, st);
+                s = ppl == 4 ? launch_v2<4>(vp, src, out, xf, st) : launch_v2<2>(vp, src, out, xf, st);
             }
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;

@@ -217,7 +217,13 @@ __device__ __forceinline__ void last3_closed(const V2Params &p, uint32_t ent)
 // (ld.global.cg) instead of the non-coherent read-only path.
 // FROM_R2: window sum of layer 2 from its label-space prefix (layer 3):
 //   W^L = x_u^L x_s^L rho^L,  rho^L = sum_{j in L} (PR2[a1][j] ^ PR2[b1][j]).
-template <int PPL, bool FROM_Y, int OUT, bool COHERENT, bool FROM_R2 = false>
+// XF (factored layer-3 state): 1 = layer 3 stores the head's running sum R^L
+// without its factor x_v^L x_s^L; 2 = the layer after it restores the factor
+// of each window it reads (the window's rows all lie in the tail u's segment,
+// so the factor is x_u^L x_s^L). The products are the same elements; only
+// where the multiplication happens moves (rows of layer 3 against the fewer
+// rows of layer 4 with a non-empty window).
+template <int PPL, bool FROM_Y, int OUT, bool COHERENT, bool FROM_R2 = false, int XF = 0>
 __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uint32_t group)
 {
     constexpr int LOGP = PPL == 4 ? 2 : 1;
@@ -235,7 +241,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     for (int i = 0; i < PPL; ++i) valid[i] = gbase + (uint32_t)lane * PPL + i < p.npoints;
 
     uint64_t xs[PPL];
-    if constexpr (FROM_Y || FROM_R2) {
+    if constexpr (FROM_Y || (FROM_R2 && XF != 1) || XF == 2) {
         const uint64_t zs = (uint32_t)lane < k ? zval(p, source, lane) : 0ull;
         combine_labels<PPL>(zs, k, lane, hi_bits, xs);
     }
@@ -250,7 +256,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     uint32_t cur = p.head[it.x];
     uint64_t zv = 0;
     auto enter_head = [&](uint32_t v) {
-        if constexpr (FROM_Y || FROM_R2) {
+        if constexpr (FROM_Y || (FROM_R2 && XF != 1)) {
             zv = (uint32_t)lane < k ? zval(p, v, lane) : 0ull;
             uint64_t xv[PPL];
             combine_labels<PPL>(zv, k, lane, hi_bits, xv);
@@ -277,7 +283,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         uint32_t m_src = 0;
         if (has) {
             m_coef = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u));
-            if constexpr (FROM_Y || FROM_R2) m_src = p.src[ent];
+            if constexpr (FROM_Y || FROM_R2 || XF == 2) m_src = p.src[ent];
         }
         if constexpr (!COHERENT) {
             if (base == it.x) pdl_enter();  // the previous layer's results are read from here on
@@ -329,7 +335,8 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) R[i] ^= rr_mul(xu[i], yrho[i]);
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? rr_mul(xvxs[i], R[i]) : 0ull;
+                    for (int i = 0; i < PPL; ++i)
+                        acc[i] = valid[i] ? (XF == 1 ? R[i] : rr_mul(xvxs[i], R[i])) : 0ull;
                 }
             } else {
               if (t % E == 0) {
@@ -357,6 +364,15 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                         const ulonglong2 b0 = COHERENT ? __ldcg(vb) : __ldg(vb);
                         w[0] = a0.x ^ b0.x; w[1] = a0.y ^ b0.y;
                     }
+                }
+                if constexpr (XF == 2) {
+                    // the window holds factored layer-3 rows of u's segment
+                    const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
+                    const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
+                    uint64_t xu[PPL];
+                    combine_labels<PPL>(zu, k, lane, hi_bits, xu);
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) w[i] = rr_mul(w[i], rr_mul(xu[i], xs[i]));
                 }
 #pragma unroll
                 for (int i = 0; i < PPL; ++i)

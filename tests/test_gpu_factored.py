@@ -1,0 +1,72 @@
+"""GPU parity of the factored layer-3 state.
+
+With the factored form, layer 3 stores each head's running sum without the
+factor x_v x_s and layer 4 multiplies it back into every window it reads. The
+field products are the same, so witnesses, per-edge sums and arrival times
+must equal the oracle bit for bit with the form forced on, forced off, and as
+the graph's cost model picks it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_08423_gb300 import capi
+from paper_2010_08423_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MODES = [capi.FLAG_FACTOR_L3_ON, capi.FLAG_FACTOR_L3_OFF, 0]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    capi.load()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("flags", MODES)
+def test_witness_all_k_plain_and_motif(flags):
+    g = W.uniform(1500, 24_000, 30, 0, 6, 606, ncolors=3)
+    with capi.Graph(g, flags) as G:
+        info = G.info()
+        if flags:
+            assert info["factored_layer3"] == (1 if flags == capi.FLAG_FACTOR_L3_ON else 0)
+        for s, k, seed in ((0, 5, 1), (3, 6, 2), (9, 7, 3), (4, 8, 4), (2, 10, 5)):
+            _, w = G.reach(s, k, seed)
+            assert np.array_equal(w, oracle.sieve(g, s, k, seed)), (s, k)
+            motif = [int(g["color"][s])] + [(j * 7 + k) % 3 for j in range(k - 1)]
+            _, w = G.reach(s, k, seed, motif=motif)
+            assert np.array_equal(w, oracle.sieve(g, s, k, seed, motif=motif)), (s, k, motif)
+
+
+@pytest.mark.parametrize("flags", MODES[:2])
+def test_per_edge_sums_and_arrivals(flags):
+    g = W.uniform(1200, 16_000, 25, 0, 5, 707)
+    with capi.Graph(g, flags) as G:
+        for s, k in ((1, 6), (5, 9)):
+            S, E, R, _ = G.arrival(s, k, 40 + k)
+            S_ref, E_ref = oracle.sieve(g, s, k, 40 + k, edges=True)
+            assert np.array_equal(S, S_ref) and np.array_equal(E, E_ref)
+            assert np.array_equal(R, oracle.arrival_times(g, E_ref))
+
+
+@pytest.mark.parametrize("flags", MODES[:2])
+def test_cut_hub_segments_and_both_point_widths(flags):
+    from test_gpu_parity import _hub_graph
+    g = _hub_graph(seed=11)
+    with capi.Graph(g, flags) as G:
+        for s, k in ((3, 6), (0, 7)):
+            want = oracle.sieve(g, s, k, 90 + k)
+            for ppl, chunk in ((2, 64), (4, 128)):
+                capi.rr_set_tuning(G.handle, k, ppl, chunk)
+                _, w = G.reach(s, k, 90 + k)
+                assert np.array_equal(w, want), (s, k, ppl, chunk)
+
+
+def test_flags_on_and_off_together_are_rejected():
+    g = W.tiny_random(5, n=6, m=10, tau=3, dmax=2)
+    with pytest.raises(capi.RRError) as ei:
+        capi.Graph(g, capi.FLAG_FACTOR_L3_ON | capi.FLAG_FACTOR_L3_OFF)
+    assert ei.value.status == capi.RR_EINVAL
