@@ -313,16 +313,26 @@ def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, zt
     c = chunk
     lg = 7 if ppl == 4 else 6
     rstride = c // (32 * ppl) * (lg + 1)
-    # layer 3 reads the label-space prefix (2k values) and multiplies twice per point;
-    # layers 4..k-3 read two state rows and multiply once per point
-    l3 = (D * c * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c))
+    R3 = info["deep_head_runs"]        # head runs over the deep rows' ranges
+    # factored layer-3 state (k >= 8 when the graph's cost model picks it)
+    fact = bool(info["factored_layer3"]) and k >= 8
+    # layer 3 reads the label-space prefix (2k values); per point it multiplies
+    # x_u by y rho for every row and, unfactored, by x_v x_s once per head run and
+    # once per row; layers >= 4 read two state rows and multiply once per point
+    # (layer 4 of the factored form twice more: by x_u x_s)
+    l3_mults = D * (k + c) if fact else D * (k + 2 * c) + R3 * c
+    l3 = (D * c * 8 + 2 * D * k * 8 + D * 20, l3_mults)
     mid = (D * c * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k))
+    l4 = (mid[0], DC * (3 * c + k)) if fact else mid
     nmid = max(0, k - 5)
-    if nmid:
-        mid_avg = ((l3[0] + (nmid - 1) * mid[0]) / nmid, (l3[1] + (nmid - 1) * mid[1]) / nmid)
+    if nmid >= 2:
+        mid_avg = ((l3[0] + l4[0] + (nmid - 2) * mid[0]) / nmid,
+                   (l3[1] + l4[1] + (nmid - 2) * mid[1]) / nmid)
+    elif nmid == 1:
+        mid_avg = l3
     else:
         mid_avg = mid
-    tail = ((D * rstride * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c)) if k == 5 else
+    tail = ((D * rstride * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c) if k == 5 else
             (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
     alg = {
         "first_layer": (P * 8 + P * 12, 0),
