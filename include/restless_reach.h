@@ -108,8 +108,8 @@ typedef struct {
  * factored layer-3 state on (queries with k >= 6) / off; by default it is
  * used for k >= 8 when it takes fewer multiplications per sieve point: layer
  * 3 then saves one product per deep row and one per head run, layer 4 spends
- * two per deep row with a non-empty window (deep_rows + deep_head_runs >
- * 2 deep_compute_rows). Results are bit-identical either way.
+ * two (weighted 1.5 each) per deep row with a non-empty window (deep_rows +
+ * deep_head_runs > 3 deep_compute_rows). Results are bit-identical either way.
  * Errors: RR_EINVAL for n == 0, m >= 2^31, an endpoint >= n or a self-loop;
  * RR_ENOMEM / RR_ECUDA on device failure (nothing is leaked). */
 rr_status rr_graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,

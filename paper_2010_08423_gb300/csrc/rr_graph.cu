@@ -513,13 +513,18 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         R.nitems = (uint32_t)items.size();
         R.nitems_coarse = (uint32_t)coarse.size();
         if (&R == &g.deep_list) {
-            // layer 3 forms x_v x_s once per head run of a warp's range
+            // factored layer-3 state when it saves multiplications: layer 3
+            // saves one product per point for every deep row and every head
+            // run (x_v x_s is formed once per head run of a warp's range);
+            // layer 4 spends two per deep row with a non-empty window, each
+            // weighted 1.5 (they are out-of-line calls, in a kernel with more
+            // registers: fitted on Chung-Lu and uniform graphs)
             uint64_t runs = 0;
             for (const uint2 &it : items)
                 for (uint32_t r = it.x; r < it.y; ++r) runs += r == it.x || heads[r] != heads[r - 1];
             g.deep_head_runs = runs;
             g.factor_l3 = g.factor_mode == 1 ||
-                          (g.factor_mode == 0 && R.count + runs > 2 * g.deep_compute_rows);
+                          (g.factor_mode == 0 && R.count + runs > 3 * g.deep_compute_rows);
         }
         RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));
         RR_CUDA(R.items_coarse.reserve(std::max<size_t>(1, coarse.size()) * sizeof(uint2)));

@@ -25,6 +25,14 @@ __device__ __forceinline__ static uint64_t rr_mul(uint64_t a, uint64_t b)
     return gf64_mul(a, b);
 }
 #endif
+// An out-of-line multiply for the extra products of an otherwise inlined
+// body: a call keeps only the caller's live values in registers, where
+// inlining more products beside the body's own raised its register count
+// (and cut the warps in flight) more than the call costs.
+__device__ __noinline__ static uint64_t rr_mul_call(uint64_t a, uint64_t b)
+{
+    return gf64_mul(a, b);
+}
 
 constexpr int kW2 = 4;  // warps per block
 
@@ -372,7 +380,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     uint64_t xu[PPL];
                     combine_labels<PPL>(zu, k, lane, hi_bits, xu);
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) w[i] = rr_mul(w[i], rr_mul(xu[i], xs[i]));
+                    for (int i = 0; i < PPL; ++i) w[i] = rr_mul_call(w[i], rr_mul_call(xu[i], xs[i]));
                 }
 #pragma unroll
                 for (int i = 0; i < PPL; ++i)
