@@ -112,10 +112,19 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def wait_first(self, timeout_s=3.0):
+        """Returns once nvidia-smi has written its first sample (or on timeout)."""
+        t_end = time.perf_counter() + timeout_s
+        while self.proc is not None and time.perf_counter() < t_end:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -145,7 +154,9 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm),
+                "window": "every 50 ms from 0.4 s of untimed steps of the same query just "
+                          "before the timed region through its end"}
 
 
 def cpu_baseline(g, k, nsteps_hint=1):
@@ -594,6 +605,16 @@ def main():
                for _ in range(args.steps)]
         sampler = ClockSampler(local_rank)
         sampler.start()
+        sampler.wait_first()
+        # untimed steps of the same query under the sampler (the timed region
+        # alone is a few ms, shorter than the sampling interval)
+        t_load = time.perf_counter() + 0.4
+        j = 0
+        while time.perf_counter() < t_load:
+            step(1_000_000 + j)
+            j += 1
+            if j % 32 == 0:
+                stream.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
