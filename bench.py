@@ -293,8 +293,9 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
 
 def gf_mul_peak(capi, torch):
     """Measured peak rate of the device GF(2^64) multiply (multiplications/s):
-    the rr_bench_gf_mul microbenchmark (register-only dependent chains, both
-    operands changing every step) over the whole GPU, timed with CUDA events."""
+    the rr_bench_gf_mul microbenchmark (register-only chains, four independent
+    products a step, every operand value entering exactly one product as in the
+    layer kernels) over the whole GPU, timed with CUDA events."""
     st = torch.cuda.Stream()
     sink = torch.zeros(1, dtype=torch.int64, device="cuda")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -691,7 +692,8 @@ def main():
                         "peak": round(mul_peak / 1e9, 2), "unit": "GF(2^64) Gmul/s",
                         "frac": d["alu_frac"],
                         "peak_kind": "measured live: rr_bench_gf_mul, register-only multiply chains "
-                                     "on all SMs (integer issue bound)", **common}
+                                     "on all SMs, each operand value in one product (ALU-pipe bound)",
+                        **common}
         else:
             roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
                         "unit": "GB/s", "frac": d["hbm_frac"], "peak_kind": peak_kind, **common}

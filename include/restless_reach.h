@@ -325,9 +325,11 @@ rr_status rr_debug_ztable(const rr_graph *g, const rr_query *q, uint64_t *out);
 rr_status rr_debug_gf_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t count);
 /* rr_bench_gf_mul: the device GF(2^64) multiply at its peak rate, for the
  * arithmetic roofline of the sieve kernels (not part of the paper's method).
- * Enqueues blocks x threads threads on `stream`, each running four dependent
- * multiply chains of `iters` steps in registers (both operands change every
- * step); *mults (host) receives the number of multiplications enqueued;
+ * Enqueues blocks x threads threads on `stream`, each running `iters` steps of
+ * four independent products in registers, every operand value entering
+ * exactly one product (as in the sieve kernels, so no operand preparation is
+ * shared between products); *mults (host) receives the number of
+ * multiplications enqueued;
  * d_sink (one uint64, device) keeps the results live and is practically never
  * written. Errors: RR_EINVAL for threads == 0 or > 1024, blocks == 0 or a NULL
  * pointer; RR_ECUDA if the launch fails. */

@@ -89,25 +89,21 @@ __device__ __forceinline__ uint64_t shfl64x(uint64_t v, int mask)
 }
 
 // Sum over j in L of the per-label values held by lanes first..first+k-1 (lane
-// first+j holds label j+1's value), for the lane's PPL consecutive points of a
-// group whose first point has high bits `hi_bits` (bits >= LOGP+5 of the point
-// index).
+// first+j holds label j+1's value), for the lane's PPL consecutive points
+// pbits + i, i < PPL (pbits: the lane's first point, its low LOGP bits zero):
+// label j+1 is in point L when bit j of L is set, so the labels above LOGP
+// follow pbits and the lowest LOGP labels the point's offset i.
 template <int PPL>
-__device__ __forceinline__ void combine_labels(uint64_t lane_val, uint32_t k, int lane,
-                                               uint32_t hi_bits, uint64_t (&out)[PPL],
-                                               uint32_t first = 0)
+__device__ __forceinline__ void combine_labels(uint64_t lane_val, uint32_t k, uint32_t pbits,
+                                               uint64_t (&out)[PPL], uint32_t first = 0)
 {
-    constexpr int LOGP = PPL == 4 ? 2 : 1;
-    uint64_t base = 0, low0 = 0, low1 = 0;
-    for (uint32_t j = 0; j < k; ++j) {
+    constexpr uint32_t LOGP = PPL == 4 ? 2 : 1;
+    const uint64_t low0 = shfl64b(lane_val, (int)first);
+    const uint64_t low1 = LOGP == 2 ? shfl64b(lane_val, (int)first + 1) : 0ull;
+    uint64_t base = 0;
+    for (uint32_t j = LOGP; j < k; ++j) {
         const uint64_t bj = shfl64b(lane_val, (int)(first + j));
-        if (j == 0) low0 = bj;
-        else if (LOGP == 2 && j == 1) low1 = bj;
-        else if (j < (uint32_t)LOGP + 5u) {
-            if (((uint32_t)lane >> (j - LOGP)) & 1u) base ^= bj;
-        } else if ((hi_bits >> (j - LOGP - 5u)) & 1u) {
-            base ^= bj;
-        }
+        if ((pbits >> j) & 1u) base ^= bj;
     }
     out[0] = base;
     out[1] = base ^ low0;
@@ -243,7 +239,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     const uint64_t key_y = p.qd->key_y;
     const uint32_t col = group * (32u * PPL) + (uint32_t)lane * PPL;
     const uint32_t gbase = p.chunk_base + group * (32u * PPL);
-    const uint32_t hi_bits = gbase >> LG;
+    const uint32_t pbits = gbase + (uint32_t)lane * PPL;  // the lane's first point
     bool valid[PPL];
 #pragma unroll
     for (int i = 0; i < PPL; ++i) valid[i] = gbase + (uint32_t)lane * PPL + i < p.npoints;
@@ -251,7 +247,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     uint64_t xs[PPL];
     if constexpr (FROM_Y || (FROM_R2 && XF != 1) || XF == 2) {
         const uint64_t zs = (uint32_t)lane < k ? zval(p, source, lane) : 0ull;
-        combine_labels<PPL>(zs, k, lane, hi_bits, xs);
+        combine_labels<PPL>(zs, k, pbits, xs);
     }
 
     // FROM_Y: the prefix over the head v's entries factors as
@@ -267,7 +263,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         if constexpr (FROM_Y || (FROM_R2 && XF != 1)) {
             zv = (uint32_t)lane < k ? zval(p, v, lane) : 0ull;
             uint64_t xv[PPL];
-            combine_labels<PPL>(zv, k, lane, hi_bits, xv);
+            combine_labels<PPL>(zv, k, pbits, xv);
 #pragma unroll
             for (int i = 0; i < PPL; ++i) xvxs[i] = rr_mul(xv[i], xs[i]);
         }
@@ -315,7 +311,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
                 const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
                 uint64_t r[PPL];
-                combine_labels<PPL>(rr_mul(coef, zu), k, lane, hi_bits, r);
+                combine_labels<PPL>(rr_mul(coef, zu), k, pbits, r);
 #pragma unroll
                 for (int i = 0; i < PPL; ++i) R[i] ^= r[i];
 #pragma unroll
@@ -338,8 +334,8 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
                     const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
                     uint64_t xu[PPL], yrho[PPL];
-                    combine_labels<PPL>(zu, k, lane, hi_bits, xu);
-                    combine_labels<PPL>(lab, k, lane, hi_bits, yrho, (t % E) * k);
+                    combine_labels<PPL>(zu, k, pbits, xu);
+                    combine_labels<PPL>(lab, k, pbits, yrho, (t % E) * k);
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) R[i] ^= rr_mul(xu[i], yrho[i]);
 #pragma unroll
@@ -355,7 +351,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
               }
               if (a != b) {
                 uint64_t c[PPL], w[PPL];
-                combine_labels<PPL>(lab, k, lane, hi_bits, c, (t % E) * k);
+                combine_labels<PPL>(lab, k, pbits, c, (t % E) * k);
                 {
                     const uint64_t *pa = p.st_in + (size_t)a * p.chunk + col;
                     const uint64_t *pb = p.st_in + (size_t)b * p.chunk + col;
@@ -378,7 +374,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
                     const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
                     uint64_t xu[PPL];
-                    combine_labels<PPL>(zu, k, lane, hi_bits, xu);
+                    combine_labels<PPL>(zu, k, pbits, xu);
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) w[i] = rr_mul_call(w[i], rr_mul_call(xu[i], xs[i]));
                 }
