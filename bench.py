@@ -326,26 +326,33 @@ def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, zt
     lg = 7 if ppl == 4 else 6
     rstride = c // (32 * ppl) * (lg + 1)
     R3 = info["deep_head_runs"]        # head runs over the deep rows' ranges
-    # factored layer-3 state (k >= 8 when the graph's cost model picks it)
-    fact = bool(info["factored_layer3"]) and k >= 8
-    # layer 3 reads the label-space prefix (2k values); per point it multiplies
-    # x_u by y rho for every row and, unfactored, by x_v x_s once per head run and
-    # once per row; layers >= 4 read two state rows and multiply once per point
-    # (layer 4 of the factored form twice more: by x_u x_s)
-    l3_mults = D * (k + c) if fact else D * (k + 2 * c) + R3 * c
-    l3 = (D * c * 8 + 2 * D * k * 8 + D * 20, l3_mults)
+    pmode = 1 if info["pair_layer3_min_k"] <= k <= 20 else 0
+    NP = k * (k + 1) // 2
+    # layers >= 4 read two state rows per window and multiply once per point
     mid = (D * c * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k))
-    l4 = (mid[0], DC * (3 * c + k)) if fact else mid
-    nmid = max(0, k - 5)
-    if nmid >= 2:
-        mid_avg = ((l3[0] + l4[0] + (nmid - 2) * mid[0]) / nmid,
-                   (l3[1] + l4[1] + (nmid - 2) * mid[1]) / nmid)
-    elif nmid == 1:
-        mid_avg = l3
+    third = None
+    if pmode:
+        # layer 3 in pair-label space, once per query: 2k label-space values in,
+        # k(k+1)/2 pair values out per deep row; k + k^2 products per row
+        third = (D * (NP * 8 + 2 * k * 8 + 20), D * (k + k * k))
+    if pmode == 1:
+        # layer 4 reads 2 NP pair values per window and multiplies three times
+        # per point (by x_u, by x_s, by c)
+        l4 = (D * c * 8 + 2 * DC * NP * 8 + D * 20, DC * (3 * c + k))
+        mids = [l4] + [mid] * (k - 7) if k >= 7 else []
+        tail = ((D * rstride * 8 + 2 * DC * NP * 8 + D * 20, DC * (3 * c + k)) if k == 6 else
+                (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
+    else:
+        # layer 3 per point from the label-space prefix: x_u times y rho for every
+        # row, x_v x_s once per head run and once per row
+        l3 = (D * c * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c)
+        mids = [l3] + [mid] * (k - 6) if k >= 6 else []
+        tail = ((D * rstride * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c) if k == 5 else
+                (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
+    if mids:
+        mid_avg = (sum(x[0] for x in mids) / len(mids), sum(x[1] for x in mids) / len(mids))
     else:
         mid_avg = mid
-    tail = ((D * rstride * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c) if k == 5 else
-            (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
     alg = {
         "first_layer": (P * 8 + P * 12, 0),
         "second_layer": (S * k * 8 + S * 20 + 2 * S * 8, S * (1 + k)),
@@ -354,6 +361,8 @@ def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, zt
         "last_layer": (2 * T3 * rstride * 8 + T3 * 16 + n * 8, T3 * rstride),
         "ztable": (n * k * 8, ztable_mults),
     }
+    if third is not None:
+        alg["third_layer"] = third
     out = {}
     for name, (kms, kn) in kt.items():
         if not kn or name not in alg:

@@ -92,9 +92,8 @@ typedef struct {
     uint64_t deep_compute_rows;    /* deep rows whose window holds a deep row */
     uint64_t deep_tail_rows;       /* rows whose window holds a deep row */
     uint64_t deep_head_runs;       /* head runs over the deep rows' scheduling ranges */
-    int factored_layer3;           /* 1: queries with k >= 8 (6 if forced) store layer
-                                      3's sums without the head's factor x_v x_s and
-                                      layer 4 restores it per window */
+    int pair_layer3_min_k;         /* smallest k whose layer 3 runs in pair-label
+                                      space (21: none; see rr_graph_load's flags) */
 } rr_graph_info;
 
 /* ---- graph ----------------------------------------------------------------
@@ -104,12 +103,13 @@ typedef struct {
  * t_e - delta(u_e) <= t_f <= t_e) and the scheduling ranges. Host arrays are
  * read only; src/dst/t have m entries, delta n, color n (or NULL).
  * flags: bit 0 set = keep the dense state layout (one state row per edge)
- * instead of storing only rows that lie in some window. Bits 1 / 2 force the
- * factored layer-3 state on (queries with k >= 6) / off; by default it is
- * used for k >= 8 when it takes fewer multiplications per sieve point: layer
- * 3 then saves one product per deep row and one per head run, layer 4 spends
- * two (weighted 1.5 each) per deep row with a non-empty window (deep_rows +
- * deep_head_runs > 3 deep_compute_rows). Results are bit-identical either way.
+ * instead of storing only rows that lie in some window. Layer 3 in pair-label
+ * space stores per deep row the k(k+1)/2 values of a symmetric label-pair
+ * matrix Q, independent of the sieve points, and layer 4 evaluates
+ * x_u^L x_s^L sum_{i,j in L} dQ_ij over each window; queries with 9 <= k <=
+ * 20 use it. Bit 1 set = use it from k = 6, bit 2 set = never (layer 3 per
+ * point from the label-space prefix); both set is RR_EINVAL. Results are
+ * bit-identical in either form.
  * Errors: RR_EINVAL for n == 0, m >= 2^31, an endpoint >= n or a self-loop;
  * RR_ENOMEM / RR_ECUDA on device failure (nothing is leaked). */
 rr_status rr_graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
@@ -355,7 +355,8 @@ rr_status rr_debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *
  * kind: 0 = first layer, 1 = middle layers reading state, 2 = last layer with
  * the fused per-vertex reduce, 3 = z-table, 4 = persistent batched kernel,
  * 5 = second layer (window sums from the first layer's scalar prefix),
- * 6 = layer k-2 writing the transformed state. While timing is enabled the
+ * 6 = layer k-2 writing the transformed state, 7 = layer 3 in pair-label
+ * space. While timing is enabled the
  * launches are issued one by one instead of as a captured CUDA graph. */
 typedef struct {
     double ms[8];

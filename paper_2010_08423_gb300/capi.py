@@ -19,8 +19,8 @@ RR_OK, RR_EINVAL, RR_ENOMEM, RR_EAGAIN, RR_ETIMEDOUT, RR_ECANCELED, RR_ECUDA, RR
 STATUS_NAMES = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_EAGAIN",
                 4: "RR_ETIMEDOUT", 5: "RR_ECANCELED", 6: "RR_ECUDA", 7: "RR_ENOPATH"}
 FLAG_DENSE_STATE = 1
-FLAG_FACTOR_L3_ON = 2
-FLAG_FACTOR_L3_OFF = 4
+FLAG_PAIR_ON = 2
+FLAG_PAIR_OFF = 4
 
 
 class RRError(RuntimeError):
@@ -42,7 +42,7 @@ class rr_graph_info(ctypes.Structure):
                 ("compact", ctypes.c_int), ("producer_window_rows", ctypes.c_uint64),
                 ("state_compute_rows", ctypes.c_uint64), ("tail_rows", ctypes.c_uint64),
                 ("deep_compute_rows", ctypes.c_uint64), ("deep_tail_rows", ctypes.c_uint64),
-                ("deep_head_runs", ctypes.c_uint64), ("factored_layer3", ctypes.c_int)]
+                ("deep_head_runs", ctypes.c_uint64), ("pair_layer3_min_k", ctypes.c_int)]
 
 
 class rr_kernel_times(ctypes.Structure):
@@ -50,7 +50,7 @@ class rr_kernel_times(ctypes.Structure):
 
 
 TIMING_KINDS = ["first_layer", "mid_layer", "last_layer", "ztable", "batch", "second_layer",
-                "tail_layer", "unused"]
+                "tail_layer", "third_layer"]
 
 
 EXPORTED = [

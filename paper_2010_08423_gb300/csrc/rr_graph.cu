@@ -513,18 +513,12 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         R.nitems = (uint32_t)items.size();
         R.nitems_coarse = (uint32_t)coarse.size();
         if (&R == &g.deep_list) {
-            // factored layer-3 state when it saves multiplications: layer 3
-            // saves one product per point for every deep row and every head
-            // run (x_v x_s is formed once per head run of a warp's range);
-            // layer 4 spends two per deep row with a non-empty window, each
-            // weighted 1.5 (they are out-of-line calls, in a kernel with more
-            // registers: fitted on Chung-Lu and uniform graphs)
+            // head runs over the fine ranges (the per-point layer 3 forms
+            // x_v x_s once per run)
             uint64_t runs = 0;
             for (const uint2 &it : items)
                 for (uint32_t r = it.x; r < it.y; ++r) runs += r == it.x || heads[r] != heads[r - 1];
             g.deep_head_runs = runs;
-            g.factor_l3 = g.factor_mode == 1 ||
-                          (g.factor_mode == 0 && R.count + runs > 3 * g.deep_compute_rows);
         }
         RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));
         RR_CUDA(R.items_coarse.reserve(std::max<size_t>(1, coarse.size()) * sizeof(uint2)));
@@ -563,8 +557,8 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     g->m = m;
     g->has_colors = color != nullptr;
     g->compact = !(flags & 1u);
-    if ((flags & 6u) == 6u) return fail(RR_EINVAL, "rr_graph_load: flags force the factored layer-3 state both on and off");
-    g->factor_mode = (flags & 2u) ? 1u : ((flags & 4u) ? 2u : 0u);
+    if ((flags & 6u) == 6u) return fail(RR_EINVAL, "rr_graph_load: flags turn the pair-label layer 3 both on and off");
+    g->pair_force = (flags & 2u) ? 2u : ((flags & 4u) ? 1u : 0u);
     RR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     cudaStream_t st = g->stream;
 

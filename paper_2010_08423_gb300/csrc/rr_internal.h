@@ -23,7 +23,7 @@ extern std::atomic<uint64_t> g_launches;
 // Kernel timing (rr_timing_*): kinds as in rr_kernel_times.
 enum TimingKind {
     kTimeFirst = 0, kTimeMid = 1, kTimeLast = 2, kTimeZ = 3, kTimeBatch = 4, kTimeSecond = 5,
-    kTimeTail = 6, kTimeKinds = 8
+    kTimeTail = 6, kTimeThird = 7, kTimeKinds = 8
 };
 extern std::atomic<bool> g_timing;
 // Records a start event on st when timing is enabled; returns an opaque slot.
@@ -218,6 +218,11 @@ struct FanOut {
 // row row_s[r] >= 1 holding the XOR of its own and the earlier producer rows'
 // layer values within its head's segment. A consumer row e reads its window
 // sum as state[row_a[e]] ^ state[row_b[e]] (row_a == 0 <=> empty window).
+// Smallest k whose layer 3 runs in pair-label space unless the graph's load
+// flags choose (rr_sieve2.cu): from k = 9 it was faster on every graph
+// measured (uniform n = 1e5 and Chung-Lu n = 2e5, 1e6), at k = 8 level or slower.
+constexpr uint32_t kPairMinK = 9;
+
 struct Graph {
     uint32_t n = 0;
     uint64_t m = 0;
@@ -230,8 +235,9 @@ struct Graph {
     uint64_t state_compute_rows = 0;    // state rows whose window holds a state row
     uint64_t deep_compute_rows = 0;     // deep rows whose window holds a deep row
     uint64_t deep_head_runs = 0;        // head runs over the deep list's fine ranges
-    uint32_t factor_mode = 0;           // 0 = cost model, 1 = on, 2 = off
-    bool factor_l3 = false;             // factored layer-3 state (k >= 6)
+    // layer 3 in pair-label space (6 <= k <= 20): 0 = by k (k >= kPairMinK),
+    // 1 = forced off, 2 = forced on (load flags)
+    uint32_t pair_force = 0;
     uint32_t max_in_degree = 0;
 
     DevBuf off;      // n+1 uint32

@@ -65,6 +65,8 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cud
 struct ZeroRows {
     uint64_t *py, *full0, *full1, *red, *pr2;
     uint32_t n, chunk, rstride, kpr2;
+    uint64_t *pr3;
+    uint32_t npr3;
 };
 
 __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, const ZeroRows &z)
@@ -83,6 +85,8 @@ __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, cons
         for (uint32_t i = tid; i < z.rstride; i += stride) z.red[i] = 0;
     if (z.pr2)
         for (uint32_t i = tid; i < z.kpr2; i += stride) z.pr2[i] = 0;
+    if (z.pr3)
+        for (uint32_t i = tid; i < z.npr3; i += stride) z.pr3[i] = 0;
 }
 
 // Layer 1; its grid also clears what zero_rows lists (saving a launch).
@@ -96,14 +100,14 @@ __global__ void __launch_bounds__(kW2 * 32) k_first_scalar(const V2Params p, uin
     first_scalar_warp(p, task, py);
 }
 
-template <int PPL, bool FROM_Y, int OUT, bool FROM_R2 = false, int XF = 0>
+template <int PPL, bool FROM_Y, int OUT, bool FROM_R2 = false, bool PAIR = false>
 __global__ void __launch_bounds__(kW2 * 32) k_layer_v2(const V2Params p)
 {
     // pdl_enter() inside layer_warp, after the graph- and query-only loads
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems * p.ngroups) return;
     const uint32_t item = task / p.ngroups;
-    layer_warp<PPL, FROM_Y, OUT, false, FROM_R2, XF>(p, item, task - item * p.ngroups);
+    layer_warp<PPL, FROM_Y, OUT, false, FROM_R2, PAIR>(p, item, task - item * p.ngroups);
 }
 
 // Carry fix-up of cut head segments (rr_v2_device.cuh): phase 1 one block
@@ -152,6 +156,22 @@ __global__ void __launch_bounds__(kW2 * 32) k_second_label(const V2Params p, uin
     second_label_warp<true>(p, task, pr2);
 }
 
+__global__ void __launch_bounds__(kW2 * 32) k_third_pair(const V2Params p, uint32_t count,
+                                                         uint64_t *__restrict__ pr3)
+{
+    // pdl_enter() inside third_pair_row, after the graph- and query-only loads
+    const uint32_t e = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (e >= count) return;
+    third_pair_row(p, e, pr3);
+}
+
+__global__ void __launch_bounds__(kW2 * 32) k_pair_prefix(const V2Params p, uint64_t *__restrict__ pr3)
+{
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems) return;
+    pair_prefix_warp(p, task, pr3);
+}
+
 __global__ void k_first2(const V2Params p, const uint32_t *__restrict__ off,
                          const uint32_t *__restrict__ row_src, const uint32_t *__restrict__ row_eid,
                          uint32_t m)
@@ -196,11 +216,10 @@ static void set_list(V2Params &vp, const RowList &L, int win)
 }
 
 // src: 0 = window sums from the per-point state, 1 = from the scalar layer-1
-// prefix (layer 2), 2 = from the label-space layer-2 prefix (layer 3).
-// xf: factored layer-3 state (layer_warp's XF): 1 on layer 3 (out 0 only),
-// 2 on layer 4.
+// prefix (layer 2), 2 = from the label-space layer-2 prefix (layer 3), 3 = from
+// pair-label layer-3 windows (layer 4).
 template <int PPL>
-static rr_status launch_v2(const V2Params &vp, int src, int out, int xf, cudaStream_t st)
+static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st)
 {
     const uint64_t tasks = (uint64_t)vp.nitems * vp.ngroups;
     if (tasks == 0) return RR_OK;
@@ -212,11 +231,10 @@ static rr_status launch_v2(const V2Params &vp, int src, int out, int xf, cudaStr
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 1>, dim3(blocks), B, st, vp));
     } else if (src == 2) {
         if (out == 1) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, true>, dim3(blocks), B, st, vp));
-        else if (xf == 1) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true, 1>, dim3(blocks), B, st, vp));
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true>, dim3(blocks), B, st, vp));
-    } else if (xf == 2) {
-        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, false, 2>, dim3(blocks), B, st, vp));
-        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, false, 2>, dim3(blocks), B, st, vp));
+    } else if (src == 3) {
+        if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, false, true>, dim3(blocks), B, st, vp));
+        else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, false, true>, dim3(blocks), B, st, vp));
     } else {
         if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0>, dim3(blocks), B, st, vp));
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1>, dim3(blocks), B, st, vp));
@@ -238,23 +256,33 @@ uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk)
 // Words of each part of the engine's scratch, in layout order: scalar layer-1
 // prefix, label-space layer-2 prefix (k per state row), two per-point buffers,
 // one transformed buffer.
+// Layer 3 in pair-label space (third_pair_row), layer 4 reading its windows:
+// queries with 6 <= k <= 20 when the graph's load flags force it, else with
+// k >= kPairMinK unless they turn it off.
+static bool pair_layer3(const Graph &g, uint32_t k)
+{
+    if (k < 6 || pair_count(k) > kMaxPairs) return false;
+    return g.pair_force ? g.pair_force == 2 : k >= kPairMinK;
+}
+
 static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
-                      uint64_t *pr2_w, uint64_t *full_w, uint64_t *red_w)
+                      uint64_t *pr2_w, uint64_t *pr3_w, uint64_t *full_w, uint64_t *red_w)
 {
     const uint64_t srows = g.state_list.count + 1;  // layer 2 (label space; k = 4 transformed)
     const uint64_t drows = g.deep_list.count + 1;   // layers >= 3
     // k = 2 and k = 3 are closed forms: no per-point state
     *py_w = k >= 3 ? (g.prod_list.count + 1 + 31) / 32 * 32 : 0;
     *pr2_w = k >= 5 ? (srows * k + 31) / 32 * 32 : 0;
+    *pr3_w = pair_layer3(g, k) ? (drows * pair_count(k) + 31) / 32 * 32 : 0;
     *full_w = k >= 4 ? drows * chunk : 0;
     *red_w = k >= 4 ? std::max(srows, drows) * v2_reduced_stride(ppl, chunk) : 0;
 }
 
 uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
 {
-    uint64_t py_w, pr2_w, full_w, red_w;
-    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &full_w, &red_w);
-    return (py_w + pr2_w + 2 * full_w + red_w) * 8ull + 4096;
+    uint64_t py_w, pr2_w, pr3_w, full_w, red_w;
+    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &full_w, &red_w);
+    return (py_w + pr2_w + pr3_w + 2 * full_w + red_w) * 8ull + 4096;
 }
 
 // z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades); rows
@@ -324,11 +352,13 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         ~PdlScope() { t_pdl = saved; }
     } pdl_scope(pdl);
     uint64_t nk = 0;
-    uint64_t py_w, pr2_w, full_w, red_w;
-    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &full_w, &red_w);
+    uint64_t py_w, pr2_w, pr3_w, full_w, red_w;
+    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &full_w, &red_w);
+    const bool pair = pair_layer3(g, k);
     uint64_t *py = d_scratch;
     uint64_t *pr2 = py + py_w;
-    uint64_t *full0 = pr2 + pr2_w;
+    uint64_t *pr3 = pr2 + pr2_w;
+    uint64_t *full0 = pr3 + pr3_w;
     uint64_t *full1 = full0 + full_w;
     uint64_t *red = full1 + full_w;
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
@@ -346,7 +376,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     // the witness and the scratch's zero rows (k = 2 has no scratch); cleared by
     // the first layer's grid when it runs
     const ZeroRows zr{k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
-                      k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, rstride, k};
+                      k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, rstride, k,
+                      pair ? pr3 : nullptr, pair_count(k)};
     const bool zero_in_first = k >= 3 && g.prod_list.nitems > 0;
     if (!zero_in_first) {
         RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, d_desc, zr));
@@ -410,6 +441,26 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         }
     }
 
+    if (pair) {
+        // layer 3 in pair-label space (independent of the point chunk), over
+        // the deep rows with their state-row windows
+        set_list(vp, g.deep_list, 1);
+        vp.layer = 3;
+        if (vp.nitems) {
+            const uint32_t count = (uint32_t)g.deep_list.count;
+            const int tslot = timing_begin(st);
+            RR_CUDA(launch_pdl(k_third_pair, dim3(blocks_for(count)), dim3(kW2 * 32), st, vp, count, pr3));
+            RR_LAUNCHED();
+            RR_CUDA(launch_pdl(k_pair_prefix, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, pr3));
+            RR_LAUNCHED();
+            timing_end(tslot, kTimeThird, st);
+            nk += 2;
+            rr_status fs = launch_fixup(g.deep_list, pr3, pair_count(k), st, &nk);
+            if (fs != RR_OK) return fs;
+        }
+    }
+    vp.pr3 = pr3;
+
     if (k == 3 && g.win_list.count) {
         // last layer in closed form (no sieve points)
         set_list(vp, g.win_list, 0);
@@ -428,14 +479,11 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         // layers 2 (k = 4) or 3 (k >= 5) .. k-2; the last of them writes the
         // transformed state
         uint64_t *bufs[2] = {full0, full1};
-        // factored layer-3 state: forced, from k = 6 (layer 4 a middle or tail
-        // layer); by the graph's cost model, from k = 8 -- with 64 or 128
-        // points layer 4's extra registers cost more than layer 3 saves
-        const bool fact = g.factor_l3 && k >= (g.factor_mode == 1 ? 6u : 8u);
-        for (uint32_t l = (k >= 5 ? 3u : 2u); l <= k - 2; ++l) {
-            const int src = (l == 2) ? 1 : (l == 3 ? 2 : 0);
+        // with layer 3 in pair-label space the per-point layers start at 4,
+        // layer 4 reading the pair windows
+        for (uint32_t l = pair ? 4u : (k >= 5 ? 3u : 2u); l <= k - 2; ++l) {
+            const int src = (l == 2) ? 1 : (l == 3 ? 2 : (pair && l == 4 ? 3 : 0));
             const int out = (l == k - 2) ? 1 : 0;
-            const int xf = !fact ? 0 : (l == 3 ? 1 : (l == 4 ? 2 : 0));
             // layer 2 (k = 4) runs over the state rows; layers >= 3 over the deep rows,
             // layer 3 reading the label-space prefix at state-row indices
             if (src == 1) set_list(vp, g.state_list, 0);
@@ -448,10 +496,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
                 // change the stored rows, and 2 points per lane halve the
                 // registers of this multiply-heavy layer (twice the warps in flight)
                 vp.ngroups = chunk / 64u;
-                s = launch_v2<2>(vp, src, out, xf, st);
+                s = launch_v2<2>(vp, src, out, st);
                 vp.ngroups = chunk / (32u * ppl);
             } else {
-                s = ppl == 4 ? launch_v2<4>(vp, src, out, xf, st) : launch_v2<2>(vp, src, out, xf, st);
+                s = ppl == 4 ? launch_v2<4>(vp, src, out, st) : launch_v2<2>(vp, src, out, st);
             }
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;

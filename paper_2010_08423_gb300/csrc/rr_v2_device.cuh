@@ -36,6 +36,14 @@ __device__ __noinline__ static uint64_t rr_mul_call(uint64_t a, uint64_t b)
 
 constexpr int kW2 = 4;  // warps per block
 
+// Layer 3 in pair-label space: a deep row holds the k(k+1)/2 values of a
+// symmetric label pair matrix, value (i, j), i >= j, at i(i+1)/2 + j.
+constexpr uint32_t kMaxPairs = 210;  // k = 20
+__host__ __device__ __forceinline__ uint32_t pair_count(uint32_t k)
+{
+    return k * (k + 1) / 2;
+}
+
 struct V2Params {
     // list
     const uint32_t *head, *eid, *src, *ia, *ib;
@@ -49,6 +57,7 @@ struct V2Params {
     uint32_t chunk_base, chunk, ngroups, npoints;
     const uint64_t *py;     // scalar layer-1 prefix, indexed by producer rank
     const uint64_t *pr2;    // layer-2 label-space prefix, k values per state row
+    const uint64_t *pr3;    // layer-3 pair-label prefix, pair_count(k) values per deep row
     const uint64_t *st_in;  // full state, stride chunk
     uint64_t *st_out;       // full (stride chunk) or reduced (stride ngroups*(lg+1))
 };
@@ -110,6 +119,40 @@ __device__ __forceinline__ void combine_labels(uint64_t lane_val, uint32_t k, ui
     if constexpr (PPL == 4) {
         out[2] = base ^ low1;
         out[3] = base ^ low0 ^ low1;
+    }
+}
+
+// Q^L = sum over i, j in L of the pair values sq(q) (value (i, j), i >= j, at
+// q = i(i+1)/2 + j, the sum of both orders for i != j) for the lane's PPL
+// points pbits + i: the labels above LOGP contribute the same base to all of
+// them, the lowest LOGP labels their diagonal and their pairs with the base's
+// labels. Every lane reads the same q at a time (broadcast loads).
+template <int PPL, class Val>
+__device__ __forceinline__ void pair_form(const Val &sq, uint32_t k, uint32_t pbits,
+                                          uint64_t (&out)[PPL])
+{
+    constexpr uint32_t LOGP = PPL == 4 ? 2 : 1;
+    uint64_t base = 0, t0 = sq(0), t1 = 0, s01 = 0;
+    if constexpr (LOGP == 2) {
+        t1 = sq(2);   // (1, 1)
+        s01 = sq(1);  // (1, 0)
+    }
+    for (uint32_t i = LOGP; i < k; ++i) {
+        const uint32_t r = i * (i + 1) / 2;
+        uint64_t row = sq(r + i);
+        for (uint32_t j = LOGP; j < i; ++j)
+            if ((pbits >> j) & 1u) row ^= sq(r + j);
+        if ((pbits >> i) & 1u) {
+            base ^= row;
+            t0 ^= sq(r);
+            if constexpr (LOGP == 2) t1 ^= sq(r + 1);
+        }
+    }
+    out[0] = base;
+    out[1] = base ^ t0;
+    if constexpr (PPL == 4) {
+        out[2] = base ^ t1;
+        out[3] = base ^ t0 ^ t1 ^ s01;
     }
 }
 
@@ -221,13 +264,12 @@ __device__ __forceinline__ void last3_closed(const V2Params &p, uint32_t ent)
 // (ld.global.cg) instead of the non-coherent read-only path.
 // FROM_R2: window sum of layer 2 from its label-space prefix (layer 3):
 //   W^L = x_u^L x_s^L rho^L,  rho^L = sum_{j in L} (PR2[a1][j] ^ PR2[b1][j]).
-// XF (factored layer-3 state): 1 = layer 3 stores the head's running sum R^L
-// without its factor x_v^L x_s^L; 2 = the layer after it restores the factor
-// of each window it reads (the window's rows all lie in the tail u's segment,
-// so the factor is x_u^L x_s^L). The products are the same elements; only
-// where the multiplication happens moves (rows of layer 3 against the fewer
-// rows of layer 4 with a non-empty window).
-template <int PPL, bool FROM_Y, int OUT, bool COHERENT, bool FROM_R2 = false, int XF = 0>
+// PAIR (layer 4 after layer 3 in pair-label space, PR3 from third_pair_row):
+// the window sum is W^L = x_u^L x_s^L Q^L, Q^L = sum_{i,j in L} dQ_ij,
+// dQ = PR3[b3] ^ PR3[a3] (the window's rows all lie in the tail u's segment,
+// whose layer-3 rows share the factor x_u x_s); Q^L is evaluated per point
+// from the pair values by XORs (pair_form).
+template <int PPL, bool FROM_Y, int OUT, bool COHERENT, bool FROM_R2 = false, bool PAIR = false>
 __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uint32_t group)
 {
     constexpr int LOGP = PPL == 4 ? 2 : 1;
@@ -245,7 +287,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     for (int i = 0; i < PPL; ++i) valid[i] = gbase + (uint32_t)lane * PPL + i < p.npoints;
 
     uint64_t xs[PPL];
-    if constexpr (FROM_Y || (FROM_R2 && XF != 1) || XF == 2) {
+    if constexpr (FROM_Y || FROM_R2 || PAIR) {
         const uint64_t zs = (uint32_t)lane < k ? zval(p, source, lane) : 0ull;
         combine_labels<PPL>(zs, k, pbits, xs);
     }
@@ -260,7 +302,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
     uint32_t cur = p.head[it.x];
     uint64_t zv = 0;
     auto enter_head = [&](uint32_t v) {
-        if constexpr (FROM_Y || (FROM_R2 && XF != 1)) {
+        if constexpr (FROM_Y || FROM_R2) {
             zv = (uint32_t)lane < k ? zval(p, v, lane) : 0ull;
             uint64_t xv[PPL];
             combine_labels<PPL>(zv, k, pbits, xv);
@@ -287,7 +329,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         uint32_t m_src = 0;
         if (has) {
             m_coef = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u));
-            if constexpr (FROM_Y || FROM_R2 || XF == 2) m_src = p.src[ent];
+            if constexpr (FROM_Y || FROM_R2 || PAIR) m_src = p.src[ent];
         }
         if constexpr (!COHERENT) {
             if (base == it.x) pdl_enter();  // the previous layer's results are read from here on
@@ -339,8 +381,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) R[i] ^= rr_mul(xu[i], yrho[i]);
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i)
-                        acc[i] = valid[i] ? (XF == 1 ? R[i] : rr_mul(xvxs[i], R[i])) : 0ull;
+                    for (int i = 0; i < PPL; ++i) acc[i] = valid[i] ? rr_mul(xvxs[i], R[i]) : 0ull;
                 }
             } else {
               if (t % E == 0) {
@@ -352,7 +393,18 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
               if (a != b) {
                 uint64_t c[PPL], w[PPL];
                 combine_labels<PPL>(lab, k, pbits, c, (t % E) * k);
-                {
+                if constexpr (PAIR) {
+                    // the window's pair values: rows b and a of u's segment
+                    const uint32_t np = pair_count(k);
+                    const uint64_t *pa = p.pr3 + (size_t)a * np, *pb = p.pr3 + (size_t)b * np;
+                    pair_form<PPL>([&](uint32_t q) { return __ldg(pb + q) ^ __ldg(pa + q); }, k, pbits, w);
+                    const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
+                    const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
+                    uint64_t xu[PPL];
+                    combine_labels<PPL>(zu, k, pbits, xu);
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) w[i] = rr_mul_call(w[i], rr_mul_call(xu[i], xs[i]));
+                } else {
                     const uint64_t *pa = p.st_in + (size_t)a * p.chunk + col;
                     const uint64_t *pb = p.st_in + (size_t)b * p.chunk + col;
                     const ulonglong2 *va = reinterpret_cast<const ulonglong2 *>(pa);
@@ -368,15 +420,6 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                         const ulonglong2 b0 = COHERENT ? __ldcg(vb) : __ldg(vb);
                         w[0] = a0.x ^ b0.x; w[1] = a0.y ^ b0.y;
                     }
-                }
-                if constexpr (XF == 2) {
-                    // the window holds factored layer-3 rows of u's segment
-                    const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
-                    const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
-                    uint64_t xu[PPL];
-                    combine_labels<PPL>(zu, k, pbits, xu);
-#pragma unroll
-                    for (int i = 0; i < PPL; ++i) w[i] = rr_mul_call(w[i], rr_mul_call(xu[i], xs[i]));
                 }
 #pragma unroll
                 for (int i = 0; i < PPL; ++i)
@@ -470,6 +513,99 @@ __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t it
             if ((uint32_t)lane < k) {
                 acc ^= rr_mul(coef, zval(p, u, lane));
                 pr2[((size_t)base + t + 1) * k + lane] = acc;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Layer 3 in pair-label space (6 <= k <= 20): the layer-3 value of deep row e
+// (tail u, head v) at point L is x_v^L x_s^L x_u^L g_e^L with
+// g_e^L = sum_{i in L} y_{e,3} (PR2[b1][i] ^ PR2[a1][i]), so the prefix over
+// v's rows is x_v^L x_s^L Q^L, Q^L = sum_{i,j in L} Q_ij, with
+//   Q_ij = XOR over v's rows f <= e of z_{u_f,i} g_{f,j}.
+// PR3 stores Q symmetrised (pair_form): k(k+1)/2 values per row, independent
+// of the point chunk; the factor x_v x_s is applied by the next layer's reads.
+// Two passes: third_pair_rows writes every row's own term (rows in parallel),
+// pair_prefix_warp turns them into the running XOR along each head's rows.
+// ---------------------------------------------------------------------------
+// The (i, j), i >= j, of pair value q = i(i+1)/2 + j.
+__device__ __forceinline__ void pair_of(uint32_t q, uint32_t &i, uint32_t &j)
+{
+    i = (uint32_t)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    if ((i + 1) * (i + 2) / 2 <= q) ++i;  // exact integer correction of the estimate
+    if (i * (i + 1) / 2 > q) --i;
+    j = q - i * (i + 1) / 2;
+}
+
+// Row e (of the deep list's count rows) per warp: its own term
+// z_{u_e,i} g_{e,j} (+ z_{u_e,j} g_{e,i}) at PR3 row e + 1. A lane owns pair
+// values lane, lane+32, ...; label lanes i < k hold g_i and z_i.
+__device__ __forceinline__ void third_pair_row(const V2Params &p, uint32_t e, uint64_t *__restrict__ pr3)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = p.k;
+    const uint32_t np = pair_count(k);
+    const uint32_t a = p.ia[e], b = p.ib[e], u = p.src[e];
+    const uint64_t y = sm_draw(p.qd->key_y, (uint64_t)p.eid[e] * 32u + 2u);  // y_{e,3}
+    uint64_t z = 0;
+    if ((uint32_t)lane < k) z = zval(p, u, lane);
+    pdl_enter();  // the layer-2 prefix is read from here on
+    uint64_t g = 0;
+    if ((uint32_t)lane < k && a != b)
+        g = rr_mul(y, p.pr2[(size_t)a * k + lane] ^ p.pr2[(size_t)b * k + lane]);
+    uint64_t *row = pr3 + ((size_t)e + 1) * np;
+    for (uint32_t q0 = 0; q0 < np; q0 += 32) {  // warp-uniform
+        const uint32_t q = q0 + (uint32_t)lane;
+        uint32_t i = 0, j = 0;
+        if (q < np) pair_of(q, i, j);
+        const uint64_t gi = shfl64b(g, (int)i), gj = shfl64b(g, (int)j);
+        const uint64_t zi = shfl64b(z, (int)i), zj = shfl64b(z, (int)j);
+        if (q < np) row[q] = i == j ? rr_mul(zi, gi) : rr_mul(zi, gj) ^ rr_mul(zj, gi);
+    }
+}
+
+// The running XOR of the rows' terms along each head's rows of a scheduling
+// range (in place; ranges cut inside a head are joined by the carry fix-up).
+// One pass per 32 pair values; 8 rows' loads in flight at a time.
+__device__ __forceinline__ void pair_prefix_warp(const V2Params &p, uint32_t item,
+                                                 uint64_t *__restrict__ pr3)
+{
+    constexpr uint32_t R = 8;
+    const int lane = threadIdx.x & 31;
+    const uint2 it = p.items[item];
+    const uint32_t np = pair_count(p.k);
+    bool waited = false;
+    for (uint32_t q0 = 0; q0 < np; q0 += 32) {  // warp-uniform
+        const uint32_t q = q0 + (uint32_t)lane;
+        const bool qv = q < np;
+        uint64_t acc = 0;
+        uint32_t cur = p.head[it.x];
+        for (uint32_t base = it.x; base < it.y; base += 32) {
+            const uint32_t ent = base + lane;
+            const uint32_t m_head = ent < it.y ? p.head[ent] : 0u;
+            if (!waited) {
+                pdl_enter();  // the rows' terms are read from here on
+                waited = true;
+            }
+            const uint32_t nb = min(32u, it.y - base);
+            for (uint32_t t = 0; t < nb; t += R) {
+                uint64_t v[R];
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r)
+                    v[r] = (qv && t + r < nb) ? pr3[((size_t)base + t + r + 1) * np + q] : 0ull;
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r) {
+                    if (t + r < nb) {  // warp-uniform
+                        const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)(t + r));
+                        if (h != cur) {
+                            acc = 0;
+                            cur = h;
+                        }
+                        acc ^= v[r];
+                        if (qv) pr3[((size_t)base + t + r + 1) * np + q] = acc;
+                    }
+                }
             }
         }
     }

@@ -1,10 +1,10 @@
-"""GPU parity of the factored layer-3 state.
+"""GPU parity of layer 3 in pair-label space.
 
-With the factored form, layer 3 stores each head's running sum without the
-factor x_v x_s and layer 4 multiplies it back into every window it reads. The
-field products are the same, so witnesses, per-edge sums and arrival times
-must equal the oracle bit for bit with the form forced on, forced off, and as
-the graph's cost model picks it.
+Layer 3 stores per deep row the k(k+1)/2 values of a symmetric label-pair
+matrix (no sieve points) and layer 4 evaluates, per point, each window's
+quadratic form sum_{i,j in L} dQ_ij times x_u x_s. The field products are the
+same, so witnesses, per-edge sums and arrival times must equal the oracle bit
+for bit with the form forced on (from k = 6), forced off, and by default.
 """
 import numpy as np
 import pytest
@@ -15,7 +15,8 @@ from paper_2010_08423_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-MODES = [capi.FLAG_FACTOR_L3_ON, capi.FLAG_FACTOR_L3_OFF, 0]
+MODES = [0, capi.FLAG_PAIR_ON, capi.FLAG_PAIR_OFF]
+MIN_K = {0: 9, capi.FLAG_PAIR_ON: 6, capi.FLAG_PAIR_OFF: 21}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,9 +31,7 @@ def _lib():
 def test_witness_all_k_plain_and_motif(flags):
     g = W.uniform(1500, 24_000, 30, 0, 6, 606, ncolors=3)
     with capi.Graph(g, flags) as G:
-        info = G.info()
-        if flags:
-            assert info["factored_layer3"] == (1 if flags == capi.FLAG_FACTOR_L3_ON else 0)
+        assert G.info()["pair_layer3_min_k"] == MIN_K[flags]
         for s, k, seed in ((0, 5, 1), (3, 6, 2), (9, 7, 3), (4, 8, 4), (2, 10, 5)):
             _, w = G.reach(s, k, seed)
             assert np.array_equal(w, oracle.sieve(g, s, k, seed)), (s, k)
@@ -41,7 +40,16 @@ def test_witness_all_k_plain_and_motif(flags):
             assert np.array_equal(w, oracle.sieve(g, s, k, seed, motif=motif)), (s, k, motif)
 
 
-@pytest.mark.parametrize("flags", MODES[:2])
+@pytest.mark.parametrize("flags", MODES)
+def test_larger_k_on_a_small_dense_graph(flags):
+    g = W.uniform(200, 4_000, 12, 0, 5, 616)
+    with capi.Graph(g, flags) as G:
+        for s, k in ((1, 11), (2, 12), (3, 13)):
+            _, w = G.reach(s, k, 70 + k)
+            assert np.array_equal(w, oracle.sieve(g, s, k, 70 + k)), (s, k)
+
+
+@pytest.mark.parametrize("flags", MODES)
 def test_per_edge_sums_and_arrivals(flags):
     g = W.uniform(1200, 16_000, 25, 0, 5, 707)
     with capi.Graph(g, flags) as G:
@@ -52,12 +60,12 @@ def test_per_edge_sums_and_arrivals(flags):
             assert np.array_equal(R, oracle.arrival_times(g, E_ref))
 
 
-@pytest.mark.parametrize("flags", MODES[:2])
+@pytest.mark.parametrize("flags", MODES)
 def test_cut_hub_segments_and_both_point_widths(flags):
     from test_gpu_parity import _hub_graph
     g = _hub_graph(seed=11)
     with capi.Graph(g, flags) as G:
-        for s, k in ((3, 6), (0, 7)):
+        for s, k in ((3, 6), (0, 7), (5, 8)):
             want = oracle.sieve(g, s, k, 90 + k)
             for ppl, chunk in ((2, 64), (4, 128)):
                 capi.rr_set_tuning(G.handle, k, ppl, chunk)
@@ -65,8 +73,8 @@ def test_cut_hub_segments_and_both_point_widths(flags):
                 assert np.array_equal(w, want), (s, k, ppl, chunk)
 
 
-def test_flags_on_and_off_together_are_rejected():
+def test_pair_on_and_off_together_are_rejected():
     g = W.tiny_random(5, n=6, m=10, tau=3, dmax=2)
     with pytest.raises(capi.RRError) as ei:
-        capi.Graph(g, capi.FLAG_FACTOR_L3_ON | capi.FLAG_FACTOR_L3_OFF)
+        capi.Graph(g, capi.FLAG_PAIR_ON | capi.FLAG_PAIR_OFF)
     assert ei.value.status == capi.RR_EINVAL
