@@ -21,6 +21,11 @@
 //    V or 0), and layer k-1 needs one multiplication per stored value instead
 //    of one per sieve point.
 // 6. k = 2 and k = 3 in closed form (a 2x2 / 3x3 permanent per edge).
+// 7. Layer 3 in pair-label space (9 <= k <= 20 by default): the sum in 3. is
+//    (x_v x_s)^L times the quadratic form sum_{i,j in L} Q_ij of the label
+//    pair matrix Q = XOR over v's rows of z_{u_e} (x) (y rho_e), so layer 3
+//    keeps k(k+1)/2 values per deep row, independent of the point chunk, and
+//    layer 4 evaluates the form of each window (times x_u x_s) per point.
 // Only the order of summation changes; every result is bit-identical to the
 // per-point engine and the oracle. One query's launch sequence is captured
 // once per shape as a CUDA graph and its kernels use programmatic dependent
