@@ -60,12 +60,39 @@ def env_rank():
 KERNEL_SOURCES = ("rr_device.cuh", "rr_v2_device.cuh", "rr_sieve2.cu", "rr_graph.cu", "rr_internal.h")
 
 
+def code_tokens(text: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed: two
+    files with equal code_tokens compile to the same kernels."""
+    import re
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":  # string or character literal, kept whole
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return re.sub(r"\s+", " ", "".join(out)).strip()
+
+
 def kernel_sources_sha1() -> str:
+    """Fingerprint of the code (not the comments) of the engine's kernel sources."""
     import hashlib
     h = hashlib.sha1()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2010_08423_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2010_08423_gb300", "csrc", name), encoding="utf-8") as fh:
+            h.update(code_tokens(fh.read()).encode())
     return h.hexdigest()
 
 
