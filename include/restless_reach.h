@@ -94,6 +94,8 @@ typedef struct {
     uint64_t deep_head_runs;       /* head runs over the deep rows' scheduling ranges */
     int pair_layer3_min_k;         /* smallest k whose layer 3 runs in pair-label
                                       space (21: none; see rr_graph_load's flags) */
+    uint32_t deep_max_range_rows;  /* rows of the longest deep-row scheduling range (at
+                                      most 4: the pair rows are built in one launch) */
 } rr_graph_info;
 
 /* ---- graph ----------------------------------------------------------------

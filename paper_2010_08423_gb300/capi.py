@@ -42,7 +42,8 @@ class rr_graph_info(ctypes.Structure):
                 ("compact", ctypes.c_int), ("producer_window_rows", ctypes.c_uint64),
                 ("state_compute_rows", ctypes.c_uint64), ("tail_rows", ctypes.c_uint64),
                 ("deep_compute_rows", ctypes.c_uint64), ("deep_tail_rows", ctypes.c_uint64),
-                ("deep_head_runs", ctypes.c_uint64), ("pair_layer3_min_k", ctypes.c_int)]
+                ("deep_head_runs", ctypes.c_uint64), ("pair_layer3_min_k", ctypes.c_int),
+                ("deep_max_range_rows", ctypes.c_uint32)]
 
 
 class rr_kernel_times(ctypes.Structure):

@@ -148,6 +148,7 @@ rr_status rr_graph_get_info(const rr_graph *g, rr_graph_info *out)
     out->deep_tail_rows = g->tail3_list.count;
     out->deep_head_runs = g->deep_head_runs;
     out->pair_layer3_min_k = g->pair_force == 2 ? 6 : (g->pair_force == 1 ? 21 : (int)kPairMinK);
+    out->deep_max_range_rows = g->deep_max_item;
     return RR_OK;
 }
 

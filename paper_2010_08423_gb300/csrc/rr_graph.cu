@@ -519,6 +519,9 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
             for (const uint2 &it : items)
                 for (uint32_t r = it.x; r < it.y; ++r) runs += r == it.x || heads[r] != heads[r - 1];
             g.deep_head_runs = runs;
+            uint32_t longest = 0;
+            for (const uint2 &it : items) longest = std::max(longest, it.y - it.x);
+            g.deep_max_item = longest;
         }
         RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));
         RR_CUDA(R.items_coarse.reserve(std::max<size_t>(1, coarse.size()) * sizeof(uint2)));

@@ -222,6 +222,8 @@ struct FanOut {
 // flags choose (rr_sieve2.cu): from k = 9 it was faster on every graph
 // measured (uniform n = 1e5 and Chung-Lu n = 2e5, 1e6), at k = 8 level or slower.
 constexpr uint32_t kPairMinK = 9;
+// Deep-row ranges of at most this many rows build the pair rows in one launch.
+constexpr uint32_t kPairFusedMaxRows = 4;
 
 struct Graph {
     uint32_t n = 0;
@@ -235,6 +237,7 @@ struct Graph {
     uint64_t state_compute_rows = 0;    // state rows whose window holds a state row
     uint64_t deep_compute_rows = 0;     // deep rows whose window holds a deep row
     uint64_t deep_head_runs = 0;        // head runs over the deep list's fine ranges
+    uint32_t deep_max_item = 0;         // rows of the deep list's longest fine range
     // layer 3 in pair-label space (6 <= k <= 20): 0 = by k (k >= kPairMinK),
     // 1 = forced off, 2 = forced on (load flags)
     uint32_t pair_force = 0;

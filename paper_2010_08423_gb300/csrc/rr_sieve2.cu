@@ -170,6 +170,14 @@ __global__ void __launch_bounds__(kW2 * 32) k_third_pair(const V2Params p, uint3
     third_pair_row(p, e, pr3);
 }
 
+__global__ void __launch_bounds__(kW2 * 32) k_third_pair_fused(const V2Params p, uint64_t *__restrict__ pr3)
+{
+    // pdl_enter() inside third_pair_fused, after the graph- and query-only loads
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems) return;
+    third_pair_fused(p, task, pr3);
+}
+
 __global__ void __launch_bounds__(kW2 * 32) k_pair_prefix(const V2Params p, uint64_t *__restrict__ pr3)
 {
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
@@ -454,12 +462,19 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         if (vp.nitems) {
             const uint32_t count = (uint32_t)g.deep_list.count;
             const int tslot = timing_begin(st);
-            RR_CUDA(launch_pdl(k_third_pair, dim3(blocks_for(count)), dim3(kW2 * 32), st, vp, count, pr3));
-            RR_LAUNCHED();
-            RR_CUDA(launch_pdl(k_pair_prefix, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, pr3));
-            RR_LAUNCHED();
+            if (g.deep_max_item <= kPairFusedMaxRows) {
+                // short ranges only: both passes in one launch
+                RR_CUDA(launch_pdl(k_third_pair_fused, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, pr3));
+                RR_LAUNCHED();
+                nk += 1;
+            } else {
+                RR_CUDA(launch_pdl(k_third_pair, dim3(blocks_for(count)), dim3(kW2 * 32), st, vp, count, pr3));
+                RR_LAUNCHED();
+                RR_CUDA(launch_pdl(k_pair_prefix, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp, pr3));
+                RR_LAUNCHED();
+                nk += 2;
+            }
             timing_end(tslot, kTimeThird, st);
-            nk += 2;
             rr_status fs = launch_fixup(g.deep_list, pr3, pair_count(k), st, &nk);
             if (fs != RR_OK) return fs;
         }

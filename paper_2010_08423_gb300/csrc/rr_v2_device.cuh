@@ -565,6 +565,64 @@ __device__ __forceinline__ void third_pair_row(const V2Params &p, uint32_t e, ui
     }
 }
 
+// Both passes in one for a graph whose deep-row ranges are all short (a few
+// rows): one warp per range, the running XOR kept in registers (lane owns pair
+// values lane + 32 sl). Saves a launch where the launches dominate.
+constexpr int kPairSlots = 7;  // ceil(kMaxPairs / 32)
+
+__device__ __forceinline__ void third_pair_fused(const V2Params &p, uint32_t item,
+                                                 uint64_t *__restrict__ pr3)
+{
+    const int lane = threadIdx.x & 31;
+    const uint2 it = p.items[item];
+    const uint32_t k = p.k;
+    const uint32_t np = pair_count(k);
+    const uint64_t key_y = p.qd->key_y;
+    uint32_t pi[kPairSlots], pj[kPairSlots];
+    uint64_t acc[kPairSlots];
+#pragma unroll
+    for (int sl = 0; sl < kPairSlots; ++sl) {
+        const uint32_t q = (uint32_t)lane + 32u * sl;
+        uint32_t i = 0, j = 0;
+        if (q < np) pair_of(q, i, j);
+        pi[sl] = i;
+        pj[sl] = j;
+        acc[sl] = 0;
+    }
+    uint32_t cur = p.head[it.x];
+    bool waited = false;
+    for (uint32_t e = it.x; e < it.y; ++e) {
+        const uint32_t h = p.head[e];
+        const uint32_t a = p.ia[e], b = p.ib[e], u = p.src[e];
+        const uint64_t y = sm_draw(key_y, (uint64_t)p.eid[e] * 32u + 2u);  // y_{e,3}
+        uint64_t z = 0;
+        if ((uint32_t)lane < k) z = zval(p, u, lane);
+        if (!waited) {
+            pdl_enter();  // the layer-2 prefix is read from here on
+            waited = true;
+        }
+        if (h != cur) {
+#pragma unroll
+            for (int sl = 0; sl < kPairSlots; ++sl) acc[sl] = 0;
+            cur = h;
+        }
+        uint64_t g = 0;
+        if ((uint32_t)lane < k && a != b)
+            g = rr_mul(y, p.pr2[(size_t)a * k + lane] ^ p.pr2[(size_t)b * k + lane]);
+        uint64_t *row = pr3 + ((size_t)e + 1) * np;
+#pragma unroll
+        for (int sl = 0; sl < kPairSlots; ++sl) {
+            if (32u * sl >= np) break;  // warp-uniform
+            const uint64_t gi = shfl64b(g, (int)pi[sl]), gj = shfl64b(g, (int)pj[sl]);
+            const uint64_t zi = shfl64b(z, (int)pi[sl]), zj = shfl64b(z, (int)pj[sl]);
+            if ((uint32_t)lane + 32u * sl < np) {
+                acc[sl] ^= pi[sl] == pj[sl] ? rr_mul(zi, gi) : rr_mul(zi, gj) ^ rr_mul(zj, gi);
+                row[lane + 32 * sl] = acc[sl];
+            }
+        }
+    }
+}
+
 // The running XOR of the rows' terms along each head's rows of a scheduling
 // range (in place; ranges cut inside a head are joined by the carry fix-up).
 // One pass per 32 pair values; 8 rows' loads in flight at a time.

@@ -73,6 +73,20 @@ def test_cut_hub_segments_and_both_point_widths(flags):
                 assert np.array_equal(w, want), (s, k, ppl, chunk)
 
 
+def test_both_pair_row_builders_on_a_sparse_graph():
+    """A graph whose deep-row ranges are all short builds the pair rows in one
+    launch (fused); the others (hub and uniform graphs above) in two."""
+    g = W.uniform(3000, 12_000, 60, 0, 8, 626)
+    with capi.Graph(g, capi.FLAG_PAIR_ON) as G:
+        assert G.info()["deep_max_range_rows"] <= 4
+        for s, k in ((0, 6), (1, 8), (2, 10)):
+            _, w = G.reach(s, k, 50 + k)
+            assert np.array_equal(w, oracle.sieve(g, s, k, 50 + k)), (s, k)
+    from test_gpu_parity import _hub_graph
+    with capi.Graph(_hub_graph(seed=11)) as G:
+        assert G.info()["deep_max_range_rows"] > 4
+
+
 def test_pair_on_and_off_together_are_rejected():
     g = W.tiny_random(5, n=6, m=10, tau=3, dmax=2)
     with pytest.raises(capi.RRError) as ei:
