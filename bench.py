@@ -358,14 +358,22 @@ def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, zt
     # layers >= 4 read two state rows per window and multiply once per point
     mid = (D * c * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k))
     third = None
+    table = bool(info.get("head_table")) and pmode == 1
+    HD = info.get("deep_heads", 0)
+    nchunks = max(1, (1 << k) // c)
     if pmode:
-        # layer 3 in pair-label space, once per query: 2k label-space values in,
-        # k(k+1)/2 pair values out per deep row; k + k^2 products per row
-        third = (D * (NP * 8 + 2 * k * 8 + 20), D * (k + k * k))
+        # per query: layer 3 in pair-label space (2k label-space values in,
+        # k(k+1)/2 pair values out per deep row; k + k^2 products per row) and,
+        # with the head table, x_h x_s for every deep-row head and point of
+        # every chunk; the same timing kind, so per launch = per query / launches
+        third = (D * (NP * 8 + 2 * k * 8 + 20) + (HD * c * 8 * nchunks if table else 0),
+                 D * (k + k * k) + (HD * c * nchunks if table else 0))
     if pmode == 1:
-        # layer 4 reads 2 NP pair values per window and multiplies three times
-        # per point (by x_u, by x_s, by c)
-        l4 = (D * c * 8 + 2 * DC * NP * 8 + D * 20, DC * (3 * c + k))
+        # layer 4 reads 2 NP pair values per window and multiplies per point by
+        # c and by x_u x_s (from the head table: 8 more bytes per point; else
+        # formed here: one more product)
+        l4 = ((D * c * 8 + 2 * DC * NP * 8 + D * 20 + DC * c * 8, DC * (2 * c + k)) if table else
+              (D * c * 8 + 2 * DC * NP * 8 + D * 20, DC * (3 * c + k)))
         mids = [l4] + [mid] * (k - 7) if k >= 7 else []
         tail = ((D * rstride * 8 + 2 * DC * NP * 8 + D * 20, DC * (3 * c + k)) if k == 6 else
                 (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
@@ -389,7 +397,9 @@ def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, zt
         "ztable": (n * k * 8, ztable_mults),
     }
     if third is not None:
-        alg["third_layer"] = third
+        per_query = kt.get("third_layer", (0, 0))[1] / queries
+        if per_query:
+            alg["third_layer"] = (third[0] / per_query, third[1] / per_query)
     out = {}
     for name, (kms, kn) in kt.items():
         if not kn or name not in alg:

@@ -96,6 +96,9 @@ typedef struct {
                                       space (21: none; see rr_graph_load's flags) */
     uint32_t deep_max_range_rows;  /* rows of the longest deep-row scheduling range (at
                                       most 4: the pair rows are built in one launch) */
+    uint32_t deep_heads;           /* distinct heads of the deep rows */
+    int head_table;                /* 1: layer 4 of the pair form reads x_u x_s from a
+                                      per-chunk table of those heads */
 } rr_graph_info;
 
 /* ---- graph ----------------------------------------------------------------
@@ -110,8 +113,10 @@ typedef struct {
  * matrix Q, independent of the sieve points, and layer 4 evaluates
  * x_u^L x_s^L sum_{i,j in L} dQ_ij over each window; queries with 9 <= k <=
  * 20 use it. Bit 1 set = use it from k = 6, bit 2 set = never (layer 3 per
- * point from the label-space prefix); both set is RR_EINVAL. Results are
- * bit-identical in either form.
+ * point from the label-space prefix). Layer 4 takes x_u x_s from a per-chunk
+ * table of the deep rows' heads when they number at most half the deep rows
+ * with a non-empty window; bit 3 / bit 4 set = always / never. Both bits of a
+ * pair set is RR_EINVAL. Results are bit-identical in every form.
  * Errors: RR_EINVAL for n == 0, m >= 2^31, an endpoint >= n or a self-loop;
  * RR_ENOMEM / RR_ECUDA on device failure (nothing is leaked). */
 rr_status rr_graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,

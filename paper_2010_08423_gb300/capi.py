@@ -21,6 +21,8 @@ STATUS_NAMES = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_EAGAIN",
 FLAG_DENSE_STATE = 1
 FLAG_PAIR_ON = 2
 FLAG_PAIR_OFF = 4
+FLAG_HEAD_TABLE_ON = 8
+FLAG_HEAD_TABLE_OFF = 16
 
 
 class RRError(RuntimeError):
@@ -43,7 +45,8 @@ class rr_graph_info(ctypes.Structure):
                 ("state_compute_rows", ctypes.c_uint64), ("tail_rows", ctypes.c_uint64),
                 ("deep_compute_rows", ctypes.c_uint64), ("deep_tail_rows", ctypes.c_uint64),
                 ("deep_head_runs", ctypes.c_uint64), ("pair_layer3_min_k", ctypes.c_int),
-                ("deep_max_range_rows", ctypes.c_uint32)]
+                ("deep_max_range_rows", ctypes.c_uint32), ("deep_heads", ctypes.c_uint32),
+                ("head_table", ctypes.c_int)]
 
 
 class rr_kernel_times(ctypes.Structure):

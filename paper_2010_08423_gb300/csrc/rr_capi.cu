@@ -149,6 +149,9 @@ rr_status rr_graph_get_info(const rr_graph *g, rr_graph_info *out)
     out->deep_head_runs = g->deep_head_runs;
     out->pair_layer3_min_k = g->pair_force == 2 ? 6 : (g->pair_force == 1 ? 21 : (int)kPairMinK);
     out->deep_max_range_rows = g->deep_max_item;
+    out->deep_heads = g->deep_list.nheads;
+    out->head_table = g->head_table_force ? (g->head_table_force == 2 ? 1 : 0)
+                                          : (2ull * g->deep_list.nheads <= g->deep_compute_rows ? 1 : 0);
     return RR_OK;
 }
 

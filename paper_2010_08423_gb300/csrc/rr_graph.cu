@@ -522,6 +522,26 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
             uint32_t longest = 0;
             for (const uint2 &it : items) longest = std::max(longest, it.y - it.x);
             g.deep_max_item = longest;
+            // distinct heads (rows are grouped by head, heads ascending) and the
+            // rank among them of every entry's tail
+            std::vector<uint32_t> dh;
+            for (size_t r = 0; r < heads.size(); ++r)
+                if (r == 0 || heads[r] != heads[r - 1]) dh.push_back(heads[r]);
+            std::vector<uint32_t> tails(R.count), trank(R.count);
+            if (R.count)
+                RR_CUDA(cudaMemcpyAsync(tails.data(), R.src.p, R.count * 4, cudaMemcpyDeviceToHost, st));
+            RR_CUDA(cudaStreamSynchronize(st));
+            for (size_t r = 0; r < tails.size(); ++r) {
+                auto f = std::lower_bound(dh.begin(), dh.end(), tails[r]);
+                trank[r] = (f != dh.end() && *f == tails[r]) ? (uint32_t)(f - dh.begin()) : UINT32_MAX;
+            }
+            R.nheads = (uint32_t)dh.size();
+            RR_CUDA(R.heads.reserve(std::max<size_t>(1, dh.size()) * 4));
+            RR_CUDA(R.trank.reserve(std::max<size_t>(1, trank.size()) * 4));
+            if (!dh.empty())
+                RR_CUDA(cudaMemcpyAsync(R.heads.p, dh.data(), dh.size() * 4, cudaMemcpyHostToDevice, st));
+            if (!trank.empty())
+                RR_CUDA(cudaMemcpyAsync(R.trank.p, trank.data(), trank.size() * 4, cudaMemcpyHostToDevice, st));
         }
         RR_CUDA(R.items.reserve(std::max<size_t>(1, items.size()) * sizeof(uint2)));
         RR_CUDA(R.items_coarse.reserve(std::max<size_t>(1, coarse.size()) * sizeof(uint2)));
@@ -562,6 +582,8 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     g->compact = !(flags & 1u);
     if ((flags & 6u) == 6u) return fail(RR_EINVAL, "rr_graph_load: flags turn the pair-label layer 3 both on and off");
     g->pair_force = (flags & 2u) ? 2u : ((flags & 4u) ? 1u : 0u);
+    if ((flags & 24u) == 24u) return fail(RR_EINVAL, "rr_graph_load: flags turn the head-factor table both on and off");
+    g->head_table_force = (flags & 8u) ? 2u : ((flags & 16u) ? 1u : 0u);
     RR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     cudaStream_t st = g->stream;
 

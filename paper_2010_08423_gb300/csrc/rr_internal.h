@@ -158,10 +158,16 @@ struct RowList {
     uint32_t nchains = 0;
     DevBuf fix2;            // uint2 (chain, first row slot) of every phase-2 fix-up task
     uint32_t nfix2 = 0;
+    // deep list only: the distinct heads of its rows (in row order) and, per
+    // entry, the rank there of its tail u (the head of the rows its window
+    // covers; UINT32_MAX when u heads none)
+    DevBuf heads, trank;
+    uint32_t nheads = 0;
     size_t bytes() const
     {
         return head.bytes + eid.bytes + src.bytes + a0.bytes + b0.bytes + a1.bytes + b1.bytes +
-               a3.bytes + b3.bytes + items.bytes + items_coarse.bytes + chains.bytes + fix2.bytes;
+               a3.bytes + b3.bytes + items.bytes + items_coarse.bytes + chains.bytes + fix2.bytes +
+               heads.bytes + trank.bytes;
     }
 };
 
@@ -241,6 +247,9 @@ struct Graph {
     // layer 3 in pair-label space (6 <= k <= 20): 0 = by k (k >= kPairMinK),
     // 1 = forced off, 2 = forced on (load flags)
     uint32_t pair_force = 0;
+    // layer 4 of the pair form takes x_u x_s from a per-chunk table of the
+    // deep rows' heads (0 = when heads <= compute rows / 2, 1 = never, 2 = always)
+    uint32_t head_table_force = 0;
     uint32_t max_in_degree = 0;
 
     DevBuf off;      // n+1 uint32

@@ -178,6 +178,16 @@ __global__ void __launch_bounds__(kW2 * 32) k_third_pair_fused(const V2Params p,
     third_pair_fused(p, task, pr3);
 }
 
+template <int PPL>
+__global__ void __launch_bounds__(kW2 * 32) k_head_factor(const V2Params p)
+{
+    // pdl_enter() inside head_factor_warp, before its stores
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.ndheads * p.ngroups) return;
+    const uint32_t r = task / p.ngroups;
+    head_factor_warp<PPL>(p, r, task - r * p.ngroups);
+}
+
 __global__ void __launch_bounds__(kW2 * 32) k_pair_prefix(const V2Params p, uint64_t *__restrict__ pr3)
 {
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
@@ -226,6 +236,7 @@ static void set_list(V2Params &vp, const RowList &L, int win)
     vp.ib = win == 0 ? L.b0.as<uint32_t>() : (win == 1 ? L.b1.as<uint32_t>() : L.b3.as<uint32_t>());
     vp.items = L.items.as<uint2>();
     vp.nitems = L.nitems;
+    vp.trank = L.trank.as<uint32_t>();  // deep list only (else unused)
 }
 
 // src: 0 = window sums from the per-point state, 1 = from the scalar layer-1
@@ -278,8 +289,18 @@ static bool pair_layer3(const Graph &g, uint32_t k)
     return g.pair_force ? g.pair_force == 2 : k >= kPairMinK;
 }
 
+// Layer 4 of the pair form reads x_u x_s from a per-chunk table of the deep
+// rows' heads (one product per head and point) instead of forming it for every
+// row with a non-empty window: when there are at most half as many heads.
+static bool head_table(const Graph &g)
+{
+    if (g.head_table_force) return g.head_table_force == 2;
+    return 2ull * g.deep_list.nheads <= g.deep_compute_rows;
+}
+
 static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
-                      uint64_t *pr2_w, uint64_t *pr3_w, uint64_t *full_w, uint64_t *red_w)
+                      uint64_t *pr2_w, uint64_t *pr3_w, uint64_t *tx_w, uint64_t *full_w,
+                      uint64_t *red_w)
 {
     const uint64_t srows = g.state_list.count + 1;  // layer 2 (label space; k = 4 transformed)
     const uint64_t drows = g.deep_list.count + 1;   // layers >= 3
@@ -287,15 +308,16 @@ static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, 
     *py_w = k >= 3 ? (g.prod_list.count + 1 + 31) / 32 * 32 : 0;
     *pr2_w = k >= 5 ? (srows * k + 31) / 32 * 32 : 0;
     *pr3_w = pair_layer3(g, k) ? (drows * pair_count(k) + 31) / 32 * 32 : 0;
+    *tx_w = pair_layer3(g, k) && head_table(g) ? (uint64_t)std::max<uint32_t>(1, g.deep_list.nheads) * chunk : 0;
     *full_w = k >= 4 ? drows * chunk : 0;
     *red_w = k >= 4 ? std::max(srows, drows) * v2_reduced_stride(ppl, chunk) : 0;
 }
 
 uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
 {
-    uint64_t py_w, pr2_w, pr3_w, full_w, red_w;
-    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &full_w, &red_w);
-    return (py_w + pr2_w + pr3_w + 2 * full_w + red_w) * 8ull + 4096;
+    uint64_t py_w, pr2_w, pr3_w, tx_w, full_w, red_w;
+    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &tx_w, &full_w, &red_w);
+    return (py_w + pr2_w + pr3_w + tx_w + 2 * full_w + red_w) * 8ull + 4096;
 }
 
 // z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades); rows
@@ -365,13 +387,14 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         ~PdlScope() { t_pdl = saved; }
     } pdl_scope(pdl);
     uint64_t nk = 0;
-    uint64_t py_w, pr2_w, pr3_w, full_w, red_w;
-    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &full_w, &red_w);
+    uint64_t py_w, pr2_w, pr3_w, tx_w, full_w, red_w;
+    v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &tx_w, &full_w, &red_w);
     const bool pair = pair_layer3(g, k);
     uint64_t *py = d_scratch;
     uint64_t *pr2 = py + py_w;
     uint64_t *pr3 = pr2 + pr2_w;
-    uint64_t *full0 = pr3 + pr3_w;
+    uint64_t *tx = pr3 + pr3_w;
+    uint64_t *full0 = tx + tx_w;
     uint64_t *full1 = full0 + full_w;
     uint64_t *red = full1 + full_w;
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
@@ -480,6 +503,9 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         }
     }
     vp.pr3 = pr3;
+    vp.tx = tx_w ? tx : nullptr;
+    vp.dheads = g.deep_list.heads.as<uint32_t>();
+    vp.ndheads = g.deep_list.nheads;
 
     if (k == 3 && g.win_list.count) {
         // last layer in closed form (no sieve points)
@@ -506,6 +532,18 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             const int out = (l == k - 2) ? 1 : 0;
             // layer 2 (k = 4) runs over the state rows; layers >= 3 over the deep rows,
             // layer 3 reading the label-space prefix at state-row indices
+            if (src == 3 && vp.tx && vp.ndheads) {
+                // this chunk's x_h x_s table for the heads of the deep rows
+                const uint64_t tasks = (uint64_t)vp.ndheads * vp.ngroups;
+                const int tslot = timing_begin(st);
+                if (ppl == 4)
+                    RR_CUDA(launch_pdl(k_head_factor<4>, dim3(blocks_for(tasks)), dim3(kW2 * 32), st, vp));
+                else
+                    RR_CUDA(launch_pdl(k_head_factor<2>, dim3(blocks_for(tasks)), dim3(kW2 * 32), st, vp));
+                timing_end(tslot, kTimeThird, st);
+                RR_LAUNCHED();
+                ++nk;
+            }
             if (src == 1) set_list(vp, g.state_list, 0);
             else set_list(vp, g.deep_list, src == 2 ? 1 : 3);
             vp.layer = l;

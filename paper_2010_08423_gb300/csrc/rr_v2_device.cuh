@@ -58,6 +58,10 @@ struct V2Params {
     const uint64_t *py;     // scalar layer-1 prefix, indexed by producer rank
     const uint64_t *pr2;    // layer-2 label-space prefix, k values per state row
     const uint64_t *pr3;    // layer-3 pair-label prefix, pair_count(k) values per deep row
+    const uint32_t *trank;  // per entry: rank of its tail among the deep rows' heads
+    const uint32_t *dheads; // the deep rows' distinct heads
+    uint32_t ndheads;
+    uint64_t *tx;           // x_h^L x_s^L per deep-row head h (rank order) and point, stride chunk
     const uint64_t *st_in;  // full state, stride chunk
     uint64_t *st_out;       // full (stride chunk) or reduced (stride ngroups*(lg+1))
 };
@@ -154,6 +158,30 @@ __device__ __forceinline__ void pair_form(const Val &sq, uint32_t k, uint32_t pb
         out[2] = base ^ t1;
         out[3] = base ^ t0 ^ t1 ^ s01;
     }
+}
+
+// x_h^L x_s^L for deep-row head rank r and the lane's PPL points of point
+// group `group` of the chunk: the factor layer 4 applies to pair windows of
+// h's rows (one table per chunk, one product per head and point).
+template <int PPL>
+__device__ __forceinline__ void head_factor_warp(const V2Params &p, uint32_t r, uint32_t group)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = p.k;
+    const uint32_t col = group * (32u * PPL) + (uint32_t)lane * PPL;
+    const uint32_t pbits = p.chunk_base + col;  // the lane's first point
+    const uint32_t h = p.dheads[r];
+    const uint64_t zs = (uint32_t)lane < k ? zval(p, p.qd->source, lane) : 0ull;
+    const uint64_t zh = (uint32_t)lane < k ? zval(p, h, lane) : 0ull;
+    uint64_t xs[PPL], xh[PPL], f[PPL];
+    combine_labels<PPL>(zs, k, pbits, xs);
+    combine_labels<PPL>(zh, k, pbits, xh);
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) f[i] = rr_mul(xh[i], xs[i]);
+    pdl_enter();  // the table is written from here on
+    ulonglong2 *pt = reinterpret_cast<ulonglong2 *>(p.tx + (size_t)r * p.chunk + col);
+    pt[0] = make_ulonglong2(f[0], f[1]);
+    if constexpr (PPL == 4) pt[1] = make_ulonglong2(f[2], f[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -329,7 +357,8 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         uint32_t m_src = 0;
         if (has) {
             m_coef = sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u));
-            if constexpr (FROM_Y || FROM_R2 || PAIR) m_src = p.src[ent];
+            if constexpr (FROM_Y || FROM_R2) m_src = p.src[ent];
+            if constexpr (PAIR) m_src = p.tx ? p.trank[ent] : p.src[ent];  // head rank or vertex
         }
         if constexpr (!COHERENT) {
             if (base == it.x) pdl_enter();  // the previous layer's results are read from here on
@@ -398,12 +427,30 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     const uint32_t np = pair_count(k);
                     const uint64_t *pa = p.pr3 + (size_t)a * np, *pb = p.pr3 + (size_t)b * np;
                     pair_form<PPL>([&](uint32_t q) { return __ldg(pb + q) ^ __ldg(pa + q); }, k, pbits, w);
-                    const uint32_t u = __shfl_sync(0xffffffffu, m_src, (int)t);
-                    const uint64_t zu = (uint32_t)lane < k ? zval(p, u, lane) : 0ull;
-                    uint64_t xu[PPL];
-                    combine_labels<PPL>(zu, k, pbits, xu);
+                    // times x_u^L x_s^L: from the chunk's head-factor table, or
+                    // formed here (u = the tail, m_src its vertex or head rank)
+                    const uint32_t ut = __shfl_sync(0xffffffffu, m_src, (int)t);
+                    if (p.tx) {
+                        const ulonglong2 *pt =
+                            reinterpret_cast<const ulonglong2 *>(p.tx + (size_t)ut * p.chunk + col);
+                        uint64_t f[PPL];
+                        const ulonglong2 f0 = __ldg(pt);
+                        f[0] = f0.x;
+                        f[1] = f0.y;
+                        if constexpr (PPL == 4) {
+                            const ulonglong2 f1 = __ldg(pt + 1);
+                            f[2] = f1.x;
+                            f[3] = f1.y;
+                        }
 #pragma unroll
-                    for (int i = 0; i < PPL; ++i) w[i] = rr_mul_call(w[i], rr_mul_call(xu[i], xs[i]));
+                        for (int i = 0; i < PPL; ++i) w[i] = rr_mul_call(w[i], f[i]);
+                    } else {
+                        const uint64_t zu = (uint32_t)lane < k ? zval(p, ut, lane) : 0ull;
+                        uint64_t xu[PPL];
+                        combine_labels<PPL>(zu, k, pbits, xu);
+#pragma unroll
+                        for (int i = 0; i < PPL; ++i) w[i] = rr_mul_call(w[i], rr_mul_call(xu[i], xs[i]));
+                    }
                 } else {
                     const uint64_t *pa = p.st_in + (size_t)a * p.chunk + col;
                     const uint64_t *pb = p.st_in + (size_t)b * p.chunk + col;

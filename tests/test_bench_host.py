@@ -36,7 +36,7 @@ INFO = {"producer_window_rows": 11444, "state_compute_rows": 1322, "deep_compute
 
 @pytest.mark.parametrize("k,min_k", [(8, 9), (10, 9), (10, 21), (12, 6)])
 def test_mid_layer_multiply_counts_per_layer3_form(k, min_k):
-    info = dict(INFO, pair_layer3_min_k=min_k)
+    info = dict(INFO, pair_layer3_min_k=min_k, head_table=0, deep_heads=1300)
     c, D, DC, H = 256, 1322, 156, 1305
     kt = {"mid_layer": (1.0, k - 5 - (1 if min_k <= k else 0)), "third_layer": (1.0, 1)}
     out = bench.kernel_rooflines(info, k, c, 2, 100000, kt, 1, 6000.0, 1e11)

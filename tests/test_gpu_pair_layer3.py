@@ -87,8 +87,24 @@ def test_both_pair_row_builders_on_a_sparse_graph():
         assert G.info()["deep_max_range_rows"] > 4
 
 
+@pytest.mark.parametrize("table", [capi.FLAG_HEAD_TABLE_ON, capi.FLAG_HEAD_TABLE_OFF])
+def test_head_factor_table_on_and_off(table):
+    from test_gpu_parity import _hub_graph
+    for g, cases in ((W.uniform(1500, 24_000, 30, 0, 6, 636, ncolors=3), ((0, 7), (5, 10))),
+                     (_hub_graph(seed=13), ((3, 6), (0, 9)))):
+        with capi.Graph(g, capi.FLAG_PAIR_ON | table) as G:
+            assert G.info()["head_table"] == (1 if table == capi.FLAG_HEAD_TABLE_ON else 0)
+            for s, k in cases:
+                _, w = G.reach(s, k, 30 + k)
+                assert np.array_equal(w, oracle.sieve(g, s, k, 30 + k)), (s, k)
+                motif = [int(g["color"][s])] + [(j + k) % 3 for j in range(k - 1)]
+                _, w = G.reach(s, k, 30 + k, motif=motif)
+                assert np.array_equal(w, oracle.sieve(g, s, k, 30 + k, motif=motif)), (s, k)
+
+
 def test_pair_on_and_off_together_are_rejected():
     g = W.tiny_random(5, n=6, m=10, tau=3, dmax=2)
-    with pytest.raises(capi.RRError) as ei:
-        capi.Graph(g, capi.FLAG_PAIR_ON | capi.FLAG_PAIR_OFF)
-    assert ei.value.status == capi.RR_EINVAL
+    for fl in (capi.FLAG_PAIR_ON | capi.FLAG_PAIR_OFF, capi.FLAG_HEAD_TABLE_ON | capi.FLAG_HEAD_TABLE_OFF):
+        with pytest.raises(capi.RRError) as ei:
+            capi.Graph(g, fl)
+        assert ei.value.status == capi.RR_EINVAL
