@@ -102,6 +102,47 @@ def test_head_factor_table_on_and_off(table):
                 assert np.array_equal(w, oracle.sieve(g, s, k, 30 + k, motif=motif)), (s, k)
 
 
+@pytest.mark.parametrize("table", [capi.FLAG_HEAD_TABLE_ON, capi.FLAG_HEAD_TABLE_OFF])
+def test_deleted_vertices_extraction_and_separators(table):
+    """The pair form with z rows of deleted vertices (extraction steps) and
+    separators: paths equal the oracle's extraction, witnesses its sieve."""
+    import torch
+    g = W.uniform(600, 6_000, 15, 0, 4, 85, ncolors=3)
+    n, s = g["n"], 3
+    with capi.Graph(g, capi.FLAG_PAIR_ON | table) as G:
+        for k in (6, 7):
+            _, _, _, _, arrive = oracle.dfs_paths(g, s, k, with_edges=True)
+            targets = [int(v) for v in np.nonzero(arrive != oracle.NO_ARRIVAL)[0][:3]]
+            assert targets
+            for target in targets:
+                assert G.extract_path(s, k, 7, target) == tuple(oracle.extract_path(g, s, k, 7, target))
+        rng = np.random.default_rng(87)
+        seps = np.zeros(n, np.uint8)
+        seps[rng.choice(n, size=60, replace=False)] = 1
+        seps[s] = 0
+        d_w = torch.zeros(n, dtype=torch.int64, device="cuda")
+        d_s = torch.from_numpy(seps).cuda()
+        for k in (6, 8):
+            capi.rr_reach_sources_device(G.handle, [s], k, 23, d_w, None, d_s)
+            torch.cuda.synchronize()
+            ref = oracle.sieve(g, 0, k, 23, sources=[s], deleted=seps)
+            assert np.array_equal(d_w.cpu().numpy().view(np.uint64), ref), k
+
+
+def test_atmost_lanes_in_the_pair_form():
+    import torch
+    g = W.uniform(1500, 20_000, 20, 0, 5, 66)
+    n, k = g["n"], 8
+    with capi.Graph(g, capi.FLAG_PAIR_ON) as G:
+        d_w = torch.zeros((k - 1, n), dtype=torch.int64, device="cuda")
+        d_bm = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        capi.rr_reach_atmost_device(G.handle, 3, k, 99, d_w, d_bm)
+        torch.cuda.synchronize()
+        w = d_w.cpu().numpy().view(np.uint64)
+        for kk in range(2, k + 1):
+            assert np.array_equal(w[kk - 2], oracle.sieve(g, 3, kk, 99)), kk
+
+
 def test_pair_on_and_off_together_are_rejected():
     g = W.tiny_random(5, n=6, m=10, tau=3, dmax=2)
     for fl in (capi.FLAG_PAIR_ON | capi.FLAG_PAIR_OFF, capi.FLAG_HEAD_TABLE_ON | capi.FLAG_HEAD_TABLE_OFF):
