@@ -116,7 +116,11 @@ typedef struct {
  * point from the label-space prefix). Layer 4 takes x_u x_s from a per-chunk
  * table of the deep rows' heads when they number at most half the deep rows
  * with a non-empty window; bit 3 / bit 4 set = always / never. Both bits of a
- * pair set is RR_EINVAL. Results are bit-identical in every form.
+ * pair set is RR_EINVAL. Results are bit-identical in every form. The pair
+ * rows ((deep rows + 1) * k(k+1)/2 words) and the head table (heads * chunk
+ * words) are part of a query's scratch and, unlike the per-point state, do not
+ * shrink with the point chunk: a server whose per-slot budget cannot hold them
+ * for its largest k refuses to start (RR_ENOMEM); bit 2 avoids that.
  * Errors: RR_EINVAL for n == 0, m >= 2^31, an endpoint >= n or a self-loop;
  * RR_ENOMEM / RR_ECUDA on device failure (nothing is leaked). */
 rr_status rr_graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
