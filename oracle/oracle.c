@@ -18,7 +18,8 @@
  *                                      "algo:restlessmotifreach",
  *   - exhaustive temporal DFS:         Sec. "Baselines" (exhaustive search).
  * No blocking, prefix sums, chunking or factoring: windows are scanned
- * linearly, sieve points one at a time, layers one at a time.
+ * linearly (each vertex's in-edges in time order, from the first one inside
+ * the window to the last), sieve points one at a time, layers one at a time.
  *
  * Readings of the paper that this file fixes (the paper is silent or garbled):
  *   - field: GF(2)[x]/(x^64+x^4+x^3+x+1) (the paper uses b = 64 but names no
@@ -205,37 +206,88 @@ static int orc_continues(uint32_t tf, uint32_t te, uint32_t delta_u)
     return d >= 0 && d <= (int64_t)delta_u;
 }
 
-/* in-edge lists: for each vertex, the input indices of edges ending there, in
- * input order (plain adjacency lists; no sorting is needed by the oracle). */
+/* in-edge lists: for each vertex, the input indices of edges ending there,
+ * ordered by (time, input index), so that the edges a walk may have arrived
+ * by before leaving u at time te (Eq. (1)'s j in {0..delta(u)}: arrival times
+ * te - delta(u) .. te) are one run of u's list. */
 typedef struct {
     uint64_t *start; /* n+1 */
     uint64_t *edge;  /* m   */
+    uint32_t *time;  /* m: time[q] = t[edge[q]] */
 } orc_inlists;
 
-static int orc_build_inlists(uint32_t n, uint64_t m, const uint32_t *dst, orc_inlists *L)
+static int orc_cmp_u64(const void *a, const void *b)
+{
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static int orc_build_inlists(uint32_t n, uint64_t m, const uint32_t *dst, const uint32_t *t,
+                             orc_inlists *L)
 {
     L->start = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
     L->edge = (uint64_t *)malloc((size_t)(m ? m : 1) * sizeof(uint64_t));
-    if (!L->start || !L->edge)
+    L->time = (uint32_t *)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
+    uint64_t *fill = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    if (!L->start || !L->edge || !L->time || !fill) {
+        free(fill);
         return 1;
+    }
     for (uint64_t e = 0; e < m; ++e)
         L->start[dst[e] + 1]++;
     for (uint32_t v = 0; v < n; ++v)
         L->start[v + 1] += L->start[v];
-    uint64_t *fill = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
-    if (!fill)
-        return 1;
     memcpy(fill, L->start, ((size_t)n + 1) * sizeof(uint64_t));
+    /* key (time, input index) per edge, then each list sorted by key */
     for (uint64_t e = 0; e < m; ++e)
-        L->edge[fill[dst[e]]++] = e;
+        L->edge[fill[dst[e]]++] = ((uint64_t)t[e] << 32) | e;
     free(fill);
+    for (uint32_t v = 0; v < n; ++v)
+        qsort(L->edge + L->start[v], (size_t)(L->start[v + 1] - L->start[v]), sizeof(uint64_t),
+              orc_cmp_u64);
+    for (uint64_t q = 0; q < m; ++q) {
+        L->time[q] = (uint32_t)(L->edge[q] >> 32);
+        L->edge[q] &= 0xFFFFFFFFULL;
+    }
     return 0;
+}
+
+/* Position of the first edge of u's list that arrives at time >= tmin. */
+static uint64_t orc_first_at_or_after(const orc_inlists *IN, uint32_t u, int64_t tmin)
+{
+    uint64_t lo = IN->start[u], hi = IN->start[u + 1];
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if ((int64_t)IN->time[mid] < tmin)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+/* Eq. (1)'s window sum for an edge leaving u at time te: the XOR of prev[f]
+ * over u's in-edges f with t_f <= te <= t_f + delta(u). In u's time-ordered
+ * list these follow the first edge arriving at te - delta(u) or later, and end
+ * at the first edge the walk cannot continue from (one arriving after te). */
+static uint64_t orc_window_sum(const orc_inlists *IN, uint32_t u, uint32_t te, uint32_t delta_u,
+                               const uint64_t *prev)
+{
+    uint64_t w = 0;
+    for (uint64_t q = orc_first_at_or_after(IN, u, (int64_t)te - (int64_t)delta_u);
+         q < IN->start[u + 1]; ++q) {
+        if (!orc_continues(IN->time[q], te, delta_u))
+            break;
+        w ^= prev[IN->edge[q]];
+    }
+    return w;
 }
 
 static void orc_free_inlists(orc_inlists *L)
 {
     free(L->start);
     free(L->edge);
+    free(L->time);
 }
 
 /*
@@ -254,9 +306,12 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
                           const uint32_t *t, const uint32_t *delta, const orc_inlists *IN,
                           uint32_t s, uint32_t k, uint64_t seed, const uint64_t *z,
                           uint32_t mask, uint64_t *x, uint64_t *prev, uint64_t *cur,
-                          uint64_t *out, uint64_t *eout, const uint8_t *sources)
+                          uint64_t *out, uint64_t *eout, const uint8_t *sources, int par)
 {
-    for (uint64_t u = 0; u < n; ++u) {
+    /* par != 0: the loops over vertices and edges are shared by the threads
+     * (each iteration writes only its own element) */
+#pragma omp parallel for if (par) schedule(static)
+    for (int64_t u = 0; u < (int64_t)n; ++u) {
         uint64_t acc = 0;
         for (uint32_t j = 1; j <= k; ++j)
             if ((mask >> (j - 1)) & 1U)
@@ -264,7 +319,8 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
         x[u] = acc;
     }
     /* layer 1 */
-    for (uint64_t e = 0; e < m; ++e) {
+#pragma omp parallel for if (par) schedule(static)
+    for (int64_t e = 0; e < (int64_t)m; ++e) {
         if (sources) {
             /* a set of sources: every edge leaving one of them starts a walk */
             prev[e] = sources[src[e]]
@@ -279,15 +335,12 @@ static void orc_one_point(uint32_t n, uint64_t m, const uint32_t *src, const uin
     }
     /* layers 2..k-1 */
     for (uint32_t l = 2; l <= k - 1; ++l) {
-        for (uint64_t e = 0; e < m; ++e) {
+#pragma omp parallel for if (par) schedule(dynamic, 4096)
+        for (int64_t e = 0; e < (int64_t)m; ++e) {
             uint32_t u = src[e];
-            uint64_t w = 0;
-            for (uint64_t q = IN->start[u]; q < IN->start[u + 1]; ++q) {
-                uint64_t f = IN->edge[q];
-                if (orc_continues(t[f], t[e], delta[u]))
-                    w ^= prev[f];
-            }
-            cur[e] = orc_gf_mul(orc_gf_mul(orc_y(seed, e, l), x[dst[e]]), w);
+            uint64_t w = orc_window_sum(IN, u, t[e], delta[u], prev);
+            /* a zero window sum makes the product zero */
+            cur[e] = w ? orc_gf_mul(orc_gf_mul(orc_y(seed, e, l), x[dst[e]]), w) : 0;
         }
         uint64_t *tmp = prev;
         prev = cur;
@@ -336,7 +389,7 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
               const uint32_t *masks, uint32_t nmasks, uint64_t *S, uint64_t *per_mask,
               uint64_t *E, const uint8_t *deleted, const uint8_t *sources, int nthreads)
 {
-    if (k < 2 || k > 20 || s >= n)
+    if (k < 2 || k > 20 || s >= n || m >= (1ULL << 32))
         return 1;
     for (uint64_t e = 0; e < m; ++e)
         if (src[e] >= n || dst[e] >= n || src[e] == dst[e])
@@ -355,7 +408,7 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                 for (uint32_t j = 0; j < k; ++j)
                     z[u * k + j] = 0;
     orc_inlists IN;
-    if (orc_build_inlists(n, m, dst, &IN)) {
+    if (orc_build_inlists(n, m, dst, t, &IN)) {
         free(z);
         return 2;
     }
@@ -363,12 +416,43 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
     if (E)
         memset(E, 0, (size_t)m * sizeof(uint64_t));
     int fail = 0;
+    int threads = 1;
 #ifdef _OPENMP
     if (nthreads > 0)
         omp_set_num_threads(nthreads);
+    threads = omp_get_max_threads();
 #else
     (void)nthreads;
 #endif
+    if ((int64_t)npts < threads) {
+        /* fewer points than threads: one point at a time, the threads sharing
+         * each layer's edges */
+        uint64_t *x = (uint64_t *)malloc((size_t)n * sizeof(uint64_t) + 8);
+        uint64_t *prev = (uint64_t *)malloc((size_t)m * sizeof(uint64_t) + 8);
+        uint64_t *cur = (uint64_t *)malloc((size_t)m * sizeof(uint64_t) + 8);
+        uint64_t *one = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+        if (!x || !prev || !cur || !one) {
+            fail = 1;
+        } else {
+            for (uint64_t p = 0; p < npts; ++p) {
+                uint32_t mask = masks ? masks[p] : (uint32_t)p;
+                memset(one, 0, (size_t)n * sizeof(uint64_t));
+                orc_one_point(n, m, src, dst, t, delta, &IN, s, k, seed, z, mask, x, prev, cur,
+                              one, E, sources, 1);
+                for (uint32_t v = 0; v < n; ++v)
+                    S[v] ^= one[v];
+                if (per_mask)
+                    memcpy(per_mask + (size_t)p * n, one, (size_t)n * sizeof(uint64_t));
+            }
+        }
+        free(x);
+        free(prev);
+        free(cur);
+        free(one);
+        orc_free_inlists(&IN);
+        free(z);
+        return fail ? 2 : 0;
+    }
 #pragma omp parallel
     {
         uint64_t *x = (uint64_t *)malloc((size_t)n * sizeof(uint64_t) + 8);
@@ -386,7 +470,7 @@ int orc_sieve(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                 uint32_t mask = masks ? masks[p] : (uint32_t)p;
                 memset(one, 0, (size_t)n * sizeof(uint64_t));
                 orc_one_point(n, m, src, dst, t, delta, &IN, s, k, seed, z, mask, x, prev,
-                              cur, one, eacc, sources);
+                              cur, one, eacc, sources, 0);
                 for (uint32_t v = 0; v < n; ++v)
                     acc[v] ^= one[v];
                 if (per_mask)

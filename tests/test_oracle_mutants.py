@@ -25,12 +25,16 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 MUTANTS = {
     "window end exclusive": ("return d >= 0 && d <= (int64_t)delta_u;",
                              "return d >= 0 && d < (int64_t)delta_u;"),
-    "delta of the head": ("if (orc_continues(t[f], t[e], delta[u]))",
-                          "if (orc_continues(t[f], t[e], delta[dst[e]]))"),
+    "delta of the head": ("uint64_t w = orc_window_sum(IN, u, t[e], delta[u], prev);",
+                          "uint64_t w = orc_window_sum(IN, u, t[e], delta[dst[e]], prev);"),
+    "window start one late": ("orc_first_at_or_after(IN, u, (int64_t)te - (int64_t)delta_u)",
+                              "orc_first_at_or_after(IN, u, (int64_t)te - (int64_t)delta_u + 1)"),
+    "window start search skips equal times": ("if ((int64_t)IN->time[mid] < tmin)",
+                                              "if ((int64_t)IN->time[mid] <= tmin)"),
     "time order reversed": ("int64_t d = (int64_t)te - (int64_t)tf;",
                             "int64_t d = (int64_t)tf - (int64_t)te;"),
-    "y dropped at layers >= 2": ("cur[e] = orc_gf_mul(orc_gf_mul(orc_y(seed, e, l), x[dst[e]]), w);",
-                                 "cur[e] = orc_gf_mul(x[dst[e]], w);"),
+    "y dropped at layers >= 2": ("cur[e] = w ? orc_gf_mul(orc_gf_mul(orc_y(seed, e, l), x[dst[e]]), w) : 0;",
+                                 "cur[e] = w ? orc_gf_mul(x[dst[e]], w) : 0;"),
     "x_s dropped at layer 1": ("prev[e] = orc_gf_mul(orc_gf_mul(orc_y(seed, e, 1), x[s]), x[dst[e]]);",
                                "prev[e] = orc_gf_mul(orc_y(seed, e, 1), x[dst[e]]);"),
     "source not enforced": ("if (src[e] == s)\n            prev[e]",
