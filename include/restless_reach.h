@@ -148,6 +148,22 @@ rr_status rr_reach_sync(const rr_graph *g, const rr_query *q, uint8_t *bitmap,
 rr_status rr_reach_device(const rr_graph *g, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, void *stream);
 
+/* rr_reach_range_device: the part of rr_reach_device's witness that the sieve
+ * points L = first .. first+count-1 contribute (Eq. (2): the polynomial is a
+ * sum over L of independent evaluations, and Algorithm 1 sums its per-vertex
+ * values over L, so the parts of disjoint ranges XOR to the full witness):
+ *   d_witness[v] = sum_{L in [first, first+count)} sum_{e: v_e = v} P_{k-1}^L[e]
+ * (n uint64, device, required; overwritten). This is how one query is split
+ * across GPUs or processes: each evaluates its range on its own copy of the
+ * graph and the parts are XOR-combined (an all-gather, then a local XOR).
+ * first must be a multiple of 128 and first + count <= 2^k; count == 0 writes
+ * zeros (first then only needs first <= 2^k). For k <= 3 the library sums all points at once in closed form, so
+ * count must be 0 or 2^k there. No bitmap: reachability needs the full sum.
+ * Same engine, scratch, stream ordering and errors as rr_reach_device;
+ * RR_EINVAL for a misaligned or out-of-range part. */
+rr_status rr_reach_range_device(const rr_graph *g, const rr_query *q, uint32_t first,
+                                uint32_t count, uint64_t *d_witness, void *stream);
+
 /* rr_reach_device_noalloc: the computation of rr_reach_device for callers that
  * must not allocate device memory while they serve queries -- a process whose
  * device memory is already owned by another allocator's pool, or a

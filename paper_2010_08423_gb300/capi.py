@@ -67,7 +67,7 @@ EXPORTED = [
     "rr_debug_gf_mul", "rr_debug_draw", "rr_last_error", "rr_kernel_launches",
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
     "rr_reach_arrival_device", "rr_extract_path", "rr_reach_sources_device", "rr_bench_gf_mul",
-    "rr_debug_wait_probe", "rr_reach_bounded_device",
+    "rr_debug_wait_probe", "rr_reach_bounded_device", "rr_reach_range_device",
 ]
 
 _lib = None
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
         "rr_reach_sync": [vp, pq, vp, vp],
         "rr_reach_device": [vp, pq, vp, vp, vp],
         "rr_reach_device_noalloc": [vp, pq, vp, vp, vp],
+        "rr_reach_range_device": [vp, pq, u32, u32, vp, vp],
         "rr_reach_batch_device": [vp, pq, u32, vp, vp, vp, vp],
         "rr_reach_atmost_device": [vp, u32, u32, u64, vp, vp, vp],
         "rr_reach_bounded_device": [vp, u32, u32, u64, vp, vp, vp, vp],
@@ -210,6 +211,15 @@ def rr_reach_device(g, source, k, seed, d_witness, d_bitmap=None, stream=None, m
     q, keep = make_query(source, k, seed, motif)
     _check(load().rr_reach_device(g, ctypes.byref(q), _dp(d_bitmap), _dp(d_witness),
                                   _dp(stream)))
+    del keep
+
+
+def rr_reach_range_device(g, source, k, seed, first, count, d_witness, stream=None, motif=None):
+    """The witness part of sieve points [first, first + count) (first a
+    multiple of 128); parts of disjoint ranges XOR to the full witness."""
+    q, keep = make_query(source, k, seed, motif)
+    _check(load().rr_reach_range_device(g, ctypes.byref(q), int(first), int(count),
+                                        _dp(d_witness), _dp(stream)))
     del keep
 
 
@@ -448,6 +458,17 @@ class Graph:
 
     def extract_path(self, source, k, seed, target, motif=None):
         return rr_extract_path(self.handle, source, k, seed, target, motif)
+
+    def reach_range(self, source, k, seed, first, count, motif=None):
+        """Witness part of sieve points [first, first + count) on the current
+        CUDA device, returned as a host uint64 array."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        d_w = torch.empty(self.n, dtype=torch.int64, device=dev)
+        st = torch.cuda.current_stream(dev)
+        rr_reach_range_device(self.handle, source, k, seed, first, count, d_w, st.cuda_stream, motif)
+        st.synchronize()
+        return d_w.cpu().numpy().view(np.uint64)
 
     def point_sums(self, source, k, seed, masks, motif=None):
         return rr_debug_point_sums(self.handle, self.n, source, k, seed, masks, motif)

@@ -187,6 +187,37 @@ rr_status rr_reach_device(const rr_graph *g, const rr_query *q, uint8_t *d_bitma
     return reach_on_stream(*g, g->ws, q, d_bitmap, d_witness, 0, (cudaStream_t)stream);
 }
 
+rr_status rr_reach_range_device(const rr_graph *g, const rr_query *q, uint32_t first,
+                                uint32_t count, uint64_t *d_witness, void *stream)
+{
+    clear_error();
+    if (!g || !q) return fail(RR_EINVAL, "rr_reach_range_device: NULL graph or query");
+    if (!d_witness) return fail(RR_EINVAL, "rr_reach_range_device: d_witness is required");
+    rr_status s = validate_query(*g, q);
+    if (s != RR_OK) return s;
+    const uint64_t npts = 1ull << q->k;
+    if (count != 0 && first % kRangeAlign)
+        return fail(RR_EINVAL, "rr_reach_range_device: first must be a multiple of " +
+                                   std::to_string(kRangeAlign));
+    if ((uint64_t)first + count > npts)
+        return fail(RR_EINVAL, "rr_reach_range_device: first + count exceeds 2^k = " +
+                                   std::to_string(npts));
+    if (q->k <= 3 && count != 0 && count != npts)
+        return fail(RR_EINVAL, "rr_reach_range_device: k <= 3 sums every point in closed form; "
+                               "count must be 0 or 2^k");
+    std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, (cudaStream_t)stream);
+    if (count == 0) {
+        RR_CUDA(cudaMemsetAsync(d_witness, 0, (size_t)g->n * 8, (cudaStream_t)stream));
+        return RR_OK;
+    }
+    PointRange range;
+    range.first = first;
+    range.end = first + count;
+    return reach_on_stream(*g, g->ws, q, nullptr, d_witness, 0, (cudaStream_t)stream, nullptr,
+                           nullptr, nullptr, range);
+}
+
 rr_status rr_reach_batch_device(const rr_graph *g, const rr_query *qs, uint32_t nq,
                                 uint8_t *d_bitmaps, uint64_t *d_witness, int32_t *d_status,
                                 void *stream)

@@ -97,7 +97,8 @@ struct Workspace {
     DevBuf pick;    // 8: the extraction step's choice
     DevBuf srcmask; // n: a set of sources (rr_reach_sources_device)
     cudaStream_t capture = nullptr;           // stream used only to capture graphs
-    std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs;
+    // captured launch sequences keyed by (query shape, sieve-point range)
+    std::vector<std::pair<std::pair<uint64_t, uint64_t>, cudaGraphExec_t>> graphs;
     std::vector<uint64_t> graph_kernels;      // kernel nodes per cached graph
     void *graph_state = nullptr;              // state.p the graphs were captured with
     void *graph_z = nullptr;
@@ -304,6 +305,17 @@ struct Graph {
 };
 
 // -------- query plan -------------------------------------------------------
+// Sieve points [first, end) of a query (end == 0: all 2^k points). The
+// per-vertex sums are XOR-linear in the points (Eq. (2) sums over L), so the
+// sums of disjoint ranges XOR to the full query's. first is a multiple of
+// kRangeAlign (every lane group of the kernels starts on such a multiple).
+constexpr uint32_t kRangeAlign = 128;
+struct PointRange {
+    uint32_t first = 0, end = 0;
+    bool full(uint32_t k) const { return first == 0 && (end == 0 || end == (1u << k)); }
+    uint32_t stop(uint32_t k) const { return end ? end : (1u << k); }
+};
+
 struct QueryKeys {
     uint64_t key_y, key_z, key_gamma, key_omega;
 };
@@ -337,7 +349,7 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
                            uint64_t *d_state, uint32_t ppl, uint32_t chunk, uint64_t *d_S,
                            const uint32_t *d_masks, uint32_t nmasks, uint64_t *d_debug_out,
                            cudaStream_t st, uint64_t *d_E = nullptr,
-                           const uint8_t *d_srcmask = nullptr);
+                           const uint8_t *d_srcmask = nullptr, PointRange range = PointRange());
 // Runs one query on `st` with scratch `ws`; d_witness (n) required. `budget`
 // bounds the state buffers (0 = 60% of free device memory). d_E (m, zeroed by
 // the caller, or null) gets for every input edge the sum over all sieve points
@@ -345,10 +357,12 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
 // d_vmask (n flags, device, or null) deletes vertices: their z rows are zero,
 // so no walk through them contributes. d_srcmask (n flags, device, or null)
 // starts walks at every flagged vertex instead of q->source.
+// range: the sieve points to sum (default all; a part needs k >= 4 and gives
+// no bitmap).
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st,
                           uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr,
-                          const uint8_t *d_srcmask = nullptr);
+                          const uint8_t *d_srcmask = nullptr, PointRange range = PointRange());
 // Bytes of scratch one query of size k needs with the shape chosen for budget.
 uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
 
@@ -370,10 +384,11 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels,
-                           bool pdl = true);
+                           bool pdl = true, PointRange range = PointRange());
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                    uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st,
-                   uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr);
+                   uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr,
+                   PointRange range = PointRange());
 
 // Held (under the graph's lock) by every call that uses the graph's scratch:
 // the call's stream first waits for the previous such call's work, and the

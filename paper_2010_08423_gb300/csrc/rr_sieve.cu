@@ -394,12 +394,18 @@ static rr_status launch_layer_ppl(const LayerParams &lp, int mode, bool masklist
 rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_z,
                            uint64_t *d_state, uint32_t ppl, uint32_t chunk, uint64_t *d_S,
                            const uint32_t *d_masks, uint32_t nmasks, uint64_t *d_debug_out,
-                           cudaStream_t st, uint64_t *d_E, const uint8_t *d_srcmask)
+                           cudaStream_t st, uint64_t *d_E, const uint8_t *d_srcmask,
+                           PointRange range)
 {
     const uint32_t k = q->k;
     const bool masklist = d_masks != nullptr;
-    const uint64_t npoints = masklist ? nmasks : (1ull << k);
-    const uint64_t nchunks = (npoints + chunk - 1) / chunk;
+    if (masklist) range = PointRange();
+    if (range.first % kRangeAlign || range.first > range.stop(k) || range.stop(k) > (1u << k))
+        return fail(RR_EINVAL, "bad sieve-point range");
+    // points [first, npoints): all 2^k, a range of them, or the mask list's entries
+    const uint64_t first = range.first;
+    const uint64_t npoints = masklist ? nmasks : range.stop(k);
+    const uint64_t nchunks = (npoints - first + chunk - 1) / chunk;
     uint64_t *buf[2] = {d_state, d_state + (size_t)g.state_rows * chunk};
     // state row 0 is the zero row of both buffers (never written by a layer)
     RR_CUDA(cudaMemsetAsync(buf[0], 0, (size_t)chunk * 8, st));
@@ -428,7 +434,7 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
     lp.masks = d_masks;
     lp.dbg_out = d_debug_out;
     for (uint64_t c = 0; c < nchunks; ++c) {
-        lp.chunk_base = (uint32_t)(c * chunk);
+        lp.chunk_base = (uint32_t)(first + c * chunk);
         for (uint32_t l = 1; l <= k - 1; ++l) {
             lp.layer = l;
             // layer l reads buf[(l-1)&1] (written by layer l-1) and writes buf[l&1]
@@ -478,11 +484,13 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget)
 
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st, uint64_t *d_E,
-                          const uint8_t *d_vmask, const uint8_t *d_srcmask)
+                          const uint8_t *d_vmask, const uint8_t *d_srcmask, PointRange range)
 {
     rr_status vs = validate_query(g, q);
     if (vs != RR_OK) return vs;
     const uint32_t k = q->k;
+    if (!range.full(k) && (k <= 3 || d_bitmap))
+        return fail(RR_EINVAL, "a part of the sieve points needs k >= 4 and gives no bitmap");
     // a set of sources runs on the per-point engine (the reduced-state engine
     // factors x_s out of layer 1); its shape is never cached per k
     const bool v2 = uses_v2(g, k) && !d_srcmask;
@@ -515,7 +523,7 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk, k)
                                 : 2ull * g.state_rows * chunk * 8ull));
     RR_CUDA(ws.z.reserve((size_t)g.n * k * 8));
-    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st, d_E, d_vmask);
+    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st, d_E, d_vmask, range);
     const QueryKeys keys = make_keys(q->seed);
     const uint32_t *d_shades = nullptr;
     if (q->motif) {
@@ -530,7 +538,7 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     if (s != RR_OK) return s;
     RR_CUDA(cudaMemsetAsync(d_witness, 0, (size_t)g.n * 8, st));
     s = run_query_layers(g, q, ws.z.as<uint64_t>(), ws.state.as<uint64_t>(), ppl, chunk, d_witness,
-                         nullptr, 0, nullptr, st, d_E, d_srcmask);
+                         nullptr, 0, nullptr, st, d_E, d_srcmask, range);
     if (s != RR_OK) return s;
     if (d_bitmap) return launch_bitmap(d_witness, g.n, d_bitmap, st);
     return RR_OK;

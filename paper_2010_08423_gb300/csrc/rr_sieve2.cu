@@ -379,8 +379,13 @@ static unsigned grid_cap(uint64_t count, unsigned block)
 
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
-                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels, bool pdl)
+                           const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels, bool pdl,
+                           PointRange range)
 {
+    // k <= 3 sums all points in closed form: only the whole range exists there
+    if (k <= 3 && !range.full(k)) return fail(RR_EINVAL, "a part of the sieve points needs k >= 4");
+    if (range.first % kRangeAlign || range.first > range.stop(k) || range.stop(k) > (1u << k))
+        return fail(RR_EINVAL, "bad sieve-point range");
     struct PdlScope {
         bool saved;
         explicit PdlScope(bool on) : saved(t_pdl) { t_pdl = on; }
@@ -427,7 +432,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     vp.k = k;
     vp.chunk = chunk;
     vp.ngroups = chunk / (32u * ppl);
-    vp.npoints = 1u << k;
+    // points at or past the range's end are masked off in every per-point layer
+    vp.npoints = range.stop(k);
 
     if (k == 2) {
         // the only layer, in closed form
@@ -518,9 +524,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         RR_LAUNCHED();
         ++nk;
     }
-    const uint64_t nchunks = k == 3 ? 0 : ((1ull << k) + chunk - 1) / chunk;
+    const uint64_t npts = range.stop(k) - range.first;
+    const uint64_t nchunks = k == 3 ? 0 : (npts + chunk - 1) / chunk;
     for (uint64_t c = 0; c < nchunks; ++c) {
-        vp.chunk_base = (uint32_t)(c * chunk);
+        vp.chunk_base = range.first + (uint32_t)(c * chunk);
         rr_status s = RR_OK;
         // layers 2 (k = 4) or 3 (k >= 5) .. k-2; the last of them writes the
         // transformed state
@@ -594,7 +601,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
 // can be timed.
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                    uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st, uint64_t *d_E,
-                   const uint8_t *d_vmask)
+                   const uint8_t *d_vmask, PointRange range)
 {
     const uint32_t k = q->k;
     RR_CUDA(ws.desc.reserve(sizeof(QueryDesc)));
@@ -634,7 +641,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     const bool bitmap = d_bitmap != nullptr;
     if (g_timing.load(std::memory_order_relaxed)) {
         rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
-                                       ws.state.as<uint64_t>(), dd, st, nullptr, ws.pdl);
+                                       ws.state.as<uint64_t>(), dd, st, nullptr, ws.pdl, range);
         RR_CUDA(cudaEventRecord(ws.ring_ev[slot], st));
         return s;
     }
@@ -643,8 +650,10 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
         ws.graph_state = ws.state.p;
         ws.graph_z = ws.z.p;
     }
-    const uint64_t key = (uint64_t)k | ((uint64_t)ppl << 8) | ((uint64_t)chunk << 16) |
-                         ((uint64_t)table << 40) | ((uint64_t)bitmap << 41);
+    const std::pair<uint64_t, uint64_t> key(
+        (uint64_t)k | ((uint64_t)ppl << 8) | ((uint64_t)chunk << 16) | ((uint64_t)table << 40) |
+            ((uint64_t)bitmap << 41),
+        (uint64_t)range.first | ((uint64_t)range.stop(k) << 32));
     cudaGraphExec_t exec = nullptr;
     uint64_t nkern = 0;
     for (size_t i = 0; i < ws.graphs.size(); ++i)
@@ -656,7 +665,8 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
         if (!ws.capture) RR_CUDA(cudaStreamCreateWithFlags(&ws.capture, cudaStreamNonBlocking));
         RR_CUDA(cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeThreadLocal));
         rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
-                                       ws.state.as<uint64_t>(), dd, ws.capture, &nkern, ws.pdl);
+                                       ws.state.as<uint64_t>(), dd, ws.capture, &nkern, ws.pdl,
+                                       range);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(ws.capture, &graph);
         if (s != RR_OK) {

@@ -110,9 +110,10 @@ def motif_powerlaw(seed_index: int = 3) -> dict:
                     GRAPH_SEED_BASE + seed_index, ncolors=8, bursts=(50, 20))
 
 
-def served_powerlaw(seed_index: int = 5) -> dict:
-    """Chung-Lu exponent 2.3, n=1e7, m=1e8, t ~ U[1,1e5], delta ~ U{10..200}."""
-    return chung_lu(10_000_000, 100_000_000, 2.3, 100_000, 10, 200,
+def served_powerlaw(seed_index: int = 5, scale: int = 1) -> dict:
+    """Chung-Lu exponent 2.3, n=1e7, m=1e8, t ~ U[1,1e5], delta ~ U{10..200};
+    scale > 1 divides n and m by it (same generator, seed and time ranges)."""
+    return chung_lu(10_000_000 // scale, 100_000_000 // scale, 2.3, 100_000, 10, 200,
                     GRAPH_SEED_BASE + seed_index)
 
 

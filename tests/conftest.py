@@ -59,3 +59,25 @@ def read_fixture(name):
             elif f[0] == "motif":
                 motif = [int(x) for x in f[1:]]
     return g, source, expect, motif
+
+
+def walk_start_sources(g, k):
+    """Vertices with an out-edge that starts some restless walk of k-1 edges
+    (edge f may follow edge e when f leaves e's head v with t_e <= t_f <=
+    t_e + delta(v)): the only sources from which a k-vertex path can exist.
+    Plain boolean reachability over edges; candidates, to be confirmed by DFS."""
+    import numpy as np
+    src = np.asarray(g["src"], dtype=np.int64)
+    dst = np.asarray(g["dst"], dtype=np.int64)
+    t = np.asarray(g["t"], dtype=np.int64)
+    d = np.asarray(g["delta"], dtype=np.int64)
+    m = src.shape[0]
+    order = np.lexsort((np.arange(m), t, src))  # out-edges by (tail, time)
+    key = src[order] * (1 << 32) + t[order]
+    lo = np.searchsorted(key, dst * (1 << 32) + t, side="left")
+    hi = np.searchsorted(key, dst * (1 << 32) + t + d[dst], side="right")
+    ok = np.ones(m, dtype=bool)  # e starts a walk of 1 edge
+    for _ in range(k - 2):
+        pre = np.concatenate([[0], np.cumsum(ok[order].astype(np.int64))])
+        ok = (pre[hi] - pre[lo]) > 0
+    return np.unique(src[ok])

@@ -224,13 +224,15 @@ def test_edge_cases():
 
 def test_bench_workload_sampled_points_and_one_sided():
     """Full n=100,000 / m=1,000,000 workload at k=8 from s=0, the benchmark's
-    launch shape: sampled single points against the oracle, and the witness
-    against brute force (no restless path of 8 vertices leaves s=0, so every
-    sum must be exactly zero)."""
+    launch shape: sampled single points against the oracle, and the whole
+    witness against the determinant identity computed by exhaustive DFS (no
+    restless path of 8 vertices leaves s=0, so every sum must be exactly zero;
+    sources with paths are checked in test_gpu_scale_parity.py)."""
     g = W.scale_uniform()
     with _graph(g) as G:
         bm, w = G.reach(0, 8, 0x5EED0002 ^ 1)
-        reach, _, npaths = oracle.dfs_paths(g, 0, 8)
+        reach, sdet, npaths = oracle.dfs_paths(g, 0, 8, 0x5EED0002 ^ 1, with_det=True)
+        assert np.array_equal(w, sdet)
         assert np.array_equal(w != 0, reach.astype(bool))
         masks = [1, 77, 200, 255]
         dev = G.point_sums(0, 8, 0x5EED0002 ^ 1, masks)

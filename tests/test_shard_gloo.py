@@ -12,15 +12,20 @@ from paper_2010_08423_gb300 import workloads as W
 
 
 def test_point_ranges_partition_the_points():
-    for k in (2, 5, 8, 12):
+    for k in (2, 3, 4, 5, 7, 8, 9, 12, 20):
         for world in (1, 2, 3, 4, 8):
             seen = []
             for r in range(world):
                 f, c = shard.point_range(k, r, world)
+                # the library's range entry takes starts on multiples of 128
+                # (k <= 3: the whole range or nothing)
+                assert c == 0 or (f % shard.RANGE_ALIGN == 0 if k > 3 else (f, c) == (0, 1 << k))
                 seen.extend(range(f, f + c))
             assert seen == list(range(1 << k)), (k, world)
     f, c = shard.point_range(10, 1, 2)
     assert f % 128 == 0 and c % 128 == 0
+    # fewer 128-point units than ranks: the last ranks get empty shares
+    assert [shard.point_range(8, r, 4) for r in range(4)] == [(0, 128), (128, 128), (256, 0), (256, 0)]
 
 
 def _free_port():
