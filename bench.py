@@ -1,23 +1,37 @@
 #!/usr/bin/env python3
-"""Benchmark: k-RestlessReach sieve queries on a resident temporal graph.
+"""Benchmark: restless-reachability sieve queries on a resident temporal graph.
 
-Workload (one step = one complete query: z-table, k-1 edge layers over all
-2^k sieve points, fused per-vertex reduce, reach bitmap):
-  uniform random directed temporal multigraph, n = 100,000, m = 1,000,000,
-  t ~ U[1, 1000], delta(v) ~ U{1..20}, k = 8, source vertex 0, plain query,
-  GF(2^64) mod x^64+x^4+x^3+x+1, splitmix64-seeded values (seed differs per step).
+Headline workload (one step = one complete query: z-table, every layer over
+all 2^k sieve points, fused per-vertex reduce, reach bitmap):
+  Chung-Lu power-law temporal multigraph (degree exponent 2.5), n = 1,000,000,
+  m = 10,000,000, timestamps in [1, 10000] drawn as Poisson(50) bursts of width
+  20, delta(v) ~ U{5..50}, 8 vertex colours; k-RestlessMotifReach with k = 10
+  from the first vertex with an out-edge, motif = its colour + 9 uniform
+  colours; GF(2^64) mod x^64+x^4+x^3+x+1, splitmix64-seeded values (the seed
+  differs per step).
 
 Metric: GF(2^64) edge-updates/s counted as the nominal 2^k * k * m per query.
 `value` is device-timed (CUDA events on the launching stream, L2 flushed
-between steps, graph resident in HBM); `e2e` is the same metric through the
-host-buffer C-ABI call rr_reach_sync (descriptor uploaded and results copied
-back into pinned host buffers every step). `roofline` reports the dominant
-kernel against the measured copy bandwidth or the measured GF(2^64) multiply
-rate, whichever binds. Extra lines: batched, served, at-most-k / bounded,
-fine-grained, a Chung-Lu motif workload and serving on an n = 1e7 graph.
+between steps, graph resident in HBM); `work` states what one query performs
+(GF(2^64) multiplications and stored state values, from the per-kernel counts)
+beside the nominal count, and `value_performed` the performed multiplications
+per second; `e2e` is the same metric through the host-buffer C-ABI call
+rr_reach_sync (descriptor uploaded and results copied back into pinned host
+buffers every step). `roofline` reports the dominant kernel against the
+measured copy bandwidth or the measured GF(2^64) multiply rate, whichever
+binds. Extra lines: the uniform k = 8 query, the dense per-point engine on the
+headline query, the small n = 1,000 graph with the full oracle, batched,
+served (with the same query list one at a time), at-most-k / bounded and
+fine-grained queries, and serving on an n = 1e7 graph.
+
+--gpus N (under torchrun): one query split over the ranks by sieve points
+(rr_reach_range_device), partial witnesses all-gathered and XOR-combined each
+step (strong scaling: the whole job answers one query per step).
 
 --impl reference times the CPU oracle (oracle/) on a bounded sample of the
-same workload: the only other place this file runs oracle code.
+headline query (one sieve point per step); the cpu_baseline leg does the same
+on one point per core and on one point on one core. These are the only places
+this file runs oracle code.
 """
 from __future__ import annotations
 
@@ -39,20 +53,59 @@ from paper_2010_08423_gb300 import workloads as W  # noqa: E402
 
 METRIC = "GF(2^64) edge-updates/s (2^k*k*m per query)"
 UNIT = "edge-updates/s"
-K = 8
-SOURCE = 0
-GRAPH_SEED = W.GRAPH_SEED_BASE + 2
-WORKLOAD = ("uniform temporal multigraph n=100000 m=1000000 t~U[1,1000] delta~U{1..20}; "
-            "plain k-RestlessReach k=8 from s=0")
+K = 10
+GRAPH_SEED = W.GRAPH_SEED_BASE + 3
+WORKLOAD = ("Chung-Lu exponent 2.5 temporal multigraph n=1000000 m=10000000, t in [1,10000] as "
+            "Poisson(50) bursts of width 20, delta~U{5..50}, 8 colours; k-RestlessMotifReach k=10 "
+            "from the first vertex with an out-edge, motif = its colour + 9 uniform colours")
+# the uniform n=1e5 / m=1e6 query (single source vertex 0, plain, k = 8)
+K_UNIFORM = 8
+UNIFORM_SEED = W.GRAPH_SEED_BASE + 2
+UNIFORM_WORKLOAD = ("uniform temporal multigraph n=100000 m=1000000 t~U[1,1000] delta~U{1..20}; "
+                    "plain k-RestlessReach k=8 from s=0")
+# bytes of the query descriptor the library uploads per query (source, k,
+# flags, 4 family keys, 4 pointers, 512-entry shade table)
+DESC_BYTES = 16 + 32 + 32 + 512 * 4
 
 
 def units_per_query(k: int, m: int) -> float:
     return float(2 ** k) * k * m
 
 
+def headline_query():
+    """The motif workload: graph, source, motif; query seeds graph_seed ^ (i+1)."""
+    g = W.motif_powerlaw()
+    s = W.first_source(g)
+    motif = W.motif_for(g, s, K, GRAPH_SEED)
+    return g, s, motif
+
+
+def step_seed(i: int, base: int = GRAPH_SEED) -> int:
+    return (base ^ (i + 1)) & ((1 << 64) - 1)
+
+
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 # the sources whose change invalidates a recorded ncu capture of the query
@@ -96,14 +149,20 @@ def kernel_sources_sha1() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(kernel: str, ppl: int, chunk: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
-    workload, or None if the kernel sources or the query shape differ from that
-    capture's."""
+TRAFFIC_RECORDS = {
+    "motif": "ncu_traffic_k10_motif_powerlaw_n1e6_m1e7.json",
+    "uniform": "ncu_traffic_k8_uniform_n1e5_m1e6.json",
+}
+
+
+def recorded_traffic(workload: str, kernel: str, ppl: int, chunk: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of
+    `workload`, or None if the kernel sources or the query shape differ from
+    that capture's."""
     try:
-        with open(os.path.join(ROOT, "profiles", "ncu_traffic_k8_uniform_n1e5_m1e6.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", TRAFFIC_RECORDS[workload])) as fh:
             rec = json.load(fh)
-    except OSError:
+    except (OSError, KeyError):
         return None
     if kernel_sources_sha1() != rec.get("source_sha1"):
         return None
@@ -186,23 +245,265 @@ class ClockSampler:
                           "before the timed region through its end"}
 
 
-def cpu_baseline(g, k, nsteps_hint=1):
-    """The oracle as it stands, on a bounded sample of the workload's sieve
-    points (one mask per host thread); value scaled to the nominal unit."""
+def kernel_rooflines_dense(info, k, chunk, ppl, m, n, kt, queries, hbm_peak, mul_peak, out_deg_s,
+                           ztable_mults=0):
+    """Per kernel kind of the per-point engine (dense state: every row a state
+    row; rows with a non-empty window multiply once per point): average launch
+    time, algorithmic bytes and GF(2^64) multiplications per launch (one
+    layer over one point chunk), fractions of the measured peaks."""
+    c = chunk
+    Wr = info["window_rows"]  # rows with a non-empty window
+    lanes = c // (32 * ppl)   # lane groups: the y z_v label products once per row and group
+    meta = 20 * m + 4 * (n + 1)
+    alg = {
+        # layer 1: the source's out-edges multiply, every row stores its prefix
+        "first_layer": (m * c * 8 + meta, out_deg_s * (c + k * lanes)),
+        # middle layers: two gathered prefix rows per row with a window, every row stored
+        "mid_layer": (m * c * 8 + Wr * 2 * c * 8 + meta, Wr * (c + k * lanes)),
+        # last layer: gathers and multiplies, per-vertex XOR into the witness
+        "last_layer": (Wr * 2 * c * 8 + meta + n * 8, Wr * (c + k * lanes)),
+        "ztable": (n * k * 8, ztable_mults),
+    }
+    out = {}
+    for name, (kms, kn) in kt.items():
+        if not kn or name not in alg:
+            continue
+        avg_s = kms / kn / 1e3
+        b, mu = alg[name]
+        gbs = b / avg_s / 1e9
+        gms = mu / avg_s / 1e9
+        fh, fa = gbs / hbm_peak, gms / (mul_peak / 1e9)
+        out[name] = {"avg_launch_us": round(avg_s * 1e6, 2), "launches_per_query": kn / queries,
+                     "alg_bytes_per_launch": int(b), "achieved_gbs": round(gbs, 1),
+                     "hbm_frac": round(fh, 4), "alg_gf_mults_per_launch": int(mu),
+                     "achieved_gmul_s": round(gms, 2), "alu_frac": round(fa, 4),
+                     "bound": "alu" if fa >= fh else "hbm", "time_ms_per_query": round(kms / queries, 4)}
+    return out
+
+
+def work_accounting(by_kernel, k, m, info, ms_per_query):
+    """What one query performs against the nominal count: GF(2^64)
+    multiplications and stored state values summed over the kernels' per-launch
+    counts, and what the dense per-point engine multiplies for the same query."""
+    mults = sum(v["alg_gf_mults_per_launch"] * v["launches_per_query"] for v in by_kernel.values())
+    nominal = units_per_query(k, m)
+    method = float(2 ** k) * (k - 1) * m
+    # the per-point engine multiplies once per point for every row with a
+    # non-empty window at layers 2..k-1 (layer 1: the source's out-edges)
+    dense = float(2 ** k) * (k - 2) * info["window_rows"]
+    return {
+        "nominal_units_per_query": nominal,
+        "method_edge_point_layer_values_per_query": method,
+        "performed_gf_mults_per_query": mults,
+        "dense_engine_gf_mults_per_query": dense,
+        "dense_over_performed_mults": dense / max(1.0, mults),
+        "nominal_over_performed": nominal / max(1.0, mults),
+        "value_performed": {"value": mults / (ms_per_query / 1e3), "unit": "GF(2^64) multiplications/s"},
+        "note": "performed = the per-launch multiplication counts of the roofline table times the "
+                "launches per query (reduced-state engine: structurally zero rows and points are "
+                "not evaluated); nominal = 2^k*k*m",
+    }
+
+
+def timed_queries(torch, stream, run, nsteps, flush):
+    """Device time (ms) of each of nsteps calls run(i) on `stream`, L2 flushed
+    (outside the events) before each."""
+    ms = []
+    with torch.cuda.stream(stream):
+        for i in range(nsteps):
+            flush.fill_(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run(i)
+            e1.record(stream)
+            stream.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def kernel_times(capi, torch, stream, run, nq):
+    """Per-kind kernel times of nq calls launched kernel by kernel."""
+    capi.rr_timing_enable(True)
+    capi.rr_timing_read(reset=True)
+    try:
+        with torch.cuda.stream(stream):
+            for i in range(nq):
+                run(i)
+            stream.synchronize()
+        return capi.rr_timing_read(reset=True)
+    finally:
+        capi.rr_timing_enable(False)
+
+
+def dominant_roofline(by_kernel, kt, mul_peak, hbm_peak, peak_kind, traffic):
+    """The roofline object of the kernel kind with the most time per query."""
+    if not by_kernel:
+        return None
+    dom = max(by_kernel, key=lambda k_: kt[k_][0])
+    d = by_kernel[dom]
+    common = {"traffic": traffic(dom) if traffic else None, "kernel": dom,
+              "avg_launch_us": d["avg_launch_us"],
+              "alg_bytes_per_launch": d["alg_bytes_per_launch"],
+              "alg_gf_mults_per_launch": d["alg_gf_mults_per_launch"],
+              "hbm_frac": d["hbm_frac"], "alu_frac": d["alu_frac"]}
+    if d["bound"] == "alu":
+        return {"bound": "alu", "achieved": d["achieved_gmul_s"], "peak": round(mul_peak / 1e9, 2),
+                "unit": "GF(2^64) Gmul/s", "frac": d["alu_frac"],
+                "peak_kind": "measured live: rr_bench_gf_mul, register-only multiply chains on all "
+                             "SMs, each operand value in one product (ALU-pipe bound)", **common}
+    return {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": d["hbm_frac"], "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)", **common}
+
+
+def motif_ztable_mults(g, motif, k):
+    """A coloured z entry multiplies once per shade of its vertex's colour (Eq. 3)."""
+    mu = np.bincount(np.asarray(motif, dtype=np.int64), minlength=256)
+    return k * int((np.bincount(np.asarray(g["color"], dtype=np.int64), minlength=256) * mu).sum())
+
+
+def uniform_metrics(capi, torch, g, mul_peak, hbm_peak, peak_kind, steps=20):
+    """The uniform n=1e5 / m=1e6 graph, plain k=8 from vertex 0 (no restless
+    path of 3 or more vertices leaves it, so the witness is zero; the full
+    sieve still runs), autotuned shape."""
+    n, m = g["n"], len(g["src"])
+    with capi.Graph(g) as G:
+        info = G.info()
+        ppl, chunk = capi.rr_autotune(G.handle, K_UNIFORM)
+        st = torch.cuda.Stream()
+        d_w = torch.empty(n, dtype=torch.int64, device="cuda")
+        d_bm = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+
+        def run(i):
+            capi.rr_reach_device(G.handle, 0, K_UNIFORM, step_seed(i, UNIFORM_SEED), d_w, d_bm,
+                                 st.cuda_stream)
+        timed_queries(torch, st, run, 3, flush)
+        ms = timed_queries(torch, st, lambda i: run(100 + i), steps, flush)
+        kt = kernel_times(capi, torch, st, lambda i: run(200 + i), 5)
+    by_kernel = kernel_rooflines(info, K_UNIFORM, chunk, ppl, n, kt, 5, hbm_peak, mul_peak)
+    per_q = sum(ms) / steps
+    roof = dominant_roofline(by_kernel, kt, mul_peak, hbm_peak, peak_kind,
+                             lambda kern: recorded_traffic("uniform", kern, ppl, chunk))
+    return {"workload": UNIFORM_WORKLOAD, "value": units_per_query(K_UNIFORM, m) / (per_q / 1e3),
+            "unit": UNIT, "ms_per_query": per_q, "steps": steps,
+            "shape": {"points_per_lane": ppl, "points_per_chunk": chunk},
+            "work": work_accounting(by_kernel, K_UNIFORM, m, info, per_q),
+            "roofline": roof, "roofline_by_kernel": by_kernel,
+            "rows": {"state": info["producer_window_rows"] + 1, "deep": info["state_compute_rows"],
+                     "deep_compute": info["deep_compute_rows"], "last_layer": info["deep_tail_rows"]},
+            "l2": "flushed between queries",
+            "parity": "tests/test_gpu_scale_parity.py: full k=8 witness from a source with "
+                      "8-vertex paths and from vertex 0, bit-exact vs the oracle"}
+
+
+def dense_metrics(capi, torch, g, s, motif, mul_peak, hbm_peak, peak_kind, nq=2):
+    """The headline query on the per-point engine with the dense state layout
+    (every row stored for every point; every row with a non-empty window
+    multiplied for every point): no structural pruning."""
+    n, m = g["n"], len(g["src"])
+    ppl, chunk = 4, 256  # 2 * (m+1) * 256 * 8 bytes of state (41 GB)
+    with capi.Graph(g, capi.FLAG_DENSE_STATE) as G:
+        info = G.info()
+        capi.rr_set_tuning(G.handle, K, ppl, chunk)
+        st = torch.cuda.Stream()
+        d_w = torch.empty(n, dtype=torch.int64, device="cuda")
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+
+        def run(i):
+            capi.rr_reach_device(G.handle, s, K, step_seed(300 + i), d_w, None, st.cuda_stream,
+                                 motif=motif)
+        timed_queries(torch, st, run, 1, flush)
+        ms = timed_queries(torch, st, lambda i: run(10 + i), nq, flush)
+        kt = kernel_times(capi, torch, st, lambda i: run(20 + i), 1)
+    out_deg_s = int(np.count_nonzero(g["src"] == s))
+    by_kernel = kernel_rooflines_dense(info, K, chunk, ppl, m, n, kt, 1, hbm_peak, mul_peak,
+                                       out_deg_s, motif_ztable_mults(g, motif, K))
+    per_q = sum(ms) / nq
+    mults = sum(v["alg_gf_mults_per_launch"] * v["launches_per_query"] for v in by_kernel.values())
+    return {"workload": "the headline query on the per-point engine, dense state layout",
+            "value": units_per_query(K, m) / (per_q / 1e3), "unit": UNIT, "ms_per_query": per_q,
+            "steps": nq, "shape": {"points_per_lane": ppl, "points_per_chunk": chunk},
+            "performed_gf_mults_per_query": mults,
+            "value_performed": {"value": mults / (per_q / 1e3), "unit": "GF(2^64) multiplications/s"},
+            "roofline": dominant_roofline(by_kernel, kt, mul_peak, hbm_peak, peak_kind, None),
+            "roofline_by_kernel": by_kernel, "l2": "flushed between queries"}
+
+
+def small_metrics(capi, torch, reps=200):
+    """n=1,000 / m=10,000, t ~ U[1,100], delta ~ U{1..5}, plain k=5 from
+    vertex 0: the GPU query (device-timed, launch-bound) beside the oracle's
+    full sieve (all 32 points, unsampled) on one thread and on all cores."""
     import oracle
-    threads = max(1, min(os.cpu_count() or 1, 64))
-    masks = np.arange(1, threads + 1, dtype=np.uint32) * 3 % (2 ** k)
+    g = W.small_uniform()
+    n, m, k = g["n"], len(g["src"]), 5
+    with capi.Graph(g) as G:
+        st = torch.cuda.Stream()
+        d_w = torch.empty(n, dtype=torch.int64, device="cuda")
+        d_bm = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(st):
+            for i in range(10):
+                capi.rr_reach_device(G.handle, 0, k, i + 1, d_w, d_bm, st.cuda_stream)
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for i in range(reps):
+                capi.rr_reach_device(G.handle, 0, k, 100 + i, d_w, d_bm, st.cuda_stream)
+            e1.record(st)
+            st.synchronize()
+        gpu_ms = e0.elapsed_time(e1) / reps
+        reached = int((d_w != 0).sum().item())
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t1 = []
+    for i in range(3):
+        t0 = time.perf_counter()
+        oracle.sieve(g, 0, k, 100 + i, threads=1)
+        t1.append(time.perf_counter() - t0)
+    ta = []
+    for i in range(3):
+        t0 = time.perf_counter()
+        oracle.sieve(g, 0, k, 100 + i, threads=cores)
+        ta.append(time.perf_counter() - t0)
+    u = units_per_query(k, m)
+    return {"workload": "uniform temporal multigraph n=1000 m=10000 t~U[1,100] delta~U{1..5}; plain "
+                        "k-RestlessReach k=5 from s=0",
+            "value": u / (gpu_ms / 1e3), "unit": UNIT, "ms_per_query": gpu_ms,
+            "reachable_vertices": reached,
+            "cpu_oracle_full": {"single_thread_ms": 1e3 * min(t1), "all_cores_ms": 1e3 * min(ta),
+                                "cores": cores, "value_single_thread": u / min(t1),
+                                "value_all_cores": u / min(ta),
+                                "sample": "all 32 sieve points (no sampling), best of 3"}}
+
+
+def cpu_baseline(g, s, motif):
+    """The oracle as it stands on the headline query: one sieve point per host
+    core (all cores) and one point on one core; values scaled by points to the
+    nominal unit (the oracle's work is the same for every point)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    m = len(g["src"])
+    masks = (640 + np.arange(cores)).astype(np.uint32) % (2 ** K)
     t0 = time.perf_counter()
-    oracle.sieve(g, SOURCE, k, GRAPH_SEED ^ 1, masks=masks, threads=threads)
-    dt = time.perf_counter() - t0
-    frac = len(masks) / 2 ** k
-    value = units_per_query(k, len(g["src"])) * frac / dt
-    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(masks)} of {2 ** k} sieve points of one k={k} query "
-                      f"({dt:.2f} s wall), scaled by points"}
+    oracle.sieve(g, s, K, step_seed(0), motif=motif, masks=masks, threads=cores)
+    dt_all = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.sieve(g, s, K, step_seed(0), motif=motif, masks=masks[:1], threads=1)
+    dt_one = time.perf_counter() - t0
+    u = units_per_query(K, m)
+    return {"value": u * len(masks) / 2 ** K / dt_all, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{len(masks)} of {2 ** K} sieve points of one k={K} query of the headline "
+                      f"workload, one point per core ({dt_all:.1f} s wall), scaled by points",
+            "single_thread": {"value": u / 2 ** K / dt_one, "unit": UNIT, "cores": 1,
+                              "sample": f"1 of {2 ** K} sieve points on one core ({dt_one:.1f} s), "
+                                        "scaled by points"},
+            "cpu_model": cpu_model(), "nproc": cores,
+            "oracle": "plain C, one point at a time, windows scanned in time order, bitwise "
+                      "shift-and-add GF(2^64) multiply (gcc -O2 -fopenmp)"}
 
 
-def batched_metrics(capi, torch, gc, nq=256, seed=GRAPH_SEED):
+def batched_metrics(capi, torch, gc, nq=256, seed=UNIFORM_SEED):
     """The same graph with 8 colours; nq queries, s ~ U, k ~ U{4..12}, odd q
     with a motif (source colour + k-1 uniform colours): one persistent batched
     launch against one launch sequence per query, results compared bit for bit."""
@@ -245,13 +546,15 @@ def batched_metrics(capi, torch, gc, nq=256, seed=GRAPH_SEED):
             "launches": "1 persistent kernel (+ z-table, first-layer and bitmap prologue/epilogue)"}
 
 
-def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
+def served_metrics(capi, g, nq=160, seed=UNIFORM_SEED ^ 0x5E,
                    workload="plain queries, k~U{6..12}, s~U, on the n=100000 m=1000000 graph",
                    warm=8):
     """Serving: Poisson arrivals of plain queries (s ~ U, k ~ U{6..12}) at 0.5x,
     0.8x and 1.1x of the server's measured capacity; latency = submit -> done.
     Warm-up: `warm` queries one at a time, then one untimed burst (the batch
-    lanes' first use grows the batch kernel's buffers)."""
+    lanes' first use grows the batch kernel's buffers). The same query list is
+    then run one query at a time through rr_reach_sync (the plain GPU form:
+    one launch sequence per query, results copied to the host), host-timed."""
     import threading
     rng = np.random.default_rng(seed)
     n = g["n"]
@@ -315,6 +618,23 @@ def served_metrics(capi, g, nq=160, seed=GRAPH_SEED ^ 0x5E,
                                       "batches": a2[2] - a1[2]}
         finally:
             capi.rr_server_destroy(srv)
+        # the identical query list, one query at a time (pinned host outputs)
+        import torch
+        h_bm = torch.empty((n + 7) // 8, dtype=torch.uint8, pin_memory=True).numpy()
+        h_w = torch.empty(n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+        for s_, k_, sd in qs[:warm]:
+            G.reach(s_, k_, sd, out=(h_bm, h_w))
+        t0 = time.perf_counter()
+        for s_, k_, sd in qs:
+            G.reach(s_, k_, sd, out=(h_bm, h_w))
+        one = nq / (time.perf_counter() - t0)
+    out["one_query_at_a_time_queries_per_s"] = one
+    out["one_query_at_a_time_api"] = "rr_reach_sync per query, same list, pinned host outputs"
+    out["capacity_over_one_at_a_time"] = out["capacity_queries_per_s"] / one
+    for lv in out["loads"]:
+        lv["over_one_at_a_time"] = lv["queries_per_s"] / one
+    out["note"] = ("below saturation the delivered rate equals the offered rate; capacity (a burst "
+                   "of the whole list) is the served form's throughput")
     return out
 
 
@@ -417,62 +737,6 @@ def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, zt
     return out
 
 
-def motif_metrics(capi, torch, mul_peak, hbm_peak, steps=5):
-    """Chung-Lu exponent 2.5, n=1e6, m=1e7, bursty t in [1,10000], delta ~
-    U{5..50}, 8 colours; k-RestlessMotifReach with k=10 from the first vertex
-    with an out-edge, motif = its colour + 9 uniform colours (seeded)."""
-    g = W.motif_powerlaw()
-    s = W.first_source(g)
-    motif = W.motif_for(g, s, 10, W.GRAPH_SEED_BASE + 3)
-    n, m = g["n"], len(g["src"])
-    t0 = time.perf_counter()
-    with capi.Graph(g) as G:
-        load_s = time.perf_counter() - t0
-        info = G.info()
-        st = torch.cuda.Stream()
-        d_w = torch.zeros(n, dtype=torch.int64, device="cuda")
-        flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
-        for i in range(2):
-            capi.rr_reach_device(G.handle, s, 10, i + 1, d_w, None, st.cuda_stream, motif=motif)
-        st.synchronize()
-        tot = 0.0
-        with torch.cuda.stream(st):
-            for i in range(steps):
-                flush.fill_(i)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                capi.rr_reach_device(G.handle, s, 10, 100 + i, d_w, None, st.cuda_stream, motif=motif)
-                e1.record(st)
-                st.synchronize()
-                tot += e0.elapsed_time(e1)
-        reach = int((d_w != 0).sum().item())
-        # per-kernel roofline from one more query launched kernel by kernel
-        capi.rr_timing_enable(True)
-        capi.rr_timing_read(reset=True)
-        try:
-            capi.rr_reach_device(G.handle, s, 10, 999, d_w, None, st.cuda_stream, motif=motif)
-            st.synchronize()
-            kt = capi.rr_timing_read(reset=True)
-        finally:
-            capi.rr_timing_enable(False)
-    units = float(2 ** 10) * 10 * m
-    ppl = 4
-    chunk = min(2 ** 10, 4 * 32 * ppl)  # the engine's default shape for k = 10
-    # a coloured z entry multiplies once per shade of its vertex's colour (Eq. 3)
-    mu = np.bincount(np.asarray(motif, dtype=np.int64), minlength=256)
-    zt = 10 * int((np.bincount(np.asarray(g["color"], dtype=np.int64), minlength=256) * mu).sum())
-    by_kernel = kernel_rooflines(info, 10, chunk, ppl, n, kt, 1, hbm_peak, mul_peak, ztable_mults=zt)
-    dom = max(by_kernel, key=lambda k_: by_kernel[k_]["time_ms_per_query"]) if by_kernel else None
-    return {"workload": "Chung-Lu exponent 2.5, n=1e6, m=1e7, bursty t in [1,10000], delta~U{5..50}, "
-                        "8 colours; k-RestlessMotifReach k=10, motif = source colour + 9 uniform colours",
-            "value": units * steps / (tot / 1e3), "unit": UNIT, "ms_per_query": tot / steps,
-            "dominant_kernel": dom, "roofline_by_kernel": by_kernel,
-            "shape": {"points_per_lane": ppl, "points_per_chunk": chunk},
-            "reachable_vertices": reach, "graph_load_s": round(load_s, 3),
-            "state_rows": info["producer_window_rows"] + 1, "deep_rows": info["state_compute_rows"],
-            "max_in_degree": info["max_in_degree"], "l2": "flushed between queries"}
-
-
 def atmost_metrics(capi, torch, g, k=10, reps=5):
     """at-most-k (the exact-k' queries for k' = 2..k, run concurrently) against
     the exact-k query on the benchmark graph. The paper's experiments report the
@@ -483,18 +747,18 @@ def atmost_metrics(capi, torch, g, k=10, reps=5):
         st = torch.cuda.Stream()
         d_w = torch.zeros((k - 1, n), dtype=torch.int64, device="cuda")
         d_bm = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
-        capi.rr_reach_atmost_device(G.handle, SOURCE, k, 1, d_w, d_bm, st.cuda_stream)
-        capi.rr_reach_device(G.handle, SOURCE, k, 1, d_w[0], None, st.cuda_stream)
+        capi.rr_reach_atmost_device(G.handle, 0, k, 1, d_w, d_bm, st.cuda_stream)
+        capi.rr_reach_device(G.handle, 0, k, 1, d_w[0], None, st.cuda_stream)
         st.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         with torch.cuda.stream(st):
             e[0].record(st)
             for i in range(reps):
-                capi.rr_reach_atmost_device(G.handle, SOURCE, k, 2 + i, d_w, d_bm, st.cuda_stream)
+                capi.rr_reach_atmost_device(G.handle, 0, k, 2 + i, d_w, d_bm, st.cuda_stream)
             e[1].record(st)
             e[2].record(st)
             for i in range(reps):
-                capi.rr_reach_device(G.handle, SOURCE, k, 2 + i, d_w[0], None, st.cuda_stream)
+                capi.rr_reach_device(G.handle, 0, k, 2 + i, d_w[0], None, st.cuda_stream)
             e[3].record(st)
             st.synchronize()
         t_atm = e[0].elapsed_time(e[1]) / reps
@@ -502,12 +766,12 @@ def atmost_metrics(capi, torch, g, k=10, reps=5):
         # bounded RestlessReach (minimum arrival and shortest length over k' <= k)
         d_r = torch.zeros(n, dtype=torch.int32, device="cuda")
         d_l = torch.zeros(n, dtype=torch.uint8, device="cuda")
-        capi.rr_reach_bounded_device(G.handle, SOURCE, k, 1, d_r, d_l, d_bm, st.cuda_stream)
+        capi.rr_reach_bounded_device(G.handle, 0, k, 1, d_r, d_l, d_bm, st.cuda_stream)
         st.synchronize()
         with torch.cuda.stream(st):
             e[0].record(st)
             for i in range(reps):
-                capi.rr_reach_bounded_device(G.handle, SOURCE, k, 2 + i, d_r, d_l, d_bm, st.cuda_stream)
+                capi.rr_reach_bounded_device(G.handle, 0, k, 2 + i, d_r, d_l, d_bm, st.cuda_stream)
             e[1].record(st)
             st.synchronize()
         t_bounded = e[0].elapsed_time(e[1]) / reps
@@ -518,7 +782,7 @@ def atmost_metrics(capi, torch, g, k=10, reps=5):
             "value": sum(2 ** kk * kk * m for kk in range(2, k + 1)) / (t_atm / 1e3), "unit": UNIT}
 
 
-def fine_metrics(capi, torch, g, k=K, reps=10):
+def fine_metrics(capi, torch, g, k=K_UNIFORM, reps=10):
     """Fine-grained oracle (Algorithm 1 with per-time outputs: per-edge sums,
     minimum arrival time R, set D) against the plain query on the benchmark
     graph and query."""
@@ -530,19 +794,19 @@ def fine_metrics(capi, torch, g, k=K, reps=10):
         d_r = torch.zeros(n, dtype=torch.int32, device="cuda")
         d_b = torch.zeros((n + 7) // 8, dtype=torch.uint8, device="cuda")
         for i in range(3):
-            capi.rr_reach_arrival_device(G.handle, SOURCE, k, 1 + i, d_w, d_r, d_e, d_b, st.cuda_stream)
-            capi.rr_reach_device(G.handle, SOURCE, k, 1 + i, d_w, None, st.cuda_stream)
+            capi.rr_reach_arrival_device(G.handle, 0, k, 1 + i, d_w, d_r, d_e, d_b, st.cuda_stream)
+            capi.rr_reach_device(G.handle, 0, k, 1 + i, d_w, None, st.cuda_stream)
         st.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         with torch.cuda.stream(st):
             e[0].record(st)
             for i in range(reps):
-                capi.rr_reach_arrival_device(G.handle, SOURCE, k, 7 + i, d_w, d_r, d_e, d_b,
+                capi.rr_reach_arrival_device(G.handle, 0, k, 7 + i, d_w, d_r, d_e, d_b,
                                              st.cuda_stream)
             e[1].record(st)
             e[2].record(st)
             for i in range(reps):
-                capi.rr_reach_device(G.handle, SOURCE, k, 7 + i, d_w, None, st.cuda_stream)
+                capi.rr_reach_device(G.handle, 0, k, 7 + i, d_w, None, st.cuda_stream)
             e[3].record(st)
             st.synchronize()
         t_fine = e[0].elapsed_time(e[1]) / reps
@@ -550,7 +814,7 @@ def fine_metrics(capi, torch, g, k=K, reps=10):
         R = d_r.cpu().numpy().view(np.uint32)
         # no restless path of 3 or more vertices leaves s on this graph; k = 2
         # shows the arrival-time output on the same source
-        capi.rr_reach_arrival_device(G.handle, SOURCE, 2, 1, d_w, d_r, d_e, d_b, st.cuda_stream)
+        capi.rr_reach_arrival_device(G.handle, 0, 2, 1, d_w, d_r, d_e, d_b, st.cuda_stream)
         st.synchronize()
         R2 = d_r.cpu().numpy().view(np.uint32)
     reached = R != 0xFFFFFFFF
@@ -564,32 +828,37 @@ def fine_metrics(capi, torch, g, k=K, reps=10):
 
 
 def run_reference(args):
+    """The oracle as it stands on the headline query: each step evaluates one
+    sieve point (a bounded sample; the oracle's work is the same for every
+    point) with the host's cores sharing each layer's edges; value scaled by
+    points to the nominal unit. Rank 0 only."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
-    g = W.scale_uniform()
-    m = len(g["src"])
     import oracle
     oracle.build()
-    threads = max(1, min(os.cpu_count() or 1, 64))
-    masks = np.arange(1, threads + 1, dtype=np.uint32) * 3 % (2 ** K)
-    frac = len(masks) / 2 ** K
-    for _ in range(args.warmup):
-        oracle.sieve(g, SOURCE, K, GRAPH_SEED ^ 1, masks=masks[:1], threads=1)
+    g, s, motif = headline_query()
+    m = len(g["src"])
+    cores = os.cpu_count() or 1
+    for i in range(args.warmup):
+        oracle.sieve(g, s, K, step_seed(i), motif=motif,
+                     masks=np.array([640 + i % 64], dtype=np.uint32), threads=cores)
     times = []
-    for step in range(args.steps):
+    for i in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sieve(g, SOURCE, K, GRAPH_SEED ^ (step + 1), masks=masks, threads=threads)
+        oracle.sieve(g, s, K, step_seed(i), motif=motif,
+                     masks=np.array([(640 + 7 * i) % 2 ** K], dtype=np.uint32), threads=cores)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
-    value = units_per_query(K, m) * frac * args.steps / tot
+    value = units_per_query(K, m) / 2 ** K * args.steps / tot
+    sample = f"1 of {2 ** K} sieve points per step, {cores} threads sharing each layer's edges"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{len(masks)} of {2 ** K} sieve points per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{len(masks)} of {2 ** K} sieve points per step, scaled by points"},
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph_seed": GRAPH_SEED, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample + ", scaled by points", "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -602,17 +871,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--no-extra", action="store_true", help="headline line only")
     ap.add_argument("--dense", action="store_true", help="dense state layout (every row stored)")
     ap.add_argument("--shape", default=None,
-                    help="points per lane x points per chunk (e.g. 2x256) instead of the autotuner; "
+                    help="points per lane x points per chunk (e.g. 4x512) instead of the autotuner; "
                          "profiling runs pin the shape the autotuner picks without a profiler")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
 
     import torch
-    from paper_2010_08423_gb300 import capi
+    from paper_2010_08423_gb300 import capi, shard
 
     rank, world, local_rank = env_rank()
     torch.cuda.set_device(local_rank)
@@ -622,9 +891,8 @@ def main():
         dist.init_process_group("nccl")
     capi.load()
 
-    g = W.scale_uniform()
-    m = len(g["src"])
-    n = g["n"]
+    g, s, motif = headline_query()
+    m, n = len(g["src"]), g["n"]
     t0 = time.perf_counter()
     G = capi.Graph(g, capi.FLAG_DENSE_STATE if args.dense else 0)
     load_s = time.perf_counter() - t0
@@ -634,15 +902,20 @@ def main():
         capi.rr_set_tuning(G.handle, K, ppl, chunk)
     else:
         ppl, chunk = capi.rr_autotune(G.handle, K)
+    first, count = shard.point_range(K, rank, world)
 
     stream = torch.cuda.Stream()
     d_w = torch.empty(n, dtype=torch.int64, device="cuda")
     d_bm = torch.empty((n + 7) // 8, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
-    seed_base = GRAPH_SEED ^ (rank << 20)
 
     def step(i):
-        capi.rr_reach_device(G.handle, SOURCE, K, seed_base ^ (i + 1), d_w, d_bm, stream.cuda_stream)
+        if world == 1:
+            capi.rr_reach_device(G.handle, s, K, step_seed(i), d_w, d_bm, stream.cuda_stream,
+                                 motif=motif)
+        else:
+            # this rank's sieve points, then the parts all-gathered and XOR-combined
+            shard.reach_sharded(G.handle, n, s, K, step_seed(i), d_w, motif=motif, stream=stream)
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
@@ -653,15 +926,13 @@ def main():
         sampler = ClockSampler(local_rank)
         sampler.start()
         sampler.wait_first()
-        # untimed steps of the same query under the sampler (the timed region
-        # alone is a few ms, shorter than the sampling interval)
+        # untimed steps of the same query under the sampler
         t_load = time.perf_counter() + 0.4
         j = 0
         while time.perf_counter() < t_load:
             step(1_000_000 + j)
             j += 1
-            if j % 32 == 0:
-                stream.synchronize()
+            stream.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -674,16 +945,13 @@ def main():
         torch.cuda.synchronize()
         launches = capi.rr_kernel_launches() - launches0
         clocks = sampler.stop()
-        # profiling pass (not timed above): per-kernel CUDA-event durations
-        # recorded by the library on the launching stream
-        capi.rr_timing_enable(True)
-        capi.rr_timing_read(reset=True)
-        for i in range(5):
-            flush.fill_(i)
-            step(10_000 + i)
-        torch.cuda.synchronize()
-        kt = capi.rr_timing_read(reset=True)
-        capi.rr_timing_enable(False)
+    reach = int((d_w != 0).sum().item())
+    # profiling pass (not timed above): per-kernel CUDA-event durations recorded
+    # by the library on the launching stream, this rank's share of the points
+    kt = kernel_times(capi, torch, stream,
+                      lambda i: capi.rr_reach_range_device(G.handle, s, K, step_seed(10_000 + i), first,
+                                                           count, d_w, stream.cuda_stream, motif),
+                      2)
     ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(ms)
     if dist:
@@ -691,15 +959,24 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
     units = units_per_query(K, m)
-    value = world * args.steps * units / (tot_ms / 1e3)
+    value = args.steps * units / (tot_ms / 1e3)  # one whole query per step for the job
 
-    # end to end through the host-buffer C ABI (rr_reach_sync: results copied
-    # back every step into pinned host buffers allocated once), L2 flushed
-    # between steps
+    # end to end through the host-buffer API: rr_reach_sync (results copied back
+    # every step into pinned host buffers allocated once); sharded: the rank's
+    # range, the exchange and the combined witness copied to the host
     h_bm = torch.empty((n + 7) // 8, dtype=torch.uint8, pin_memory=True).numpy()
     h_w = torch.empty(n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    h_wt = torch.from_numpy(h_w.view(np.int64))
+
+    def e2e_step(i):
+        if world == 1:
+            G.reach(s, K, step_seed(i), motif=motif, out=(h_bm, h_w))
+        else:
+            full = shard.reach_sharded(G.handle, n, s, K, step_seed(i), d_w, motif=motif,
+                                       stream=stream)
+            h_wt.copy_(full)
     for i in range(2):
-        G.reach(SOURCE, K, seed_base ^ (1000 + i), out=(h_bm, h_w))
+        e2e_step(2000 + i)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -708,83 +985,82 @@ def main():
         flush.fill_(i)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G.reach(SOURCE, K, seed_base ^ (2000 + i), out=(h_bm, h_w))
+        e2e_step(3000 + i)
         e2e_s += time.perf_counter() - t0
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * args.steps * units / e2e_s
+    e2e_value = args.steps * units / e2e_s
 
-    # roofline: algorithmic bytes and GF(2^64) multiplications per launch of
-    # each kernel kind, against the measured copy bandwidth and the measured
-    # multiply rate; the dominant kernel reports the binding one
     peaks, peak_kind = measured_peaks()
     mul_peak = gf_mul_peak(capi, torch)
-    by_kernel = kernel_rooflines(info, K, chunk, ppl, n, kt, 5, peaks["hbm_gbs"], mul_peak)
-    if args.dense:
-        by_kernel = {}
-    dom = max(by_kernel, key=lambda k_: kt[k_][0]) if by_kernel else None
-    roofline = None
-    if dom:
-        d = by_kernel[dom]
-        traffic = recorded_traffic(dom, ppl, chunk)
-        common = {"traffic": traffic, "kernel": dom, "avg_launch_us": d["avg_launch_us"],
-                  "alg_bytes_per_launch": d["alg_bytes_per_launch"],
-                  "alg_gf_mults_per_launch": d["alg_gf_mults_per_launch"],
-                  "hbm_frac": d["hbm_frac"], "alu_frac": d["alu_frac"]}
-        if d["bound"] == "alu":
-            roofline = {"bound": "alu", "achieved": d["achieved_gmul_s"],
-                        "peak": round(mul_peak / 1e9, 2), "unit": "GF(2^64) Gmul/s",
-                        "frac": d["alu_frac"],
-                        "peak_kind": "measured live: rr_bench_gf_mul, register-only multiply chains "
-                                     "on all SMs, each operand value in one product (ALU-pipe bound)",
-                        **common}
-        else:
-            roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
-                        "unit": "GB/s", "frac": d["hbm_frac"], "peak_kind": peak_kind, **common}
+    by_kernel = {} if args.dense else kernel_rooflines(
+        info, K, chunk, ppl, n, kt, 2, peaks["hbm_gbs"], mul_peak,
+        ztable_mults=motif_ztable_mults(g, motif, K))
+    roofline = dominant_roofline(by_kernel, kt, mul_peak, peaks["hbm_gbs"], peak_kind,
+                                 lambda kern: recorded_traffic("motif", kern, ppl, chunk))
     tot_k = max(1e-9, sum(v[0] for v in kt.values()))
     kernel_share = {k_: round(v[0] / tot_k, 4) for k_, v in kt.items() if v[1]}
+    ms_per_step = tot_ms / args.steps
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph_seed": GRAPH_SEED, "l2": "flushed between steps",
+            "config": {"workload": WORKLOAD, "graph_seed": GRAPH_SEED, "source": s, "k": K,
+                       "motif": [int(c) for c in motif], "l2": "flushed between steps",
                        "state_layout": "dense" if args.dense else "compact",
                        "points_per_lane": ppl, "points_per_chunk": chunk,
+                       "parallelism": "single GPU" if world == 1 else
+                       f"sieve points split over {world} ranks, partial witnesses all-gathered "
+                       "and XOR-combined every step",
+                       "rank0_points": [first, count],
                        "state_rows": info["producer_window_rows"] + 1,
                        "deep_rows": info["state_compute_rows"],
                        "deep_compute_rows": info["deep_compute_rows"],
                        "last_layer_rows": info["deep_tail_rows"],
                        "producer_rows": info["state_rows"] - 1, "window_rows": info["window_rows"],
-                       "graph_load_s": round(load_s, 3)},
+                       "max_in_degree": info["max_in_degree"],
+                       "pair_layer3": info["pair_layer3_min_k"] <= K, "head_table": info["head_table"],
+                       "graph_load_s": round(load_s, 3), "reachable_vertices": reach},
+            "work": work_accounting(by_kernel, K, m, info, ms_per_step) if by_kernel else None,
             "roofline": roofline,
             "roofline_by_kernel": by_kernel,
             "kernel_time_share": kernel_share,
-            "kernel_ms_per_query": round(tot_k / 5, 4),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 272,
-                    "d2h_bytes_per_step": n * 8 + (n + 7) // 8,
-                    "api": "rr_reach_sync (pinned host outputs, query descriptor uploaded per step)"},
-            "gpu_launches": int(launches), "clocks": clocks}
+            "kernel_ms_per_query": round(tot_k / 2, 4),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": DESC_BYTES,
+                    "d2h_bytes_per_step": n * 8 + ((n + 7) // 8 if world == 1 else 0),
+                    "api": "rr_reach_sync (pinned host outputs, query descriptor uploaded per step)"
+                           if world == 1 else "shard.reach_sharded + witness copied to pinned host memory"},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "parity": "tests/test_gpu_scale_parity.py: sieve points 640..703 of this query on this "
+                      "graph, autotuned shape, bit-exact vs the oracle"}
+    if world > 1:
+        line["work"] = None  # per-rank kernel counts cover one share of the points
+    G.close()
     if rank == 0 and not args.no_extra:
-        gc = W.scale_uniform(ncolors=8)
-        line["batched"] = batched_metrics(capi, torch, gc)
-        line["served"] = served_metrics(capi, g)
-        line["atmost_k"] = atmost_metrics(capi, torch, g)
-        line["fine_grained"] = fine_metrics(capi, torch, g)
-        line["motif_powerlaw"] = motif_metrics(capi, torch, mul_peak, peaks["hbm_gbs"])
+        line["uniform_k8"] = uniform_metrics(capi, torch, W.scale_uniform(), mul_peak,
+                                             peaks["hbm_gbs"], peak_kind)
+        line["dense"] = dense_metrics(capi, torch, g, s, motif, mul_peak, peaks["hbm_gbs"], peak_kind)
+        line["dense"]["compact_over_dense"] = line["dense"]["ms_per_query"] / ms_per_step
+        line["small"] = small_metrics(capi, torch)
+        gu = W.scale_uniform()
+        line["batched"] = batched_metrics(capi, torch, W.scale_uniform(ncolors=8))
+        line["served"] = served_metrics(capi, gu)
+        line["atmost_k"] = atmost_metrics(capi, torch, gu)
+        line["fine_grained"] = fine_metrics(capi, torch, gu)
+        del gu
         g5 = W.served_powerlaw()
         line["served_powerlaw"] = served_metrics(
-            capi, g5, nq=16, seed=W.GRAPH_SEED_BASE + 5, warm=4,
+            capi, g5, nq=100, seed=W.GRAPH_SEED_BASE + 5, warm=4,
             workload="plain queries, k~U{6..12}, s~U, on the Chung-Lu exponent 2.3 graph "
                      "n=1e7 m=1e8 t~U[1,1e5] delta~U{10..200}")
         del g5
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, K)
+        line["cpu_baseline"] = cpu_baseline(g, s, motif)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    G.close()
     if dist:
         dist.destroy_process_group()
     return 0

@@ -89,6 +89,7 @@ def test_motif_powerlaw_n1e6_k10_point_range():
     with capi.Graph(g) as G:
         info = G.info()
         # the launch shape the benchmark times on this graph
+        capi.rr_autotune(G.handle, k)
         assert info["pair_layer3_min_k"] <= k and info["head_table"] == 1
         assert info["max_in_degree"] > 128  # hub segments cut into pieces
         w = _device_witness(G, s, k, seed, motif=motif, first=first, count=count)
