@@ -26,6 +26,8 @@ def main(argv=None) -> int:
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--motif", action="store_true", help="a motif query (source colour + k-1 colours)")
+    ap.add_argument("--shape", default=None,
+                    help="points per lane x points per chunk (e.g. 4x512), as rr_set_tuning")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: one persistent batched launch of this many queries, "
                          "k ~ U{4..12}, odd ones coloured")
@@ -56,6 +58,9 @@ def main(argv=None) -> int:
             print(f"{args.workload} batch of {len(qs)} ms {e0.elapsed_time(e1):.3f}")
         return 0
     with capi.Graph(g) as G:
+        if args.shape:
+            ppl, chunk = (int(x) for x in args.shape.lower().split("x"))
+            capi.rr_set_tuning(G.handle, args.k, ppl, chunk)
         d_w = torch.zeros(g["n"], dtype=torch.int64, device="cuda")
         st = torch.cuda.Stream()
         for i in range(args.warmup):
