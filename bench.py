@@ -503,32 +503,92 @@ def cpu_baseline(g, s, motif):
                       "shift-and-add GF(2^64) multiply (gcc -O2 -fopenmp)"}
 
 
-def batched_metrics(capi, torch, gc, nq=256, seed=UNIFORM_SEED):
+def batch_kernel_alg(info, qs, max_chunk, n):
+    """Algorithmic bytes and GF(2^64) multiplications of the persistent batch
+    kernel for the queries qs: per unit (one query's chunk of points) the same
+    per-layer counts as the one-query kernels, with layer 3 per point (the
+    batch has no pair-label form); k <= 3 and the label-space layer 2 run in
+    the prologue kernels and are not counted here."""
+    S = info["producer_window_rows"]
+    D = info["state_compute_rows"]
+    DC = info["deep_compute_rows"]
+    T3 = info["deep_tail_rows"]
+    T2 = info["tail_rows"]
+    R3 = info["deep_head_runs"]
+    tot_b = tot_m = 0.0
+    for q in qs:
+        k = q["k"]
+        if k <= 3:
+            continue
+        npts = 2 ** k
+        ppl = 4 if npts >= 128 else 2
+        c = max(32 * ppl, min(npts, max_chunk))
+        lg = 7 if ppl == 4 else 6
+        rs = c // (32 * ppl) * (lg + 1)
+        nch = (npts + c - 1) // c
+        if k == 4:
+            layers = [(S * rs * 8 + S * 20 + 2 * S * 8, S * (1 + k + c)),
+                      (2 * T2 * rs * 8 + T2 * 16 + n * 8, T2 * rs)]
+        else:
+            l3 = (D * (rs if k == 5 else c) * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c)
+            mid = (D * c * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k))
+            tail = (D * rs * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k))
+            last = (2 * T3 * rs * 8 + T3 * 16 + n * 8, T3 * rs)
+            layers = [l3] + ([mid] * (k - 6) + [tail] if k >= 6 else []) + [last]
+        tot_b += nch * sum(x[0] for x in layers)
+        tot_m += nch * sum(x[1] for x in layers)
+    return tot_b, tot_m
+
+
+def batched_metrics(capi, torch, gc, mul_peak, hbm_peak, nq=256, seed=UNIFORM_SEED):
     """The same graph with 8 colours; nq queries, s ~ U, k ~ U{4..12}, odd q
     with a motif (source colour + k-1 uniform colours): one persistent batched
-    launch against one launch sequence per query, results compared bit for bit."""
+    launch in the automatic shape and in the shape rr_autotune_batch picks on
+    this query list, against one launch sequence per query; results compared
+    bit for bit."""
     qs = W.query_set(gc, nq, 4, 12, seed)
     n = gc["n"]
     m = len(gc["src"])
     units = sum(units_per_query(q["k"], m) for q in qs)
     with capi.Graph(gc) as G:
+        info = G.info()
         stream = torch.cuda.Stream()
         d_b = torch.zeros((nq, n), dtype=torch.int64, device="cuda")
         d_s = torch.zeros((nq, n), dtype=torch.int64, device="cuda")
         d_st = torch.zeros(nq, dtype=torch.int32, device="cuda")
-        # warm-up with the whole batch (captures graphs, grows the batch buffers)
-        capi.rr_reach_batch_device(G.handle, qs, d_b, None, d_st, stream.cuda_stream)
+
+        def batch_ms(reps=3):
+            capi.rr_reach_batch_device(G.handle, qs, d_b, None, d_st, stream.cuda_stream)
+            stream.synchronize()
+            best = 1e30
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                capi.rr_reach_batch_device(G.handle, qs, d_b, None, d_st, stream.cuda_stream)
+                e1.record(stream)
+                stream.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            return best / 1e3
+        t_auto = batch_ms()
+        t0 = time.perf_counter()
+        tuned = capi.rr_autotune_batch(G.handle, qs)
+        tune_s = time.perf_counter() - t0
+        t_batch = batch_ms()
+        # the batch kernel alone, from the library's per-launch events
+        capi.rr_timing_enable(True)
+        capi.rr_timing_read(reset=True)
+        try:
+            capi.rr_reach_batch_device(G.handle, qs, d_b, None, d_st, stream.cuda_stream)
+            stream.synchronize()
+            kt = capi.rr_timing_read(reset=True)
+        finally:
+            capi.rr_timing_enable(False)
         for q in qs[:8]:
             capi.rr_reach_device(G.handle, q["source"], q["k"], q["seed"], d_s[0], None,
                                  stream.cuda_stream, motif=q["motif"])
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
-            e0.record(stream)
-            capi.rr_reach_batch_device(G.handle, qs, d_b, None, d_st, stream.cuda_stream)
-            e1.record(stream)
-            stream.synchronize()
-            t_batch = e0.elapsed_time(e1) / 1e3
             e0.record(stream)
             for i, q in enumerate(qs):
                 capi.rr_reach_device(G.handle, q["source"], q["k"], q["seed"], d_s[i], None,
@@ -537,12 +597,27 @@ def batched_metrics(capi, torch, gc, nq=256, seed=UNIFORM_SEED):
             stream.synchronize()
             t_single = e0.elapsed_time(e1) / 1e3
         same = bool(torch.equal(d_b, d_s)) and int(d_st.abs().sum().item()) == 0
+    kms, kn = kt.get("batch", (0.0, 0))
+    roof = None
+    if kn:
+        ab, am = batch_kernel_alg(info, qs, tuned["max_chunk"], n)
+        ks = kms / kn / 1e3
+        fa, fh = am / ks / mul_peak, ab / ks / 1e9 / hbm_peak
+        roof = {"kernel": "k_batch", "avg_launch_us": round(ks * 1e6, 1),
+                "alg_gf_mults_per_launch": int(am), "alg_bytes_per_launch": int(ab),
+                "achieved_gmul_s": round(am / ks / 1e9, 2), "alu_frac": round(fa, 4),
+                "achieved_gbs": round(ab / ks / 1e9, 1), "hbm_frac": round(fh, 4),
+                "bound": "alu" if fa >= fh else "hbm",
+                "peak": "the multiply rate measured live (rr_bench_gf_mul) and the measured copy bandwidth"}
     return {"workload": f"{nq} queries on the n=100000 m=1000000 graph with 8 colours, "
                         "k~U{4..12}, odd queries coloured (motif = source colour + k-1 uniform)",
             "queries_per_s": nq / t_batch, "value": units / t_batch, "unit": UNIT,
+            "autotuned_shape": tuned, "autotune_s": round(tune_s, 2),
+            "automatic_shape_queries_per_s": nq / t_auto,
             "one_query_per_launch_queries_per_s": nq / t_single,
             "one_query_per_launch_value": units / t_single,
             "speedup": t_single / t_batch, "bit_exact_vs_single": same,
+            "roofline": roof,
             "launches": "1 persistent kernel (+ z-table, first-layer and bitmap prologue/epilogue)"}
 
 
@@ -1046,7 +1121,8 @@ def main():
         line["dense"]["compact_over_dense"] = line["dense"]["ms_per_query"] / ms_per_step
         line["small"] = small_metrics(capi, torch)
         gu = W.scale_uniform()
-        line["batched"] = batched_metrics(capi, torch, W.scale_uniform(ncolors=8))
+        line["batched"] = batched_metrics(capi, torch, W.scale_uniform(ncolors=8), mul_peak,
+                                          peaks["hbm_gbs"])
         line["served"] = served_metrics(capi, gu)
         line["atmost_k"] = atmost_metrics(capi, torch, gu)
         line["fine_grained"] = fine_metrics(capi, torch, gu)

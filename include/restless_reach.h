@@ -170,15 +170,22 @@ rr_status rr_reach_range_device(const rr_graph *g, const rr_query *q, uint32_t f
  * latency-critical loop that cannot afford the device-wide synchronisation a
  * cudaMalloc/cudaFree brings. It calls no cudaMalloc, cudaFree or other
  * allocating routine: its scratch (z-table, shade table, both prefix-state
- * buffers) is one static device array of 256 MiB in the library, kept by every
- * GPU this entry point is used on until the process exits. The paper has no
- * counterpart; this is a deployment variant of the same sieve.
+ * buffers) is one static device array of 256 MiB in the library, resident on
+ * every device where the library's device code is loaded until the process
+ * exits (with CUDA's default lazy module loading from the first use of that
+ * code on the device; with CUDA_MODULE_LOADING=EAGER on every device the
+ * process creates a context on), and counted as used by cudaMemGetInfo-based
+ * budgets such as rr_server_create's. The paper has no counterpart; this is a
+ * deployment variant of the same sieve.
  * Arguments are those of rr_reach_device; the graph's device must be current.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture
  * starts. Queries whose scratch would exceed 256 MiB (n*k*8 bytes of z-table
- * plus 2 * state_rows * 64 * 8 bytes of state for the smallest point chunk)
- * are rejected with RR_ENOMEM and a message giving both sizes. Every call
+ * plus 2 * state_rows * c * 8 bytes of state for the smallest point chunk, c =
+ * 32 * points per lane: 64 points for k <= 6, 128 from k = 7 unless
+ * rr_set_tuning chose 2 points per lane) are rejected with RR_ENOMEM and a
+ * message giving both sizes. The graph's tuning for k is read under the
+ * graph's lock, so rr_autotune and rr_set_tuning may run beside it. Every call
  * shares the array and clears what must start at zero itself; calls whose
  * work overlaps on the GPU (unordered streams) race on it, so order them on
  * one stream. */
@@ -335,6 +342,33 @@ rr_status rr_server_set_batching(rr_server *s, uint32_t min_batch, uint32_t max_
  * k and stores the winner in the graph; rr_set_tuning forces one. */
 rr_status rr_autotune(rr_graph *g, uint32_t k, uint32_t *best_ppl, uint32_t *best_chunk);
 rr_status rr_set_tuning(rr_graph *g, uint32_t k, uint32_t ppl, uint32_t chunk);
+
+/* Shape of the persistent batch (rr_reach_batch_device and the server's batch
+ * lanes), kept per graph; 0 in a field = the automatic rule.
+ *   blocks_per_sm  kernel variant by the blocks per SM its register budget is
+ *                  set for: 2 (150 registers), 4 (128) or 6 (80, a few spills);
+ *   ranges         1 = fine scheduling ranges (one head run each), 2 = coarse
+ *                  (about 32 row-list entries each);
+ *   max_chunk      largest point chunk of a unit: 128, 256 or 512 (a query with
+ *                  at least 128 points takes chunks of at least 128).
+ * The automatic rule takes coarse ranges with 6 blocks when the first wave's
+ * tasks are at least half the resident warps, else fine ranges with 2, and
+ * chunks up to 512. rr_autotune_batch picks the batch's tile (scheduling range)
+ * and sieve points per block by measurement: it runs the batch qs[0..nq) once
+ * untimed and twice timed per candidate -- the 12 combinations of 2/4/6
+ * blocks, fine/coarse ranges and 256/512-point chunks -- keeps the fastest in
+ * the graph and returns it in *best (may be NULL). Results are bit-identical in
+ * every shape. Uses the graph's scratch (ordered as rr_reach_device). Errors:
+ * RR_EINVAL for a NULL graph, nq == 0 or an invalid query; RR_ENOMEM / RR_ECUDA. */
+typedef struct {
+    uint32_t blocks_per_sm;
+    uint32_t ranges;
+    uint32_t max_chunk;
+} rr_batch_tuning;
+rr_status rr_autotune_batch(rr_graph *g, const rr_query *qs, uint32_t nq, rr_batch_tuning *best);
+/* Forces a batch shape (fields as above; RR_EINVAL for other values). */
+rr_status rr_set_batch_tuning(rr_graph *g, const rr_batch_tuning *t);
+rr_status rr_get_batch_tuning(const rr_graph *g, rr_batch_tuning *out);
 
 /* ---- verification entry points ---------------------------------------------
  * rr_debug_point_sums: per-vertex sums of single sieve points: out[p*n + v] =

@@ -49,6 +49,11 @@ class rr_graph_info(ctypes.Structure):
                 ("head_table", ctypes.c_int)]
 
 
+class rr_batch_tuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_uint32), ("ranges", ctypes.c_uint32),
+                ("max_chunk", ctypes.c_uint32)]
+
+
 class rr_kernel_times(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
 
@@ -68,6 +73,7 @@ EXPORTED = [
     "rr_timing_enable", "rr_timing_read", "rr_reach_device_noalloc", "rr_reach_atmost_device",
     "rr_reach_arrival_device", "rr_extract_path", "rr_reach_sources_device", "rr_bench_gf_mul",
     "rr_debug_wait_probe", "rr_reach_bounded_device", "rr_reach_range_device",
+    "rr_autotune_batch", "rr_set_batch_tuning", "rr_get_batch_tuning",
 ]
 
 _lib = None
@@ -116,6 +122,9 @@ def load(build_if_missing: bool = True):
         "rr_query_times": [vp, u64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)],
         "rr_autotune": [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)],
+        "rr_autotune_batch": [vp, pq, u32, ctypes.POINTER(rr_batch_tuning)],
+        "rr_set_batch_tuning": [vp, ctypes.POINTER(rr_batch_tuning)],
+        "rr_get_batch_tuning": [vp, ctypes.POINTER(rr_batch_tuning)],
         "rr_set_tuning": [vp, u32, u32, u32],
         "rr_debug_point_sums": [vp, pq, vp, u32, vp],
         "rr_debug_graph": [vp, vp, vp, vp, vp],
@@ -377,6 +386,27 @@ def rr_autotune(g, k):
     p, c = ctypes.c_uint32(), ctypes.c_uint32()
     _check(load().rr_autotune(g, int(k), ctypes.byref(p), ctypes.byref(c)))
     return p.value, c.value
+
+
+def rr_autotune_batch(g, queries) -> dict:
+    """Times the persistent batch's shapes on `queries` (dicts as for
+    rr_reach_batch_device), keeps the fastest in the graph and returns it."""
+    arr, keep = _query_array(queries)
+    t = rr_batch_tuning()
+    _check(load().rr_autotune_batch(g, arr, len(queries), ctypes.byref(t)))
+    del keep
+    return {f: getattr(t, f) for f, _ in rr_batch_tuning._fields_}
+
+
+def rr_set_batch_tuning(g, blocks_per_sm=0, ranges=0, max_chunk=0):
+    t = rr_batch_tuning(int(blocks_per_sm), int(ranges), int(max_chunk))
+    _check(load().rr_set_batch_tuning(g, ctypes.byref(t)))
+
+
+def rr_get_batch_tuning(g) -> dict:
+    t = rr_batch_tuning()
+    _check(load().rr_get_batch_tuning(g, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in rr_batch_tuning._fields_}
 
 
 def rr_set_tuning(g, k, ppl, chunk):

@@ -224,9 +224,10 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
 }
 
 // MINB = blocks per SM the register budget is set for: 6 (80 registers, a few
-// spilled) for large batches, where more resident warps hide the tasks'
-// latencies; 2 (no spills) for small batches, whose critical path is the
-// per-task time.
+// spilled) or 4 (128 registers) for large batches, where more resident warps
+// hide the tasks' latencies; 2 (no spills) for small batches, whose critical
+// path is the per-task time. The automatic rule takes 6 for coarse ranges and
+// 2 for fine ones; rr_autotune_batch times all three.
 template <int MINB>
 __global__ void __launch_bounds__(kW2 * 32, MINB) k_batch(const BatchArgs a)
 {
@@ -540,9 +541,11 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             qbytes += need;
             grp.push_back(bq[gi++]);
         }
-        // largest point chunk (<= 512) for which at least one slot fits the rest
-        uint32_t max_chunk = 512;
-        while (max_chunk > 64 && slot_words_for(g, max_chunk) * 8 > budget - std::min(budget, qbytes))
+        // largest point chunk (<= 512, or the tuned one) for which at least one
+        // slot fits the rest
+        uint32_t max_chunk = g.batch_max_chunk ? g.batch_max_chunk : 512;
+        // (not below 128: a query with 4 points per lane takes 128-point chunks)
+        while (max_chunk > 128 && slot_words_for(g, max_chunk) * 8 > budget - std::min(budget, qbytes))
             max_chunk >>= 1;
         if (slot_words_for(g, max_chunk) * 8 + qbytes > budget)
             return fail(RR_ENOMEM, "rr_reach_batch_device: one query and one slot do not fit device memory");
@@ -590,17 +593,16 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         // low; a batch whose first wave would leave resident warps without a
         // task even at the deepest layers takes the fine ranges (one head run
         // each), which shorten each layer's critical path.
-        if (!B.blocks_per_sm) {
+        if (!B.occupancy[2]) {
             int dev = 0;
             RR_CUDA(cudaGetDevice(&dev));
             RR_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, dev));
-            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.blocks_per_sm, k_batch<2>, kW2 * 32, 0));
-            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.blocks_per_sm_wide, k_batch<6>,
-                                                                  kW2 * 32, 0));
-            B.blocks_per_sm = std::max(1, B.blocks_per_sm);
-            B.blocks_per_sm_wide = std::max(1, B.blocks_per_sm_wide);
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.occupancy[2], k_batch<2>, kW2 * 32, 0));
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.occupancy[4], k_batch<4>, kW2 * 32, 0));
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.occupancy[6], k_batch<6>, kW2 * 32, 0));
+            for (int v : {2, 4, 6}) B.occupancy[v] = std::max(1, B.occupancy[v]);
         }
-        const uint64_t resident_warps = (uint64_t)B.sms * B.blocks_per_sm * kW2;
+        const uint64_t resident_warps = (uint64_t)B.sms * B.occupancy[2] * kW2;
         const uint64_t slot_bytes = slot_words_for(g, max_chunk) * 8;
         // as many slots as memory allows (up to every unit at once): units in
         // flight together hide each other's layer-to-layer dependencies
@@ -611,7 +613,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         uint64_t wave_tasks = 0;
         for (size_t i = 0; i < std::min<size_t>(units.size(), nslots); ++i)
             wave_tasks += (uint64_t)g.deep_list.nitems_coarse * (units[i].chunk / (32u * units[i].ppl));
-        const bool coarse = 2 * wave_tasks >= resident_warps;
+        const bool coarse = g.batch_ranges ? g.batch_ranges == 2 : 2 * wave_tasks >= resident_warps;
+        const int minb = g.batch_minb ? (int)g.batch_minb : (coarse ? 6 : 2);
 
         // segments in task order: wave, layer, unit; after a layer that writes
         // prefix state, the unit's carry fix-up segments (phase 1, phase 2)
@@ -831,10 +834,10 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         a.status = status;
         a.timeout_ns = 2000000000ull;
         if (total) {
-            const unsigned blocks =
-                (unsigned)std::max(1, B.sms * (coarse ? B.blocks_per_sm_wide : B.blocks_per_sm));
+            const unsigned blocks = (unsigned)std::max(1, B.sms * B.occupancy[minb]);
             const int bslot = timing_begin(st);
-            if (coarse) k_batch<6><<<blocks, kW2 * 32, 0, st>>>(a);
+            if (minb == 6) k_batch<6><<<blocks, kW2 * 32, 0, st>>>(a);
+            else if (minb == 4) k_batch<4><<<blocks, kW2 * 32, 0, st>>>(a);
             else k_batch<2><<<blocks, kW2 * 32, 0, st>>>(a);
             timing_end(bslot, kTimeBatch, st);
             RR_LAUNCHED();
@@ -972,6 +975,64 @@ rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t se
 // Times each candidate (points per lane, points per chunk) on a plain query of
 // size k from vertex 0 -- the best of interleaved rounds of about 2 ms of
 // queries each -- and keeps the fastest.
+// Times the persistent batch on `qs` for every shape candidate -- kernel
+// variant (2, 4 or 6 blocks per SM), fine or coarse scheduling ranges, largest
+// point chunk 256 or 512 -- best of two runs each after one untimed run, and
+// keeps the fastest in the graph (every later batch on the graph, and the
+// server's batch lanes, use it). Results do not depend on the shape.
+rr_status autotune_batch(Graph &g, const rr_query *qs, uint32_t nq, uint32_t *minb,
+                         uint32_t *ranges, uint32_t *max_chunk)
+{
+    DevBuf W;
+    RR_CUDA(W.reserve((size_t)nq * g.n * 8));
+    cudaEvent_t e0, e1;
+    RR_CUDA(cudaEventCreate(&e0));
+    RR_CUDA(cudaEventCreate(&e1));
+    const uint32_t save[3] = {g.batch_minb, g.batch_ranges, g.batch_max_chunk};
+    uint32_t best[3] = {0, 0, 0};
+    float best_ms = 1e30f;
+    rr_status st = RR_OK;
+    for (uint32_t mb : {2u, 4u, 6u})
+        for (uint32_t rg : {1u, 2u})
+            for (uint32_t mc : {256u, 512u}) {
+                g.batch_minb = mb;
+                g.batch_ranges = rg;
+                g.batch_max_chunk = mc;
+                float cand = 1e30f;
+                for (int rep = 0; rep < 3 && st == RR_OK; ++rep) {
+                    RR_CUDA(cudaEventRecord(e0, g.stream));
+                    st = batch_device(g, qs, nq, nullptr, W.as<uint64_t>(), nullptr, g.stream);
+                    RR_CUDA(cudaEventRecord(e1, g.stream));
+                    RR_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    RR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep > 0) cand = std::min(cand, ms);
+                }
+                if (st != RR_OK) break;
+                if (cand < best_ms) {
+                    best_ms = cand;
+                    best[0] = mb;
+                    best[1] = rg;
+                    best[2] = mc;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != RR_OK) {
+        g.batch_minb = save[0];
+        g.batch_ranges = save[1];
+        g.batch_max_chunk = save[2];
+        return st;
+    }
+    g.batch_minb = best[0];
+    g.batch_ranges = best[1];
+    g.batch_max_chunk = best[2];
+    if (minb) *minb = best[0];
+    if (ranges) *ranges = best[1];
+    if (max_chunk) *max_chunk = best[2];
+    return RR_OK;
+}
+
 rr_status autotune(Graph &g, uint32_t k, uint32_t *best_ppl, uint32_t *best_chunk)
 {
     const uint64_t npts = 1ull << k;

@@ -87,6 +87,8 @@ rr_status debug_wait_probe(uint64_t timeout_ns, int abort_preset, int32_t *statu
                            uint64_t *elapsed_ns);
 rr_status debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *out);
 rr_status autotune(Graph &g, uint32_t k, uint32_t *ppl, uint32_t *chunk);
+rr_status autotune_batch(Graph &g, const rr_query *qs, uint32_t nq, uint32_t *minb,
+                         uint32_t *ranges, uint32_t *max_chunk);
 rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st);
 
@@ -319,6 +321,54 @@ rr_status rr_autotune(rr_graph *g, uint32_t k, uint32_t *best_ppl, uint32_t *bes
     std::lock_guard<std::mutex> lk(g->mu);
     ScratchOrder order(*g, g->stream);
     return autotune(*g, k, best_ppl, best_chunk);
+}
+
+rr_status rr_autotune_batch(rr_graph *g, const rr_query *qs, uint32_t nq, rr_batch_tuning *best)
+{
+    clear_error();
+    if (!g || !qs || nq == 0) return fail(RR_EINVAL, "rr_autotune_batch: NULL graph or no queries");
+    for (uint32_t i = 0; i < nq; ++i) {
+        rr_status s = validate_query(*g, &qs[i]);
+        if (s != RR_OK) return fail(s, "query " + std::to_string(i) + ": " + rr_last_error());
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    ScratchOrder order(*g, g->stream);
+    uint32_t mb = 0, rg = 0, mc = 0;
+    rr_status s = autotune_batch(*g, qs, nq, &mb, &rg, &mc);
+    if (s != RR_OK) return s;
+    if (best) {
+        best->blocks_per_sm = mb;
+        best->ranges = rg;
+        best->max_chunk = mc;
+    }
+    return RR_OK;
+}
+
+rr_status rr_set_batch_tuning(rr_graph *g, const rr_batch_tuning *t)
+{
+    clear_error();
+    if (!g || !t) return fail(RR_EINVAL, "rr_set_batch_tuning: NULL argument");
+    if (t->blocks_per_sm != 0 && t->blocks_per_sm != 2 && t->blocks_per_sm != 4 && t->blocks_per_sm != 6)
+        return fail(RR_EINVAL, "rr_set_batch_tuning: blocks_per_sm must be 0, 2, 4 or 6");
+    if (t->ranges > 2) return fail(RR_EINVAL, "rr_set_batch_tuning: ranges must be 0, 1 or 2");
+    if (t->max_chunk != 0 && t->max_chunk != 128 && t->max_chunk != 256 && t->max_chunk != 512)
+        return fail(RR_EINVAL, "rr_set_batch_tuning: max_chunk must be 0, 128, 256 or 512");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->batch_minb = t->blocks_per_sm;
+    g->batch_ranges = t->ranges;
+    g->batch_max_chunk = t->max_chunk;
+    return RR_OK;
+}
+
+rr_status rr_get_batch_tuning(const rr_graph *g, rr_batch_tuning *out)
+{
+    clear_error();
+    if (!g || !out) return fail(RR_EINVAL, "rr_get_batch_tuning: NULL argument");
+    std::lock_guard<std::mutex> lk(g->mu);
+    out->blocks_per_sm = g->batch_minb;
+    out->ranges = g->batch_ranges;
+    out->max_chunk = g->batch_max_chunk;
+    return RR_OK;
 }
 
 rr_status rr_set_tuning(rr_graph *g, uint32_t k, uint32_t ppl, uint32_t chunk)

@@ -181,8 +181,9 @@ struct BatchBuffers {
     size_t h_cap = 0;
     cudaEvent_t stage_ev = nullptr;
     bool stage_pending = false;
-    int blocks_per_sm = 0;       // occupancy of the persistent kernel (0 = not queried yet)
-    int blocks_per_sm_wide = 0;  // the same for its large-batch variant
+    // occupancy of the persistent kernel's variants (index: the blocks per SM
+    // its register budget is set for; 0 = not queried yet)
+    int occupancy[8] = {0};
     int sms = 0;
     ~BatchBuffers()
     {
@@ -293,6 +294,10 @@ struct Graph {
     uint32_t tune_ppl[32] = {0};
     uint32_t tune_chunk[32] = {0};
     uint64_t tune_gen = 1;
+    // shape of the persistent batch (rr_autotune_batch / rr_set_batch_tuning;
+    // 0 = the automatic rule): kernel variant by blocks per SM (2, 4 or 6),
+    // scheduling ranges (1 fine, 2 coarse) and the largest point chunk
+    uint32_t batch_minb = 0, batch_ranges = 0, batch_max_chunk = 0;
 
     size_t device_bytes() const
     {
@@ -334,6 +339,12 @@ void make_shades(const uint8_t *motif, uint32_t k, ShadeTable *out);
 // the double-buffered state (2 * state_rows * chunk * 8 bytes) fits budget.
 // Returns false if even the smallest chunk does not fit.
 bool choose_shape(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl, uint32_t *chunk);
+// The same with the (ppl, chunk) preference given explicitly (0 = automatic)
+// instead of read from the graph's tuning; shape_ppl is the points per lane it
+// uses (the smallest chunk is 32 * that many points).
+bool choose_shape_tuned(const Graph &g, uint32_t k, uint64_t budget, uint32_t tune_ppl,
+                        uint32_t tune_chunk, uint32_t *ppl, uint32_t *chunk);
+uint32_t shape_ppl(uint32_t k, uint32_t tune_ppl);
 
 // -------- kernels (rr_sieve.cu) --------------------------------------------
 struct LayerParams;

@@ -11,13 +11,17 @@
 // calls no cudaMalloc, cudaFree or other allocating routine.
 //
 // The scratch is the file-scope array below (kNoAllocScratchBytes = 256 MiB).
-// Every GPU on which this entry point is used keeps that array for the life of
-// the process. The array is shared by every call: a call reuses what the
-// previous call left there and clears what must start at zero itself (the zero
-// state row of both prefix buffers; the witness output is cleared too), so calls
-// whose work overlaps on the GPU -- for instance calls issued on different
-// streams without ordering between them -- race on the array and give wrong
-// results. Order such calls on one stream.
+// It is resident on every device where this library's device code is loaded,
+// for the life of the process: under CUDA's default lazy module loading from
+// the first use of this file's device code on that device, under eager loading
+// (CUDA_MODULE_LOADING=EAGER) on every device where the process creates a
+// context. Device-memory budgets computed from cudaMemGetInfo see it as used.
+// The array is shared by every call: a call reuses what the previous call left
+// there and clears what must start at zero itself (the zero state row of both
+// prefix buffers; the witness output is cleared too), so calls whose work
+// overlaps on the GPU -- for instance calls issued on different streams without
+// ordering between them -- race on the array and give wrong results. Order such
+// calls on one stream.
 #include <mutex>
 
 #include "rr_internal.h"
@@ -51,6 +55,16 @@ static rr_status noalloc_scratch(int dev, uint64_t **out)
     return RR_OK;
 }
 
+// Copies a motif's shade table (a kernel argument, so no host memory is read
+// by a copy) into its place in the scratch array.
+__global__ void k_put_shades(const ShadeTable sh, uint32_t *__restrict__ dst)
+{
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) {
+        dst[i] = sh.first[i];
+        dst[256 + i] = sh.mu[i];
+    }
+}
+
 }  // namespace rr
 
 using namespace rr;
@@ -82,13 +96,25 @@ extern "C" rr_status rr_reach_device_noalloc(const rr_graph *g, const rr_query *
         return fail(RR_ENOMEM, "rr_reach_device_noalloc: the z-table of this query (" +
                                    std::to_string(fixed_bytes) + " bytes) exceeds the " +
                                    std::to_string(kNoAllocScratchBytes) + "-byte static scratch");
+    // the graph's tuning for k, read under its lock (rr_autotune and
+    // rr_set_tuning change it there)
+    uint32_t tune_ppl = 0, tune_chunk = 0;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        tune_ppl = g->tune_ppl[k];
+        tune_chunk = g->tune_chunk[k];
+    }
     uint32_t ppl = 0, chunk = 0;
-    if (!choose_shape(*g, k, kNoAllocScratchBytes - fixed_bytes, &ppl, &chunk))
+    if (!choose_shape_tuned(*g, k, kNoAllocScratchBytes - fixed_bytes, tune_ppl, tune_chunk, &ppl,
+                            &chunk)) {
+        const uint64_t unit = 32ull * shape_ppl(k, tune_ppl);  // the smallest point chunk
         return fail(RR_ENOMEM,
                     "rr_reach_device_noalloc: this graph needs " +
-                        std::to_string(fixed_bytes + 2ull * g->state_rows * 64 * 8) +
-                        " bytes of scratch for the smallest point chunk, more than the " +
-                        std::to_string(kNoAllocScratchBytes) + "-byte static scratch");
+                        std::to_string(fixed_bytes + 2ull * g->state_rows * unit * 8) +
+                        " bytes of scratch for the smallest point chunk (" + std::to_string(unit) +
+                        " points), more than the " + std::to_string(kNoAllocScratchBytes) +
+                        "-byte static scratch");
+    }
     uint64_t *d_z = scratch;
     uint32_t *d_shades = reinterpret_cast<uint32_t *>(scratch + z_words);
     uint64_t *d_state = scratch + z_words + shade_words;
@@ -97,7 +123,8 @@ extern "C" rr_status rr_reach_device_noalloc(const rr_graph *g, const rr_query *
     if (q->motif) {
         ShadeTable sh;
         make_shades(q->motif, k, &sh);
-        RR_CUDA(cudaMemcpyAsync(d_shades, &sh, sizeof sh, cudaMemcpyHostToDevice, st));
+        k_put_shades<<<1, 256, 0, st>>>(sh, d_shades);
+        RR_LAUNCHED();
     }
     s = launch_ztable(*g, k, make_keys(q->seed), q->motif != nullptr, d_shades, d_z, st);
     if (s != RR_OK) return s;

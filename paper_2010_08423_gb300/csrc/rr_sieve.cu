@@ -327,10 +327,21 @@ rr_status validate_query(const Graph &g, const rr_query *q)
 bool choose_shape(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl_out,
                   uint32_t *chunk_out)
 {
+    return choose_shape_tuned(g, k, budget, g.tune_ppl[k], g.tune_chunk[k], ppl_out, chunk_out);
+}
+
+uint32_t shape_ppl(uint32_t k, uint32_t tune_ppl)
+{
+    return tune_ppl ? tune_ppl : ((1ull << k) >= 128 ? 4u : 2u);
+}
+
+bool choose_shape_tuned(const Graph &g, uint32_t k, uint64_t budget, uint32_t tune_ppl,
+                        uint32_t tune_chunk, uint32_t *ppl_out, uint32_t *chunk_out)
+{
     const uint64_t npts = 1ull << k;
-    uint32_t ppl = g.tune_ppl[k] ? g.tune_ppl[k] : (npts >= 128 ? 4u : 2u);
+    uint32_t ppl = shape_ppl(k, tune_ppl);
     uint64_t unit = 32ull * ppl;
-    uint64_t want = g.tune_chunk[k] ? g.tune_chunk[k] : npts;
+    uint64_t want = tune_chunk ? tune_chunk : npts;
     if (want < unit) want = unit;
     if (want > 2048) want = 2048;
     want = (want + unit - 1) / unit * unit;

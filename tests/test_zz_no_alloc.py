@@ -45,6 +45,47 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row():
             assert np.array_equal(got_bm, want_bm)
 
 
+def test_noalloc_several_point_chunks_through_the_shared_array():
+    """A shape with 64-point chunks (rr_set_tuning) makes a k = 9 query run 8
+    chunks, each reusing the same prefix buffers inside the static array; the
+    result must still equal the allocating entry point's, twice in a row."""
+    import torch
+
+    torch.cuda.set_device(0)
+    capi.load()
+    g = W.uniform(3000, 40_000, 40, 0, 6, 424243, ncolors=3)
+    n = g["n"]
+    with capi.Graph(g) as G:
+        capi.rr_set_tuning(G.handle, 9, 2, 64)
+        stream = torch.cuda.Stream()
+        for seed in (21, 22):
+            _, want_w = G.reach(2, 9, seed)
+            assert np.count_nonzero(want_w) > 0
+            d_w = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+            capi.rr_reach_device_noalloc(G.handle, 2, 9, seed, d_w, None, stream.cuda_stream)
+            stream.synchronize()
+            assert np.array_equal(d_w.cpu().numpy().view(np.uint64), want_w)
+
+
+def test_noalloc_rejects_state_beyond_the_static_scratch():
+    """A small graph (tiny z-table) whose windows cover almost every row: the
+    prefix state of the smallest point chunk (2 x rows x 64 points x 8 bytes)
+    does not fit the 256 MiB array."""
+    import torch
+
+    capi.load()
+    g = W.uniform(1000, 400_000, 20, 5, 10, 424244)
+    with capi.Graph(g) as G:
+        info = G.info()
+        assert 2 * info["state_rows"] * 64 * 8 > 256 << 20
+        d_w = torch.zeros(g["n"], dtype=torch.int64, device="cuda")
+        with pytest.raises(capi.RRError) as ei:
+            capi.rr_reach_device_noalloc(G.handle, 0, 5, 1, d_w)
+        assert ei.value.status == capi.RR_ENOMEM
+        msg = capi.rr_last_error()
+        assert "smallest point chunk (64 points)" in msg and "static scratch" in msg
+
+
 def test_noalloc_rejects_queries_beyond_the_static_scratch():
     capi.load()
     # n * k * 8 bytes of z-table alone exceed the 256 MiB scratch
