@@ -160,6 +160,43 @@ __device__ __forceinline__ void pair_form(const Val &sq, uint32_t k, uint32_t pb
     }
 }
 
+// pair_form with the pair values spread over the warp (lane l holds values l
+// and l + 32, at most 64 values: k <= 10), read by shuffles that every lane
+// executes (only the XORs depend on the lane's points).
+template <int PPL>
+__device__ __forceinline__ void pair_form_shfl(uint64_t d0, uint64_t d1, uint32_t k, uint32_t pbits,
+                                               uint64_t (&out)[PPL])
+{
+    constexpr uint32_t LOGP = PPL == 4 ? 2 : 1;
+    auto sq = [&](uint32_t q) { return q < 32u ? shfl64b(d0, (int)q) : shfl64b(d1, (int)(q - 32u)); };
+    uint64_t base = 0, t0 = sq(0), t1 = 0, s01 = 0;
+    if constexpr (LOGP == 2) {
+        t1 = sq(2);
+        s01 = sq(1);
+    }
+    for (uint32_t i = LOGP; i < k; ++i) {  // warp-uniform
+        const uint32_t r = i * (i + 1) / 2;
+        uint64_t row = sq(r + i);
+        for (uint32_t j = LOGP; j < i; ++j) {  // warp-uniform
+            const uint64_t v = sq(r + j);
+            if ((pbits >> j) & 1u) row ^= v;
+        }
+        const uint64_t v0 = sq(r);
+        const uint64_t v1 = LOGP == 2 ? sq(r + 1) : 0ull;
+        if ((pbits >> i) & 1u) {
+            base ^= row;
+            t0 ^= v0;
+            if constexpr (LOGP == 2) t1 ^= v1;
+        }
+    }
+    out[0] = base;
+    out[1] = base ^ t0;
+    if constexpr (PPL == 4) {
+        out[2] = base ^ t1;
+        out[3] = base ^ t0 ^ t1 ^ s01;
+    }
+}
+
 // x_h^L x_s^L for deep-row head rank r and the lane's PPL points of point
 // group `group` of the chunk: the factor layer 4 applies to pair windows of
 // h's rows (one table per chunk, one product per head and point).
@@ -426,7 +463,15 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     // the window's pair values: rows b and a of u's segment
                     const uint32_t np = pair_count(k);
                     const uint64_t *pa = p.pr3 + (size_t)a * np, *pb = p.pr3 + (size_t)b * np;
-                    pair_form<PPL>([&](uint32_t q) { return __ldg(pb + q) ^ __ldg(pa + q); }, k, pbits, w);
+                    if (np <= 64) {
+                        // lane l holds pair values l and l + 32 (coalesced loads), read by shuffle
+                        const uint32_t q0 = (uint32_t)lane, q1 = q0 + 32u;
+                        const uint64_t d0 = q0 < np ? (__ldg(pb + q0) ^ __ldg(pa + q0)) : 0ull;
+                        const uint64_t d1 = q1 < np ? (__ldg(pb + q1) ^ __ldg(pa + q1)) : 0ull;
+                        pair_form_shfl<PPL>(d0, d1, k, pbits, w);
+                    } else {
+                        pair_form<PPL>([&](uint32_t q) { return __ldg(pb + q) ^ __ldg(pa + q); }, k, pbits, w);
+                    }
                     // times x_u^L x_s^L: from the chunk's head-factor table, or
                     // formed here (u = the tail, m_src its vertex or head rank)
                     const uint32_t ut = __shfl_sync(0xffffffffu, m_src, (int)t);
@@ -740,14 +785,26 @@ __device__ __forceinline__ void fixup_phase1(uint64_t *__restrict__ buf, uint32_
                                              uint32_t e, uint32_t tid, uint32_t nthreads)
 {
     constexpr uint32_t R = RowList::kMaxRun;
+    constexpr uint32_t kAhead = 8;  // pieces whose last rows are loaded together
     for (uint32_t c = tid; c < width; c += nthreads) {
         uint64_t carry = ld_state<COHERENT>(buf + (size_t)(b + R) * width + c);  // piece 0's last row
-        for (uint32_t ps = b + R; ps < e; ps += R) {
-            const uint32_t pe = min(e, ps + R);  // piece [ps, pe): rows ps+1 .. pe
-            uint64_t *last = buf + (size_t)pe * width + c;
-            const uint64_t fixed = ld_state<COHERENT>(last) ^ carry;
-            *last = fixed;
-            carry = fixed;
+        for (uint32_t ps0 = b + R; ps0 < e; ps0 += kAhead * R) {
+            // the last rows of up to kAhead pieces [ps, pe) (rows ps+1 .. pe) are
+            // independent loads; only the running XOR is a chain
+            uint64_t v[kAhead];
+#pragma unroll
+            for (uint32_t i = 0; i < kAhead; ++i) {
+                const uint32_t ps = ps0 + i * R;
+                v[i] = ps < e ? ld_state<COHERENT>(buf + (size_t)min(e, ps + R) * width + c) : 0ull;
+            }
+#pragma unroll
+            for (uint32_t i = 0; i < kAhead; ++i) {
+                const uint32_t ps = ps0 + i * R;
+                if (ps < e) {
+                    carry ^= v[i];
+                    buf[(size_t)min(e, ps + R) * width + c] = carry;
+                }
+            }
         }
     }
 }
