@@ -472,7 +472,7 @@ bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl_
     const uint32_t ppl = g.tune_ppl[k] ? g.tune_ppl[k] : (npts >= 128 ? 4u : 2u);
     const uint64_t unit = 32ull * ppl;
     uint64_t want = g.tune_chunk[k] ? g.tune_chunk[k] : npts;
-    want = std::max<uint64_t>(unit, std::min<uint64_t>(want, 4 * unit));  // <= 4 groups
+    want = std::max<uint64_t>(unit, std::min<uint64_t>(want, 8 * unit));  // <= 8 groups
     want = (want + unit - 1) / unit * unit;
     while (want > unit && v2_scratch_bytes(g, ppl, (uint32_t)want, k) > budget) want -= unit;
     if (v2_scratch_bytes(g, ppl, (uint32_t)want, k) > budget) return false;

@@ -160,15 +160,37 @@ __device__ __forceinline__ void pair_form(const Val &sq, uint32_t k, uint32_t pb
     }
 }
 
-// pair_form with the pair values spread over the warp (lane l holds values l
-// and l + 32, at most 64 values: k <= 10), read by shuffles that every lane
-// executes (only the XORs depend on the lane's points).
-template <int PPL>
-__device__ __forceinline__ void pair_form_shfl(uint64_t d0, uint64_t d1, uint32_t k, uint32_t pbits,
+// pair_form with the pair values spread over the warp: lane l holds value
+// l + 32 s in d[s] (two slots: up to 64 values, k <= 10; with more values the
+// layer reads them by broadcast loads, which measured faster there), read by
+// shuffles that every lane executes (only the XORs depend on the lane's points;
+// the slot of a value is warp-uniform, so exactly one shuffle runs per value).
+template <int NS>
+__device__ __forceinline__ uint64_t shfl_slot(const uint64_t (&d)[NS], uint32_t q)
+{
+    static_assert(NS == 2, "two slots (k <= 10)");
+    const int l = (int)(q & 31u);
+    return q < 32u ? shfl64b(d[0], l) : shfl64b(d[1], l);
+}
+
+template <int NS>
+__device__ __forceinline__ void pair_window_regs(const uint64_t *__restrict__ pr3, uint32_t a, uint32_t b,
+                                                 uint32_t np, int lane, uint64_t (&d)[NS])
+{
+    const uint64_t *pa = pr3 + (size_t)a * np, *pb = pr3 + (size_t)b * np;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const uint32_t q = 32u * s + (uint32_t)lane;
+        d[s] = q < np ? (__ldg(pb + q) ^ __ldg(pa + q)) : 0ull;
+    }
+}
+
+template <int PPL, int NS>
+__device__ __forceinline__ void pair_form_shfl(const uint64_t (&d)[NS], uint32_t k, uint32_t pbits,
                                                uint64_t (&out)[PPL])
 {
     constexpr uint32_t LOGP = PPL == 4 ? 2 : 1;
-    auto sq = [&](uint32_t q) { return q < 32u ? shfl64b(d0, (int)q) : shfl64b(d1, (int)(q - 32u)); };
+    auto sq = [&](uint32_t q) { return shfl_slot<NS>(d, q); };
     uint64_t base = 0, t0 = sq(0), t1 = 0, s01 = 0;
     if constexpr (LOGP == 2) {
         t1 = sq(2);
@@ -463,12 +485,11 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     // the window's pair values: rows b and a of u's segment
                     const uint32_t np = pair_count(k);
                     const uint64_t *pa = p.pr3 + (size_t)a * np, *pb = p.pr3 + (size_t)b * np;
-                    if (np <= 64) {
-                        // lane l holds pair values l and l + 32 (coalesced loads), read by shuffle
-                        const uint32_t q0 = (uint32_t)lane, q1 = q0 + 32u;
-                        const uint64_t d0 = q0 < np ? (__ldg(pb + q0) ^ __ldg(pa + q0)) : 0ull;
-                        const uint64_t d1 = q1 < np ? (__ldg(pb + q1) ^ __ldg(pa + q1)) : 0ull;
-                        pair_form_shfl<PPL>(d0, d1, k, pbits, w);
+                    if (np <= 64) {  // k <= 10
+                        // the window's values spread over the warp by coalesced loads
+                        uint64_t d[2];
+                        pair_window_regs<2>(p.pr3, a, b, np, lane, d);
+                        pair_form_shfl<PPL, 2>(d, k, pbits, w);
                     } else {
                         pair_form<PPL>([&](uint32_t q) { return __ldg(pb + q) ^ __ldg(pa + q); }, k, pbits, w);
                     }
@@ -842,7 +863,7 @@ __device__ __forceinline__ void fixup_phase2(uint64_t *__restrict__ buf, uint32_
 // group's fixed high labels j' (slot lg), and the warp XOR-reduces into S[v].
 // ---------------------------------------------------------------------------
 template <int LG, bool COHERENT>
-__device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
+__device__ __forceinline__ void last_pass(const V2Params &p, uint32_t task, uint32_t g0, bool first)
 {
     const int lane = threadIdx.x & 31;
     const uint2 it = p.items[task];
@@ -850,11 +871,14 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
     const uint64_t key_y = p.qd->key_y;
     uint64_t *const S = p.qd->S;
     uint64_t *const E = p.qd->E;  // per-edge sums wanted (fine-grained output)
-    const uint32_t slots = p.ngroups * (LG + 1);
+    constexpr uint32_t kGroupsPerPass = 32 / (LG + 1);
+    const uint32_t row_slots = p.ngroups * (LG + 1);  // stored values per transformed row
+    const uint32_t slots = min(kGroupsPerPass, p.ngroups - g0) * (LG + 1);  // this pass's
     const bool active = (uint32_t)lane < slots;
-    const uint32_t g = (uint32_t)lane / (LG + 1);
-    const uint32_t j = (uint32_t)lane - g * (LG + 1);
+    const uint32_t g = g0 + (uint32_t)lane / (LG + 1);
+    const uint32_t j = (uint32_t)lane % (LG + 1);
     const uint32_t gbase = p.chunk_base + g * (1u << LG);
+    const uint32_t col = g0 * (LG + 1) + (uint32_t)lane;
 
     auto zsel_of = [&](uint32_t v) -> uint64_t {
         if (!active) return 0ull;
@@ -884,7 +908,7 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
         const uint32_t m_eid = has ? p.eid[ent] : 0u;
         const uint64_t m_y = has ? sm_draw(key_y, (uint64_t)m_eid * 32u + (p.layer - 1u)) : 0ull;
         if constexpr (!COHERENT) {
-            if (base == it.x) pdl_enter();  // the transformed state is read from here on
+            if (first && base == it.x) pdl_enter();  // the transformed state is read from here on
         }
         const uint32_t nb = min(32u, it.y - base);
         for (uint32_t t = 0; t < nb; ++t) {
@@ -900,14 +924,14 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
             const uint64_t y = shfl64b(m_y, (int)t);
             uint64_t yt = 0;
             if (active) {
-                const uint64_t *sa = p.st_in + (size_t)a * slots + lane;
-                const uint64_t *sb = p.st_in + (size_t)b * slots + lane;
+                const uint64_t *sa = p.st_in + (size_t)a * row_slots + col;
+                const uint64_t *sb = p.st_in + (size_t)b * row_slots + col;
                 const uint64_t tv = COHERENT ? (__ldcg(sa) ^ __ldcg(sb)) : (*sa ^ *sb);
                 yt = rr_mul(y, tv);
                 acc ^= yt;
             }
             if (E) {
-                // this entry's own sum over the chunk's points: the flush's
+                // this entry's own sum over the pass's points: the flush's
                 // product taken per entry instead of per head
                 uint64_t c = active ? rr_mul(zsel, yt) : 0ull;
 #pragma unroll
@@ -919,6 +943,17 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
         }
     }
     flush(cur);
+}
+
+// A warp covers 32 / (LG + 1) point groups at a time (one lane per stored
+// value); a chunk with more groups takes several passes over the rows.
+template <int LG, bool COHERENT>
+__device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
+{
+    constexpr uint32_t kGroupsPerPass = 32 / (LG + 1);
+#pragma unroll 1
+    for (uint32_t g0 = 0; g0 < p.ngroups; g0 += kGroupsPerPass)
+        last_pass<LG, COHERENT>(p, task, g0, g0 == 0);
 }
 
 }  // namespace rr
