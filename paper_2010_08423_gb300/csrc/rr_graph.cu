@@ -510,6 +510,28 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         if (!fix2.empty())
             RR_CUDA(cudaMemcpyAsync(R.fix2.p, fix2.data(), fix2.size() * sizeof(uint2),
                                     cudaMemcpyHostToDevice, st));
+        if (&R == &g.deep_list) {
+            // carry slots of the pieces after the first of every cut segment
+            std::vector<uint32_t> row_carry(R.count + 1, 0u), slot0(std::max<size_t>(1, chains.size()), 0u);
+            uint32_t next = 1;  // slot 0: the zero row
+            for (size_t c = 0; c < chains.size(); ++c) {
+                const uint32_t R_ = RowList::kMaxRun;
+                slot0[c] = next;
+                for (uint32_t b = chains[c].x + R_, piece = 0; b < chains[c].y; b += R_, ++piece) {
+                    const uint32_t e = std::min(chains[c].y, b + R_);
+                    for (uint32_t ent = b; ent < e; ++ent) row_carry[ent + 1] = next + piece;
+                }
+                next += (chains[c].y - chains[c].x + R_ - 1) / R_ - 1;
+            }
+            R.ncarry = next;
+            RR_CUDA(R.row_carry.reserve(row_carry.size() * 4));
+            RR_CUDA(cudaMemcpyAsync(R.row_carry.p, row_carry.data(), row_carry.size() * 4,
+                                    cudaMemcpyHostToDevice, st));
+            RR_CUDA(R.chain_slot0.reserve(slot0.size() * 4));
+            RR_CUDA(cudaMemcpyAsync(R.chain_slot0.p, slot0.data(), slot0.size() * 4,
+                                    cudaMemcpyHostToDevice, st));
+            RR_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+        }
         R.nitems = (uint32_t)items.size();
         R.nitems_coarse = (uint32_t)coarse.size();
         if (&R == &g.deep_list) {

@@ -159,6 +159,14 @@ struct RowList {
     uint32_t nchains = 0;
     DevBuf fix2;            // uint2 (chain, first row slot) of every phase-2 fix-up task
     uint32_t nfix2 = 0;
+    // deep list only, for the one-query kernels' per-point state: instead of
+    // fixing the later pieces' rows in place, the fix-up stores the carry into
+    // every piece after the first (one row of a carry table per piece, slot 0
+    // a zero row) and readers add the carries of both window ends. row_carry
+    // (count + 1 entries, by state row) = the carry slot of the row's piece;
+    // chain_slot0 (per chain) = the slot of its second piece.
+    DevBuf row_carry, chain_slot0;
+    uint32_t ncarry = 1;    // carry slots including the zero slot
     // deep list only: the distinct heads of its rows (in row order) and, per
     // entry, the rank there of its tail u (the head of the rows its window
     // covers; UINT32_MAX when u heads none)
@@ -168,7 +176,7 @@ struct RowList {
     {
         return head.bytes + eid.bytes + src.bytes + a0.bytes + b0.bytes + a1.bytes + b1.bytes +
                a3.bytes + b3.bytes + items.bytes + items_coarse.bytes + chains.bytes + fix2.bytes +
-               heads.bytes + trank.bytes;
+               heads.bytes + trank.bytes + row_carry.bytes + chain_slot0.bytes;
     }
 };
 

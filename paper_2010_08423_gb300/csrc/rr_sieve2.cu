@@ -72,6 +72,7 @@ struct ZeroRows {
     uint32_t n, chunk, rstride, kpr2;
     uint64_t *pr3;
     uint32_t npr3;
+    uint64_t *carry;  // the carry table's zero row (chunk values) or null
 };
 
 __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, const ZeroRows &z)
@@ -92,6 +93,8 @@ __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, cons
         for (uint32_t i = tid; i < z.kpr2; i += stride) z.pr2[i] = 0;
     if (z.pr3)
         for (uint32_t i = tid; i < z.npr3; i += stride) z.pr3[i] = 0;
+    if (z.carry)
+        for (uint32_t i = tid; i < z.chunk; i += stride) z.carry[i] = 0;
 }
 
 // Layer 1; its grid also clears what zero_rows lists (saving a launch).
@@ -134,6 +137,17 @@ __global__ void k_fix2(const uint2 *__restrict__ chains, const uint2 *__restrict
     const uint2 t = tasks[blockIdx.x];
     const uint2 ch = chains[t.x];
     fixup_phase2<false>(buf, width, ch.x, ch.y, t.y, threadIdx.x, blockDim.x);
+}
+
+// The carry table of the deep list's per-point state (rr_v2_device.cuh
+// carry_rows): one block per cut segment.
+__global__ void k_carry(const uint2 *__restrict__ chains, const uint32_t *__restrict__ slot0,
+                        uint32_t nchains, const uint64_t *buf, uint64_t *carry, uint32_t width)
+{
+    pdl_enter();
+    if (blockIdx.x >= nchains) return;
+    const uint2 ch = chains[blockIdx.x];
+    carry_rows(buf, carry, width, ch.x, ch.y, slot0[blockIdx.x], threadIdx.x, blockDim.x);
 }
 
 static rr_status launch_fixup(const RowList &L, uint64_t *buf, uint32_t width, cudaStream_t st,
@@ -298,6 +312,13 @@ static bool head_table(const Graph &g)
     return 2ull * g.deep_list.nheads <= g.deep_compute_rows;
 }
 
+// Words of the carry table of the deep list's per-point state (zero when no
+// head segment of the deep list is cut or no layer keeps per-point state there).
+static uint64_t carry_words(const Graph &g, uint32_t chunk, uint32_t k)
+{
+    return (k >= 6 && g.deep_list.nchains) ? (uint64_t)g.deep_list.ncarry * chunk : 0;
+}
+
 static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
                       uint64_t *pr2_w, uint64_t *pr3_w, uint64_t *tx_w, uint64_t *full_w,
                       uint64_t *red_w)
@@ -317,7 +338,7 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 {
     uint64_t py_w, pr2_w, pr3_w, tx_w, full_w, red_w;
     v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &tx_w, &full_w, &red_w);
-    return (py_w + pr2_w + pr3_w + tx_w + 2 * full_w + red_w) * 8ull + 4096;
+    return (py_w + pr2_w + pr3_w + tx_w + 2 * full_w + red_w + carry_words(g, chunk, k)) * 8ull + 4096;
 }
 
 // z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades); rows
@@ -402,6 +423,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     uint64_t *full0 = tx + tx_w;
     uint64_t *full1 = full0 + full_w;
     uint64_t *red = full1 + full_w;
+    uint64_t *carry = carry_words(g, chunk, k) ? red + red_w : nullptr;
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
 
     {
@@ -418,7 +440,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     // the first layer's grid when it runs
     const ZeroRows zr{k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
                       k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, rstride, k,
-                      pair ? pr3 : nullptr, pair_count(k)};
+                      pair ? pr3 : nullptr, pair_count(k), carry};
     const bool zero_in_first = k >= 3 && g.prod_list.nitems > 0;
     if (!zero_in_first) {
         RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, d_desc, zr));
@@ -556,6 +578,9 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             vp.layer = l;
             vp.st_in = bufs[(l - 1) & 1u];
             vp.st_out = out == 1 ? red : bufs[l & 1u];
+            // per-point state read from the previous layer carries lazily
+            vp.carry = src == 0 ? carry : nullptr;
+            vp.row_carry = carry ? g.deep_list.row_carry.as<uint32_t>() : nullptr;
             if (src == 2 && out == 0 && ppl == 4) {
                 // layer 3 writing full state: the lane-to-point map does not
                 // change the stored rows, and 2 points per lane halve the
@@ -568,9 +593,18 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             }
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;
-            s = launch_fixup(src == 1 ? g.state_list : g.deep_list, vp.st_out,
-                             out == 1 ? rstride : chunk, st, &nk);
-            if (s != RR_OK) return s;
+            if (carry && out == 0 && src != 1) {
+                // per-point state of the deep list: the carry table, read by the next layer
+                RR_CUDA(launch_pdl(k_carry, dim3(g.deep_list.nchains), dim3(128), st,
+                                   g.deep_list.chains.as<uint2>(), g.deep_list.chain_slot0.as<uint32_t>(),
+                                   g.deep_list.nchains, (const uint64_t *)vp.st_out, carry, chunk));
+                RR_LAUNCHED();
+                ++nk;
+            } else {
+                s = launch_fixup(src == 1 ? g.state_list : g.deep_list, vp.st_out,
+                                 out == 1 ? rstride : chunk, st, &nk);
+                if (s != RR_OK) return s;
+            }
         }
         // layer k-1 from the transformed state (state-row indices when k = 4)
         if (k == 4) set_list(vp, g.tail_list, 1);

@@ -64,6 +64,11 @@ struct V2Params {
     uint64_t *tx;           // x_h^L x_s^L per deep-row head h (rank order) and point, stride chunk
     const uint64_t *st_in;  // full state, stride chunk
     uint64_t *st_out;       // full (stride chunk) or reduced (stride ngroups*(lg+1))
+    // st_in's cut head segments carry lazily (one-query kernels): row r's true
+    // prefix is st_in[r] ^ carry[row_carry[r]] (carry row 0 is zero); null:
+    // st_in holds true prefixes
+    const uint32_t *row_carry;
+    const uint64_t *carry;
 };
 
 // z_{u,j}: from the table when the query has one (motif queries, Eq. 3), else
@@ -412,6 +417,14 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
         const uint32_t m_head = has ? p.head[ent] : 0u;
         const uint32_t m_a = has ? p.ia[ent] : 0u;
         const uint32_t m_b = has ? p.ib[ent] : 0u;
+        // carry slots of the window's end rows (lazily carried input state)
+        uint32_t m_ca = 0, m_cb = 0;
+        if constexpr (!FROM_Y && !FROM_R2 && !PAIR) {
+            if (p.carry && has) {
+                m_ca = p.row_carry[m_a];
+                m_cb = p.row_carry[m_b];
+            }
+        }
         uint64_t m_coef = 0;
         uint32_t m_src = 0;
         if (has) {
@@ -532,6 +545,26 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                         const ulonglong2 a0 = COHERENT ? __ldcg(va) : __ldg(va);
                         const ulonglong2 b0 = COHERENT ? __ldcg(vb) : __ldg(vb);
                         w[0] = a0.x ^ b0.x; w[1] = a0.y ^ b0.y;
+                    }
+                    if constexpr (!COHERENT) {
+                        // window ends in different pieces of a cut head segment:
+                        // their carries differ by the pieces' totals between them
+                        const uint32_t ca = __shfl_sync(0xffffffffu, m_ca, (int)t);
+                        const uint32_t cb = __shfl_sync(0xffffffffu, m_cb, (int)t);
+                        if (ca != cb) {  // warp-uniform
+                            const ulonglong2 *ka =
+                                reinterpret_cast<const ulonglong2 *>(p.carry + (size_t)ca * p.chunk + col);
+                            const ulonglong2 *kb =
+                                reinterpret_cast<const ulonglong2 *>(p.carry + (size_t)cb * p.chunk + col);
+                            const ulonglong2 x0 = __ldg(ka), y0 = __ldg(kb);
+                            w[0] ^= x0.x ^ y0.x;
+                            w[1] ^= x0.y ^ y0.y;
+                            if constexpr (PPL == 4) {
+                                const ulonglong2 x1 = __ldg(ka + 1), y1 = __ldg(kb + 1);
+                                w[2] ^= x1.x ^ y1.x;
+                                w[3] ^= x1.y ^ y1.y;
+                            }
+                        }
                     }
                 }
 #pragma unroll
@@ -853,6 +886,39 @@ __device__ __forceinline__ void fixup_phase2(uint64_t *__restrict__ buf, uint32_
         const uint32_t row = ps + 1 + slot % (R - 1);
         if (row >= min(e, ps + R)) continue;  // past a short last piece, or its last row
         buf[(size_t)row * width + c] ^= ld_state<COHERENT>(buf + (size_t)ps * width + c);
+    }
+}
+
+// Lazy form of phase 1 for the one-query kernels' per-point state: instead of
+// fixing rows in place, writes for every piece p >= 1 of the cut segment [b, e)
+// the carry into it -- the XOR of the totals (last rows) of pieces 0..p-1 --
+// to row slot0 + p - 1 of the carry table; readers add it (V2Params::carry).
+__device__ __forceinline__ void carry_rows(const uint64_t *__restrict__ buf, uint64_t *__restrict__ carry,
+                                           uint32_t width, uint32_t b, uint32_t e, uint32_t slot0,
+                                           uint32_t tid, uint32_t nthreads)
+{
+    constexpr uint32_t R = RowList::kMaxRun;
+    constexpr uint32_t kAhead = 8;  // pieces whose last rows are loaded together
+    for (uint32_t c = tid; c < width; c += nthreads) {
+        uint64_t acc = 0;
+        uint32_t slot = slot0;
+        // piece p-1 = entries [b + (p-1)R, b + pR): its last row is b + pR
+        for (uint32_t ps0 = b + R; ps0 < e; ps0 += kAhead * R) {
+            uint64_t v[kAhead];
+#pragma unroll
+            for (uint32_t i = 0; i < kAhead; ++i) {
+                const uint32_t ps = ps0 + i * R;  // the start entry of piece p
+                v[i] = ps < e ? buf[(size_t)ps * width + c] : 0ull;
+            }
+#pragma unroll
+            for (uint32_t i = 0; i < kAhead; ++i) {
+                if (ps0 + i * R < e) {
+                    acc ^= v[i];
+                    carry[(size_t)slot * width + c] = acc;
+                    ++slot;
+                }
+            }
+        }
     }
 }
 
