@@ -316,7 +316,7 @@ static bool head_table(const Graph &g)
 // head segment of the deep list is cut or no layer keeps per-point state there).
 static uint64_t carry_words(const Graph &g, uint32_t chunk, uint32_t k)
 {
-    return (k >= 6 && g.deep_list.nchains) ? (uint64_t)g.deep_list.ncarry * chunk : 0;
+    return (k >= 6 && g.deep_list.nchains) ? ((uint64_t)g.deep_list.ncarry * chunk + 31) / 32 * 32 : 0;
 }
 
 static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
@@ -331,7 +331,10 @@ static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, 
     *pr3_w = pair_layer3(g, k) ? (drows * pair_count(k) + 31) / 32 * 32 : 0;
     *tx_w = pair_layer3(g, k) && head_table(g) ? (uint64_t)std::max<uint32_t>(1, g.deep_list.nheads) * chunk : 0;
     *full_w = k >= 4 ? drows * chunk : 0;
-    *red_w = k >= 4 ? std::max(srows, drows) * v2_reduced_stride(ppl, chunk) : 0;
+    // whole 256-byte blocks: the next buffer (the carry table) is read with
+    // 16-byte vector loads, and a transformed row holds 7 values per group
+    // with 2 points per lane
+    *red_w = k >= 4 ? (std::max(srows, drows) * v2_reduced_stride(ppl, chunk) + 31) / 32 * 32 : 0;
 }
 
 uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)

@@ -327,6 +327,23 @@ def _hub_graph(seed=5, n=300, hub_in=2000, hub_out=2000, rest=2000, tau=10, delt
             "delta": np.full(n, delta, np.uint32), "color": rng.integers(0, 3, n).astype(np.uint8)}
 
 
+def test_cut_hub_segments_two_points_per_lane_odd_groups():
+    """Cut hub segments with 2 points per lane and 1, 3 or 7 lane groups per
+    chunk (7, 21 or 49 transformed values a row, an odd count) and with 3
+    groups of 4 points: the per-point state's carry table that follows the
+    transformed buffer stays aligned for its vector loads, and the sums exact."""
+    g = _hub_graph()
+    with _graph(g) as G:
+        nonzero = 0
+        for k, ppl, chunk in ((6, 2, 64), (7, 2, 192), (8, 2, 192), (9, 4, 384), (10, 2, 448)):
+            capi.rr_set_tuning(G.handle, k, ppl, chunk)
+            ref = oracle.sieve(g, 9, k, 90 + k)
+            _, w = G.reach(9, k, 90 + k)
+            assert np.array_equal(w, ref), (k, ppl, chunk)
+            nonzero += int(np.count_nonzero(ref) > 0)
+        assert nonzero >= 3
+
+
 def test_cut_hub_segments_carry_fixup():
     """A vertex with ~2,000 in- and out-rows: its head segment in every row
     list is cut into pieces of 128 rows computed in parallel and stitched by the
