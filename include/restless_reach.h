@@ -355,8 +355,8 @@ rr_status rr_set_tuning(rr_graph *g, uint32_t k, uint32_t ppl, uint32_t chunk);
  * tasks are at least half the resident warps, else fine ranges with 2, and
  * chunks up to 512. rr_autotune_batch picks the batch's tile (scheduling range)
  * and sieve points per block by measurement: it runs the batch qs[0..nq) once
- * untimed and twice timed per candidate -- the 12 combinations of 2/4/6
- * blocks, fine/coarse ranges and 256/512-point chunks -- keeps the fastest in
+ * untimed and twice timed per candidate -- the 18 combinations of 2/4/6
+ * blocks, fine/coarse ranges and 256/512/1024-point chunks -- keeps the fastest in
  * the graph and returns it in *best (may be NULL). Results are bit-identical in
  * every shape. Uses the graph's scratch (ordered as rr_reach_device). Errors:
  * RR_EINVAL for a NULL graph, nq == 0 or an invalid query; RR_ENOMEM / RR_ECUDA. */

@@ -413,8 +413,10 @@ __global__ void k_batch_bitmap(uint32_t n, const QueryDesc *__restrict__ descs)
 
 // zero row (row 0) of every slot's three buffers: `width` words of each full
 // buffer (its widest row) and 32 words of the transformed buffer
+// Zero row 0 of both full buffers (width values) and of the transformed buffer
+// (red_width values) of every slot.
 __global__ void k_batch_zero_rows(uint64_t *slot_base, uint64_t slot_words, uint64_t full_words,
-                                  uint32_t nslots, uint32_t width)
+                                  uint32_t nslots, uint32_t width, uint32_t red_width)
 {
     const uint32_t s = blockIdx.x;
     if (s >= nslots) return;
@@ -423,7 +425,7 @@ __global__ void k_batch_zero_rows(uint64_t *slot_base, uint64_t slot_words, uint
         b[i] = 0;
         b[full_words + i] = 0;
     }
-    for (uint32_t i = threadIdx.x; i < 32; i += blockDim.x) b[2 * full_words + i] = 0;
+    for (uint32_t i = threadIdx.x; i < red_width; i += blockDim.x) b[2 * full_words + i] = 0;
 }
 
 ListPtrs list_ptrs(const RowList &L, bool coarse)
@@ -496,11 +498,19 @@ uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, b
 
 }  // namespace
 
-// Bytes of device memory one batch slot holds for max chunk `chunk`.
+// Values a transformed row holds in a slot of max chunk `chunk`: 8 per lane
+// group of 128 points (4 points per lane), at least the 7 of one 64-point
+// group (2 points per lane), rounded up to 32.
+static uint64_t red_words_for(uint32_t chunk)
+{
+    return std::max<uint64_t>(32, (chunk + 127) / 128 * 8);
+}
+
+// Words of device memory one batch slot holds for max chunk `chunk`.
 static uint64_t slot_words_for(const Graph &g, uint32_t chunk)
 {
     const uint64_t srows = g.state_list.count + 1, drows = g.deep_list.count + 1;
-    return drows * chunk * 2 + std::max(srows, drows) * 32;
+    return drows * chunk * 2 + std::max(srows, drows) * red_words_for(chunk);
 }
 
 rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
@@ -803,7 +813,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         }
         k_batch_zero_rows<<<nslots, 256, 0, st>>>(d_slots.as<uint64_t>(), slot_bytes / 8,
                                                   (g.deep_list.count + 1) * max_chunk, nslots,
-                                                  max_chunk);
+                                                  max_chunk, (uint32_t)red_words_for(max_chunk));
         RR_LAUNCHED();
 
         BatchArgs a{};
@@ -977,7 +987,7 @@ rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t se
 // queries each -- and keeps the fastest.
 // Times the persistent batch on `qs` for every shape candidate -- kernel
 // variant (2, 4 or 6 blocks per SM), fine or coarse scheduling ranges, largest
-// point chunk 256 or 512 -- best of two runs each after one untimed run, and
+// point chunk 256, 512 or 1024 -- best of two runs each after one untimed run, and
 // keeps the fastest in the graph (every later batch on the graph, and the
 // server's batch lanes, use it). Results do not depend on the shape.
 rr_status autotune_batch(Graph &g, const rr_query *qs, uint32_t nq, uint32_t *minb,
@@ -994,7 +1004,7 @@ rr_status autotune_batch(Graph &g, const rr_query *qs, uint32_t nq, uint32_t *mi
     rr_status st = RR_OK;
     for (uint32_t mb : {2u, 4u, 6u})
         for (uint32_t rg : {1u, 2u})
-            for (uint32_t mc : {256u, 512u}) {
+            for (uint32_t mc : {256u, 512u, 1024u}) {
                 g.batch_minb = mb;
                 g.batch_ranges = rg;
                 g.batch_max_chunk = mc;

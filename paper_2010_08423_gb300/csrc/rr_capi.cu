@@ -351,8 +351,9 @@ rr_status rr_set_batch_tuning(rr_graph *g, const rr_batch_tuning *t)
     if (t->blocks_per_sm != 0 && t->blocks_per_sm != 2 && t->blocks_per_sm != 4 && t->blocks_per_sm != 6)
         return fail(RR_EINVAL, "rr_set_batch_tuning: blocks_per_sm must be 0, 2, 4 or 6");
     if (t->ranges > 2) return fail(RR_EINVAL, "rr_set_batch_tuning: ranges must be 0, 1 or 2");
-    if (t->max_chunk != 0 && t->max_chunk != 128 && t->max_chunk != 256 && t->max_chunk != 512)
-        return fail(RR_EINVAL, "rr_set_batch_tuning: max_chunk must be 0, 128, 256 or 512");
+    if (t->max_chunk != 0 && t->max_chunk != 128 && t->max_chunk != 256 && t->max_chunk != 512 &&
+        t->max_chunk != 1024)
+        return fail(RR_EINVAL, "rr_set_batch_tuning: max_chunk must be 0, 128, 256, 512 or 1024");
     std::lock_guard<std::mutex> lk(g->mu);
     g->batch_minb = t->blocks_per_sm;
     g->batch_ranges = t->ranges;
