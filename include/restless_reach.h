@@ -99,6 +99,10 @@ typedef struct {
     uint32_t deep_heads;           /* distinct heads of the deep rows */
     int head_table;                /* 1: layer 4 of the pair form reads x_u x_s from a
                                       per-chunk table of those heads */
+    int pair_tail;                 /* 1: queries with k >= 6 (k >= 7 with layer 3 in
+                                      pair-label space) and at most 8 point groups per
+                                      chunk run layer k-2 in label space from the pair
+                                      sums of layer k-3 (rr_graph_load's flags) */
 } rr_graph_info;
 
 /* ---- graph ----------------------------------------------------------------
@@ -116,7 +120,14 @@ typedef struct {
  * point from the label-space prefix). Layer 4 takes x_u x_s from a per-chunk
  * table of the deep rows' heads when they number at most half the deep rows
  * with a non-empty window; bit 3 / bit 4 set = always / never. Both bits of a
- * pair set is RR_EINVAL. Results are bit-identical in every form. The pair
+ * pair set is RR_EINVAL. The last layer needs of layer k-2 only its sums over
+ * the points of a group times x_w^L, and with layer k-2's factor y x_v^L those
+ * are bilinear forms over layer k-3's sums on the points holding one or two
+ * given labels: with the pair tail, layer k-3 stores those sums (a 32-value
+ * block per deep row and group of points) instead of per-point state, and
+ * layer k-2 keeps 16 label-space values per deep row; bit 5 set = never (layer
+ * k-2 per point, writing its sums over single labels). Results are
+ * bit-identical in every form. The pair
  * rows ((deep rows + 1) * k(k+1)/2 words) and the head table (heads * chunk
  * words) are part of a query's scratch and, unlike the per-point state, do not
  * shrink with the point chunk: a server whose per-slot budget cannot hold them
@@ -416,12 +427,13 @@ rr_status rr_debug_draw(uint64_t key, uint64_t first, uint64_t count, uint64_t *
  * kind: 0 = first layer, 1 = middle layers reading state, 2 = last layer with
  * the fused per-vertex reduce, 3 = z-table, 4 = persistent batched kernel,
  * 5 = second layer (window sums from the first layer's scalar prefix),
- * 6 = layer k-2 writing the transformed state, 7 = layer 3 in pair-label
- * space. While timing is enabled the
+ * 6 = the last per-point layer, writing the transformed state (layer k-2, or
+ * k-3 with the pair tail), 7 = layer 3 in pair-label space, 8 = the pair
+ * tail's layer k-2 in label space. While timing is enabled the
  * launches are issued one by one instead of as a captured CUDA graph. */
 typedef struct {
-    double ms[8];
-    uint64_t launches[8];
+    double ms[9];
+    uint64_t launches[9];
 } rr_kernel_times;
 rr_status rr_timing_enable(int enable);
 rr_status rr_timing_read(rr_kernel_times *out, int reset);

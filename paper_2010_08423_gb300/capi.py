@@ -23,6 +23,7 @@ FLAG_PAIR_ON = 2
 FLAG_PAIR_OFF = 4
 FLAG_HEAD_TABLE_ON = 8
 FLAG_HEAD_TABLE_OFF = 16
+FLAG_PAIR_TAIL_OFF = 32
 
 
 class RRError(RuntimeError):
@@ -46,7 +47,7 @@ class rr_graph_info(ctypes.Structure):
                 ("deep_compute_rows", ctypes.c_uint64), ("deep_tail_rows", ctypes.c_uint64),
                 ("deep_head_runs", ctypes.c_uint64), ("pair_layer3_min_k", ctypes.c_int),
                 ("deep_max_range_rows", ctypes.c_uint32), ("deep_heads", ctypes.c_uint32),
-                ("head_table", ctypes.c_int)]
+                ("head_table", ctypes.c_int), ("pair_tail", ctypes.c_int)]
 
 
 class rr_batch_tuning(ctypes.Structure):
@@ -55,11 +56,11 @@ class rr_batch_tuning(ctypes.Structure):
 
 
 class rr_kernel_times(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
+    _fields_ = [("ms", ctypes.c_double * 9), ("launches", ctypes.c_uint64 * 9)]
 
 
 TIMING_KINDS = ["first_layer", "mid_layer", "last_layer", "ztable", "batch", "second_layer",
-                "tail_layer", "third_layer"]
+                "tail_layer", "third_layer", "label_tail_layer"]
 
 
 EXPORTED = [

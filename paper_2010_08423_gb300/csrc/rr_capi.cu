@@ -154,6 +154,7 @@ rr_status rr_graph_get_info(const rr_graph *g, rr_graph_info *out)
     out->deep_heads = g->deep_list.nheads;
     out->head_table = g->head_table_force ? (g->head_table_force == 2 ? 1 : 0)
                                           : (2ull * g->deep_list.nheads <= g->deep_compute_rows ? 1 : 0);
+    out->pair_tail = g->pair_tail_off ? 0 : 1;
     return RR_OK;
 }
 

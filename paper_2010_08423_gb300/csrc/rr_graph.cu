@@ -606,6 +606,7 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     g->pair_force = (flags & 2u) ? 2u : ((flags & 4u) ? 1u : 0u);
     if ((flags & 24u) == 24u) return fail(RR_EINVAL, "rr_graph_load: flags turn the head-factor table both on and off");
     g->head_table_force = (flags & 8u) ? 2u : ((flags & 16u) ? 1u : 0u);
+    g->pair_tail_off = (flags & 32u) != 0;
     RR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     cudaStream_t st = g->stream;
 

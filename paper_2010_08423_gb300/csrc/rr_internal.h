@@ -23,7 +23,7 @@ extern std::atomic<uint64_t> g_launches;
 // Kernel timing (rr_timing_*): kinds as in rr_kernel_times.
 enum TimingKind {
     kTimeFirst = 0, kTimeMid = 1, kTimeLast = 2, kTimeZ = 3, kTimeBatch = 4, kTimeSecond = 5,
-    kTimeTail = 6, kTimeThird = 7, kTimeKinds = 8
+    kTimeTail = 6, kTimeThird = 7, kTimeLabelTail = 8, kTimeKinds = 9
 };
 extern std::atomic<bool> g_timing;
 // Records a start event on st when timing is enabled; returns an opaque slot.
@@ -260,6 +260,9 @@ struct Graph {
     // layer 4 of the pair form takes x_u x_s from a per-chunk table of the
     // deep rows' heads (0 = when heads <= compute rows / 2, 1 = never, 2 = always)
     uint32_t head_table_force = 0;
+    // layers k-2 and k-1 from the pair sums of layer k-3 (label-space layer
+    // k-2) unless the load flags turn it off
+    bool pair_tail_off = false;
     uint32_t max_in_degree = 0;
 
     DevBuf off;      // n+1 uint32

@@ -66,13 +66,15 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cud
 // What a query clears before its layers: the witness (n values; n = 0 skips
 // it) and the zero rows of the scratch -- row 0 of the scalar prefix, of both
 // full state buffers (chunk values each), of the transformed buffer (rstride
-// values) and of the label-space prefix (kpr2 values). Null pointers skip.
+// values: its row width), of the label-space prefix (kpr2 values) and of the
+// pair tail's rows. Null pointers skip.
 struct ZeroRows {
     uint64_t *py, *full0, *full1, *red, *pr2;
     uint32_t n, chunk, rstride, kpr2;
     uint64_t *pr3;
     uint32_t npr3;
     uint64_t *carry;  // the carry table's zero row (chunk values) or null
+    uint64_t *lrows;  // the pair tail's label-space rows (kLabelTailWidth values) or null
 };
 
 __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, const ZeroRows &z)
@@ -95,6 +97,8 @@ __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, cons
         for (uint32_t i = tid; i < z.npr3; i += stride) z.pr3[i] = 0;
     if (z.carry)
         for (uint32_t i = tid; i < z.chunk; i += stride) z.carry[i] = 0;
+    if (z.lrows)
+        for (uint32_t i = tid; i < kLabelTailWidth; i += stride) z.lrows[i] = 0;
 }
 
 // Layer 1; its grid also clears what zero_rows lists (saving a launch).
@@ -234,6 +238,25 @@ __global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
     last_warp<LG, false>(p, task);
 }
 
+// Pair tail (rr_v2_device.cuh): layer k-2 in label space from layer k-3's
+// pair sums, and the last layer from its rows.
+template <int LG>
+__global__ void __launch_bounds__(kW2 * 32) k_label_tail(const V2Params p)
+{
+    __shared__ uint64_t sm[kW2][192];
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems) return;
+    label_tail_warp<LG>(p, task, sm[threadIdx.x >> 5]);
+}
+
+template <int LG>
+__global__ void __launch_bounds__(kW2 * 32) k_last_label(const V2Params p)
+{
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= p.nitems) return;
+    last_label_warp<LG>(p, task);
+}
+
 static unsigned blocks_for(uint64_t tasks)
 {
     return (unsigned)((tasks + kW2 - 1) / kW2);
@@ -269,15 +292,18 @@ static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 1>, dim3(blocks), B, st, vp));
     } else if (src == 2) {
         if (out == 1) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, true>, dim3(blocks), B, st, vp));
+        else if (out == 2) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 2, true>, dim3(blocks), B, st, vp));
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true>, dim3(blocks), B, st, vp));
     } else if (src == 3) {
         if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, false, true>, dim3(blocks), B, st, vp));
+        else if (out == 2) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 2, false, true>, dim3(blocks), B, st, vp));
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, false, true>, dim3(blocks), B, st, vp));
     } else {
         if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0>, dim3(blocks), B, st, vp));
+        else if (out == 2) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 2>, dim3(blocks), B, st, vp));
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1>, dim3(blocks), B, st, vp));
     }
-    timing_end(tslot, src == 1 ? kTimeSecond : (out == 1 ? kTimeTail : kTimeMid), st);
+    timing_end(tslot, src == 1 ? kTimeSecond : (out != 0 ? kTimeTail : kTimeMid), st);
     RR_LAUNCHED();
     return RR_OK;
 }
@@ -319,6 +345,22 @@ static uint64_t carry_words(const Graph &g, uint32_t chunk, uint32_t k)
     return (k >= 6 && g.deep_list.nchains) ? ((uint64_t)g.deep_list.ncarry * chunk + 31) / 32 * 32 : 0;
 }
 
+// Layers k-2 and k-1 from layer k-3's pair sums (the pair tail): when layer
+// k-3 keeps per-point state (k >= 6; k >= 7 with layer 3 in pair-label space)
+// and a chunk has at most kPairTailMaxGroups point groups, unless the load
+// flags turn it off.
+static bool pair_tail(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
+{
+    const uint32_t first = pair_layer3(g, k) ? 4u : 3u;  // the first per-point layer
+    return !g.pair_tail_off && k >= 6 && first + 3 <= k && chunk / (32u * ppl) <= kPairTailMaxGroups;
+}
+
+// Words of the pair tail's label-space rows (layer k-2), zero when it is off.
+static uint64_t label_tail_words(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
+{
+    return pair_tail(g, ppl, chunk, k) ? ((uint64_t)g.deep_list.count + 1) * kLabelTailWidth : 0;
+}
+
 static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
                       uint64_t *pr2_w, uint64_t *pr3_w, uint64_t *tx_w, uint64_t *full_w,
                       uint64_t *red_w)
@@ -335,13 +377,18 @@ static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, 
     // 16-byte vector loads, and a transformed row holds 7 values per group
     // with 2 points per lane
     *red_w = k >= 4 ? (std::max(srows, drows) * v2_reduced_stride(ppl, chunk) + 31) / 32 * 32 : 0;
+    // with the pair tail it holds layer k-3's pair sums (a 32-value block per
+    // deep row and point group)
+    if (pair_tail(g, ppl, chunk, k))
+        *red_w = std::max<uint64_t>(*red_w, drows * (chunk / (32u * ppl)) * kPairTailSlots);
 }
 
 uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
 {
     uint64_t py_w, pr2_w, pr3_w, tx_w, full_w, red_w;
     v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &tx_w, &full_w, &red_w);
-    return (py_w + pr2_w + pr3_w + tx_w + 2 * full_w + red_w + carry_words(g, chunk, k)) * 8ull + 4096;
+    return (py_w + pr2_w + pr3_w + tx_w + 2 * full_w + red_w + carry_words(g, chunk, k) +
+            label_tail_words(g, ppl, chunk, k)) * 8ull + 4096;
 }
 
 // z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades); rows
@@ -428,6 +475,11 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     uint64_t *red = full1 + full_w;
     uint64_t *carry = carry_words(g, chunk, k) ? red + red_w : nullptr;
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
+    // the pair tail: layer k-3 writes pair sums into `red`, layer k-2 its
+    // label-space rows after the carry table
+    const bool ptail = pair_tail(g, ppl, chunk, k);
+    uint64_t *lrows = ptail ? red + red_w + carry_words(g, chunk, k) : nullptr;
+    const uint32_t red_width = ptail ? chunk / (32u * ppl) * kPairTailSlots : rstride;
 
     {
         if (table) {  // plain queries without deletions draw z on the fly
@@ -442,8 +494,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     // the witness and the scratch's zero rows (k = 2 has no scratch); cleared by
     // the first layer's grid when it runs
     const ZeroRows zr{k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
-                      k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, rstride, k,
-                      pair ? pr3 : nullptr, pair_count(k), carry};
+                      k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, red_width, k,
+                      pair ? pr3 : nullptr, pair_count(k), carry, lrows};
     const bool zero_in_first = k >= 3 && g.prod_list.nitems > 0;
     if (!zero_in_first) {
         RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, d_desc, zr));
@@ -554,14 +606,17 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     for (uint64_t c = 0; c < nchunks; ++c) {
         vp.chunk_base = range.first + (uint32_t)(c * chunk);
         rr_status s = RR_OK;
-        // layers 2 (k = 4) or 3 (k >= 5) .. k-2; the last of them writes the
-        // transformed state
+        // per-point layers 2 (k = 4) or 3 (k >= 5) .. k-2, or .. k-3 with the
+        // pair tail; the last of them writes the transformed state (its sums
+        // over label sets of the point groups: single labels, or with the
+        // pair tail at most two)
         uint64_t *bufs[2] = {full0, full1};
+        const uint32_t last_pp = ptail ? k - 3 : k - 2;
         // with layer 3 in pair-label space the per-point layers start at 4,
         // layer 4 reading the pair windows
-        for (uint32_t l = pair ? 4u : (k >= 5 ? 3u : 2u); l <= k - 2; ++l) {
+        for (uint32_t l = pair ? 4u : (k >= 5 ? 3u : 2u); l <= last_pp; ++l) {
             const int src = (l == 2) ? 1 : (l == 3 ? 2 : (pair && l == 4 ? 3 : 0));
-            const int out = (l == k - 2) ? 1 : 0;
+            const int out = l == last_pp ? (ptail ? 2 : 1) : 0;
             // layer 2 (k = 4) runs over the state rows; layers >= 3 over the deep rows,
             // layer 3 reading the label-space prefix at state-row indices
             if (src == 3 && vp.tx && vp.ndheads) {
@@ -580,7 +635,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             else set_list(vp, g.deep_list, src == 2 ? 1 : 3);
             vp.layer = l;
             vp.st_in = bufs[(l - 1) & 1u];
-            vp.st_out = out == 1 ? red : bufs[l & 1u];
+            vp.st_out = out != 0 ? red : bufs[l & 1u];
             // per-point state read from the previous layer carries lazily
             vp.carry = src == 0 ? carry : nullptr;
             vp.row_carry = carry ? g.deep_list.row_carry.as<uint32_t>() : nullptr;
@@ -605,19 +660,45 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
                 ++nk;
             } else {
                 s = launch_fixup(src == 1 ? g.state_list : g.deep_list, vp.st_out,
-                                 out == 1 ? rstride : chunk, st, &nk);
+                                 out == 0 ? chunk : red_width, st, &nk);
+                if (s != RR_OK) return s;
+            }
+        }
+        if (ptail) {
+            // layer k-2 in label space from the pair sums of its windows
+            set_list(vp, g.deep_list, 3);
+            vp.layer = k - 2;
+            vp.st_in = red;
+            vp.st_out = lrows;
+            vp.carry = nullptr;
+            vp.row_carry = nullptr;
+            if (vp.nitems) {
+                const int tslot = timing_begin(st);
+                if (ppl == 4) RR_CUDA(launch_pdl(k_label_tail<7>, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp));
+                else RR_CUDA(launch_pdl(k_label_tail<6>, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp));
+                timing_end(tslot, kTimeLabelTail, st);
+                RR_LAUNCHED();
+                ++nk;
+                s = launch_fixup(g.deep_list, lrows, kLabelTailWidth, st, &nk);
                 if (s != RR_OK) return s;
             }
         }
         // layer k-1 from the transformed state (state-row indices when k = 4)
+        // or from the pair tail's label-space rows
         if (k == 4) set_list(vp, g.tail_list, 1);
         else set_list(vp, g.tail3_list, 3);
         vp.layer = k - 1;
-        vp.st_in = red;
+        vp.st_in = ptail ? lrows : red;
         if (vp.nitems) {
             const int tslot = timing_begin(st);
-            if (ppl == 4) RR_CUDA(launch_pdl(k_last_v2<7>, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp));
-            else RR_CUDA(launch_pdl(k_last_v2<6>, dim3(blocks_for(vp.nitems)), dim3(kW2 * 32), st, vp));
+            const dim3 grid(blocks_for(vp.nitems)), B(kW2 * 32);
+            if (ptail) {
+                if (ppl == 4) RR_CUDA(launch_pdl(k_last_label<7>, grid, B, st, vp));
+                else RR_CUDA(launch_pdl(k_last_label<6>, grid, B, st, vp));
+            } else {
+                if (ppl == 4) RR_CUDA(launch_pdl(k_last_v2<7>, grid, B, st, vp));
+                else RR_CUDA(launch_pdl(k_last_v2<6>, grid, B, st, vp));
+            }
             timing_end(tslot, kTimeLast, st);
             RR_LAUNCHED();
             ++nk;

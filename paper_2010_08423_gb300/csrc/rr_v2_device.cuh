@@ -44,6 +44,30 @@ __host__ __device__ __forceinline__ uint32_t pair_count(uint32_t k)
     return k * (k + 1) / 2;
 }
 
+// Pair tail: layer k-3 stores, per deep row and point group, the sums of its
+// per-point state over the group's points that hold a given set A of at most
+// two in-group labels (LG of them): slot 0 for A = {} (the group total), 1 + a
+// for A = {a}, 1 + LG + b(b-1)/2 + a for A = {a < b}; 29 slots (LG = 7) or 22
+// (LG = 6) of a 32-value block. Layer k-2 then keeps kLabelTailWidth values
+// per deep row (LG label values and one per point group, at most 8 groups).
+constexpr uint32_t kPairTailSlots = 32;
+constexpr uint32_t kLabelTailWidth = 16;
+constexpr uint32_t kPairTailMaxGroups = 8;
+template <int LG>
+__host__ __device__ __forceinline__ uint32_t pair_tail_slot(uint32_t A)
+{
+#ifdef __CUDA_ARCH__
+    const int c = __popc(A);
+    const uint32_t a = (uint32_t)__ffs((int)A) - 1u, b = 31u - (uint32_t)__clz((int)A);
+#else
+    const int c = __builtin_popcount(A);
+    const uint32_t a = A ? (uint32_t)__builtin_ctz(A) : 0u, b = A ? 31u - (uint32_t)__builtin_clz(A) : 0u;
+#endif
+    if (c == 0) return 0u;
+    if (c == 1) return 1u + a;
+    return 1u + (uint32_t)LG + b * (b - 1u) / 2u + a;
+}
+
 struct V2Params {
     // list
     const uint32_t *head, *eid, *src, *ia, *ib;
@@ -615,6 +639,36 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                 }
                 if (lane <= LG)
                     p.st_out[(row * p.ngroups + group) * (LG + 1) + lane] = val;
+            } else if constexpr (OUT == 2) {
+                // superset sums over the group's 32*PPL points: afterwards the
+                // lane's value i (its point's in-group label set A = the lane
+                // bits above the in-lane bits i) is the sum of acc over the
+                // group's points containing A; the sets of at most two labels
+                // are stored (slot pair_tail_slot(A))
+                uint64_t v[PPL];
+#pragma unroll
+                for (int i = 0; i < PPL; ++i) v[i] = acc[i];
+                v[0] ^= v[1];
+                if constexpr (PPL == 4) {
+                    v[2] ^= v[3];
+                    v[0] ^= v[2];
+                    v[1] ^= v[3];
+                }
+#pragma unroll
+                for (int bb = 0; bb < 5; ++bb) {
+                    const bool up = (lane >> bb) & 1;
+#pragma unroll
+                    for (int i = 0; i < PPL; ++i) {
+                        const uint64_t o = shfl64x(v[i], 1 << bb);
+                        if (!up) v[i] ^= o;
+                    }
+                }
+                uint64_t *blk = p.st_out + (row * p.ngroups + group) * kPairTailSlots;
+#pragma unroll
+                for (int i = 0; i < PPL; ++i) {
+                    const uint32_t A = ((uint32_t)lane << LOGP) | (uint32_t)i;
+                    if (__popc(A) <= 2) blk[pair_tail_slot<LG>(A)] = v[i];
+                }
             }
         }
     }
@@ -1020,6 +1074,218 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
 #pragma unroll 1
     for (uint32_t g0 = 0; g0 < p.ngroups; g0 += kGroupsPerPass)
         last_pass<LG, COHERENT>(p, task, g0, g0 == 0);
+}
+
+// ---------------------------------------------------------------------------
+// Pair tail, layer k-2 in label space. The last layer uses layer k-2 only
+// through sum over a group g's points of x_w^L P^L(f), and with
+// P^L = y x_v^L W^L (a row of head v, W its window of layer k-3) that sum is a
+// bilinear form in the z values of w and v over the pair sums of W: writing
+// x^L = sum_{i in I, i in L} z_i + A_g (I = the LG in-group labels, A_g = sum
+// of z_j over the labels above them that every point of g holds),
+//   sum_{L in g} x_w^L x_v^L W^L = sum_{i,j in I} zw_i zv_j T_g{i,j}
+//       + sum_i zw_i A_{v,g} T_g{i} + A_{w,g} sum_j zv_j T_g{j} + A_{w,g} A_{v,g} V_g,
+// T_g{i,j} the sum of W^L over g's points holding labels i and j (T_g{i,i} =
+// T_g{i}), V_g over all of g's points. Grouped by w's factors, a row adds
+//   G_i     = y (sum_{j in I} zv_j sum_g T_g{i,j} + sum_g A_{v,g} T_g{i})   (i in I)
+//   G_{g,*} = y (sum_{j in I} zv_j T_g{j} + A_{v,g} V_g)                     (g < ng)
+// and the last layer takes sum_i zw_i dR_i + sum_g A_{w,g} dR_{g,*} from the
+// windows of R, the prefix of G over v's rows (stride kLabelTailWidth).
+// One warp per scheduling range of the deep rows. Per row with a non-empty
+// window: lane l forms the y-scaled multiplier m_l (y zv_l for l < LG,
+// y A_{v,l-LG} above); lane s of the slot pass sums slot s of the window over
+// the groups and multiplies it by the multipliers its label pair or single
+// label needs; lane q of each group pass takes (group q/8, slot q%8) of the
+// singles and totals. The products meet their targets in `sm` (192 values).
+// ---------------------------------------------------------------------------
+template <int LG>
+__device__ __forceinline__ void label_tail_warp(const V2Params &p, uint32_t item, uint64_t *sm)
+{
+    constexpr uint32_t NS = 1u + LG + LG * (LG - 1) / 2;  // used slots of a group block
+    constexpr uint32_t kPB = 64;                          // group-pass products at sm[kPB..]
+    const uint32_t lane = threadIdx.x & 31;
+    const uint2 it = p.items[item];
+    const uint32_t k = p.k;
+    const uint32_t ng = p.ngroups;
+    const uint64_t key_y = p.qd->key_y;
+    const uint32_t blk_w = ng * kPairTailSlots;            // values per input row
+    const uint32_t rb_passes = (ng * 8u + 31u) / 32u;      // group passes (ng <= 8: at most 2)
+    const uint32_t ntarget = LG + ng;
+
+    // slot pass: what lane s computes (s < NS). single i: P0 = m_i T -> R_i;
+    // pair (i < j): P0 = m_j T -> R_i and P1 = m_i T -> R_j; s = 0 (total): nothing
+    uint32_t srcA = 0, srcB = 0;
+    bool useA = false, useB = false;
+    if (lane >= 1 && lane <= (uint32_t)LG) {
+        srcA = lane - 1;
+        useA = true;
+    } else if (lane > (uint32_t)LG && lane < NS) {
+        const uint32_t idx = lane - 1 - LG;
+        uint32_t j = 1;
+        while ((j + 1) * j / 2 <= idx) ++j;  // largest j with j(j-1)/2 <= idx
+        const uint32_t i = idx - j * (j - 1) / 2;
+        srcA = j;
+        srcB = i;
+        useA = useB = true;
+    }
+    // target lane t: the smem positions it sums (see the gather below)
+    uint32_t cur = p.head[it.x];
+    uint64_t M = 0;  // lane l < LG: zv_l; lane LG+g: A_{v,g}
+    auto enter_head = [&](uint32_t v) {
+        const uint64_t zv = lane < k ? zval(p, v, lane) : 0ull;
+        const uint32_t gbase = p.chunk_base + (lane - (uint32_t)LG) * (1u << LG);
+        uint64_t a = 0;
+        for (uint32_t j = LG; j < k; ++j) {  // warp-uniform
+            const uint64_t zj = shfl64b(zv, (int)j);
+            if ((gbase >> j) & 1u) a ^= zj;
+        }
+        M = lane < (uint32_t)LG ? zv : (lane < ntarget ? a : 0ull);
+    };
+    enter_head(cur);
+    uint64_t R = 0;
+    for (uint32_t base = it.x; base < it.y; base += 32) {
+        const uint32_t ent = base + lane;
+        const bool has = ent < it.y;
+        const uint32_t m_head = has ? p.head[ent] : 0u;
+        const uint32_t m_a = has ? p.ia[ent] : 0u;
+        const uint32_t m_b = has ? p.ib[ent] : 0u;
+        const uint64_t m_coef = has ? sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + (p.layer - 1u)) : 0ull;
+        if (base == it.x) pdl_enter();  // the pair sums are read, and R written, from here on
+        const uint32_t nb = min(32u, it.y - base);
+        for (uint32_t t = 0; t < nb; ++t) {
+            const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
+            if (h != cur) {
+                R = 0;
+                cur = h;
+                enter_head(cur);
+            }
+            const uint32_t a = __shfl_sync(0xffffffffu, m_a, (int)t);
+            const uint32_t b = __shfl_sync(0xffffffffu, m_b, (int)t);
+            const uint64_t y = shfl64b(m_coef, (int)t);
+            if (a != b) {  // warp-uniform
+                const uint64_t m = rr_mul(y, M);
+                const uint64_t *ra = p.st_in + (size_t)a * blk_w;
+                const uint64_t *rb = p.st_in + (size_t)b * blk_w;
+                // slot pass
+                uint64_t ts = 0;
+                if (lane < NS)
+                    for (uint32_t g = 0; g < ng; ++g)
+                        ts ^= __ldg(rb + g * kPairTailSlots + lane) ^ __ldg(ra + g * kPairTailSlots + lane);
+                const uint64_t mA = shfl64b(m, (int)srcA), mB = shfl64b(m, (int)srcB);
+                sm[2 * lane] = rr_mul(useA ? mA : 0ull, ts);
+                sm[2 * lane + 1] = rr_mul(useB ? mB : 0ull, ts);
+                // group passes: (g, s) = (q / 8, q % 8); s = 0 the total V_g,
+                // s = 1 + i the single T_g{i}: P0 = A'_g T -> R_i (s > 0) or
+                // R_{g,*} (s = 0), P1 = m_i T -> R_{g,*} (s > 0)
+                for (uint32_t r = 0; r < rb_passes; ++r) {
+                    const uint32_t q = lane + 32u * r;
+                    const uint32_t g = q >> 3, s = q & 7u;
+                    const bool ok = g < ng && s <= (uint32_t)LG;
+                    const uint64_t tv = ok ? (__ldg(rb + g * kPairTailSlots + s) ^
+                                              __ldg(ra + g * kPairTailSlots + s)) : 0ull;
+                    const uint64_t mg = shfl64b(m, (int)min((uint32_t)LG + g, 31u));
+                    const uint64_t mi = shfl64b(m, (int)(s == 0 ? 0u : s - 1u));
+                    sm[kPB + 2 * q] = rr_mul(ok ? mg : 0ull, tv);
+                    sm[kPB + 2 * q + 1] = rr_mul(ok && s > 0 ? mi : 0ull, tv);
+                }
+                __syncwarp();
+                uint64_t G = 0;
+                if (lane < (uint32_t)LG) {
+                    const uint32_t i = lane;
+                    for (uint32_t o = 0; o < (uint32_t)LG; ++o) {
+                        const uint32_t lo = min(i, o), hi = max(i, o);
+                        const uint32_t slot = lo == hi ? 1u + i : 1u + LG + hi * (hi - 1) / 2 + lo;
+                        G ^= sm[2 * slot + (i > o ? 1u : 0u)];
+                    }
+                    for (uint32_t g = 0; g < ng; ++g) G ^= sm[kPB + 2 * (g * 8u + 1u + i)];
+                } else if (lane < ntarget) {
+                    const uint32_t g = lane - LG;
+                    G = sm[kPB + 2 * (g * 8u)];
+                    for (uint32_t i = 0; i < (uint32_t)LG; ++i) G ^= sm[kPB + 2 * (g * 8u + 1u + i) + 1];
+                }
+                __syncwarp();
+                R ^= G;
+            }
+            const size_t row = (size_t)base + t + 1;  // deep row of this entry
+            if (lane < kLabelTailWidth) p.st_out[row * kLabelTailWidth + lane] = R;
+        }
+    }
+}
+
+// Last layer of the pair tail: lane t < LG + ng accumulates sum_f y_f dR_t over
+// the rows f of one head vertex w (dR = the window of R), then multiplies once
+// by zw_t (t < LG) or A_{w,t-LG}, and the warp XOR-reduces into S[w].
+template <int LG>
+__device__ __forceinline__ void last_label_warp(const V2Params &p, uint32_t task)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint2 it = p.items[task];
+    const uint32_t k = p.k;
+    const uint64_t key_y = p.qd->key_y;
+    uint64_t *const S = p.qd->S;
+    uint64_t *const E = p.qd->E;  // per-edge sums wanted (fine-grained output)
+    const bool active = lane < (uint32_t)LG + p.ngroups;
+    const uint32_t gbase = p.chunk_base + (lane - (uint32_t)LG) * (1u << LG);  // lanes >= LG
+
+    auto zsel_of = [&](uint32_t v) -> uint64_t {
+        if (!active) return 0ull;
+        if (lane < (uint32_t)LG) return lane < k ? zval(p, v, lane) : 0ull;
+        uint64_t zz = 0;
+        for (uint32_t j = LG; j < k; ++j)
+            if ((gbase >> j) & 1u) zz ^= zval(p, v, j);
+        return zz;
+    };
+
+    uint32_t cur = p.head[it.x];
+    uint64_t zsel = zsel_of(cur);
+    uint64_t acc = 0;
+    auto flush = [&](uint32_t v) {
+        uint64_t t = active ? rr_mul(zsel, acc) : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t ^= shfl64x(t, off);
+        if (lane == 0 && t) atomicXor(reinterpret_cast<unsigned long long *>(S + v),
+                                      (unsigned long long)t);
+    };
+    for (uint32_t base = it.x; base < it.y; base += 32) {
+        const uint32_t ent = base + lane;
+        const bool has = ent < it.y;
+        const uint32_t m_head = has ? p.head[ent] : 0u;
+        const uint32_t m_a = has ? p.ia[ent] : 0u;
+        const uint32_t m_b = has ? p.ib[ent] : 0u;
+        const uint32_t m_eid = has ? p.eid[ent] : 0u;
+        const uint64_t m_y = has ? sm_draw(key_y, (uint64_t)m_eid * 32u + (p.layer - 1u)) : 0ull;
+        if (base == it.x) pdl_enter();  // R is read from here on
+        const uint32_t nb = min(32u, it.y - base);
+        for (uint32_t t = 0; t < nb; ++t) {
+            const uint32_t h = __shfl_sync(0xffffffffu, m_head, (int)t);
+            if (h != cur) {
+                flush(cur);
+                acc = 0;
+                cur = h;
+                zsel = zsel_of(cur);
+            }
+            const uint32_t a = __shfl_sync(0xffffffffu, m_a, (int)t);
+            const uint32_t b = __shfl_sync(0xffffffffu, m_b, (int)t);
+            const uint64_t y = shfl64b(m_y, (int)t);
+            uint64_t yt = 0;
+            if (active && a != b) {
+                const uint64_t dr = __ldg(p.st_in + (size_t)a * kLabelTailWidth + lane) ^
+                                    __ldg(p.st_in + (size_t)b * kLabelTailWidth + lane);
+                yt = rr_mul(y, dr);
+                acc ^= yt;
+            }
+            if (E) {
+                // this entry's own sum: the flush's product taken per entry
+                uint64_t c = active ? rr_mul(zsel, yt) : 0ull;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) c ^= shfl64x(c, off);
+                const uint32_t e = __shfl_sync(0xffffffffu, m_eid, (int)t);
+                if (lane == 0 && c) atomicXor(reinterpret_cast<unsigned long long *>(E + e),
+                                              (unsigned long long)c);
+            }
+        }
+    }
+    flush(cur);
 }
 
 }  // namespace rr
