@@ -623,11 +623,13 @@ def batched_metrics(capi, torch, gc, mul_peak, hbm_peak, nq=256, seed=UNIFORM_SE
 
 def served_metrics(capi, g, nq=160, seed=UNIFORM_SEED ^ 0x5E,
                    workload="plain queries, k~U{6..12}, s~U, on the n=100000 m=1000000 graph",
-                   warm=8):
+                   warm=8, batching_probe=True):
     """Serving: Poisson arrivals of plain queries (s ~ U, k ~ U{6..12}) at 0.5x,
     0.8x and 1.1x of the server's measured capacity; latency = submit -> done.
-    Warm-up: `warm` queries one at a time, then one untimed burst (the batch
-    lanes' first use grows the batch kernel's buffers). The same query list is
+    Warm-up: `warm` queries one at a time, then one untimed burst (every slot
+    captures its launch sequences). Capacity = a burst of the whole list on the
+    server's default (4 slots, batch lanes off); with batching_probe the same
+    burst is also timed with batches of up to 64 queries. The same query list is
     then run one query at a time through rr_reach_sync (the plain GPU form:
     one launch sequence per query, results copied to the host), host-timed."""
     import threading
@@ -653,6 +655,19 @@ def served_metrics(capi, g, nq=160, seed=UNIFORM_SEED ^ 0x5E,
             a1 = capi.rr_server_stats(srv)
             out["capacity_admission"] = {"single": a1[0] - a0[0], "batched": a1[1] - a0[1],
                                          "batches": a1[2] - a0[2]}
+            if batching_probe:
+                # the same burst with the batch lanes on (the server's default is
+                # off: the slots' concurrent launch sequences), untimed warm burst first
+                capi.rr_server_set_batching(srv, 8, 64)
+                for t in [capi.rr_query_submit(srv, s_, k_, sd) for s_, k_, sd in qs[:64]]:
+                    capi.rr_query_poll(srv, t, n, -1)
+                t0 = time.perf_counter()
+                ts = [capi.rr_query_submit(srv, s_, k_, sd) for s_, k_, sd in qs]
+                for t in ts:
+                    capi.rr_query_poll(srv, t, n, -1)
+                out["capacity_with_batches_of_up_to_64_queries_per_s"] = nq / (time.perf_counter() - t0)
+                capi.rr_server_set_batching(srv, 0, 0)
+                a1 = capi.rr_server_stats(srv)
             loads = []
             for frac in (0.5, 0.8, 1.1):
                 rate = frac * cap
@@ -763,34 +778,54 @@ def kernel_rooflines(info, k, chunk, ppl, n, kt, queries, hbm_peak, mul_peak, zt
         # every chunk; the same timing kind, so per launch = per query / launches
         third = (D * (NP * 8 + 2 * k * 8 + 20) + (HD * c * 8 * nchunks if table else 0),
                  D * (k + k * k) + (HD * c * nchunks if table else 0))
+    ng = c // (32 * ppl)               # point groups of a chunk
+    # the pair tail: layers k-2 and k-1 from layer k-3's sums over one- and
+    # two-label point sets (kernels: per-point layers up to k-3, then layer k-2
+    # in label space with 16-value rows)
+    ptail = bool(info.get("pair_tail")) and k >= (7 if pmode else 6) and ng <= 8
+    ns = 1 + lg + lg * (lg - 1) // 2   # used values of a group's 32-value block
+    tail_out = ng * 32 if ptail else rstride  # values the last per-point layer stores per row
+    last_pp = k - 3 if ptail else k - 2
     if pmode == 1:
         # layer 4 reads 2 NP pair values per window and multiplies per point by
         # c and by x_u x_s (from the head table: 8 more bytes per point; else
         # formed here: one more product)
         l4 = ((D * c * 8 + 2 * DC * NP * 8 + D * 20 + DC * c * 8, DC * (2 * c + k)) if table else
               (D * c * 8 + 2 * DC * NP * 8 + D * 20, DC * (3 * c + k)))
-        mids = [l4] + [mid] * (k - 7) if k >= 7 else []
-        tail = ((D * rstride * 8 + 2 * DC * NP * 8 + D * 20, DC * (3 * c + k)) if k == 6 else
-                (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
+        mids = [l4] + [mid] * (last_pp - 5) if last_pp >= 5 else []
+        tail = ((D * tail_out * 8 + l4[0] - D * c * 8, l4[1]) if last_pp == 4 else
+                (D * tail_out * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
     else:
         # layer 3 per point from the label-space prefix: x_u times y rho for every
         # row, x_v x_s once per head run and once per row
         l3 = (D * c * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c)
-        mids = [l3] + [mid] * (k - 6) if k >= 6 else []
-        tail = ((D * rstride * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c) if k == 5 else
-                (D * rstride * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
+        mids = [l3] + [mid] * (last_pp - 4) if last_pp >= 4 else []
+        tail = ((D * tail_out * 8 + 2 * D * k * 8 + D * 20, D * (k + 2 * c) + R3 * c) if last_pp == 3 else
+                (D * tail_out * 8 + 2 * DC * c * 8 + D * 20, DC * (c + k)))
     if mids:
         mid_avg = (sum(x[0] for x in mids) / len(mids), sum(x[1] for x in mids) / len(mids))
     else:
         mid_avg = mid
+    if ptail:
+        # layer k-2 reads the used values of both window ends' blocks and keeps
+        # 16 values per deep row; per row with a window: lg + ng y-scaled
+        # multipliers, lg^2 products over the pair and single sums summed over
+        # the groups, 2 lg ng over the groups' single sums, ng over their totals
+        label_tail = (2 * DC * ng * ns * 8 + D * 16 * 8 + D * 20,
+                      DC * (lg + ng + lg * lg + 2 * lg * ng + ng))
+        last = (2 * T3 * (lg + ng) * 8 + T3 * 16 + n * 8, T3 * (lg + ng))
+    else:
+        last = (2 * T3 * rstride * 8 + T3 * 16 + n * 8, T3 * rstride)
     alg = {
         "first_layer": (P * 8 + P * 12, 0),
         "second_layer": (S * k * 8 + S * 20 + 2 * S * 8, S * (1 + k)),
         "mid_layer": mid_avg,
         "tail_layer": tail,
-        "last_layer": (2 * T3 * rstride * 8 + T3 * 16 + n * 8, T3 * rstride),
+        "last_layer": last,
         "ztable": (n * k * 8, ztable_mults),
     }
+    if ptail:
+        alg["label_tail_layer"] = label_tail
     if third is not None:
         per_query = kt.get("third_layer", (0, 0))[1] / queries
         if per_query:
@@ -1129,7 +1164,7 @@ def main():
         del gu
         g5 = W.served_powerlaw()
         line["served_powerlaw"] = served_metrics(
-            capi, g5, nq=100, seed=W.GRAPH_SEED_BASE + 5, warm=4,
+            capi, g5, nq=100, seed=W.GRAPH_SEED_BASE + 5, warm=4, batching_probe=False,
             workload="plain queries, k~U{6..12}, s~U, on the Chung-Lu exponent 2.3 graph "
                      "n=1e7 m=1e8 t~U[1,1e5] delta~U{10..200}")
         del g5

@@ -37,14 +37,20 @@ enum BatchKind : uint32_t {
     kThirdTail = 7,    // layer 3 when k = 5, transformed state out
     kLastDeep = 8,     // layer k-1 (k >= 5) from the transformed deep-row state
     kFix1 = 9,         // carry fix-up of cut segments, phase 1 (one task per cut segment)
-    kFix2 = 10         // carry fix-up, phase 2 (one task per kFixRows row slots)
+    kFix2 = 10,        // carry fix-up, phase 2 (one task per kFixRows row slots)
+    // the pair tail (k >= 8, 256-point chunks): layer k-3 writes its sums over
+    // one- and two-label point sets, layer k-2 runs in label space, layer k-1
+    // reads its rows
+    kMidPair = 12,     // layer k-3, pair sums out
+    kLabelTail = 13,   // layer k-2 in label space (one task per scheduling range)
+    kLastLabel = 14    // layer k-1 from the label-space rows
 };
 
 // does a layer of this kind write prefix state (that cut segments must fix)?
 __host__ __device__ inline bool writes_state(uint32_t kind)
 {
     return kind == kSecondTail || kind == kThirdFull || kind == kThirdTail || kind == kMidFull ||
-           kind == kMidTail;
+           kind == kMidTail || kind == kMidPair || kind == kLabelTail;
 }
 __host__ __device__ inline bool writes_transformed(uint32_t kind)
 {
@@ -87,6 +93,7 @@ struct BatchArgs {
     const uint64_t *pr2_off; // per query, in words
     uint64_t *slot_base;
     uint64_t slot_words, rows, full_words;  // rows = state rows + 1; full_words = rows * max chunk
+    uint64_t red_words;   // words of a slot's transformed buffer (the label-space rows follow)
     uint32_t *done;       // per unit: tasks completed
     uint32_t *ctl;        // [0] next task, [1] abort
     int32_t *status;      // per query
@@ -137,7 +144,7 @@ __device__ __forceinline__ void set_list(V2Params &vp, const ListPtrs &L, int wi
 
 template <int PPL>
 __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg, const BatchUnit &u,
-                                         uint32_t local)
+                                         uint32_t local, uint64_t *sm)
 {
     V2Params vp{};
     vp.qd = a.descs + u.q;
@@ -154,11 +161,15 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
     uint64_t *full0 = a.slot_base + (size_t)u.slot * a.slot_words;
     uint64_t *full1 = full0 + a.full_words;
     uint64_t *red = full1 + a.full_words;
+    uint64_t *lrows = red + a.red_words;
     uint64_t *bufs[2] = {full0, full1};
     const uint32_t l = sg.layer;
-    const bool last = sg.kind == kLast || sg.kind == kLastDeep;
-    const uint32_t item = last ? local : local / sg.ngroups;
-    const uint32_t group = last ? 0u : local - item * sg.ngroups;
+    // kinds with one task per scheduling range (no point-group split)
+    const bool per_item = sg.kind == kLast || sg.kind == kLastDeep || sg.kind == kLabelTail ||
+                          sg.kind == kLastLabel;
+    const uint32_t item = per_item ? local : local / sg.ngroups;
+    const uint32_t group = per_item ? 0u : local - item * sg.ngroups;
+    constexpr int LG = PPL == 4 ? 7 : 6;
     switch (sg.kind) {
     case kSecondFull:
         set_list(vp, a.state, 0);
@@ -192,13 +203,34 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
         vp.st_out = red;
         layer_warp<PPL, false, 1, true>(vp, item, group);
         break;
+    case kMidPair:
+        set_list(vp, a.deep, 3);
+        vp.st_in = bufs[(l - 1) & 1u];
+        vp.st_out = red;
+        layer_warp<PPL, false, 2, true>(vp, item, group);
+        break;
+    case kLabelTail:
+        set_list(vp, a.deep, 3);
+        vp.st_in = red;
+        vp.st_out = lrows;
+        label_tail_warp<LG, true>(vp, item, sm);
+        break;
+    case kLastLabel:
+        set_list(vp, a.tail3, 3);
+        vp.st_in = lrows;
+        last_label_warp<LG, true>(vp, item);
+        break;
     case kFix1:
     case kFix2: {
         const ListPtrs &L = sg.fixed_kind == kSecondTail ? a.state : a.deep;
-        constexpr uint32_t LG = PPL == 4 ? 7u : 6u;
-        const bool tr = writes_transformed(sg.fixed_kind);
-        uint64_t *buf = tr ? red : bufs[l & 1u];
-        const uint32_t width = tr ? (u.chunk / (32u * PPL)) * (LG + 1) : u.chunk;
+        const uint32_t fk = sg.fixed_kind;
+        const bool tr = writes_transformed(fk);
+        const bool pr = fk == kMidPair;
+        uint64_t *buf = fk == kLabelTail ? lrows : ((tr || pr) ? red : bufs[l & 1u]);
+        const uint32_t ng = u.chunk / (32u * PPL);
+        const uint32_t width = fk == kLabelTail ? kLabelTailWidth
+                               : pr ? ng * kPairTailSlots
+                               : tr ? ng * (uint32_t)(LG + 1) : u.chunk;
         const int lane = threadIdx.x & 31;
         if (sg.kind == kFix1) {
             const uint2 ch = L.chains[local];
@@ -213,12 +245,12 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
     case kLastDeep:
         set_list(vp, a.tail3, 3);
         vp.st_in = red;
-        last_warp<PPL == 4 ? 7 : 6, true>(vp, item);
+        last_warp<LG, true>(vp, item);
         break;
     default:
         set_list(vp, a.tail, 1);
         vp.st_in = red;
-        last_warp<PPL == 4 ? 7 : 6, true>(vp, item);
+        last_warp<LG, true>(vp, item);
         break;
     }
 }
@@ -232,6 +264,8 @@ template <int MINB>
 __global__ void __launch_bounds__(kW2 * 32, MINB) k_batch(const BatchArgs a)
 {
     const int lane = threadIdx.x & 31;
+    __shared__ uint64_t sm_tail[kW2][192];  // the label-space layer's products (per warp)
+    uint64_t *sm = sm_tail[threadIdx.x >> 5];
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(a.ctl, 1u);
@@ -254,8 +288,8 @@ __global__ void __launch_bounds__(kW2 * 32, MINB) k_batch(const BatchArgs a)
             // layer 3 writing full state takes 2 points per lane whatever the
             // unit's shape: the stored rows do not depend on the lane-to-point
             // map, and this multiply-heavy layer needs half the registers so
-            if (u.ppl == 4 && sg.kind != kThirdFull) run_task<4>(a, sg, u, t - sg.begin);
-            else run_task<2>(a, sg, u, t - sg.begin);
+            if (u.ppl == 4 && sg.kind != kThirdFull) run_task<4>(a, sg, u, t - sg.begin, sm);
+            else run_task<2>(a, sg, u, t - sg.begin, sm);
         }
         __threadfence();  // release side: publish this task's writes
         __syncwarp();
@@ -411,12 +445,10 @@ __global__ void k_batch_bitmap(uint32_t n, const QueryDesc *__restrict__ descs)
     }
 }
 
-// zero row (row 0) of every slot's three buffers: `width` words of each full
-// buffer (its widest row) and 32 words of the transformed buffer
-// Zero row 0 of both full buffers (width values) and of the transformed buffer
-// (red_width values) of every slot.
+// Zero row 0 of both full buffers (width values), of the transformed buffer
+// (red_width values) and of the label-space rows of every slot.
 __global__ void k_batch_zero_rows(uint64_t *slot_base, uint64_t slot_words, uint64_t full_words,
-                                  uint32_t nslots, uint32_t width, uint32_t red_width)
+                                  uint32_t nslots, uint32_t width, uint32_t red_width, uint64_t red_words)
 {
     const uint32_t s = blockIdx.x;
     if (s >= nslots) return;
@@ -426,6 +458,7 @@ __global__ void k_batch_zero_rows(uint64_t *slot_base, uint64_t slot_words, uint
         b[full_words + i] = 0;
     }
     for (uint32_t i = threadIdx.x; i < red_width; i += blockDim.x) b[2 * full_words + i] = 0;
+    for (uint32_t i = threadIdx.x; i < kLabelTailWidth; i += blockDim.x) b[2 * full_words + red_words + i] = 0;
 }
 
 ListPtrs list_ptrs(const RowList &L, bool coarse)
@@ -478,14 +511,26 @@ static rr_status batch_fixup(const ListPtrs &L, uint64_t *base, const uint64_t *
 
 // Tasks of layer l of a unit with (k, ppl, chunk), over the coarse or the fine
 // scheduling ranges of the layer's row list.
-uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, bool coarse,
-                     uint32_t *kind)
+uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t chunk, uint32_t ngroups,
+                     bool coarse, uint32_t *kind)
 {
     auto items = [coarse](const RowList &L) { return coarse ? L.nitems_coarse : L.nitems; };
     if (k <= 3) return 0;  // closed forms in the prologue
+    // the pair tail: 256-point chunks need k >= 8, so layer k-3 >= 5 is a
+    // middle layer
+    const bool ptail = !g.pair_tail_off && k >= 8 && chunk >= kPairTailMinChunk &&
+                       ngroups <= kPairTailMaxGroups;
     if (l == k - 1) {
-        *kind = k == 4 ? kLast : kLastDeep;
+        *kind = k == 4 ? kLast : (ptail ? kLastLabel : kLastDeep);
         return k == 4 ? items(g.tail_list) : items(g.tail3_list);
+    }
+    if (ptail && l == k - 2) {
+        *kind = kLabelTail;
+        return items(g.deep_list);
+    }
+    if (ptail && l == k - 3) {
+        *kind = kMidPair;
+        return items(g.deep_list) * ngroups;
     }
     if (l == 2) {
         if (k >= 5) return 0;  // label-space layer 2 runs in the prologue
@@ -498,19 +543,28 @@ uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t ngroups, b
 
 }  // namespace
 
-// Values a transformed row holds in a slot of max chunk `chunk`: 8 per lane
-// group of 128 points (4 points per lane), at least the 7 of one 64-point
-// group (2 points per lane), rounded up to 32.
+// Values a transformed row holds in a slot of max chunk `chunk`: a 32-value
+// block of pair sums per lane group of 128 points (4 points per lane; the sums
+// over single labels take 8), one block for a 64-point group (2 points per
+// lane).
 static uint64_t red_words_for(uint32_t chunk)
 {
-    return std::max<uint64_t>(32, (chunk + 127) / 128 * 8);
+    return std::max<uint64_t>(kPairTailSlots, (chunk + 127) / 128 * kPairTailSlots);
 }
 
-// Words of device memory one batch slot holds for max chunk `chunk`.
-static uint64_t slot_words_for(const Graph &g, uint32_t chunk)
+// Words of a slot's transformed buffer for max chunk `chunk`.
+static uint64_t red_buffer_words(const Graph &g, uint32_t chunk)
 {
     const uint64_t srows = g.state_list.count + 1, drows = g.deep_list.count + 1;
-    return drows * chunk * 2 + std::max(srows, drows) * red_words_for(chunk);
+    return std::max(srows, drows) * red_words_for(chunk);
+}
+
+// Words of device memory one batch slot holds for max chunk `chunk`: two full
+// buffers, the transformed buffer, the pair tail's label-space rows.
+static uint64_t slot_words_for(const Graph &g, uint32_t chunk)
+{
+    const uint64_t drows = g.deep_list.count + 1;
+    return drows * chunk * 2 + red_buffer_words(g, chunk) + drows * kLabelTailWidth;
 }
 
 rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t *d_bitmaps,
@@ -667,7 +721,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                     if (l > u.k - 1) continue;
                     uint32_t ngroups = u.chunk / (32u * u.ppl);
                     uint32_t kind;
-                    uint32_t nt = layer_tasks(g, u.k, l, ngroups, coarse, &kind);
+                    uint32_t nt = layer_tasks(g, u.k, l, u.chunk, ngroups, coarse, &kind);
                     if (nt == 0) continue;
                     if (kind == kThirdFull && u.ppl == 4) {
                         // layer 3 runs with 2 points per lane (see run_task)
@@ -813,7 +867,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         }
         k_batch_zero_rows<<<nslots, 256, 0, st>>>(d_slots.as<uint64_t>(), slot_bytes / 8,
                                                   (g.deep_list.count + 1) * max_chunk, nslots,
-                                                  max_chunk, (uint32_t)red_words_for(max_chunk));
+                                                  max_chunk, (uint32_t)red_words_for(max_chunk),
+                                                  red_buffer_words(g, max_chunk));
         RR_LAUNCHED();
 
         BatchArgs a{};
@@ -839,6 +894,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         a.slot_words = slot_bytes / 8;
         a.rows = rows;
         a.full_words = (g.deep_list.count + 1) * max_chunk;
+        a.red_words = red_buffer_words(g, max_chunk);
         a.done = d_done.as<uint32_t>();
         a.ctl = d_ctl.as<uint32_t>();
         a.status = status;

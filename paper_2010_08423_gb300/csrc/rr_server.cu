@@ -5,18 +5,18 @@
 // soon as a slot is free and the device-memory budget holds the query's
 // scratch, enqueues the query's layer launches on the slot's stream (so the
 // work of queries admitted at different times overlaps on the GPU), and
-// retires queries whose completion event has fired. Under a backlog (at
-// least kMinBatch queued queries of the reduced-state engine) the queued
-// queries go instead, up to kMaxBatch at a time, to one of two batch lanes,
-// each running the persistent batch kernel over its queries: a backlog of
-// short queries is served at the batch kernel's rate rather than the
-// single-query rate, and with two lanes the next batch is planned while the
-// current one runs. Batching is on by default only on graphs of at most
-// kBatchEdgeLimit edges: there one query's layers are too short to keep the
-// GPU busy on their own (n = 1e5, m = 1e6, k ~ U{6..12}: 8.4k against 6.8k
-// queries/s), while on larger graphs they fill it and the per-query launch
-// sequence is faster than the batch kernel (n = 1e7, m = 1e8: 3.1 against
-// 3.7 queries/s). Results are bit-identical to rr_reach_sync either way.
+// retires queries whose completion event has fired. With batching turned on
+// (rr_server_set_batching), a backlog of at least min_batch queued queries of
+// the reduced-state engine goes instead, up to max_batch at a time, to one of
+// two batch lanes, each running the persistent batch kernel over its queries;
+// with two lanes the next batch is planned while the current one runs.
+// Batching is off by default: the slots' concurrent launch sequences (each
+// query a captured CUDA graph of programmatically dependent launches) serve
+// faster than the batch kernel both where one query's layers are short
+// (n = 1e5, m = 1e6, plain k ~ U{6..12}, a burst of 160 queries: about
+// 13,000 queries/s on 4 slots against 9,000 with batches of up to 64) and
+// where they fill the GPU (n = 1e7, m = 1e8). Results are bit-identical to
+// rr_reach_sync either way.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -69,17 +69,15 @@ struct Slot {
 struct BatchLane {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    DevBuf w, bm, status;            // kMaxBatch witnesses / bitmaps / abort statuses
+    DevBuf w, bm, status;            // lane_cap witnesses / bitmaps / abort statuses
     int32_t *h_status = nullptr;     // pinned copy of the statuses
     std::vector<uint64_t> tickets;   // the batch's queries, in order
     std::vector<int> results;        // their result buffers
     bool busy = false;
 };
 
-constexpr uint32_t kMinBatch = 8;
-constexpr uint32_t kMaxBatch = 64;
+constexpr uint32_t kMinBatch = 8;    // lanes exist when both hold at least this many queries
 constexpr uint32_t kLaneCap = 256;  // largest batch a lane's buffers hold
-constexpr uint64_t kBatchEdgeLimit = 1ull << 24;
 
 struct Server {
     const Graph *g = nullptr;
@@ -170,7 +168,7 @@ rr_status Server::make_lanes()
 }
 
 // Queued queries the batch kernel can take (reduced-state engine), counted
-// from the front of the queue up to kMinBatch.
+// from the front of the queue up to min_batch.
 uint32_t Server::batchable_queued() const
 {
     if (!min_batch) return 0;
@@ -486,19 +484,12 @@ rr_status rr_server_create(const rr_graph *g, uint64_t device_mem_budget, uint32
         spares.push_back(id);
     }
     s->free_results = spares;
-    // batch lanes, when the graph runs the reduced-state engine and a quarter
-    // of the budget holds two lanes' outputs for at least kMinBatch queries
+    // batch lanes (allocated when rr_server_set_batching turns batching on),
+    // when the graph runs the reduced-state engine and a quarter of the budget
+    // holds two lanes' outputs for at least kMinBatch queries
     const uint64_t per_query = (uint64_t)g->n * 8 + ((uint64_t)g->n + 7) / 8;
     const uint64_t fit = s->budget / 4 / (2 * per_query);
-    if (uses_v2(*g, 2) && fit >= kMinBatch) {
-        s->lane_cap = (uint32_t)std::min<uint64_t>(kLaneCap, fit);
-        if (g->m <= kBatchEdgeLimit) {
-            rr_status ls = s->make_lanes();
-            if (ls != RR_OK) return ls;
-            s->min_batch = kMinBatch;
-            s->max_batch = std::min(kMaxBatch, s->lane_cap);
-        }
-    }
+    if (uses_v2(*g, 2) && fit >= kMinBatch) s->lane_cap = (uint32_t)std::min<uint64_t>(kLaneCap, fit);
     s->th = std::thread([p = s.get()] { p->run(); });
     *out = s.release();
     return RR_OK;

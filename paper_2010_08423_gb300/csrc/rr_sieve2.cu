@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_label_tail(const V2Params p)
     __shared__ uint64_t sm[kW2][192];
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
-    label_tail_warp<LG>(p, task, sm[threadIdx.x >> 5]);
+    label_tail_warp<LG, false>(p, task, sm[threadIdx.x >> 5]);
 }
 
 template <int LG>
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_last_label(const V2Params p)
 {
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
-    last_label_warp<LG>(p, task);
+    last_label_warp<LG, false>(p, task);
 }
 
 static unsigned blocks_for(uint64_t tasks)
@@ -284,6 +284,9 @@ static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st
 {
     const uint64_t tasks = (uint64_t)vp.nitems * vp.ngroups;
     if (tasks == 0) return RR_OK;
+    // pair sums (out 2) come only from a middle layer: the pair tail needs
+    // 256-point chunks, so k >= 8 and layer k-3 >= 5
+    if (out == 2 && src != 0) return fail(RR_EINVAL, "internal: pair sums from a first per-point layer");
     const int tslot = timing_begin(st);
     const unsigned blocks = blocks_for(tasks);
     const dim3 B(kW2 * 32);
@@ -292,11 +295,9 @@ static rr_status launch_v2(const V2Params &vp, int src, int out, cudaStream_t st
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, true, 1>, dim3(blocks), B, st, vp));
     } else if (src == 2) {
         if (out == 1) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, true>, dim3(blocks), B, st, vp));
-        else if (out == 2) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 2, true>, dim3(blocks), B, st, vp));
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, true>, dim3(blocks), B, st, vp));
     } else if (src == 3) {
         if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0, false, true>, dim3(blocks), B, st, vp));
-        else if (out == 2) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 2, false, true>, dim3(blocks), B, st, vp));
         else RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 1, false, true>, dim3(blocks), B, st, vp));
     } else {
         if (out == 0) RR_CUDA(launch_pdl(k_layer_v2<PPL, false, 0>, dim3(blocks), B, st, vp));
@@ -347,12 +348,14 @@ static uint64_t carry_words(const Graph &g, uint32_t chunk, uint32_t k)
 
 // Layers k-2 and k-1 from layer k-3's pair sums (the pair tail): when layer
 // k-3 keeps per-point state (k >= 6; k >= 7 with layer 3 in pair-label space)
-// and a chunk has at most kPairTailMaxGroups point groups, unless the load
-// flags turn it off.
+// and a chunk has kPairTailMinChunk points or more in at most
+// kPairTailMaxGroups point groups, unless the load flags turn it off. (256
+// points need k >= 8: layer k-3 is then a middle layer.)
 static bool pair_tail(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
 {
     const uint32_t first = pair_layer3(g, k) ? 4u : 3u;  // the first per-point layer
-    return !g.pair_tail_off && k >= 6 && first + 3 <= k && chunk / (32u * ppl) <= kPairTailMaxGroups;
+    return !g.pair_tail_off && k >= 6 && first + 3 <= k && chunk >= kPairTailMinChunk &&
+           chunk / (32u * ppl) <= kPairTailMaxGroups;
 }
 
 // Words of the pair tail's label-space rows (layer k-2), zero when it is off.

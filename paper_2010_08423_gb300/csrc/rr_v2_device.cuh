@@ -53,6 +53,10 @@ __host__ __device__ __forceinline__ uint32_t pair_count(uint32_t k)
 constexpr uint32_t kPairTailSlots = 32;
 constexpr uint32_t kLabelTailWidth = 16;
 constexpr uint32_t kPairTailMaxGroups = 8;
+// Layer k-2 in label space costs 5 to 7 products per lane and row, the
+// per-point layer it replaces chunk/32: the pair tail runs for chunks of at
+// least this many points.
+constexpr uint32_t kPairTailMinChunk = 256;
 template <int LG>
 __host__ __device__ __forceinline__ uint32_t pair_tail_slot(uint32_t A)
 {
@@ -1097,8 +1101,10 @@ __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
 // the groups and multiplies it by the multipliers its label pair or single
 // label needs; lane q of each group pass takes (group q/8, slot q%8) of the
 // singles and totals. The products meet their targets in `sm` (192 values).
+// COHERENT: the pair sums were written earlier in the same launch (read
+// through L2).
 // ---------------------------------------------------------------------------
-template <int LG>
+template <int LG, bool COHERENT>
 __device__ __forceinline__ void label_tail_warp(const V2Params &p, uint32_t item, uint64_t *sm)
 {
     constexpr uint32_t NS = 1u + LG + LG * (LG - 1) / 2;  // used slots of a group block
@@ -1111,22 +1117,21 @@ __device__ __forceinline__ void label_tail_warp(const V2Params &p, uint32_t item
     const uint32_t blk_w = ng * kPairTailSlots;            // values per input row
     const uint32_t rb_passes = (ng * 8u + 31u) / 32u;      // group passes (ng <= 8: at most 2)
     const uint32_t ntarget = LG + ng;
+    auto ld = [](const uint64_t *q) { return COHERENT ? __ldcg(q) : __ldg(q); };
 
     // slot pass: what lane s computes (s < NS). single i: P0 = m_i T -> R_i;
-    // pair (i < j): P0 = m_j T -> R_i and P1 = m_i T -> R_j; s = 0 (total): nothing
-    uint32_t srcA = 0, srcB = 0;
-    bool useA = false, useB = false;
+    // pair (i < j): P0 = m_j T -> R_i and P1 = m_i T -> R_j; s = 0 (total):
+    // nothing. Packed: bits 0-4 the lane of P0's multiplier, 5-9 P1's, bit 10
+    // / 11 set when P0 / P1 is used.
+    uint32_t dec = 0;
     if (lane >= 1 && lane <= (uint32_t)LG) {
-        srcA = lane - 1;
-        useA = true;
+        dec = (lane - 1) | (1u << 10);
     } else if (lane > (uint32_t)LG && lane < NS) {
         const uint32_t idx = lane - 1 - LG;
         uint32_t j = 1;
         while ((j + 1) * j / 2 <= idx) ++j;  // largest j with j(j-1)/2 <= idx
         const uint32_t i = idx - j * (j - 1) / 2;
-        srcA = j;
-        srcB = i;
-        useA = useB = true;
+        dec = j | (i << 5) | (3u << 10);
     }
     // target lane t: the smem positions it sums (see the gather below)
     uint32_t cur = p.head[it.x];
@@ -1170,10 +1175,10 @@ __device__ __forceinline__ void label_tail_warp(const V2Params &p, uint32_t item
                 uint64_t ts = 0;
                 if (lane < NS)
                     for (uint32_t g = 0; g < ng; ++g)
-                        ts ^= __ldg(rb + g * kPairTailSlots + lane) ^ __ldg(ra + g * kPairTailSlots + lane);
-                const uint64_t mA = shfl64b(m, (int)srcA), mB = shfl64b(m, (int)srcB);
-                sm[2 * lane] = rr_mul(useA ? mA : 0ull, ts);
-                sm[2 * lane + 1] = rr_mul(useB ? mB : 0ull, ts);
+                        ts ^= ld(rb + g * kPairTailSlots + lane) ^ ld(ra + g * kPairTailSlots + lane);
+                const uint64_t mA = shfl64b(m, (int)(dec & 31u)), mB = shfl64b(m, (int)((dec >> 5) & 31u));
+                sm[2 * lane] = rr_mul((dec >> 10) & 1u ? mA : 0ull, ts);
+                sm[2 * lane + 1] = rr_mul((dec >> 11) & 1u ? mB : 0ull, ts);
                 // group passes: (g, s) = (q / 8, q % 8); s = 0 the total V_g,
                 // s = 1 + i the single T_g{i}: P0 = A'_g T -> R_i (s > 0) or
                 // R_{g,*} (s = 0), P1 = m_i T -> R_{g,*} (s > 0)
@@ -1181,8 +1186,8 @@ __device__ __forceinline__ void label_tail_warp(const V2Params &p, uint32_t item
                     const uint32_t q = lane + 32u * r;
                     const uint32_t g = q >> 3, s = q & 7u;
                     const bool ok = g < ng && s <= (uint32_t)LG;
-                    const uint64_t tv = ok ? (__ldg(rb + g * kPairTailSlots + s) ^
-                                              __ldg(ra + g * kPairTailSlots + s)) : 0ull;
+                    const uint64_t tv = ok ? (ld(rb + g * kPairTailSlots + s) ^
+                                              ld(ra + g * kPairTailSlots + s)) : 0ull;
                     const uint64_t mg = shfl64b(m, (int)min((uint32_t)LG + g, 31u));
                     const uint64_t mi = shfl64b(m, (int)(s == 0 ? 0u : s - 1u));
                     sm[kPB + 2 * q] = rr_mul(ok ? mg : 0ull, tv);
@@ -1215,7 +1220,7 @@ __device__ __forceinline__ void label_tail_warp(const V2Params &p, uint32_t item
 // Last layer of the pair tail: lane t < LG + ng accumulates sum_f y_f dR_t over
 // the rows f of one head vertex w (dR = the window of R), then multiplies once
 // by zw_t (t < LG) or A_{w,t-LG}, and the warp XOR-reduces into S[w].
-template <int LG>
+template <int LG, bool COHERENT>
 __device__ __forceinline__ void last_label_warp(const V2Params &p, uint32_t task)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -1269,8 +1274,9 @@ __device__ __forceinline__ void last_label_warp(const V2Params &p, uint32_t task
             const uint64_t y = shfl64b(m_y, (int)t);
             uint64_t yt = 0;
             if (active && a != b) {
-                const uint64_t dr = __ldg(p.st_in + (size_t)a * kLabelTailWidth + lane) ^
-                                    __ldg(p.st_in + (size_t)b * kLabelTailWidth + lane);
+                const uint64_t *ra = p.st_in + (size_t)a * kLabelTailWidth + lane;
+                const uint64_t *rb = p.st_in + (size_t)b * kLabelTailWidth + lane;
+                const uint64_t dr = COHERENT ? (__ldcg(ra) ^ __ldcg(rb)) : (__ldg(ra) ^ __ldg(rb));
                 yt = rr_mul(y, dr);
                 acc ^= yt;
             }

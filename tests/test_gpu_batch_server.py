@@ -159,15 +159,17 @@ def test_server_result_alone_equals_result_in_mix(mixed):
 
 
 def test_server_backlog_goes_through_batch_lanes(mixed):
-    """A burst of queued queries is admitted in batches (persistent kernel) and
-    every result still equals the single-query result; a query cancelled in
-    the middle of the burst ends cancelled, the others are unaffected."""
+    """With batching turned on, a burst of queued queries is admitted in batches
+    (persistent kernel) and every result still equals the single-query result;
+    a query cancelled in the middle of the burst ends cancelled, the others are
+    unaffected."""
     g, qs = mixed
     n = g["n"]
     burst = (qs * 6)[:90]
     with capi.Graph(g) as G:
         srv = capi.rr_server_create(G.handle, 0, 2)
         try:
+            capi.rr_server_set_batching(srv, 8, 64)
             ts = [capi.rr_query_submit(srv, q["source"], q["k"], q["seed"], q["motif"])
                   for q in burst]
             capi.rr_query_cancel(srv, ts[45])
@@ -201,16 +203,22 @@ def test_server_batching_switch():
                 with pytest.raises(capi.RRError) as ei:
                     capi.rr_server_set_batching(srv, *bad)
                 assert ei.value.status == capi.RR_EINVAL
-            capi.rr_server_set_batching(srv, 0, 0)  # off: every query takes a slot
+            # off by default: a burst takes the slots
             ts = [capi.rr_query_submit(srv, i % 50, 5 + i % 4, i) for i in range(40)]
             ws = [capi.rr_query_poll(srv, t, n, -1)[2] for t in ts]
             assert capi.rr_server_stats(srv) == (40, 0, 0)
+            capi.rr_server_set_batching(srv, 8, 64)
+            capi.rr_server_set_batching(srv, 0, 0)  # off again: every query takes a slot
+            ts = [capi.rr_query_submit(srv, i % 50, 5 + i % 4, i) for i in range(40)]
+            for w, t in zip(ws, ts):
+                assert np.array_equal(capi.rr_query_poll(srv, t, n, -1)[2], w)
+            assert capi.rr_server_stats(srv) == (80, 0, 0)
             capi.rr_server_set_batching(srv, 2, 256)  # on again, every backlog of 2
             ts = [capi.rr_query_submit(srv, i % 50, 5 + i % 4, i) for i in range(40)]
             for w, t in zip(ws, ts):
                 assert np.array_equal(capi.rr_query_poll(srv, t, n, -1)[2], w)
             single, batched, batches = capi.rr_server_stats(srv)
-            assert single + batched == 80 and batched >= 2 and batches >= 1
+            assert single + batched == 120 and batched >= 2 and batches >= 1
         finally:
             capi.rr_server_destroy(srv)
 

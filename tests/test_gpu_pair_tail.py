@@ -1,11 +1,12 @@
 """The pair tail: layer k-3 stores its sums over the points of a group that
 hold one or two given labels, layer k-2 runs in label space from them, and the
-last layer reads its label-space rows. Against the oracle and against the
-per-point tail (load flag bit 5), bit for bit: witness and per-edge sums over
-k = 6..11, both lane shapes, chunks of 1 to 8 point groups (16 and 32 groups
-fall back to the per-point tail), layer 3 per point or in pair-label space
-(layer 4 then writes the pair sums at k = 7), cut hub segments, point ranges
-whose chunks do not start at a multiple of the chunk size, motif queries."""
+last layer reads its label-space rows (chunks of 256 points or more in at most
+8 point groups; other shapes keep the per-point tail). Against the oracle and
+against the per-point tail (load flag bit 5), bit for bit: witness and
+per-edge sums over k = 6..12, both lane shapes, chunks of 2 to 8 point groups
+and shapes on either side of the limits, layer 3 per point or in pair-label
+space, cut hub segments, point ranges whose chunks do not start at a multiple
+of the chunk size, motif queries, and the persistent batch."""
 import numpy as np
 import pytest
 
@@ -32,10 +33,12 @@ def test_info_reports_the_pair_tail():
         assert G.info()["pair_tail"] == 0
 
 
-# (k, points per lane, points per chunk): 1, 2, 4 and 8 point groups; the
-# (11, 2, 2048) shape has 32 groups and keeps the per-point tail
-SHAPES = [(6, 2, 64), (6, 4, 128), (7, 2, 128), (7, 4, 128), (8, 2, 256), (8, 4, 256),
-          (9, 2, 512), (9, 4, 512), (10, 4, 1024), (10, 2, 256), (11, 4, 1024), (11, 2, 2048)]
+# (k, points per lane, points per chunk): 2, 4 and 8 point groups of 256 points
+# or more; (6, 2, 64), (7, 4, 128) and (9, 2, 192) are below 256 points and
+# (11, 2, 2048) has 32 groups: those keep the per-point tail
+SHAPES = [(6, 2, 64), (7, 4, 128), (8, 2, 256), (8, 4, 256), (9, 2, 192), (9, 2, 512),
+          (9, 4, 512), (10, 4, 1024), (10, 2, 256), (10, 4, 384), (11, 4, 1024), (11, 2, 2048),
+          (12, 4, 512)]
 
 
 @pytest.mark.parametrize("pair_flag", [capi.FLAG_PAIR_OFF, capi.FLAG_PAIR_ON])
@@ -85,7 +88,7 @@ def test_cut_hub_segments():
     with capi.Graph(g) as G:
         assert G.info()["max_in_degree"] >= 1900
         nonzero = 0
-        for k, ppl, chunk in ((6, 2, 64), (7, 4, 128), (8, 2, 192), (9, 4, 384), (10, 4, 1024)):
+        for k, ppl, chunk in ((8, 2, 256), (8, 4, 256), (9, 4, 384), (10, 4, 1024), (10, 2, 448)):
             capi.rr_set_tuning(G.handle, k, ppl, chunk)
             ref = oracle.sieve(g, 9, k, 190 + k)
             _, w = G.reach(9, k, 190 + k)
@@ -107,3 +110,29 @@ def test_ranges_off_the_chunk_grid():
             ref = oracle.sieve(g, 5, k, 77 + k, masks=np.arange(first, first + count, dtype=np.uint32))
             assert np.array_equal(part, ref), (k, first, count)
             assert np.count_nonzero(ref) > 0, (k, first, count)
+
+
+def test_batch_matches_single_queries_and_oracle():
+    """The persistent batch with the pair tail (units of 256 points or more)
+    and without it (load flag bit 5), against single queries and the oracle."""
+    import torch
+    g = W.uniform(1500, 20_000, 30, 0, 5, 12, ncolors=3)
+    rng = np.random.default_rng(9)
+    qs = []
+    for i in range(24):
+        k = int(rng.integers(4, 13))
+        s = int(rng.integers(0, g["n"]))
+        motif = ([int(g["color"][s])] + [int(x) for x in rng.integers(0, 3, k - 1)]) if i % 2 else None
+        qs.append({"source": s, "k": k, "seed": int(rng.integers(1, 2**62)), "motif": motif})
+    refs = [oracle.sieve(g, q["source"], q["k"], q["seed"], motif=q["motif"]) for q in qs]
+    assert sum(int(np.count_nonzero(r) > 0) for r in refs) >= 12
+    for flags in (0, capi.FLAG_PAIR_TAIL_OFF):
+        with capi.Graph(g, flags) as G:
+            for mc in (256, 512, 1024):
+                capi.rr_set_batch_tuning(G.handle, 6, 2, mc)
+                d_w = torch.zeros((len(qs), g["n"]), dtype=torch.int64, device="cuda")
+                capi.rr_reach_batch_device(G.handle, qs, d_w)
+                torch.cuda.synchronize()
+                w = d_w.cpu().numpy().view(np.uint64)
+                for i, r in enumerate(refs):
+                    assert np.array_equal(w[i], r), (flags, mc, i, qs[i]["k"])
