@@ -142,6 +142,14 @@ __device__ __forceinline__ void set_list(V2Params &vp, const ListPtrs &L, int wi
     vp.nitems = L.nitems;
 }
 
+// The label-space layer of the pair tail as a call of its own: inlined, its
+// live values raised the register pressure of every task kind of the kernel.
+template <int LG>
+__device__ __noinline__ void batch_label_tail(const V2Params vp, uint32_t item, uint64_t *sm)
+{
+    label_tail_warp<LG, true>(vp, item, sm);
+}
+
 template <int PPL>
 __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg, const BatchUnit &u,
                                          uint32_t local, uint64_t *sm)
@@ -213,7 +221,7 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
         set_list(vp, a.deep, 3);
         vp.st_in = red;
         vp.st_out = lrows;
-        label_tail_warp<LG, true>(vp, item, sm);
+        batch_label_tail<LG>(vp, item, sm);
         break;
     case kLastLabel:
         set_list(vp, a.tail3, 3);
@@ -516,9 +524,11 @@ uint32_t layer_tasks(const Graph &g, uint32_t k, uint32_t l, uint32_t chunk, uin
 {
     auto items = [coarse](const RowList &L) { return coarse ? L.nitems_coarse : L.nitems; };
     if (k <= 3) return 0;  // closed forms in the prologue
-    // the pair tail: 256-point chunks need k >= 8, so layer k-3 >= 5 is a
-    // middle layer
-    const bool ptail = !g.pair_tail_off && k >= 8 && chunk >= kPairTailMinChunk &&
+    // the pair tail, from 512-point units here (k >= 9; layer k-3 >= 6 is a
+    // middle layer): the label-space layer runs one warp per scheduling range,
+    // which costs more in the batch's dependency chains than in a one-query
+    // launch (256-point units of k = 8 queries were 3% slower with it)
+    const bool ptail = !g.pair_tail_off && k >= 9 && chunk >= 2 * kPairTailMinChunk &&
                        ngroups <= kPairTailMaxGroups;
     if (l == k - 1) {
         *kind = k == 4 ? kLast : (ptail ? kLastLabel : kLastDeep);
