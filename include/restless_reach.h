@@ -126,8 +126,10 @@ typedef struct {
  * given labels: with the pair tail, layer k-3 stores those sums (a 32-value
  * block per deep row and group of points) instead of per-point state, and
  * layer k-2 keeps 16 label-space values per deep row; bit 5 set = never (layer
- * k-2 per point, writing its sums over single labels). Results are
- * bit-identical in every form. The pair
+ * k-2 per point, writing its sums over single labels). Bit 6 / bit 7 set =
+ * rr_reach_atmost_device runs every k' as a query of its own / always takes
+ * the k' it can from the k query's layers (by default: when those layers are
+ * long). Results are bit-identical in every form. The pair
  * rows ((deep rows + 1) * k(k+1)/2 words) and the head table (heads * chunk
  * words) are part of a query's scratch and, unlike the per-point state, do not
  * shrink with the point chunk: a server whose per-slot budget cannot hold them
@@ -283,11 +285,19 @@ rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target,
  * k' = 2..k. d_witness ((k-1) * n uint64, device) gets the witness of k' in row
  * k'-2; d_bitmap (ceil(n/8) bytes, device, may be NULL) gets the union of the
  * reach sets: vertices reached by a restless path of at most k vertices.
- * Ordered on `stream`: the k-1 queries run concurrently on streams of the
- * library's own that start after the work already on `stream` and that
+ * For one seed the k'-vertex query's per-point layers agree with the
+ * k-vertex query's on the first 2^k' points, so the k query also yields the
+ * queries k' >= 5 (k' >= 6 with the pair-label layer 3): after its per-point
+ * layer k'-2 it forms k''s sums over single labels from its stored rows and
+ * runs k''s last layer. That is done where the k query's per-point layers are
+ * long (deep rows with a window times min(2^k, 1024) at least 2^23; with
+ * short layers the concurrent queries finish first; rr_graph_load's bits 6
+ * and 7 force either form). Ordered on
+ * `stream`: the k query and the smaller queries run concurrently on streams of
+ * the library's own that start after the work already on `stream` and that
  * `stream` waits for; when their scratch does not fit 60% of free device memory
- * together they run one after another on `stream`. Scratch stays allocated
- * with the graph. Errors as rr_reach_device. */
+ * together every k' runs as its own query, one after another on `stream`.
+ * Scratch stays allocated with the graph. Errors as rr_reach_device. */
 rr_status rr_reach_atmost_device(const rr_graph *g, uint32_t source, uint32_t k, uint64_t seed,
                                  uint8_t *d_bitmap, uint64_t *d_witness, void *stream);
 

@@ -24,6 +24,8 @@ FLAG_PAIR_OFF = 4
 FLAG_HEAD_TABLE_ON = 8
 FLAG_HEAD_TABLE_OFF = 16
 FLAG_PAIR_TAIL_OFF = 32
+FLAG_ATMOST_LANES = 64
+FLAG_ATMOST_BRANCHES = 128
 
 
 class RRError(RuntimeError):

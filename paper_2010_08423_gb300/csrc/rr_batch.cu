@@ -971,12 +971,6 @@ rr_status ensure_fan_lanes(const Graph &g, uint32_t lanes)
     return RR_OK;
 }
 
-// at-most-k (Algorithm 2 stopped at k): the exact-k' queries for k' = 2..k,
-// row k'-2 of d_witness each. They run concurrently, one lane (workspace and
-// stream) each, largest k' first and on the stream of highest priority, forked
-// from and joined back to `st`; if the
-// scratch of all of them does not fit 60% of free device memory they run in
-// order on the graph's own workspace instead.
 // Runs the persistent kernel's bounded wait on a counter that is never
 // incremented (see k_wait_probe); synchronous.
 rr_status debug_wait_probe(uint64_t timeout_ns, int abort_preset, int32_t *status,
@@ -1005,6 +999,15 @@ rr_status debug_wait_probe(uint64_t timeout_ns, int abort_preset, int32_t *statu
     return RR_OK;
 }
 
+// at-most-k (Algorithm 2 stopped at k): the exact-k' queries for k' = 2..k,
+// row k'-2 of d_witness each. For one seed the k'-vertex query's per-point
+// layers agree with the k-vertex query's on the first 2^k' points, so on the
+// reduced-state engine the k query also yields k' = atmost_first_branch..k-1
+// (its per-point layer k'-2 as their tail: enqueue_query_v2's branches); the
+// rest run concurrently, one lane (workspace and stream) each, largest k'
+// first and on the stream of highest priority, forked from and joined back to
+// `st`. If the scratch of all lanes does not fit 60% of free device memory the
+// queries run in order on the graph's own workspace instead.
 rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
                         uint8_t *d_bitmap, uint64_t *d_witness, cudaStream_t st)
 {
@@ -1027,13 +1030,25 @@ rr_status atmost_device(const Graph &g, uint32_t source, uint32_t k, uint64_t se
         FanOut &F = g.fan;
         rr_status ls = ensure_fan_lanes(g, lanes);
         if (ls != RR_OK) return ls;
+        // k' = bfirst..k-1 come from the k query's own layers (lane 0), the
+        // smaller k' run on their own lanes
+        const uint32_t bfirst = atmost_branches(g, k);
         RR_CUDA(cudaEventRecord(F.fork, st));
         for (uint32_t kk = k; kk >= 2; --kk) {
+            if (bfirst && kk >= bfirst && kk < k) continue;
             const uint32_t j = k - kk;  // lane
             const rr_query q{source, kk, seed, nullptr};
             RR_CUDA(cudaStreamWaitEvent(F.st[j], F.fork, 0));
-            rr_status s = reach_on_stream(g, *F.ws[j], &q, nullptr, d_witness + (size_t)(kk - 2) * g.n,
-                                          per_lane, F.st[j]);
+            rr_status s;
+            if (kk == k && bfirst) {
+                uint64_t *bw = d_witness + (size_t)(bfirst - 2) * g.n;
+                RR_CUDA(cudaMemsetAsync(bw, 0, (size_t)(k - bfirst) * g.n * 8, F.st[j]));
+                s = reach_on_stream(g, *F.ws[j], &q, nullptr, d_witness + (size_t)(kk - 2) * g.n, per_lane,
+                                    F.st[j], nullptr, nullptr, nullptr, PointRange(), bfirst, bw, nullptr);
+            } else {
+                s = reach_on_stream(g, *F.ws[j], &q, nullptr, d_witness + (size_t)(kk - 2) * g.n, per_lane,
+                                    F.st[j]);
+            }
             RR_CUDA(cudaEventRecord(F.done[j], F.st[j]));
             RR_CUDA(cudaStreamWaitEvent(st, F.done[j], 0));
             if (s != RR_OK) return s;

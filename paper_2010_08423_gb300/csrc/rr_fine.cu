@@ -113,20 +113,34 @@ rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness,
 
 rr_status arrival_on(const Graph &g, Workspace &ws, const rr_query *q, uint64_t *d_witness,
                      uint64_t *d_E, uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
-                     const uint8_t *d_vmask, uint64_t budget)
+                     const uint8_t *d_vmask, uint64_t budget, uint32_t bfirst)
 {
     if (!d_E) {
         RR_CUDA(ws.edges.reserve((size_t)std::max<uint64_t>(1, g.m) * 8));
         d_E = ws.edges.as<uint64_t>();
     }
+    const uint32_t nb = bfirst ? q->k - bfirst : 0;  // at-most-k branches k' = bfirst..k-1
+    const size_t mw = (size_t)std::max<uint64_t>(1, g.m);
+    if (nb) {
+        RR_CUDA(ws.bS.reserve((size_t)nb * g.n * 8));
+        RR_CUDA(ws.bE.reserve((size_t)nb * mw * 8));
+        RR_CUDA(ws.bR.reserve((size_t)nb * g.n * 4));
+        RR_CUDA(cudaMemsetAsync(ws.bS.p, 0, (size_t)nb * g.n * 8, st));
+        RR_CUDA(cudaMemsetAsync(ws.bE.p, 0, (size_t)nb * mw * 8, st));
+        RR_CUDA(cudaMemsetAsync(ws.bR.p, 0xFF, (size_t)nb * g.n * 4, st));
+    }
     if (g.m) RR_CUDA(cudaMemsetAsync(d_E, 0, (size_t)g.m * 8, st));
     RR_CUDA(cudaMemsetAsync(d_R, 0xFF, (size_t)g.n * 4, st));
-    rr_status s = reach_on_stream(g, ws, q, nullptr, d_witness, budget, st, d_E, d_vmask);
+    rr_status s = reach_on_stream(g, ws, q, nullptr, d_witness, budget, st, d_E, d_vmask, nullptr,
+                                  PointRange(), bfirst, nb ? ws.bS.as<uint64_t>() : nullptr,
+                                  nb ? ws.bE.as<uint64_t>() : nullptr);
     if (s != RR_OK) return s;
-    if (g.m) {
+    for (uint32_t b = 0; g.m && b <= nb; ++b) {  // the query's own arrivals, then each branch's
+        const uint64_t *E = b == 0 ? d_E : ws.bE.as<uint64_t>() + (size_t)(b - 1) * mw;
+        uint32_t *R = b == 0 ? d_R : ws.bR.as<uint32_t>() + (size_t)(b - 1) * g.n;
         k_arrival<<<grid_for(g.m, 256), 256, 0, st>>>((uint32_t)g.m, g.row_head.as<uint32_t>(),
                                                        g.row_t.as<uint32_t>(), g.row_eid.as<uint32_t>(),
-                                                       d_E, d_R);
+                                                       E, R);
         RR_LAUNCHED();
     }
     if (d_bitmap) {
@@ -290,8 +304,11 @@ rr_status atmost_arrival_device(const Graph &g, uint32_t source, uint32_t k, uin
         rr_status s = ensure_fan_lanes(g, lanes);
         if (s != RR_OK) return s;
         FanOut &F = g.fan;
+        // k' = bfirst..k-1 come from the k query's own layers (lane 0)
+        const uint32_t bfirst = atmost_branches(g, k);
         RR_CUDA(cudaEventRecord(F.fork, st));
         for (uint32_t kk = k; kk >= 2; --kk) {
+            if (bfirst && kk >= bfirst && kk < k) continue;
             const uint32_t j = k - kk;  // lane
             Workspace &ws = *F.ws[j];
             RR_CUDA(ws.S.reserve((size_t)g.n * 8));
@@ -300,13 +317,17 @@ rr_status atmost_arrival_device(const Graph &g, uint32_t source, uint32_t k, uin
             const rr_query q{source, kk, seed, nullptr};
             RR_CUDA(cudaStreamWaitEvent(F.st[j], F.fork, 0));
             s = arrival_on(g, ws, &q, ws.S.as<uint64_t>(), ws.edges.as<uint64_t>(),
-                           ws.arrival.as<uint32_t>(), nullptr, F.st[j], nullptr, per_lane - extra);
+                           ws.arrival.as<uint32_t>(), nullptr, F.st[j], nullptr, per_lane - extra,
+                           kk == k ? bfirst : 0u);
             RR_CUDA(cudaEventRecord(F.done[j], F.st[j]));
             RR_CUDA(cudaStreamWaitEvent(st, F.done[j], 0));
             if (s != RR_OK) return s;
         }
         for (uint32_t kk = 2; kk <= k; ++kk) {
-            k_merge_arrival<<<grid, 256, 0, st>>>(g.n, F.ws[k - kk]->arrival.as<uint32_t>(), kk, d_R, d_L);
+            const uint32_t *R = bfirst && kk >= bfirst && kk < k
+                                    ? F.ws[0]->bR.as<uint32_t>() + (size_t)(kk - bfirst) * g.n
+                                    : F.ws[k - kk]->arrival.as<uint32_t>();
+            k_merge_arrival<<<grid, 256, 0, st>>>(g.n, R, kk, d_R, d_L);
             RR_LAUNCHED();
         }
     }

@@ -607,6 +607,8 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     if ((flags & 24u) == 24u) return fail(RR_EINVAL, "rr_graph_load: flags turn the head-factor table both on and off");
     g->head_table_force = (flags & 8u) ? 2u : ((flags & 16u) ? 1u : 0u);
     g->pair_tail_off = (flags & 32u) != 0;
+    if ((flags & 192u) == 192u) return fail(RR_EINVAL, "rr_graph_load: flags turn the at-most-k branches both on and off");
+    g->atmost_branches = (flags & 128u) ? 2u : ((flags & 64u) ? 1u : 0u);
     RR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
     cudaStream_t st = g->stream;
 

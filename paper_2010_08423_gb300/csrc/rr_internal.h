@@ -96,6 +96,7 @@ struct Workspace {
     DevBuf vmask;   // n: deleted vertices (path extraction)
     DevBuf pick;    // 8: the extraction step's choice
     DevBuf srcmask; // n: a set of sources (rr_reach_sources_device)
+    DevBuf bS, bE, bR;  // at-most-k branches' witnesses (n), per-edge sums (m), arrivals (n)
     cudaStream_t capture = nullptr;           // stream used only to capture graphs
     // captured launch sequences keyed by (query shape, sieve-point range)
     std::vector<std::pair<std::pair<uint64_t, uint64_t>, cudaGraphExec_t>> graphs;
@@ -106,6 +107,13 @@ struct Workspace {
     // ring_ev[i] (recorded after the launch that consumed it) has completed
     static constexpr int kRing = 64;
     QueryDesc *h_ring = nullptr;
+    // at-most-k branches (reach_v2's bfirst): their descriptors, staged per
+    // ring slot (kMaxBranches each) and uploaded to bdesc
+    static constexpr uint32_t kMaxBranches = 16;
+    QueryDesc *h_bring = nullptr;
+    DevBuf bdesc;
+    cudaStream_t side = nullptr;  // the branches' stream
+    cudaEvent_t bev[3] = {};
     cudaEvent_t ring_ev[kRing] = {};
     bool ring_used[kRing] = {};
     uint32_t ring_pos = 0;
@@ -118,7 +126,7 @@ struct Workspace {
     size_t bytes() const
     {
         return state.bytes + z.bytes + S.bytes + shade.bytes + bitmap.bytes + desc.bytes + edges.bytes +
-               arrival.bytes + vmask.bytes + pick.bytes + srcmask.bytes;
+               arrival.bytes + vmask.bytes + pick.bytes + srcmask.bytes + bS.bytes + bE.bytes + bR.bytes;
     }
     void drop_graphs()
     {
@@ -133,6 +141,10 @@ struct Workspace {
         for (int i = 0; i < kRing; ++i)
             if (ring_ev[i]) cudaEventDestroy(ring_ev[i]);
         if (h_ring) cudaFreeHost(h_ring);
+        if (h_bring) cudaFreeHost(h_bring);
+        if (side) cudaStreamDestroy(side);
+        for (cudaEvent_t e : bev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -263,6 +275,9 @@ struct Graph {
     // layers k-2 and k-1 from the pair sums of layer k-3 (label-space layer
     // k-2) unless the load flags turn it off
     bool pair_tail_off = false;
+    // at-most-k: k' >= the first branch from the k query's layers (2), every
+    // k' on its own lane (1), or by the k query's per-point work (0; load flags)
+    uint32_t atmost_branches = 0;
     uint32_t max_in_degree = 0;
 
     DevBuf off;      // n+1 uint32
@@ -381,10 +396,14 @@ rr_status run_query_layers(const Graph &g, const rr_query *q, const uint64_t *d_
 // starts walks at every flagged vertex instead of q->source.
 // range: the sieve points to sum (default all; a part needs k >= 4 and gives
 // no bitmap).
+// bfirst / b_witness / b_edges: at-most-k branches as in reach_v2 (the
+// reduced-state engine only; RR_EINVAL otherwise).
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st,
                           uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr,
-                          const uint8_t *d_srcmask = nullptr, PointRange range = PointRange());
+                          const uint8_t *d_srcmask = nullptr, PointRange range = PointRange(),
+                          uint32_t bfirst = 0, uint64_t *b_witness = nullptr,
+                          uint64_t *b_edges = nullptr);
 // Bytes of scratch one query of size k needs with the shape chosen for budget.
 uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget);
 
@@ -397,20 +416,44 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                        uint64_t *d_witness, int32_t *d_status, cudaStream_t st);
 bool choose_shape_v2(const Graph &g, uint32_t k, uint64_t budget, uint32_t *ppl, uint32_t *chunk);
 uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk);
-uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k);
+uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k,
+                          bool branches = false);
 // Enqueues the whole launch sequence of one k >= 3 query (z-table, witness
 // clear, all layers, bitmap) reading per-query values from d_desc; returns
 // the number of kernels enqueued in *kernels.
 // table: z is read from a z-table built from the descriptor (motif queries and
 // queries with deleted vertices); otherwise plain z is drawn on the fly.
+// At-most-k branches (bfirst > 0, plain queries): the k'-vertex queries for
+// k' = bfirst..k-1 are taken from this query's layers -- for the same seed their
+// per-point states equal this query's on their first 2^k' points -- so after
+// its per-point layer k'-2 the query also writes k''s transformed state and
+// runs k''s last layer with descriptor d_bdesc[k' - bfirst]. bfirst must be at
+// least atmost_first_branch(g, k); the pair tail is off in such a query.
+// side (or null: st) runs the branches beside the query, bev[0..2] (three
+// events) ordering them: each branch starts after its layer, the query waits
+// for the branch's transform after its next layer, and for all branches at
+// its end.
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels,
-                           bool pdl = true, PointRange range = PointRange());
+                           bool pdl = true, PointRange range = PointRange(),
+                           const QueryDesc *d_bdesc = nullptr, uint32_t bfirst = 0,
+                           cudaStream_t side = nullptr, cudaEvent_t *bev = nullptr);
+// b_witness / b_edges: witness (n values) and per-edge sums (m values, or
+// null) of branch k' at offset (k' - bfirst) rows; the branches' witness rows
+// must be zero before the call.
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                    uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st,
                    uint64_t *d_E = nullptr, const uint8_t *d_vmask = nullptr,
-                   PointRange range = PointRange());
+                   PointRange range = PointRange(), uint32_t bfirst = 0,
+                   uint64_t *b_witness = nullptr, uint64_t *b_edges = nullptr);
+// Smallest k' an at-most-k query of size k can take from its own layers (the
+// first per-point layer + 2), or 0 when none.
+uint32_t atmost_first_branch(const Graph &g, uint32_t k);
+// The first branch at-most-k takes from the k query (0: every k' on its own
+// lane): the load flags' choice, else atmost_first_branch where the k query's
+// per-point layers are long.
+uint32_t atmost_branches(const Graph &g, uint32_t k);
 
 // Held (under the graph's lock) by every call that uses the graph's scratch:
 // the call's stream first waits for the previous such call's work, and the
@@ -439,9 +482,12 @@ rr_status arrival_device(const Graph &g, const rr_query *q, uint64_t *d_witness,
                          uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
                          const uint8_t *d_vmask = nullptr);
 // The fine-grained query on workspace `ws` (budget as reach_on_stream).
+// bfirst > 0: also the at-most-k branches k' = bfirst..k-1 (reach_v2), their
+// witnesses, per-edge sums and minimum arrivals in ws.bS / ws.bE / ws.bR at
+// row k' - bfirst.
 rr_status arrival_on(const Graph &g, Workspace &ws, const rr_query *q, uint64_t *d_witness,
                      uint64_t *d_E, uint32_t *d_R, uint8_t *d_bitmap, cudaStream_t st,
-                     const uint8_t *d_vmask, uint64_t budget);
+                     const uint8_t *d_vmask, uint64_t budget, uint32_t bfirst = 0);
 // Bounded RestlessReach: minimum arrival over k' = 2..k, shortest length, D.
 rr_status atmost_arrival_device(const Graph &g, uint32_t source, uint32_t k, uint64_t seed,
                                 uint32_t *d_R, uint8_t *d_L, uint8_t *d_bitmap, cudaStream_t st);

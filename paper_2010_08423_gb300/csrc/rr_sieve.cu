@@ -495,7 +495,8 @@ uint64_t query_scratch_bytes(const Graph &g, uint32_t k, uint64_t budget)
 
 rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                           uint64_t *d_witness, uint64_t budget, cudaStream_t st, uint64_t *d_E,
-                          const uint8_t *d_vmask, const uint8_t *d_srcmask, PointRange range)
+                          const uint8_t *d_vmask, const uint8_t *d_srcmask, PointRange range,
+                          uint32_t bfirst, uint64_t *b_witness, uint64_t *b_edges)
 {
     rr_status vs = validate_query(g, q);
     if (vs != RR_OK) return vs;
@@ -505,6 +506,9 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
     // a set of sources runs on the per-point engine (the reduced-state engine
     // factors x_s out of layer 1); its shape is never cached per k
     const bool v2 = uses_v2(g, k) && !d_srcmask;
+    if (bfirst && (!v2 || q->motif || d_vmask || !range.full(k) || bfirst < atmost_first_branch(g, k) ||
+                   k - bfirst > Workspace::kMaxBranches))
+        return fail(RR_EINVAL, "internal: at-most-k branches need a plain whole query on the reduced-state engine");
     if (d_srcmask && budget == 0) {
         size_t free_b = 0, total_b = 0;
         RR_CUDA(cudaMemGetInfo(&free_b, &total_b));
@@ -531,10 +535,12 @@ rr_status reach_on_stream(const Graph &g, Workspace &ws, const rr_query *q, uint
             ws.shape_gen[k] = g.tune_gen;
         }
     }
-    RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk, k)
+    RR_CUDA(ws.state.reserve(v2 ? v2_scratch_bytes(g, ppl, chunk, k, bfirst != 0)
                                 : 2ull * g.state_rows * chunk * 8ull));
     RR_CUDA(ws.z.reserve((size_t)g.n * k * 8));
-    if (v2) return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st, d_E, d_vmask, range);
+    if (v2)
+        return reach_v2(g, ws, q, d_bitmap, d_witness, ppl, chunk, st, d_E, d_vmask, range, bfirst,
+                        b_witness, b_edges);
     const QueryKeys keys = make_keys(q->seed);
     const uint32_t *d_shades = nullptr;
     if (q->motif) {

@@ -75,6 +75,8 @@ struct ZeroRows {
     uint32_t npr3;
     uint64_t *carry;  // the carry table's zero row (chunk values) or null
     uint64_t *lrows;  // the pair tail's label-space rows (kLabelTailWidth values) or null
+    uint64_t *bred;   // the at-most-k branches' transformed buffer (bred_w values) or null
+    uint32_t bred_w;
 };
 
 __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, const ZeroRows &z)
@@ -99,6 +101,8 @@ __device__ __forceinline__ void zero_rows(const QueryDesc *__restrict__ qd, cons
         for (uint32_t i = tid; i < z.chunk; i += stride) z.carry[i] = 0;
     if (z.lrows)
         for (uint32_t i = tid; i < kLabelTailWidth; i += stride) z.lrows[i] = 0;
+    if (z.bred)
+        for (uint32_t i = tid; i < z.bred_w; i += stride) z.bred[i] = 0;
 }
 
 // Layer 1; its grid also clears what zero_rows lists (saving a launch).
@@ -257,6 +261,16 @@ __global__ void __launch_bounds__(kW2 * 32) k_last_label(const V2Params p)
     last_label_warp<LG, false>(p, task);
 }
 
+// At-most-k branch: one layer's stored rows as a smaller query's transformed
+// state (transform_rows_warp).
+template <int PPL>
+__global__ void __launch_bounds__(kW2 * 32) k_branch_transform(const V2Params p, uint32_t nrows)
+{
+    const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
+    if (task >= (nrows + 31) / 32 * p.ngroups) return;
+    transform_rows_warp<PPL>(p, task, nrows);
+}
+
 static unsigned blocks_for(uint64_t tasks)
 {
     return (unsigned)((tasks + kW2 - 1) / kW2);
@@ -358,6 +372,24 @@ static bool pair_tail(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
            chunk / (32u * ppl) <= kPairTailMaxGroups;
 }
 
+uint32_t atmost_first_branch(const Graph &g, uint32_t k)
+{
+    const uint32_t b = (pair_layer3(g, k) ? 4u : 3u) + 2u;  // first per-point layer + 2
+    return b < k ? b : 0u;
+}
+
+uint32_t atmost_branches(const Graph &g, uint32_t k)
+{
+    if (!uses_v2(g, k) || g.atmost_branches == 1) return 0;
+    // by default only where the k query's per-point layers are long: with
+    // short, latency-bound layers the concurrent queries finish first (n = 1e5,
+    // m = 1e6, k = 10: 0.24 ms against 0.27, k = 12: 0.63 against 0.68; a
+    // Chung-Lu n = 2e5 graph, k = 10: 8.2 ms against 5.4)
+    const bool long_layers =
+        (uint64_t)g.deep_compute_rows * std::min<uint64_t>(1ull << k, 1024) >= (1ull << 23);
+    return g.atmost_branches == 2 || long_layers ? atmost_first_branch(g, k) : 0u;
+}
+
 // Words of the pair tail's label-space rows (layer k-2), zero when it is off.
 static uint64_t label_tail_words(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
 {
@@ -386,12 +418,21 @@ static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, 
         *red_w = std::max<uint64_t>(*red_w, drows * (chunk / (32u * ppl)) * kPairTailSlots);
 }
 
-uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
+// At-most-k branches' own transformed buffer (single-label sums, the
+// per-point tail's row width), after the pair tail's rows.
+static uint64_t branch_words(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
+{
+    const uint64_t drows = g.deep_list.count + 1;
+    return k >= 6 ? (drows * v2_reduced_stride(ppl, chunk) + 31) / 32 * 32 : 0;
+}
+
+uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, bool branches)
 {
     uint64_t py_w, pr2_w, pr3_w, tx_w, full_w, red_w;
     v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &tx_w, &full_w, &red_w);
     return (py_w + pr2_w + pr3_w + tx_w + 2 * full_w + red_w + carry_words(g, chunk, k) +
-            label_tail_words(g, ppl, chunk, k)) * 8ull + 4096;
+            (label_tail_words(g, ppl, chunk, k) + 31) / 32 * 32 +
+            (branches ? branch_words(g, ppl, chunk, k) : 0)) * 8ull + 4096;
 }
 
 // z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades); rows
@@ -451,10 +492,58 @@ static unsigned grid_cap(uint64_t count, unsigned block)
     return (unsigned)g;
 }
 
+// At-most-k branch kb after per-point layer kb - 2 (vp: that layer's launch
+// parameters, vp.st_out its rows; carry: the carry table k_carry wrote for it,
+// or null): the rows' sums over single labels of the point groups below
+// 2^kb into `red`, then kb's last layer with descriptor d_bd.
+static rr_status enqueue_branch(const Graph &g, const V2Params &vp, uint32_t kb, const QueryDesc *d_bd,
+                                uint64_t *carry, uint64_t *red, uint32_t ppl, uint64_t stop_k,
+                                cudaStream_t st, cudaEvent_t tr_done, uint64_t *nk)
+{
+    V2Params vb = vp;
+    const uint64_t stop = std::min<uint64_t>(stop_k, 1ull << kb);  // the branch's points end
+    const uint32_t gs = 32u * ppl;
+    vb.ngroups = (uint32_t)std::min<uint64_t>(vp.ngroups, (stop - vp.chunk_base + gs - 1) / gs);
+    vb.npoints = (uint32_t)stop;
+    vb.st_in = vp.st_out;
+    vb.st_out = red;
+    vb.carry = carry;
+    vb.row_carry = carry ? g.deep_list.row_carry.as<uint32_t>() : nullptr;
+    const uint32_t nrows = (uint32_t)g.deep_list.count;
+    const uint64_t tasks = (uint64_t)(nrows + 31) / 32 * vb.ngroups;
+    if (tasks) {
+        const int tslot = timing_begin(st);
+        if (ppl == 4) RR_CUDA(launch_pdl(k_branch_transform<4>, dim3(blocks_for(tasks)), dim3(kW2 * 32), st, vb, nrows));
+        else RR_CUDA(launch_pdl(k_branch_transform<2>, dim3(blocks_for(tasks)), dim3(kW2 * 32), st, vb, nrows));
+        timing_end(tslot, kTimeTail, st);
+        RR_LAUNCHED();
+        ++*nk;
+    }
+    if (tr_done) RR_CUDA(cudaEventRecord(tr_done, st));
+    vb.qd = d_bd;
+    vb.k = kb;
+    vb.layer = kb - 1;
+    vb.st_in = red;
+    vb.carry = nullptr;
+    vb.row_carry = nullptr;
+    set_list(vb, g.tail3_list, 3);
+    if (vb.nitems) {
+        const int tslot = timing_begin(st);
+        const dim3 grid(blocks_for(vb.nitems)), B(kW2 * 32);
+        if (ppl == 4) RR_CUDA(launch_pdl(k_last_v2<7>, grid, B, st, vb));
+        else RR_CUDA(launch_pdl(k_last_v2<6>, grid, B, st, vb));
+        timing_end(tslot, kTimeLast, st);
+        RR_LAUNCHED();
+        ++*nk;
+    }
+    return RR_OK;
+}
+
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels, bool pdl,
-                           PointRange range)
+                           PointRange range, const QueryDesc *d_bdesc, uint32_t bfirst,
+                           cudaStream_t side, cudaEvent_t *bev)
 {
     // k <= 3 sums all points in closed form: only the whole range exists there
     if (k <= 3 && !range.full(k)) return fail(RR_EINVAL, "a part of the sieve points needs k >= 4");
@@ -480,8 +569,16 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
     // the pair tail: layer k-3 writes pair sums into `red`, layer k-2 its
     // label-space rows after the carry table
-    const bool ptail = pair_tail(g, ppl, chunk, k);
+    // (off with at-most-k branches: branch k-1 reads layer k-3's per-point rows)
+    const bool ptail = bfirst == 0 && pair_tail(g, ppl, chunk, k);
     uint64_t *lrows = ptail ? red + red_w + carry_words(g, chunk, k) : nullptr;
+    // at-most-k branches: their transformed buffer, so that they can run on
+    // the side stream while the query goes on
+    bool side_used = false;
+    if (bfirst && side && !bev) return fail(RR_EINVAL, "internal: branch side stream without events");
+    uint64_t *bred = bfirst ? red + red_w + carry_words(g, chunk, k) +
+                                  (label_tail_words(g, ppl, chunk, k) + 31) / 32 * 32
+                            : nullptr;
     const uint32_t red_width = ptail ? chunk / (32u * ppl) * kPairTailSlots : rstride;
 
     {
@@ -498,7 +595,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     // the first layer's grid when it runs
     const ZeroRows zr{k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
                       k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, red_width, k,
-                      pair ? pr3 : nullptr, pair_count(k), carry, lrows};
+                      pair ? pr3 : nullptr, pair_count(k), carry, lrows, bred, rstride};
     const bool zero_in_first = k >= 3 && g.prod_list.nitems > 0;
     if (!zero_in_first) {
         RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, d_desc, zr));
@@ -615,6 +712,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         // pair tail at most two)
         uint64_t *bufs[2] = {full0, full1};
         const uint32_t last_pp = ptail ? k - 3 : k - 2;
+        bool tr_pending = false;
         // with layer 3 in pair-label space the per-point layers start at 4,
         // layer 4 reading the pair windows
         for (uint32_t l = pair ? 4u : (k >= 5 ? 3u : 2u); l <= last_pp; ++l) {
@@ -654,6 +752,11 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             }
             if (s != RR_OK) return s;
             nk += vp.nitems ? 1 : 0;
+            if (tr_pending) {
+                // the previous layer's branch has read its rows and carries
+                RR_CUDA(cudaStreamWaitEvent(st, bev[1], 0));
+                tr_pending = false;
+            }
             if (carry && out == 0 && src != 1) {
                 // per-point state of the deep list: the carry table, read by the next layer
                 RR_CUDA(launch_pdl(k_carry, dim3(g.deep_list.nchains), dim3(128), st,
@@ -664,6 +767,24 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             } else {
                 s = launch_fixup(src == 1 ? g.state_list : g.deep_list, vp.st_out,
                                  out == 0 ? chunk : red_width, st, &nk);
+                if (s != RR_OK) return s;
+            }
+            // at-most-k branch: this layer is layer k'-2 of the k'-vertex query
+            // (k' = l + 2), whose points below 2^k' it holds; their sums over
+            // single labels, then that query's last layer
+            // (on the side stream when given: it reads this layer's rows and
+            // carries, which the query overwrites after its next layer)
+            const uint32_t kb = l + 2;
+            if (bfirst && out == 0 && kb >= bfirst && kb < k && (uint64_t)vp.chunk_base < (1ull << kb)) {
+                cudaStream_t bs = st;
+                if (side) {
+                    RR_CUDA(cudaEventRecord(bev[0], st));
+                    RR_CUDA(cudaStreamWaitEvent(side, bev[0], 0));
+                    bs = side;
+                    side_used = tr_pending = true;
+                }
+                s = enqueue_branch(g, vp, kb, d_bdesc + (kb - bfirst), carry, bred, ppl, range.stop(k), bs,
+                                   side ? bev[1] : nullptr, &nk);
                 if (s != RR_OK) return s;
             }
         }
@@ -707,6 +828,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             ++nk;
         }
     }
+    if (side_used) {  // the branches' last layers
+        RR_CUDA(cudaEventRecord(bev[2], side));
+        RR_CUDA(cudaStreamWaitEvent(st, bev[2], 0));
+    }
     if (bitmap) {
         RR_CUDA(launch_pdl(k_bitmap_q, dim3(grid_cap((g.n + 7) / 8, 256)), dim3(256), st, g.n, d_desc));
         RR_LAUNCHED();
@@ -722,7 +847,8 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
 // can be timed.
 rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_bitmap,
                    uint64_t *d_witness, uint32_t ppl, uint32_t chunk, cudaStream_t st, uint64_t *d_E,
-                   const uint8_t *d_vmask, PointRange range)
+                   const uint8_t *d_vmask, PointRange range, uint32_t bfirst, uint64_t *b_witness,
+                   uint64_t *b_edges)
 {
     const uint32_t k = q->k;
     RR_CUDA(ws.desc.reserve(sizeof(QueryDesc)));
@@ -758,11 +884,33 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     ws.h_ring[slot] = hd;
     RR_CUDA(cudaMemcpyAsync(ws.desc.p, &ws.h_ring[slot], sizeof hd, cudaMemcpyHostToDevice, st));
     ws.ring_used[slot] = true;
+    const uint32_t nb = bfirst ? k - bfirst : 0;  // at-most-k branches k' = bfirst..k-1
+    if (nb) {
+        if (nb > Workspace::kMaxBranches) return fail(RR_EINVAL, "internal: too many at-most-k branches");
+        RR_CUDA(ws.bdesc.reserve(sizeof(QueryDesc) * Workspace::kMaxBranches));
+        if (!ws.h_bring)
+            RR_CUDA(cudaMallocHost(&ws.h_bring, sizeof(QueryDesc) * Workspace::kRing * Workspace::kMaxBranches));
+        QueryDesc *hb = ws.h_bring + (size_t)slot * Workspace::kMaxBranches;  // free with the ring slot
+        for (uint32_t b = 0; b < nb; ++b) {
+            hb[b] = hd;
+            hb[b].k = bfirst + b;
+            hb[b].S = b_witness + (size_t)b * g.n;
+            hb[b].E = b_edges ? b_edges + (size_t)b * g.m : nullptr;
+            hb[b].bitmap = nullptr;
+        }
+        RR_CUDA(cudaMemcpyAsync(ws.bdesc.p, hb, sizeof(QueryDesc) * nb, cudaMemcpyHostToDevice, st));
+    }
+    const QueryDesc *dbd = nb ? ws.bdesc.as<QueryDesc>() : nullptr;
+    if (nb && !ws.side) {
+        RR_CUDA(cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : ws.bev) RR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     const bool table = q->motif != nullptr || d_vmask != nullptr;
     const bool bitmap = d_bitmap != nullptr;
     if (g_timing.load(std::memory_order_relaxed)) {
         rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
-                                       ws.state.as<uint64_t>(), dd, st, nullptr, ws.pdl, range);
+                                       ws.state.as<uint64_t>(), dd, st, nullptr, ws.pdl, range, dbd,
+                                       nb ? bfirst : 0u, ws.side, ws.bev);
         RR_CUDA(cudaEventRecord(ws.ring_ev[slot], st));
         return s;
     }
@@ -773,7 +921,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
     }
     const std::pair<uint64_t, uint64_t> key(
         (uint64_t)k | ((uint64_t)ppl << 8) | ((uint64_t)chunk << 16) | ((uint64_t)table << 40) |
-            ((uint64_t)bitmap << 41),
+            ((uint64_t)bitmap << 41) | ((uint64_t)(nb ? bfirst : 0u) << 48),
         (uint64_t)range.first | ((uint64_t)range.stop(k) << 32));
     cudaGraphExec_t exec = nullptr;
     uint64_t nkern = 0;
@@ -787,7 +935,7 @@ rr_status reach_v2(const Graph &g, Workspace &ws, const rr_query *q, uint8_t *d_
         RR_CUDA(cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeThreadLocal));
         rr_status s = enqueue_query_v2(g, k, table, bitmap, ppl, chunk, ws.z.as<uint64_t>(),
                                        ws.state.as<uint64_t>(), dd, ws.capture, &nkern, ws.pdl,
-                                       range);
+                                       range, dbd, nb ? bfirst : 0u, ws.side, ws.bev);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(ws.capture, &graph);
         if (s != RR_OK) {

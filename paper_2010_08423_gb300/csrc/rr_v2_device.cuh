@@ -372,12 +372,105 @@ __device__ __forceinline__ void last3_closed(const V2Params &p, uint32_t ent)
     if (p.qd->E) p.qd->E[e] = val;  // one entry per edge
 }
 
+// Sums of a lane group's per-point values (acc, the lane's PPL points) over
+// the group's 32*PPL points holding each in-group label: lane j < LG returns
+// T_j -- the in-lane labels from U, the lane labels from the half-cube sums of
+// V -- and lane LG the total V. Every lane takes part in the shuffles.
+template <int PPL>
+__device__ __forceinline__ uint64_t single_label_sums(const uint64_t (&acc)[PPL], int lane)
+{
+    constexpr int LOGP = PPL == 4 ? 2 : 1;
+    constexpr int LG = LOGP + 5;
+    uint64_t V = 0;
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) V ^= acc[i];
+    uint64_t U0 = acc[1] ^ (PPL == 4 ? acc[3] : 0ull);
+    uint64_t U1 = PPL == 4 ? (acc[2] ^ acc[3]) : 0ull;
+    uint64_t X = V, Y[5];
+#pragma unroll
+    for (int bb = 0; bb < 5; ++bb) {
+        const uint64_t P = shfl64x(X, 1 << bb);
+        Y[bb] = ((lane >> bb) & 1) ? X : P;
+        X ^= P;
+#pragma unroll
+        for (int b2 = 0; b2 < bb; ++b2) Y[b2] ^= shfl64x(Y[b2], 1 << bb);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        U0 ^= shfl64x(U0, off);
+        if constexpr (PPL == 4) U1 ^= shfl64x(U1, off);
+    }
+    // slot j < LG: T_j ; slot LG: V
+    if (LOGP == 2 && lane == 1) return U1;
+    if (lane == 0) return U0;
+    if (lane < LG) {
+        const int bb = lane - LOGP;
+        return bb == 0 ? Y[0] : bb == 1 ? Y[1] : bb == 2 ? Y[2] : bb == 3 ? Y[3] : Y[4];
+    }
+    return X;
+}
+
+// At-most-k branch: the stored per-point rows of one layer, restricted to the
+// points below p.npoints, as the sums over single labels of each point group
+// -- what layer k'-2 of the k'-vertex query writes as its transformed state,
+// since for the same seed the two queries' layers agree on those points. The
+// lazy carries of cut hub segments are added first, so the rows are true
+// prefixes. One warp per (32 consecutive deep rows, point group); p.st_out
+// has p.ngroups groups of LG + 1 values per row.
+template <int PPL>
+__device__ __forceinline__ void transform_rows_warp(const V2Params &p, uint32_t task, uint32_t nrows)
+{
+    constexpr int LOGP = PPL == 4 ? 2 : 1;
+    constexpr int LG = LOGP + 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t group = task % p.ngroups, rb = task / p.ngroups;
+    const uint32_t col = group * (32u * PPL) + (uint32_t)lane * PPL;
+    const uint32_t first = p.chunk_base + col;  // the lane's first point
+    bool valid[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) valid[i] = first + i < p.npoints;
+    const uint32_t r0 = 1 + rb * 32, r1 = min(nrows + 1, r0 + 32);  // deep rows 1..nrows
+    const uint32_t m_slot = (p.carry && r0 + (uint32_t)lane < r1) ? p.row_carry[r0 + lane] : 0u;
+    pdl_enter();  // the layer's rows and carries are read from here on
+    for (uint32_t r = r0; r < r1; ++r) {
+        const uint32_t slot = __shfl_sync(0xffffffffu, m_slot, (int)(r - r0));
+        const ulonglong2 *pr = reinterpret_cast<const ulonglong2 *>(p.st_in + (size_t)r * p.chunk + col);
+        uint64_t acc[PPL];
+        const ulonglong2 a0 = __ldg(pr);
+        acc[0] = a0.x;
+        acc[1] = a0.y;
+        if constexpr (PPL == 4) {
+            const ulonglong2 a1 = __ldg(pr + 1);
+            acc[2] = a1.x;
+            acc[3] = a1.y;
+        }
+        if (slot) {  // warp-uniform
+            const ulonglong2 *pc = reinterpret_cast<const ulonglong2 *>(p.carry + (size_t)slot * p.chunk + col);
+            const ulonglong2 c0 = __ldg(pc);
+            acc[0] ^= c0.x;
+            acc[1] ^= c0.y;
+            if constexpr (PPL == 4) {
+                const ulonglong2 c1 = __ldg(pc + 1);
+                acc[2] ^= c1.x;
+                acc[3] ^= c1.y;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PPL; ++i)
+            if (!valid[i]) acc[i] = 0;
+        const uint64_t val = single_label_sums<PPL>(acc, lane);
+        if (lane <= LG) p.st_out[((size_t)r * p.ngroups + group) * (LG + 1) + lane] = val;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Layers 2..k-2.
 //   FROM_Y: window sum W^L = Y_e x_s^L x_u^L (layer 2), Y_e = PY[a0] ^ PY[b0];
 //   else  : W^L = state[a1] ^ state[b1] (layers >= 3).
 //   OUT 0: write the per-point prefix to the state row of the entry;
-//   OUT 1: write the group's transformed prefix (T_0..T_{lg-1}, V).
+//   OUT 1: write the group's transformed prefix (T_0..T_{lg-1}, V);
+//   OUT 2: write its sums over label sets of at most two in-group labels
+//          (the pair tail).
 // One warp per (scheduling range, point group); lanes own PPL points each.
 // ---------------------------------------------------------------------------
 // COHERENT: state written earlier in the same launch is read through L2
@@ -610,37 +703,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
                     reinterpret_cast<ulonglong2 *>(po)[0] = make_ulonglong2(acc[0], acc[1]);
                 }
             } else if constexpr (OUT == 1) {
-                // T_j over the group's 32*PPL points: in-lane label bits from U,
-                // lane bits from the half-cube sums of V, and the total V.
-                uint64_t V = 0;
-#pragma unroll
-                for (int i = 0; i < PPL; ++i) V ^= acc[i];
-                uint64_t U0 = acc[1] ^ (PPL == 4 ? acc[3] : 0ull);
-                uint64_t U1 = PPL == 4 ? (acc[2] ^ acc[3]) : 0ull;
-                uint64_t X = V, Y[5];
-#pragma unroll
-                for (int bb = 0; bb < 5; ++bb) {
-                    const uint64_t P = shfl64x(X, 1 << bb);
-                    Y[bb] = ((lane >> bb) & 1) ? X : P;
-                    X ^= P;
-#pragma unroll
-                    for (int b2 = 0; b2 < bb; ++b2) Y[b2] ^= shfl64x(Y[b2], 1 << bb);
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    U0 ^= shfl64x(U0, off);
-                    if constexpr (PPL == 4) U1 ^= shfl64x(U1, off);
-                }
-                // slot j < LG: T_j ; slot LG: V
-                uint64_t val;
-                if (LOGP == 2 && lane == 1) val = U1;
-                else if (lane == 0) val = U0;
-                else if (lane < LG) {
-                    const int bb = lane - LOGP;
-                    val = bb == 0 ? Y[0] : bb == 1 ? Y[1] : bb == 2 ? Y[2] : bb == 3 ? Y[3] : Y[4];
-                } else {
-                    val = X;
-                }
+                const uint64_t val = single_label_sums<PPL>(acc, lane);
                 if (lane <= LG)
                     p.st_out[(row * p.ngroups + group) * (LG + 1) + lane] = val;
             } else if constexpr (OUT == 2) {
