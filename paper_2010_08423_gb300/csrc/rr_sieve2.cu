@@ -26,6 +26,16 @@
 //    pair matrix Q = XOR over v's rows of z_{u_e} (x) (y rho_e), so layer 3
 //    keeps k(k+1)/2 values per deep row, independent of the point chunk, and
 //    layer 4 evaluates the form of each window (times x_u x_s) per point.
+// 8. The pair tail (chunks of at least 256 points): the last layer uses layer
+//    k-2 only through sums over point groups of x_w^L P^L, and with layer
+//    k-2's factor y x_v^L those are bilinear forms in the z values of w and v
+//    over layer k-3's sums on the points holding one or two given labels; so
+//    layer k-3 stores those sums and layer k-2 runs in label space
+//    (label_tail_warp in rr_v2_device.cuh).
+// 9. At-most-k from one query: for one seed a k'-vertex query's per-point
+//    layers equal the k-vertex query's on its first 2^k' points, so the k
+//    query, after its layer k'-2, forms k''s single-label sums from its rows
+//    and runs k''s last layer (the branches of enqueue_query_v2).
 // Only the order of summation changes; every result is bit-identical to the
 // per-point engine and the oracle. One query's launch sequence is captured
 // once per shape as a CUDA graph and its kernels use programmatic dependent
@@ -330,11 +340,6 @@ uint32_t v2_reduced_stride(uint32_t ppl, uint32_t chunk)
     return chunk / (32u * ppl) * (lg + 1u);
 }
 
-// Scratch the reduced-state engine needs for one query (bytes): scalar
-// prefix, two full state buffers, one transformed buffer.
-// Words of each part of the engine's scratch, in layout order: scalar layer-1
-// prefix, label-space layer-2 prefix (k per state row), two per-point buffers,
-// one transformed buffer.
 // Layer 3 in pair-label space (third_pair_row), layer 4 reading its windows:
 // queries with 6 <= k <= 20 when the graph's load flags force it, else with
 // k >= kPairMinK unless they turn it off.
@@ -396,6 +401,10 @@ static uint64_t label_tail_words(const Graph &g, uint32_t ppl, uint32_t chunk, u
     return pair_tail(g, ppl, chunk, k) ? ((uint64_t)g.deep_list.count + 1) * kLabelTailWidth : 0;
 }
 
+// Words of each part of the engine's scratch, in layout order: scalar layer-1
+// prefix, label-space layer-2 prefix (k per state row), pair rows, head table,
+// two per-point buffers, one transformed buffer (then the carry table, the
+// pair tail's label-space rows and the at-most-k branches' transformed buffer).
 static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, uint64_t *py_w,
                       uint64_t *pr2_w, uint64_t *pr3_w, uint64_t *tx_w, uint64_t *full_w,
                       uint64_t *red_w)
