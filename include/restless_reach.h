@@ -369,16 +369,17 @@ rr_status rr_set_tuning(rr_graph *g, uint32_t k, uint32_t ppl, uint32_t chunk);
 /* Shape of the persistent batch (rr_reach_batch_device and the server's batch
  * lanes), kept per graph; 0 in a field = the automatic rule.
  *   blocks_per_sm  kernel variant by the blocks per SM its register budget is
- *                  set for: 2 (150 registers), 4 (128) or 6 (80, a few spills);
+ *                  set for: 2 (168 registers), 4 (128), 5 (96, a few spills) or 6
+ *                  (80, more spills);
  *   ranges         1 = fine scheduling ranges (one head run each), 2 = coarse
  *                  (about 32 row-list entries each);
- *   max_chunk      largest point chunk of a unit: 128, 256 or 512 (a query with
- *                  at least 128 points takes chunks of at least 128).
- * The automatic rule takes coarse ranges with 6 blocks when the first wave's
+ *   max_chunk      largest point chunk of a unit: 128, 256, 512 or 1024 (a query
+ *                  with at least 128 points takes chunks of at least 128).
+ * The automatic rule takes coarse ranges with 5 blocks when the first wave's
  * tasks are at least half the resident warps, else fine ranges with 2, and
  * chunks up to 512. rr_autotune_batch picks the batch's tile (scheduling range)
  * and sieve points per block by measurement: it runs the batch qs[0..nq) once
- * untimed and twice timed per candidate -- the 18 combinations of 2/4/6
+ * untimed and twice timed per candidate -- the 24 combinations of 2/4/5/6
  * blocks, fine/coarse ranges and 256/512/1024-point chunks -- keeps the fastest in
  * the graph and returns it in *best (may be NULL). Results are bit-identical in
  * every shape. Uses the graph's scratch (ordered as rr_reach_device). Errors:

@@ -264,10 +264,11 @@ __device__ __forceinline__ void run_task(const BatchArgs &a, const BatchSeg &sg,
 }
 
 // MINB = blocks per SM the register budget is set for: 6 (80 registers, a few
-// spilled) or 4 (128 registers) for large batches, where more resident warps
-// hide the tasks' latencies; 2 (no spills) for small batches, whose critical
-// path is the per-task time. The automatic rule takes 6 for coarse ranges and
-// 2 for fine ones; rr_autotune_batch times all three.
+// spilled), 5 (96, fewer spilled) or 4 (128 registers) for large batches,
+// where more resident warps hide the tasks' latencies; 2 (no spills) for small
+// batches, whose critical path is the per-task time. The automatic rule takes
+// 5 for coarse ranges (as fast as 6 within 1%, a sixth of its local-memory
+// requests) and 2 for fine ones; rr_autotune_batch times all four.
 template <int MINB>
 __global__ void __launch_bounds__(kW2 * 32, MINB) k_batch(const BatchArgs a)
 {
@@ -673,8 +674,9 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             RR_CUDA(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, dev));
             RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.occupancy[2], k_batch<2>, kW2 * 32, 0));
             RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.occupancy[4], k_batch<4>, kW2 * 32, 0));
+            RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.occupancy[5], k_batch<5>, kW2 * 32, 0));
             RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B.occupancy[6], k_batch<6>, kW2 * 32, 0));
-            for (int v : {2, 4, 6}) B.occupancy[v] = std::max(1, B.occupancy[v]);
+            for (int v : {2, 4, 5, 6}) B.occupancy[v] = std::max(1, B.occupancy[v]);
         }
         const uint64_t resident_warps = (uint64_t)B.sms * B.occupancy[2] * kW2;
         const uint64_t slot_bytes = slot_words_for(g, max_chunk) * 8;
@@ -688,7 +690,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         for (size_t i = 0; i < std::min<size_t>(units.size(), nslots); ++i)
             wave_tasks += (uint64_t)g.deep_list.nitems_coarse * (units[i].chunk / (32u * units[i].ppl));
         const bool coarse = g.batch_ranges ? g.batch_ranges == 2 : 2 * wave_tasks >= resident_warps;
-        const int minb = g.batch_minb ? (int)g.batch_minb : (coarse ? 6 : 2);
+        const int minb = g.batch_minb ? (int)g.batch_minb : (coarse ? 5 : 2);
 
         // segments in task order: wave, layer, unit; after a layer that writes
         // prefix state, the unit's carry fix-up segments (phase 1, phase 2)
@@ -913,6 +915,7 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             const unsigned blocks = (unsigned)std::max(1, B.sms * B.occupancy[minb]);
             const int bslot = timing_begin(st);
             if (minb == 6) k_batch<6><<<blocks, kW2 * 32, 0, st>>>(a);
+            else if (minb == 5) k_batch<5><<<blocks, kW2 * 32, 0, st>>>(a);
             else if (minb == 4) k_batch<4><<<blocks, kW2 * 32, 0, st>>>(a);
             else k_batch<2><<<blocks, kW2 * 32, 0, st>>>(a);
             timing_end(bslot, kTimeBatch, st);
@@ -1083,7 +1086,7 @@ rr_status autotune_batch(Graph &g, const rr_query *qs, uint32_t nq, uint32_t *mi
     uint32_t best[3] = {0, 0, 0};
     float best_ms = 1e30f;
     rr_status st = RR_OK;
-    for (uint32_t mb : {2u, 4u, 6u})
+    for (uint32_t mb : {2u, 4u, 5u, 6u})
         for (uint32_t rg : {1u, 2u})
             for (uint32_t mc : {256u, 512u, 1024u}) {
                 g.batch_minb = mb;

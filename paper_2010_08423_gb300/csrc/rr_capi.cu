@@ -349,8 +349,9 @@ rr_status rr_set_batch_tuning(rr_graph *g, const rr_batch_tuning *t)
 {
     clear_error();
     if (!g || !t) return fail(RR_EINVAL, "rr_set_batch_tuning: NULL argument");
-    if (t->blocks_per_sm != 0 && t->blocks_per_sm != 2 && t->blocks_per_sm != 4 && t->blocks_per_sm != 6)
-        return fail(RR_EINVAL, "rr_set_batch_tuning: blocks_per_sm must be 0, 2, 4 or 6");
+    if (t->blocks_per_sm != 0 && t->blocks_per_sm != 2 && t->blocks_per_sm != 4 && t->blocks_per_sm != 5 &&
+        t->blocks_per_sm != 6)
+        return fail(RR_EINVAL, "rr_set_batch_tuning: blocks_per_sm must be 0, 2, 4, 5 or 6");
     if (t->ranges > 2) return fail(RR_EINVAL, "rr_set_batch_tuning: ranges must be 0, 1 or 2");
     if (t->max_chunk != 0 && t->max_chunk != 128 && t->max_chunk != 256 && t->max_chunk != 512 &&
         t->max_chunk != 1024)

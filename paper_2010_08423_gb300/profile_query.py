@@ -28,6 +28,9 @@ def main(argv=None) -> int:
     ap.add_argument("--motif", action="store_true", help="a motif query (source colour + k-1 colours)")
     ap.add_argument("--shape", default=None,
                     help="points per lane x points per chunk (e.g. 4x512), as rr_set_tuning")
+    ap.add_argument("--batch-shape", default=None,
+                    help="blocks per SM, ranges, max chunk of the batch (e.g. 5,2,1024), "
+                         "as rr_set_batch_tuning")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: one persistent batched launch of this many queries, "
                          "k ~ U{4..12}, odd ones coloured")
@@ -45,6 +48,8 @@ def main(argv=None) -> int:
     if args.batch:
         qs = W.query_set(g, args.batch, 4, 12, W.GRAPH_SEED_BASE + 4)
         with capi.Graph(g) as G:
+            if args.batch_shape:
+                capi.rr_set_batch_tuning(G.handle, *(int(x) for x in args.batch_shape.split(",")))
             d_w = torch.zeros((len(qs), g["n"]), dtype=torch.int64, device="cuda")
             st = torch.cuda.Stream()
             for _ in range(args.warmup):

@@ -41,7 +41,7 @@ def _torch():
 
 
 def test_every_batch_shape_and_the_autotuned_one_match_single_queries(mixed):
-    """The persistent batch in each forced shape (kernel variant with 2, 4 or 6
+    """The persistent batch in each forced shape (kernel variant with 2, 4, 5 or 6
     blocks per SM, fine or coarse ranges, 128/512/1024-point chunks) and in the
     shape rr_autotune_batch picks gives the single queries' sums bit for bit."""
     torch = _torch()
@@ -52,7 +52,7 @@ def test_every_batch_shape_and_the_autotuned_one_match_single_queries(mixed):
         stream = torch.cuda.Stream()
         d_w = torch.empty((len(qs), n), dtype=torch.int64, device="cuda")
         d_st = torch.empty((len(qs),), dtype=torch.int32, device="cuda")
-        shapes = [(mb, rg, mc) for mb in (2, 4, 6) for rg in (1, 2) for mc in (128, 512, 1024)]
+        shapes = [(mb, rg, mc) for mb in (2, 4, 5, 6) for rg in (1, 2) for mc in (128, 512, 1024)]
         for mb, rg, mc in shapes:
             capi.rr_set_batch_tuning(G.handle, mb, rg, mc)
             assert capi.rr_get_batch_tuning(G.handle) == {"blocks_per_sm": mb, "ranges": rg,
@@ -63,7 +63,7 @@ def test_every_batch_shape_and_the_autotuned_one_match_single_queries(mixed):
             assert (d_st.cpu().numpy() == 0).all()
             assert np.array_equal(d_w.cpu().numpy().view(np.uint64), singles), (mb, rg, mc)
         best = capi.rr_autotune_batch(G.handle, qs)
-        assert best["blocks_per_sm"] in (2, 4, 6) and best["ranges"] in (1, 2)
+        assert best["blocks_per_sm"] in (2, 4, 5, 6) and best["ranges"] in (1, 2)
         assert best["max_chunk"] in (256, 512, 1024)
         assert capi.rr_get_batch_tuning(G.handle) == best
         d_w.fill_(-1)
