@@ -289,7 +289,8 @@ rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target,
  * k-vertex query's on the first 2^k' points, so the k query also yields the
  * queries k' >= 5 (k' >= 6 with the pair-label layer 3): after its per-point
  * layer k'-2 it forms k''s sums over single labels from its stored rows and
- * runs k''s last layer. That is done where the k query's per-point layers are
+ * runs k''s last layer (with the pair tail, k-1's last layer reads those sums
+ * straight from layer k-3's pair sums). That is done where the k query's per-point layers are
  * long (deep rows with a window times min(2^k, 1024) at least 2^23; with
  * short layers the concurrent queries finish first; rr_graph_load's bits 6
  * and 7 force either form). Ordered on

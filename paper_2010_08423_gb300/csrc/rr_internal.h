@@ -113,7 +113,7 @@ struct Workspace {
     QueryDesc *h_bring = nullptr;
     DevBuf bdesc;
     cudaStream_t side = nullptr;  // the branches' stream
-    cudaEvent_t bev[3] = {};
+    cudaEvent_t bev[4] = {};
     cudaEvent_t ring_ev[kRing] = {};
     bool ring_used[kRing] = {};
     uint32_t ring_pos = 0;
@@ -428,11 +428,13 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 // per-point states equal this query's on their first 2^k' points -- so after
 // its per-point layer k'-2 the query also writes k''s transformed state and
 // runs k''s last layer with descriptor d_bdesc[k' - bfirst]. bfirst must be at
-// least atmost_first_branch(g, k); the pair tail is off in such a query.
-// side (or null: st) runs the branches beside the query, bev[0..2] (three
+// least atmost_first_branch(g, k). With the pair tail, branch k-1 is k-1's
+// last layer alone, over the single-label slots of layer k-3's pair sums (the
+// pair tail stays off where a point group would straddle 2^(k-1)).
+// side (or null: st) runs the branches beside the query, bev[0..3] (four
 // events) ordering them: each branch starts after its layer, the query waits
-// for the branch's transform after its next layer, and for all branches at
-// its end.
+// for the branch's transform after its next layer, before the next chunk's
+// pair sums for branch k-1, and for all branches at its end.
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels,

@@ -243,13 +243,14 @@ __global__ void k_last3(const V2Params p, uint32_t count)
         last3_closed(p, e);
 }
 
-template <int LG>
+// PB: from the pair tail's sums of a larger query (at-most-k branch k-1).
+template <int LG, bool PB = false>
 __global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
 {
     // pdl_enter() inside last_warp, after the graph- and query-only loads
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
-    last_warp<LG, false>(p, task);
+    last_warp<LG, false, PB>(p, task);
 }
 
 // Pair tail (rr_v2_device.cuh): layer k-2 in label space from layer k-3's
@@ -548,6 +549,40 @@ static rr_status enqueue_branch(const Graph &g, const V2Params &vp, uint32_t kb,
     return RR_OK;
 }
 
+// At-most-k branch k-1 with the pair tail (vp: the launch parameters of the k
+// query's layer k-3, its pair sums in vp.st_out after their fix-up): their
+// single-label slots are what layer k-3 of the (k-1)-vertex query would store
+// for its point groups below 2^(k-1), so the branch is that query's last layer
+// alone. The groups must not straddle 2^(k-1).
+static rr_status enqueue_pair_branch(const Graph &g, const V2Params &vp, uint32_t kb, const QueryDesc *d_bd,
+                                     uint32_t ppl, uint64_t stop_k, cudaStream_t st, uint64_t *nk)
+{
+    V2Params vb = vp;
+    const uint64_t stop = std::min<uint64_t>(stop_k, 1ull << kb);
+    const uint32_t gs = 32u * ppl;
+    if (stop % gs) return fail(RR_EINVAL, "internal: a point group straddles the branch's points");
+    vb.ngroups = (uint32_t)std::min<uint64_t>(vp.ngroups, (stop - vp.chunk_base) / gs);
+    vb.blk_groups = vp.ngroups;
+    vb.npoints = (uint32_t)stop;
+    vb.qd = d_bd;
+    vb.k = kb;
+    vb.layer = kb - 1;
+    vb.st_in = vp.st_out;
+    vb.carry = nullptr;
+    vb.row_carry = nullptr;
+    set_list(vb, g.tail3_list, 3);
+    if (vb.nitems && vb.ngroups) {
+        const int tslot = timing_begin(st);
+        const dim3 grid(blocks_for(vb.nitems)), B(kW2 * 32);
+        if (ppl == 4) RR_CUDA(launch_pdl(k_last_v2<7, true>, grid, B, st, vb));
+        else RR_CUDA(launch_pdl(k_last_v2<6, true>, grid, B, st, vb));
+        timing_end(tslot, kTimeLast, st);
+        RR_LAUNCHED();
+        ++*nk;
+    }
+    return RR_OK;
+}
+
 rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, uint32_t ppl,
                            uint32_t chunk, uint64_t *d_z, uint64_t *d_scratch,
                            const QueryDesc *d_desc, cudaStream_t st, uint64_t *kernels, bool pdl,
@@ -577,13 +612,13 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     uint64_t *carry = carry_words(g, chunk, k) ? red + red_w : nullptr;
     const uint32_t rstride = v2_reduced_stride(ppl, chunk);
     // the pair tail: layer k-3 writes pair sums into `red`, layer k-2 its
-    // label-space rows after the carry table
-    // (off with at-most-k branches: branch k-1 reads layer k-3's per-point rows)
-    const bool ptail = bfirst == 0 && pair_tail(g, ppl, chunk, k);
+    // label-space rows after the carry table (with at-most-k branches only
+    // where no point group straddles 2^(k-1): branch k-1 reads the sums)
+    const bool ptail = pair_tail(g, ppl, chunk, k) && (bfirst == 0 || (1ull << (k - 1)) % (32u * ppl) == 0);
     uint64_t *lrows = ptail ? red + red_w + carry_words(g, chunk, k) : nullptr;
     // at-most-k branches: their transformed buffer, so that they can run on
     // the side stream while the query goes on
-    bool side_used = false;
+    bool side_used = false, red_pending = false;
     if (bfirst && side && !bev) return fail(RR_EINVAL, "internal: branch side stream without events");
     uint64_t *bred = bfirst ? red + red_w + carry_words(g, chunk, k) +
                                   (label_tail_words(g, ppl, chunk, k) + 31) / 32 * 32
@@ -722,6 +757,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         uint64_t *bufs[2] = {full0, full1};
         const uint32_t last_pp = ptail ? k - 3 : k - 2;
         bool tr_pending = false;
+        // branch k-1 reads the pair sums in `red` on the side stream until bev[3]
         // with layer 3 in pair-label space the per-point layers start at 4,
         // layer 4 reading the pair windows
         for (uint32_t l = pair ? 4u : (k >= 5 ? 3u : 2u); l <= last_pp; ++l) {
@@ -746,6 +782,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
             vp.layer = l;
             vp.st_in = bufs[(l - 1) & 1u];
             vp.st_out = out != 0 ? red : bufs[l & 1u];
+            if (out != 0 && red_pending) {  // the previous chunk's branch k-1 has read `red`
+                RR_CUDA(cudaStreamWaitEvent(st, bev[3], 0));
+                red_pending = false;
+            }
             // per-point state read from the previous layer carries lazily
             vp.carry = src == 0 ? carry : nullptr;
             vp.row_carry = carry ? g.deep_list.row_carry.as<uint32_t>() : nullptr;
@@ -795,6 +835,21 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
                 s = enqueue_branch(g, vp, kb, d_bdesc + (kb - bfirst), carry, bred, ppl, range.stop(k), bs,
                                    side ? bev[1] : nullptr, &nk);
                 if (s != RR_OK) return s;
+            }
+            if (bfirst && out == 2 && k - 1 >= bfirst && (uint64_t)vp.chunk_base < (1ull << (k - 1))) {
+                // branch k-1 from the fixed-up pair sums
+                cudaStream_t bs = st;
+                if (side) {
+                    RR_CUDA(cudaEventRecord(bev[0], st));
+                    RR_CUDA(cudaStreamWaitEvent(side, bev[0], 0));
+                    bs = side;
+                }
+                s = enqueue_pair_branch(g, vp, k - 1, d_bdesc + (k - 1 - bfirst), ppl, range.stop(k), bs, &nk);
+                if (s != RR_OK) return s;
+                if (side) {
+                    RR_CUDA(cudaEventRecord(bev[3], side));
+                    side_used = red_pending = true;
+                }
             }
         }
         if (ptail) {

@@ -97,6 +97,9 @@ struct V2Params {
     // st_in holds true prefixes
     const uint32_t *row_carry;
     const uint64_t *carry;
+    // pair-sum blocks per stored row, for a last layer that reads the pair
+    // tail's layer k-3 sums (at-most-k branch k-1)
+    uint32_t blk_groups;
 };
 
 // z_{u,j}: from the table when the query has one (motif queries, Eq. 3), else
@@ -1048,8 +1051,11 @@ __device__ __forceinline__ void carry_rows(const uint64_t *__restrict__ buf, uin
 // sum_e y_{e,k-1} T_{g,j}(W_e) over the rows e of one head vertex v, then
 // multiplies once by z_{v,j} (j < lg) or by the XOR of z_{v,j'} over the
 // group's fixed high labels j' (slot lg), and the warp XOR-reduces into S[v].
+// PB: the state is the pair tail's sums of a larger query (p.blk_groups blocks
+// of kPairTailSlots per row), whose slots 1 + j and 0 are T_{g,j} and the
+// group total.
 // ---------------------------------------------------------------------------
-template <int LG, bool COHERENT>
+template <int LG, bool COHERENT, bool PB = false>
 __device__ __forceinline__ void last_pass(const V2Params &p, uint32_t task, uint32_t g0, bool first)
 {
     const int lane = threadIdx.x & 31;
@@ -1059,13 +1065,14 @@ __device__ __forceinline__ void last_pass(const V2Params &p, uint32_t task, uint
     uint64_t *const S = p.qd->S;
     uint64_t *const E = p.qd->E;  // per-edge sums wanted (fine-grained output)
     constexpr uint32_t kGroupsPerPass = 32 / (LG + 1);
-    const uint32_t row_slots = p.ngroups * (LG + 1);  // stored values per transformed row
+    // stored values per transformed row
+    const uint32_t row_slots = PB ? p.blk_groups * kPairTailSlots : p.ngroups * (LG + 1);
     const uint32_t slots = min(kGroupsPerPass, p.ngroups - g0) * (LG + 1);  // this pass's
     const bool active = (uint32_t)lane < slots;
     const uint32_t g = g0 + (uint32_t)lane / (LG + 1);
     const uint32_t j = (uint32_t)lane % (LG + 1);
     const uint32_t gbase = p.chunk_base + g * (1u << LG);
-    const uint32_t col = g0 * (LG + 1) + (uint32_t)lane;
+    const uint32_t col = PB ? g * kPairTailSlots + (j < (uint32_t)LG ? 1u + j : 0u) : g0 * (LG + 1) + (uint32_t)lane;
 
     auto zsel_of = [&](uint32_t v) -> uint64_t {
         if (!active) return 0ull;
@@ -1134,13 +1141,13 @@ __device__ __forceinline__ void last_pass(const V2Params &p, uint32_t task, uint
 
 // A warp covers 32 / (LG + 1) point groups at a time (one lane per stored
 // value); a chunk with more groups takes several passes over the rows.
-template <int LG, bool COHERENT>
+template <int LG, bool COHERENT, bool PB = false>
 __device__ __forceinline__ void last_warp(const V2Params &p, uint32_t task)
 {
     constexpr uint32_t kGroupsPerPass = 32 / (LG + 1);
 #pragma unroll 1
     for (uint32_t g0 = 0; g0 < p.ngroups; g0 += kGroupsPerPass)
-        last_pass<LG, COHERENT>(p, task, g0, g0 == 0);
+        last_pass<LG, COHERENT, PB>(p, task, g0, g0 == 0);
 }
 
 // ---------------------------------------------------------------------------

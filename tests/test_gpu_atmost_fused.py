@@ -5,7 +5,8 @@ layer 3) come from the k query. Every row must equal the single query's
 witness and the lanes-only form's (load flag bit 6; bit 7 forces the branches
 on these small graphs), bit for bit: k = 6..12,
 one and several point chunks, layer 3 per point or in pair-label space, cut
-hub segments; a few rows against the oracle."""
+hub segments, branch k-1 from the pair tail's sums; a few rows against the
+oracle."""
 import numpy as np
 import pytest
 
@@ -91,3 +92,42 @@ def test_bounded_reach_with_branches(k):
                 D = np.unpackbits(d_b.cpu().numpy(), bitorder="little")[:n].astype(bool)
                 assert np.array_equal(D, R_ref != oracle.NO_ARRIVAL)
     assert (L_ref >= 5).sum() > 3
+
+
+@pytest.mark.parametrize("k,ppl,chunk", [(7, 2, 256), (7, 4, 256), (8, 4, 256), (9, 2, 512),
+                                         (10, 4, 512), (11, 4, 1024), (12, 2, 256)])
+def test_branch_from_pair_sums(k, ppl, chunk):
+    """With the pair tail the k query's layer k-3 stores pair sums, and branch
+    k-1 is the (k-1)-vertex query's last layer over their single-label slots:
+    it must equal the pair tail off and the single queries, on a hub whose
+    cut segments the sums' fix-up completes, with 64- and 128-point groups and
+    one or several chunks below 2^(k-1). With 128-point groups and k = 7 a
+    group straddles 2^6, so there the pair tail stays off. Once with each
+    launch enqueued (kernel timing on, which counts the label-space layer) and
+    once from the captured graph."""
+    from test_gpu_parity import _hub_graph
+    g = _hub_graph()
+    n = g["n"]
+    seed = 31 + k
+    with capi.Graph(g, capi.FLAG_ATMOST_BRANCHES) as G, \
+            capi.Graph(g, capi.FLAG_ATMOST_BRANCHES | capi.FLAG_PAIR_TAIL_OFF) as H:
+        for X in (G, H):
+            capi.rr_set_tuning(X.handle, k, ppl, chunk)
+        capi.rr_timing_enable(True)
+        try:
+            capi.rr_timing_read(reset=True)
+            w_t, bm_t = _atmost(G, n, 9, k, seed)
+            tail_launches = capi.rr_timing_read(reset=True)["label_tail_layer"][1]
+            w_off, bm_off = _atmost(H, n, 9, k, seed)
+            assert capi.rr_timing_read(reset=True)["label_tail_layer"][1] == 0
+        finally:
+            capi.rr_timing_enable(False)
+        straddles = (1 << (k - 1)) % (32 * ppl) != 0
+        assert (tail_launches == 0) == straddles, tail_launches
+        w, bm = _atmost(G, n, 9, k, seed)
+        assert np.array_equal(w, w_t) and np.array_equal(bm, bm_t)
+        assert np.array_equal(w, w_off) and np.array_equal(bm, bm_off)
+        for kk in range(2, k + 1):
+            assert np.array_equal(w[kk - 2], G.reach(9, kk, seed)[1]), kk
+        assert np.array_equal(w[k - 3], oracle.sieve(g, 9, k - 1, seed))
+        assert np.count_nonzero(w[k - 3]) > 0
