@@ -129,7 +129,10 @@ typedef struct {
  * k-2 per point, writing its sums over single labels). Bit 6 / bit 7 set =
  * rr_reach_atmost_device runs every k' as a query of its own / always takes
  * the k' it can from the k query's layers (by default: when those layers are
- * long). Results are bit-identical in every form. The pair
+ * long). A k = 4 query over all its points runs layer 2 in label space and
+ * its last layer in closed form (per row, y_{e,3} times the 4 x 4 permanent of
+ * z_s, z_v, z_w and the window's label-space sums); bit 8 set = per point
+ * instead. Results are bit-identical in every form. The pair
  * rows ((deep rows + 1) * k(k+1)/2 words) and the head table (heads * chunk
  * words) are part of a query's scratch and, unlike the per-point state, do not
  * shrink with the point chunk: a server whose per-slot budget cannot hold them

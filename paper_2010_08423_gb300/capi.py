@@ -26,6 +26,7 @@ FLAG_HEAD_TABLE_OFF = 16
 FLAG_PAIR_TAIL_OFF = 32
 FLAG_ATMOST_LANES = 64
 FLAG_ATMOST_BRANCHES = 128
+FLAG_K4_PER_POINT = 256
 
 
 class RRError(RuntimeError):

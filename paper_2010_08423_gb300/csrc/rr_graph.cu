@@ -275,7 +275,7 @@ __global__ void k_v2_scatter(const uint32_t *__restrict__ row_dst, const uint32_
         }
         if (c2[r]) {
             const uint32_t i = rank2[r] - 1;
-            T.head[i] = h; T.eid[i] = e; T.a1[i] = a1[r]; T.b1[i] = b1[r];
+            T.head[i] = h; T.eid[i] = e; T.src[i] = u; T.a1[i] = a1[r]; T.b1[i] = b1[r];
         }
     }
 }
@@ -403,7 +403,7 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         const size_t bytes = (size_t)std::max<uint32_t>(1, counts[i]) * 4;
         RR_CUDA(R.head.reserve(bytes));
         RR_CUDA(R.eid.reserve(bytes));
-        if (i != 3) RR_CUDA(R.src.reserve(bytes));
+        RR_CUDA(R.src.reserve(bytes));  // the tail list's: the k = 4 closed form's z_v
         if (i == 1 || i == 2) {
             RR_CUDA(R.a0.reserve(bytes));
             RR_CUDA(R.b0.reserve(bytes));
@@ -607,6 +607,7 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     if ((flags & 24u) == 24u) return fail(RR_EINVAL, "rr_graph_load: flags turn the head-factor table both on and off");
     g->head_table_force = (flags & 8u) ? 2u : ((flags & 16u) ? 1u : 0u);
     g->pair_tail_off = (flags & 32u) != 0;
+    g->k4_per_point = (flags & 256u) != 0;
     if ((flags & 192u) == 192u) return fail(RR_EINVAL, "rr_graph_load: flags turn the at-most-k branches both on and off");
     g->atmost_branches = (flags & 128u) ? 2u : ((flags & 64u) ? 1u : 0u);
     RR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));

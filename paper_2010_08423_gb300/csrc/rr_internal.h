@@ -275,6 +275,9 @@ struct Graph {
     // layers k-2 and k-1 from the pair sums of layer k-3 (label-space layer
     // k-2) unless the load flags turn it off
     bool pair_tail_off = false;
+    // k = 4 per point (layer 2 over the sieve points) instead of the closed
+    // form over the label-space layer 2 (load flags)
+    bool k4_per_point = false;
     // at-most-k: k' >= the first branch from the k query's layers (2), every
     // k' on its own lane (1), or by the k query's per-point work (0; load flags)
     uint32_t atmost_branches = 0;

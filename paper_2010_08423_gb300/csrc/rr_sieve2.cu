@@ -243,6 +243,19 @@ __global__ void k_last3(const V2Params p, uint32_t count)
         last3_closed(p, e);
 }
 
+// k = 4: the last layer in closed form over the label-space layer 2
+// (last4_closed), a quad of lanes per row of the tail list.
+__global__ void __launch_bounds__(256) k_last4(const V2Params p, uint32_t count)
+{
+    const uint32_t j = threadIdx.x & 3u;
+    const uint64_t zs_j = zval(p, p.qd->source, j);  // reads the z table
+    pdl_enter();
+    // warp-uniform steps of 8 rows: every warp stays whole for its shuffles
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = gridDim.x * blockDim.x / 32u;
+    for (uint64_t base = (uint64_t)warp * 8u; base < count; base += (uint64_t)nwarps * 8u)
+        last4_closed(p, (uint32_t)base + ((threadIdx.x & 31u) >> 2), count, zs_j);
+}
+
 // PB: from the pair tail's sums of a larger query (at-most-k branch k-1).
 template <int LG, bool PB = false>
 __global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
@@ -414,7 +427,7 @@ static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, 
     const uint64_t drows = g.deep_list.count + 1;   // layers >= 3
     // k = 2 and k = 3 are closed forms: no per-point state
     *py_w = k >= 3 ? (g.prod_list.count + 1 + 31) / 32 * 32 : 0;
-    *pr2_w = k >= 5 ? (srows * k + 31) / 32 * 32 : 0;
+    *pr2_w = k >= 4 ? (srows * k + 31) / 32 * 32 : 0;  // k = 4: the closed-form last layer's
     *pr3_w = pair_layer3(g, k) ? (drows * pair_count(k) + 31) / 32 * 32 : 0;
     *tx_w = pair_layer3(g, k) && head_table(g) ? (uint64_t)std::max<uint32_t>(1, g.deep_list.nheads) * chunk : 0;
     *full_w = k >= 4 ? drows * chunk : 0;
@@ -638,7 +651,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     // the witness and the scratch's zero rows (k = 2 has no scratch); cleared by
     // the first layer's grid when it runs
     const ZeroRows zr{k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
-                      k >= 4 ? red : nullptr, k >= 5 ? pr2 : nullptr, g.n, chunk, red_width, k,
+                      k >= 4 ? red : nullptr, k >= 4 ? pr2 : nullptr, g.n, chunk, red_width, k,
                       pair ? pr3 : nullptr, pair_count(k), carry, lrows, bred, rstride};
     const bool zero_in_first = k >= 3 && g.prod_list.nitems > 0;
     if (!zero_in_first) {
@@ -689,7 +702,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     }
     vp.py = py;
     vp.pr2 = pr2;
-    if (k >= 5) {
+    // k = 4 over the whole range: layer 2 in label space and the last layer in
+    // closed form (no per-point state)
+    const bool closed4 = k == 4 && range.full(k) && !g.k4_per_point;
+    if (k >= 5 || closed4) {
         // layer 2 in label space (independent of the point chunk)
         set_list(vp, g.state_list, 0);
         vp.layer = 2;
@@ -745,8 +761,18 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         RR_LAUNCHED();
         ++nk;
     }
+    if (closed4 && g.tail_list.count) {
+        set_list(vp, g.tail_list, 1);
+        vp.layer = 3;
+        const int tslot = timing_begin(st);
+        RR_CUDA(launch_pdl(k_last4, dim3(grid_cap((g.tail_list.count + 7) / 8 * 32, 256)), dim3(256), st, vp,
+                           (uint32_t)g.tail_list.count));
+        timing_end(tslot, kTimeLast, st);
+        RR_LAUNCHED();
+        ++nk;
+    }
     const uint64_t npts = range.stop(k) - range.first;
-    const uint64_t nchunks = k == 3 ? 0 : (npts + chunk - 1) / chunk;
+    const uint64_t nchunks = k == 3 || closed4 ? 0 : (npts + chunk - 1) / chunk;
     for (uint64_t c = 0; c < nchunks; ++c) {
         vp.chunk_base = range.first + (uint32_t)(c * chunk);
         rr_status s = RR_OK;

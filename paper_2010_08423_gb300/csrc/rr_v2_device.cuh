@@ -375,6 +375,68 @@ __device__ __forceinline__ void last3_closed(const V2Params &p, uint32_t ent)
     if (p.qd->E) p.qd->E[e] = val;  // one entry per edge
 }
 
+// ---------------------------------------------------------------------------
+// k = 4, last layer in closed form over the label-space layer 2. A state row
+// f' of vertex v holds, over the points, P_2^L[f'] = x_v^L x_s^L
+// sum_{j in L} (y_{f',2} Y_{f'}) z_{u_{f'},j}, so the window of entry e (tail
+// v, head w) sums to x_v^L x_s^L D^L with D^L = sum_{j in L} dPR2_j, the
+// window's difference of the label-space prefix. The last layer multiplies by
+// y_{e,3} x_w^L, and summed over all L in [4] the product of the four linear
+// forms x_s, x_v, x_w, D counts each choice of one label per form 2^{4 - #}
+// times: only the bijections survive, so e adds
+//     y_{e,3} perm(z_s; z_v; z_w; dPR2)
+// to S[w]. A quad of lanes takes one entry, lane j owning label column j:
+// with b = z_v, c = z_w, d = dPR2 and Q_{ab} = c_a d_b + c_b d_a (the 2x2
+// permanents of the last two rows), lane j forms c_j d_{j^x} (x = 1, 2, 3),
+// which with its partner j^x gives Q_{j,j^x}; then the expansion along z_v of
+// the 3x3 minor without column j,
+//     t_j = b_{j^1} Q_{j^2,j^3} + b_{j^2} Q_{j^1,j^3} + b_{j^3} Q_{j^1,j^2},
+// and perm = sum_j z_{s,j} t_j over the quad: 8 products per lane. The tail
+// list is grouped by head, so the quads of a warp XOR their values along runs
+// of equal heads and the run's last quad adds the run's sum: one atomic per
+// head and warp.
+// ---------------------------------------------------------------------------
+// Called by whole warps; ent = a warp-aligned base / 4 + quad (8 entries per warp).
+__device__ __forceinline__ void last4_closed(const V2Params &p, uint32_t ent, uint32_t count, uint64_t zs_j)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = lane & 3, quad = lane >> 2;
+    const bool has = ent < count;
+    const uint32_t w = has ? p.head[ent] : 0xffffffffu;
+    uint64_t d = 0;
+    if (has) d = p.pr2[(size_t)p.ia[ent] * 4u + j] ^ p.pr2[(size_t)p.ib[ent] * 4u + j];
+    uint64_t val = 0;
+    if (__any_sync(0xffffffffu, d != 0)) {  // warp-uniform
+        const uint32_t v = has ? p.src[ent] : 0u;
+        const uint64_t b = has ? zval(p, v, (uint32_t)j) : 0ull;
+        const uint64_t c = has ? zval(p, w, (uint32_t)j) : 0ull;
+        // c_j d_{j^x}, then Q_{j,j^x} = c_j d_{j^x} + c_{j^x} d_j
+        const uint64_t q1 = rr_mul(c, shfl64x(d, 1)), q2 = rr_mul(c, shfl64x(d, 2)), q3 = rr_mul(c, shfl64x(d, 3));
+        const uint64_t Q1 = q1 ^ shfl64x(q1, 1), Q2 = q2 ^ shfl64x(q2, 2), Q3 = q3 ^ shfl64x(q3, 3);
+        // Q_{j^2,j^3}: lane j^2's Q1; Q_{j^1,j^3}: lane j^1's Q2; Q_{j^1,j^2}: lane j^1's Q3
+        const uint64_t t = rr_mul(shfl64x(b, 1), shfl64x(Q1, 2)) ^ rr_mul(shfl64x(b, 2), shfl64x(Q2, 1)) ^
+                           rr_mul(shfl64x(b, 3), shfl64x(Q3, 1));
+        uint64_t perm = rr_mul(zs_j, t);
+        perm ^= shfl64x(perm, 1);
+        perm ^= shfl64x(perm, 2);
+        const uint32_t e = has ? p.eid[ent] : 0u;
+        val = rr_mul(sm_draw(p.qd->key_y, (uint64_t)e * 32u + 2u), perm);  // y_{e,3}
+        if (has && j == 0 && p.qd->E) p.qd->E[e] = val;  // one entry per edge
+    }
+    // XOR along the runs of equal heads (contiguous quads)
+    const uint32_t prev = __shfl_sync(0xffffffffu, w, lane >= 4 ? lane - 4 : lane);
+    const uint32_t starts = __ballot_sync(0xffffffffu, j == 0 && (quad == 0 || prev != w));
+    const int run0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));  // first lane of the run
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+        const uint64_t o = shfl64b(val, lane >= off ? lane - off : lane);
+        if (lane - off >= run0) val ^= o;
+    }
+    const bool run_end = quad == 7 || ((starts >> (lane + 4 - j)) & 1u);
+    if (has && j == 0 && run_end && val)
+        atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + w), (unsigned long long)val);
+}
+
 // Sums of a lane group's per-point values (acc, the lane's PPL points) over
 // the group's 32*PPL points holding each in-group label: lane j < LG returns
 // T_j -- the in-lane labels from U, the lane labels from the half-cube sums of
