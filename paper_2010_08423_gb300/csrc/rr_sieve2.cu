@@ -187,10 +187,10 @@ static rr_status launch_fixup(const RowList &L, uint64_t *buf, uint32_t width, c
 
 __global__ void __launch_bounds__(kW2 * 32) k_second_label(const V2Params p, uint64_t *__restrict__ pr2)
 {
-    // pdl_enter() inside second_label_warp, after the graph- and query-only loads
+    // pdl_enter() inside second_label_scan_warp, after the graph- and query-only loads
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
     if (task >= p.nitems) return;
-    second_label_warp<true>(p, task, pr2);
+    second_label_scan_warp<true>(p, task, pr2);
 }
 
 __global__ void __launch_bounds__(kW2 * 32) k_third_pair(const V2Params p, uint32_t count,

@@ -807,7 +807,7 @@ __device__ __forceinline__ void layer_warp(const V2Params &p, uint32_t item, uin
 }
 
 // ---------------------------------------------------------------------------
-// Layer 2 in label space (k >= 5): for every state row f of head v,
+// Layer 2 in label space (k >= 4): for every state row f of head v,
 //   PR2[f][j] = XOR over v's state rows f' <= f of (y_{f',2} Y_{f'}) z_{u_{f'},j}
 // so that P_2^L[f'] = x_v^L x_s^L sum_{j in L} (y Y)_{f'} z_{u_{f'},j}. Independent of
 // the point chunk; lane j owns label j (one multiplication per lane and row).
@@ -846,6 +846,54 @@ __device__ __forceinline__ void second_label_warp(const V2Params &p, uint32_t it
                 acc ^= rr_mul(coef, zval(p, u, lane));
                 pr2[((size_t)base + t + 1) * k + lane] = acc;
             }
+        }
+    }
+}
+
+// The same layer with the rows across the lanes (the one-query kernel): lane t
+// takes row base + t and, label by label, its term c_t z_{u_t,j} (c_t =
+// y_{e,2} Y_e); an XOR scan over the lanes along runs of equal heads, plus the
+// prefix that the head's rows of the previous 32 left (lane j keeps label j's),
+// gives PR2. k products per lane per 32 rows instead of 32 on k lanes.
+template <bool LATE_WAIT>
+__device__ __forceinline__ void second_label_scan_warp(const V2Params &p, uint32_t item,
+                                                       uint64_t *__restrict__ pr2)
+{
+    const int lane = threadIdx.x & 31;
+    const uint2 it = p.items[item];
+    const uint32_t k = p.k;
+    const uint64_t key_y = p.qd->key_y;
+    uint64_t carry = 0;                // lane j < k: label j's prefix at the previous 32's last row
+    uint32_t last_head = 0xffffffffu;  // the previous 32's last head (none yet)
+    for (uint32_t base = it.x; base < it.y; base += 32) {
+        const uint32_t ent = base + (uint32_t)lane;
+        const bool has = ent < it.y;
+        const uint32_t h = has ? p.head[ent] : 0xfffffffeu;
+        const uint32_t u = has ? p.src[ent] : 0u;
+        const uint64_t y = has ? sm_draw(key_y, (uint64_t)p.eid[ent] * 32u + 1u) : 0ull;  // y_{e,2}
+        const uint32_t ia = has ? p.ia[ent] : 0u, ib = has ? p.ib[ent] : 0u;
+        if constexpr (LATE_WAIT) {
+            if (base == it.x) pdl_enter();  // the layer-1 prefix is read from here on
+        }
+        const uint64_t coef = has ? rr_mul(y, p.py[ia] ^ p.py[ib]) : 0ull;  // y_{e,2} Y_e
+        const bool any = __any_sync(0xffffffffu, coef != 0);
+        const uint32_t hp = __shfl_up_sync(0xffffffffu, h, 1);
+        const uint32_t starts = __ballot_sync(0xffffffffu, lane == 0 || hp != h);
+        const int run0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));  // first lane of the run
+        const bool cont = run0 == 0 && h == last_head;  // the run goes on from the previous 32
+        last_head = __shfl_sync(0xffffffffu, h, 31);
+        for (uint32_t j = 0; j < k; ++j) {
+            uint64_t val = any ? rr_mul(coef, zval(p, u, j)) : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint64_t o = shfl64b(val, lane >= off ? lane - off : lane);
+                if (lane - off >= run0) val ^= o;
+            }
+            const uint64_t cj = shfl64b(carry, (int)j);  // every lane takes part
+            if (cont) val ^= cj;
+            if (has) pr2[((size_t)ent + 1) * k + j] = val;
+            const uint64_t v31 = shfl64b(val, 31);
+            if ((uint32_t)lane == j) carry = v31;
         }
     }
 }
