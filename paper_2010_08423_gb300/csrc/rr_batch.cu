@@ -29,7 +29,8 @@ namespace {
 enum BatchKind : uint32_t {
     kSecondFull = 0,   // layer 2, window sums from the scalar prefix, full state out
     kSecondTail = 1,   // layer 2 when k = 4, transformed state out
-    // 2: unused (k <= 3 queries finish in the prologue: k_batch_first2, k_batch_last3)
+    // 2: unused (k <= 3 queries finish in the prologue: k_batch_first2, k_batch_last3;
+    // so does k = 4 in closed form: k_batch_last4)
     kMidFull = 3,      // layers 3..k-3
     kMidTail = 4,      // layer k-2 (k >= 6), transformed state out
     kLast = 5,         // layer k-1 from the transformed state
@@ -320,9 +321,10 @@ __global__ void k_wait_probe(BatchArgs a, const uint32_t *ctr, uint64_t *out)
 }
 
 // Prologue / epilogue over all queries of the batch (blockIdx.y = query).
+// (the vertices in colour order: a warp's shade loops have one length)
 __global__ void k_batch_ztable(uint32_t n, const QueryDesc *__restrict__ descs,
-                               const uint8_t *__restrict__ color, uint64_t *__restrict__ z_all,
-                               const uint64_t *__restrict__ z_off)
+                               const uint8_t *__restrict__ color, const uint32_t *__restrict__ order,
+                               uint64_t *__restrict__ z_all, const uint64_t *__restrict__ z_off)
 {
     const QueryDesc *qd = descs + blockIdx.y;
     const uint32_t k = qd->k;
@@ -332,8 +334,9 @@ __global__ void k_batch_ztable(uint32_t n, const QueryDesc *__restrict__ descs,
     const uint64_t total = (uint64_t)n * k;
     for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t u = idx / k;
-        const uint32_t j = (uint32_t)(idx - u * k);
+        const uint64_t pos = total <= 0xffffffffull ? (uint64_t)((uint32_t)idx / k) : idx / k;
+        const uint32_t j = (uint32_t)(idx - pos * k);
+        const uint64_t u = order ? order[pos] : pos;
         uint64_t val = 0;
         if (!colored) {
             val = sm_draw(qd->key_z, u * 32u + j);
@@ -343,7 +346,7 @@ __global__ void k_batch_ztable(uint32_t n, const QueryDesc *__restrict__ descs,
             for (uint32_t d = d0; d < d0 + mu; ++d)
                 val ^= gf64_mul(sm_draw(qd->key_g, u * 32u + d), sm_draw(qd->key_o, (uint64_t)d * 32u + j));
         }
-        z[idx] = val;
+        z[u * k + j] = val;
     }
 }
 
@@ -365,16 +368,17 @@ k_batch_first(ListPtrs prod, const QueryDesc *__restrict__ descs, uint64_t *__re
     first_scalar_warp(vp, task, py);
 }
 
-// layer 2 in label space for the batch's queries with k >= 5
+// layer 2 in label space for the batch's queries with k >= kmin (4, or 5
+// with k = 4 per point), the rows across the lanes
 __global__ void __launch_bounds__(kW2 * 32)
 k_batch_second(ListPtrs state, const QueryDesc *__restrict__ descs, const uint64_t *__restrict__ z_all,
                const uint64_t *__restrict__ z_off, const uint64_t *__restrict__ py_all,
                const uint64_t *__restrict__ py_off, uint64_t *__restrict__ pr2_all,
-               const uint64_t *__restrict__ pr2_off, uint32_t n)
+               const uint64_t *__restrict__ pr2_off, uint32_t n, uint32_t kmin)
 {
     const QueryDesc *qd = descs + blockIdx.y;
     const uint32_t k = qd->k;
-    if (k < 5) return;
+    if (k < kmin) return;
     uint64_t *pr2 = pr2_all + pr2_off[blockIdx.y];
     if (blockIdx.x == 0 && threadIdx.x < k) pr2[threadIdx.x] = 0;
     const uint32_t task = blockIdx.x * kW2 + (threadIdx.x >> 5);
@@ -393,7 +397,7 @@ k_batch_second(ListPtrs state, const QueryDesc *__restrict__ descs, const uint64
     vp.ib = state.b0;
     vp.items = state.items;
     vp.nitems = state.nitems;
-    second_label_warp<false>(vp, task, pr2);
+    second_label_scan_warp<false>(vp, task, pr2);
 }
 
 // the batch's k = 2 queries in closed form (blockIdx.y = query)
@@ -435,6 +439,33 @@ __global__ void k_batch_last3(ListPtrs win, uint32_t count, const QueryDesc *__r
     vp.ib = win.b0;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
         last3_closed(vp, e);
+}
+
+// the batch's k = 4 queries in closed form over their label-space layer 2
+// (blockIdx.y = query; last4_closed, a quad of lanes per tail row)
+__global__ void __launch_bounds__(256)
+k_batch_last4(ListPtrs tail, uint32_t count, const QueryDesc *__restrict__ descs,
+              const uint64_t *__restrict__ z_all, const uint64_t *__restrict__ z_off,
+              const uint64_t *__restrict__ pr2_all, const uint64_t *__restrict__ pr2_off, uint32_t n)
+{
+    const QueryDesc *qd = descs + blockIdx.y;
+    if (qd->k != 4) return;  // the whole block
+    V2Params vp{};
+    vp.qd = qd;
+    vp.z = qd->colored ? z_all + z_off[blockIdx.y] : nullptr;
+    vp.pr2 = pr2_all + pr2_off[blockIdx.y];
+    vp.n = n;
+    vp.k = 4;
+    vp.layer = 3;
+    vp.head = tail.head;
+    vp.eid = tail.eid;
+    vp.src = tail.src;
+    vp.ia = tail.a1;
+    vp.ib = tail.b1;
+    const uint64_t zs_j = zval(vp, qd->source, threadIdx.x & 3u);
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = gridDim.x * blockDim.x / 32u;
+    for (uint64_t base = (uint64_t)warp * 8u; base < count; base += (uint64_t)nwarps * 8u)
+        last4_closed(vp, (uint32_t)base + ((threadIdx.x & 31u) >> 2), count, zs_j);
 }
 
 __global__ void k_batch_bitmap(uint32_t n, const QueryDesc *__restrict__ descs)
@@ -480,14 +511,15 @@ ListPtrs list_ptrs(const RowList &L, bool coarse)
                     L.chains.as<uint2>(),  L.fix2.as<uint2>(),   L.nchains, L.nfix2};
 }
 
-// prologue fix-ups of the per-query scalar (width 1) or label-space (width k,
-// queries with k >= 5 only) prefixes: blockIdx.y = query
+// prologue fix-ups of the per-query scalar (width 1, label_space 0) or
+// label-space (width k, queries with k >= label_space only) prefixes:
+// blockIdx.y = query
 __global__ void k_batch_fix1(ListPtrs L, uint64_t *base, const uint64_t *__restrict__ off,
                              const QueryDesc *__restrict__ descs, int label_space)
 {
     if (blockIdx.x >= L.nchains) return;
     const uint32_t k = descs[blockIdx.y].k;
-    if (label_space && k < 5) return;
+    if (label_space && k < (uint32_t)label_space) return;
     const uint2 ch = L.chains[blockIdx.x];
     fixup_phase1<false>(base + off[blockIdx.y], label_space ? k : 1u, ch.x, ch.y, threadIdx.x,
                         blockDim.x);
@@ -498,7 +530,7 @@ __global__ void k_batch_fix2(ListPtrs L, uint64_t *base, const uint64_t *__restr
 {
     if (blockIdx.x >= L.nfix2) return;
     const uint32_t k = descs[blockIdx.y].k;
-    if (label_space && k < 5) return;
+    if (label_space && k < (uint32_t)label_space) return;
     const uint2 t = L.fix2[blockIdx.x];
     const uint2 ch = L.chains[t.x];
     fixup_phase2<false>(base + off[blockIdx.y], label_space ? k : 1u, ch.x, ch.y, t.y, threadIdx.x,
@@ -627,6 +659,9 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
 
         // units
         std::vector<BatchUnit> units;
+        // the smallest k with a label-space layer 2 (k = 4 in closed form unless the
+        // load flags keep it per point)
+        const uint32_t kmin2 = g.k4_per_point ? 5u : 4u;
         std::vector<QueryDesc> descs(grp.size());
         std::vector<uint64_t> z_off(grp.size()), py_off(grp.size()), pr2_off(grp.size());
         uint64_t zw = 0, pr2w = 0;
@@ -654,12 +689,14 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
             if (q.motif) zw += ((uint64_t)g.n * q.k + 31) / 32 * 32;
             py_off[j] = j * py_words;
             pr2_off[j] = pr2w;
-            if (q.k >= 5) pr2w += (rows * q.k + 31) / 32 * 32;
+            if (q.k >= kmin2) pr2w += (rows * q.k + 31) / 32 * 32;
             const uint64_t npts = 1ull << q.k;
             const uint32_t ppl = npts >= 128 ? 4u : 2u;
             uint32_t chunk = (uint32_t)std::max<uint64_t>(32ull * ppl, std::min<uint64_t>(npts, max_chunk));
             chunk = std::max<uint32_t>(chunk, 32u * ppl);
-            const uint64_t nch = q.k <= 3 ? 0 : (npts + chunk - 1) / chunk;  // k <= 3: prologue
+            // k <= 3 and k = 4 in closed form finish in the prologue
+            const bool prologue = q.k <= 3 || (q.k == 4 && kmin2 == 4);
+            const uint64_t nch = prologue ? 0 : (npts + chunk - 1) / chunk;
             for (uint64_t c = 0; c < nch; ++c)
                 units.push_back(BatchUnit{(uint32_t)j, q.k, (uint32_t)(c * chunk), chunk, ppl, 0,
                                           grp[j]});
@@ -821,8 +858,8 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
         const unsigned gz = (unsigned)std::min<uint64_t>(1024, ((uint64_t)g.n * 20 + 255) / 256);
         int tslot = timing_begin(st);
         k_batch_ztable<<<dim3(gz, (unsigned)grp.size()), 256, 0, st>>>(
-            g.n, d_descs.as<QueryDesc>(), g.color.as<uint8_t>(), d_z.as<uint64_t>(),
-            d_zoff.as<uint64_t>());
+            g.n, d_descs.as<QueryDesc>(), g.color.as<uint8_t>(), g.color_order.as<uint32_t>(),
+            d_z.as<uint64_t>(), d_zoff.as<uint64_t>());
         timing_end(tslot, kTimeZ, st);
         RR_LAUNCHED();
         const ListPtrs prod = list_ptrs(g.prod_list, false);
@@ -843,19 +880,31 @@ rr_status batch_device(const Graph &g, const rr_query *qs, uint32_t nq, uint8_t 
                          kW2 * 32, 0, st>>>(list_ptrs(g.state_list, false), d_descs.as<QueryDesc>(),
                                             d_z.as<uint64_t>(), d_zoff.as<uint64_t>(),
                                             d_py.as<uint64_t>(), d_pyoff.as<uint64_t>(),
-                                            B.pr2.as<uint64_t>(), B.pr2off.as<uint64_t>(), g.n);
+                                            B.pr2.as<uint64_t>(), B.pr2off.as<uint64_t>(), g.n, kmin2);
         timing_end(tslot, kTimeSecond, st);
         RR_LAUNCHED();
         {
             rr_status fs = batch_fixup(list_ptrs(g.state_list, false), B.pr2.as<uint64_t>(),
                                        B.pr2off.as<uint64_t>(), d_descs.as<QueryDesc>(),
-                                       (uint32_t)grp.size(), 1, st);
+                                       (uint32_t)grp.size(), (int)kmin2, st);
             if (fs != RR_OK) return fs;
         }
-        bool any2 = false, any3 = false;
+        bool any2 = false, any3 = false, any4 = false;
         for (uint32_t j : grp) {
             any2 |= qs[j].k == 2;
             any3 |= qs[j].k == 3;
+            any4 |= qs[j].k == 4 && kmin2 == 4;
+        }
+        if (any4 && g.tail_list.count) {
+            const uint32_t cnt = (uint32_t)g.tail_list.count;
+            const int t4 = timing_begin(st);
+            k_batch_last4<<<dim3(std::min<uint32_t>(2048, (uint32_t)(((uint64_t)cnt + 7) / 8 * 32 + 255) / 256),
+                                 (unsigned)grp.size()),
+                            256, 0, st>>>(list_ptrs(g.tail_list, false), cnt, d_descs.as<QueryDesc>(),
+                                          d_z.as<uint64_t>(), d_zoff.as<uint64_t>(), B.pr2.as<uint64_t>(),
+                                          B.pr2off.as<uint64_t>(), g.n);
+            timing_end(t4, kTimeLast, st);
+            RR_LAUNCHED();
         }
         if (any2 && g.m) {
             const uint32_t m32 = (uint32_t)g.m;

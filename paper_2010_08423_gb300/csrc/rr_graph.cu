@@ -617,6 +617,13 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     if (color) {
         RR_CUDA(g->color.reserve(n));
         RR_CUDA(cudaMemcpyAsync(g->color.p, color, n, cudaMemcpyHostToDevice, st));
+        // counting sort of the vertices by colour
+        std::vector<uint32_t> start(257, 0), order(n);
+        for (uint32_t v = 0; v < n; ++v) ++start[color[v] + 1u];
+        for (int c = 0; c < 256; ++c) start[c + 1] += start[c];
+        for (uint32_t v = 0; v < n; ++v) order[start[color[v]]++] = v;
+        RR_CUDA(g->color_order.reserve((size_t)n * 4));
+        RR_CUDA(cudaMemcpy(g->color_order.p, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     }
     const size_t mb = (size_t)(m ? m : 1);
     for (DevBuf *b : {&g->row_a, &g->row_b, &g->row_s, &g->row_eid, &g->row_src, &g->row_lo,

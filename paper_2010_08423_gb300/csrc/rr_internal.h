@@ -294,6 +294,10 @@ struct Graph {
     DevBuf row_t;    // m uint32: time of the row's edge
     DevBuf row_head; // m uint32: head v of the row (the row lies in v's segment)
     DevBuf color;    // n uint8 (if coloured)
+    // n uint32 (if coloured): the vertices by colour, ascending (stable), so
+    // that the threads of a warp that build a motif query's z-table share one
+    // shade count
+    DevBuf color_order;
     DevBuf items;    // uint2 (v0, v1) vertex ranges, largest first
     uint32_t nitems = 0;
     std::vector<uint32_t> h_item_rows;  // rows per item (host copy, same order)
@@ -332,7 +336,7 @@ struct Graph {
     {
         return off.bytes + row_a.bytes + row_b.bytes + row_s.bytes + row_eid.bytes +
                row_src.bytes + row_lo.bytes + row_hi.bytes + row_t.bytes + row_head.bytes +
-               color.bytes + items.bytes +
+               color.bytes + color_order.bytes + items.bytes +
                prod_list.bytes() + state_list.bytes() + win_list.bytes() + tail_list.bytes() +
                deep_list.bytes() + tail3_list.bytes();
     }

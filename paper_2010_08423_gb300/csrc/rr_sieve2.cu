@@ -459,9 +459,11 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 }
 
 // z_{u,j} from the descriptor's keys (plain iid draws or Eq. (3) shades); rows
-// of deleted vertices are zero.
+// of deleted vertices are zero. Coloured graphs visit the vertices in colour
+// order (`order`), so a warp's shade loops have one length.
 __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__ qd,
-                           const uint8_t *__restrict__ color, uint64_t *__restrict__ z)
+                           const uint8_t *__restrict__ color, const uint32_t *__restrict__ order,
+                           uint64_t *__restrict__ z)
 {
     pdl_enter();
     const uint64_t total = (uint64_t)n * k;
@@ -469,8 +471,9 @@ __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__
     const uint64_t kz = qd->key_z, kg = qd->key_g, ko = qd->key_o;
     for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t u = idx / k;
-        const uint32_t j = (uint32_t)(idx - u * k);
+        const uint64_t pos = total <= 0xffffffffull ? (uint64_t)((uint32_t)idx / k) : idx / k;
+        const uint32_t j = (uint32_t)(idx - pos * k);
+        const uint64_t u = colored && order ? order[pos] : pos;
         uint64_t val = 0;
         if (!colored) {
             val = sm_draw(kz, u * 32u + j);
@@ -481,7 +484,7 @@ __global__ void k_ztable_q(uint32_t n, uint32_t k, const QueryDesc *__restrict__
                 val ^= gf64_mul(sm_draw(kg, u * 32u + d), sm_draw(ko, (uint64_t)d * 32u + j));
         }
         if (qd->vmask && qd->vmask[u]) val = 0;
-        z[idx] = val;
+        z[u * k + j] = val;
     }
 }
 
@@ -642,7 +645,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         if (table) {  // plain queries without deletions draw z on the fly
             const int tslot = timing_begin(st);
             RR_CUDA(launch_pdl(k_ztable_q, dim3(grid_cap((uint64_t)g.n * k, 256)), dim3(256), st, g.n, k,
-                               d_desc, g.color.as<uint8_t>(), d_z));
+                               d_desc, g.color.as<uint8_t>(), g.color_order.as<uint32_t>(), d_z));
             timing_end(tslot, kTimeZ, st);
             RR_LAUNCHED();
             ++nk;

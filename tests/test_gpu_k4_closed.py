@@ -91,3 +91,29 @@ def test_atmost_range_and_extraction():
         for t in targets:
             p = G.extract_path(3, 4, 8, int(t))
             assert p == H.extract_path(3, 4, 8, int(t)), t
+
+
+def test_persistent_batch():
+    """The batch's k = 4 queries finish in its prologue (label-space layer 2 for
+    every query with k >= 4, then the closed form); with load flag bit 8 they
+    run per point in the persistent kernel. Mixed k = 3..6, plain and motif,
+    on the hub graph and a uniform one, against single queries and the oracle."""
+    import torch
+    for idx in (0, 2):
+        name, g, _ = _graphs()[idx]
+        n = g["n"]
+        ncol = int(g["color"].max()) + 1
+        qs = W.query_set(g, 24, 3, 6, 0x5EED0044 + idx, colored_every_other=True, ncolors=ncol)
+        assert sum(q["k"] == 4 for q in qs) >= 3
+        for flags in (0, capi.FLAG_K4_PER_POINT):
+            with capi.Graph(g, flags) as G:
+                d_w = torch.zeros((len(qs), n), dtype=torch.int64, device="cuda")
+                capi.rr_reach_batch_device(G.handle, qs, d_w)
+                torch.cuda.synchronize()
+                w = d_w.cpu().numpy().view(np.uint64)
+                for i, q in enumerate(qs):
+                    _, ref = G.reach(q["source"], q["k"], q["seed"], motif=q["motif"])
+                    assert np.array_equal(w[i], ref), (name, flags, i, q["k"])
+                    if q["k"] == 4:
+                        assert np.array_equal(ref, oracle.sieve(g, q["source"], 4, q["seed"],
+                                                                motif=q["motif"])), (name, i)
