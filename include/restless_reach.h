@@ -132,7 +132,11 @@ typedef struct {
  * long). A k = 4 query over all its points runs layer 2 in label space and
  * its last layer in closed form (per row, y_{e,3} times the 4 x 4 permanent of
  * z_s, z_v, z_w and the window's label-space sums); bit 8 set = per point
- * instead. Results are bit-identical in every form. The pair
+ * instead. Bit 9 set = a k = 5 query over all its points runs layer 3 in
+ * pair-label space and its last layer in closed form (per row, y_{e,4} times
+ * the sum over the splits of the five labels into one for z_w, a pair for z_v
+ * and z_s and a pair for the window's pair sums) instead of per point (the
+ * default: faster on the graphs measured). Results are bit-identical in every form. The pair
  * rows ((deep rows + 1) * k(k+1)/2 words) and the head table (heads * chunk
  * words) are part of a query's scratch and, unlike the per-point state, do not
  * shrink with the point chunk: a server whose per-slot budget cannot hold them
@@ -290,10 +294,10 @@ rr_status rr_extract_path(const rr_graph *g, const rr_query *q, uint32_t target,
  * reach sets: vertices reached by a restless path of at most k vertices.
  * For one seed the k'-vertex query's per-point layers agree with the
  * k-vertex query's on the first 2^k' points, so the k query also yields the
- * queries k' >= 5 (k' >= 6 with the pair-label layer 3): after its per-point
- * layer k'-2 it forms k''s sums over single labels from its stored rows and
- * runs k''s last layer (with the pair tail, k-1's last layer reads those sums
- * straight from layer k-3's pair sums). That is done where the k query's per-point layers are
+ * queries k' >= 5: after its per-point layer k'-2 it forms k''s sums over
+ * single labels from its stored rows and runs k''s last layer (with the pair
+ * tail, k-1's last layer reads those sums straight from layer k-3's pair sums;
+ * with the pair-label layer 3, k' = 5 is the closed form over its pair rows). That is done where the k query's per-point layers are
  * long (deep rows with a window times min(2^k, 1024) at least 2^23; with
  * short layers the concurrent queries finish first; rr_graph_load's bits 6
  * and 7 force either form). Ordered on

@@ -27,6 +27,7 @@ FLAG_PAIR_TAIL_OFF = 32
 FLAG_ATMOST_LANES = 64
 FLAG_ATMOST_BRANCHES = 128
 FLAG_K4_PER_POINT = 256
+FLAG_K5_CLOSED = 512
 
 
 class RRError(RuntimeError):

@@ -242,7 +242,8 @@ __global__ void k_v2_scatter3(const uint32_t *__restrict__ row_dst, const uint32
         }
         if (c4[r]) {
             const uint32_t i = rank4[r] - 1;
-            T.head[i] = row_dst[r]; T.eid[i] = row_eid[r]; T.a3[i] = a3[r]; T.b3[i] = b3[r];
+            T.head[i] = row_dst[r]; T.eid[i] = row_eid[r]; T.src[i] = row_src[r];
+            T.a3[i] = a3[r]; T.b3[i] = b3[r];
         }
     }
 }
@@ -447,11 +448,11 @@ rr_status build_lists_v2(Graph &g, const uint32_t *row_dst, const uint32_t *tpro
         const size_t db = (size_t)std::max<uint32_t>(1, c3[0]) * 4;
         const size_t tb = (size_t)std::max<uint32_t>(1, c3[1]) * 4;
         for (DevBuf *b : {&D.head, &D.eid, &D.src, &D.a1, &D.b1, &D.a3, &D.b3}) RR_CUDA(b->reserve(db));
-        for (DevBuf *b : {&T.head, &T.eid, &T.a3, &T.b3}) RR_CUDA(b->reserve(tb));
+        for (DevBuf *b : {&T.head, &T.eid, &T.src, &T.a3, &T.b3}) RR_CUDA(b->reserve(tb));
         ListOut od{D.head.as<uint32_t>(), D.eid.as<uint32_t>(), D.src.as<uint32_t>(), nullptr, nullptr,
                    D.a1.as<uint32_t>(), D.b1.as<uint32_t>(), D.a3.as<uint32_t>(), D.b3.as<uint32_t>()};
-        ListOut ot{T.head.as<uint32_t>(), T.eid.as<uint32_t>(), nullptr, nullptr, nullptr, nullptr,
-                   nullptr, T.a3.as<uint32_t>(), T.b3.as<uint32_t>()};
+        ListOut ot{T.head.as<uint32_t>(), T.eid.as<uint32_t>(), T.src.as<uint32_t>(), nullptr, nullptr,
+                   nullptr, nullptr, T.a3.as<uint32_t>(), T.b3.as<uint32_t>()};
         k_v2_scatter3<<<grid_for(m, 256), 256, 0, st>>>(
             row_dst, g.row_eid.as<uint32_t>(), g.row_src.as<uint32_t>(), a1.as<uint32_t>(),
             b1.as<uint32_t>(), a3.as<uint32_t>(), b3.as<uint32_t>(), d.as<uint32_t>(),
@@ -608,6 +609,7 @@ rr_status graph_load(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t
     g->head_table_force = (flags & 8u) ? 2u : ((flags & 16u) ? 1u : 0u);
     g->pair_tail_off = (flags & 32u) != 0;
     g->k4_per_point = (flags & 256u) != 0;
+    g->k5_closed = (flags & 512u) != 0;
     if ((flags & 192u) == 192u) return fail(RR_EINVAL, "rr_graph_load: flags turn the at-most-k branches both on and off");
     g->atmost_branches = (flags & 128u) ? 2u : ((flags & 64u) ? 1u : 0u);
     RR_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));

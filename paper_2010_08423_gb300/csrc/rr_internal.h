@@ -278,6 +278,10 @@ struct Graph {
     // k = 4 per point (layer 2 over the sieve points) instead of the closed
     // form over the label-space layer 2 (load flags)
     bool k4_per_point = false;
+    // k = 5 in closed form over the pair-label layer 3 instead of per point
+    // (load flags; per point is faster on the measured graphs, the closed form
+    // there as an exact alternative)
+    bool k5_closed = false;
     // at-most-k: k' >= the first branch from the k query's layers (2), every
     // k' on its own lane (1), or by the k query's per-point work (0; load flags)
     uint32_t atmost_branches = 0;
@@ -435,7 +439,8 @@ uint64_t v2_scratch_bytes(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t
 // per-point states equal this query's on their first 2^k' points -- so after
 // its per-point layer k'-2 the query also writes k''s transformed state and
 // runs k''s last layer with descriptor d_bdesc[k' - bfirst]. bfirst must be at
-// least atmost_first_branch(g, k). With the pair tail, branch k-1 is k-1's
+// least atmost_first_branch(g, k); with the pair-label layer 3, branch 5 is the
+// closed form over this query's pair rows. With the pair tail, branch k-1 is k-1's
 // last layer alone, over the single-label slots of layer k-3's pair sums (the
 // pair tail stays off where a point group would straddle 2^(k-1)).
 // side (or null: st) runs the branches beside the query, bev[0..3] (four

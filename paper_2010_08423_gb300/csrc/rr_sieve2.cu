@@ -256,6 +256,24 @@ __global__ void __launch_bounds__(256) k_last4(const V2Params p, uint32_t count)
         last4_closed(p, (uint32_t)base + ((threadIdx.x & 31u) >> 2), count, zs_j);
 }
 
+// k = 5: the last layer in closed form over the pair-label layer 3
+// (last5_closed), eight lanes per row of the deep-tail list; np = values per
+// pair row (pair_count of the query that wrote them).
+__global__ void __launch_bounds__(256) k_last5(const V2Params p, uint32_t count, uint32_t np)
+{
+    const uint32_t c = threadIdx.x & 7u;
+    const bool act = c < 5u;
+    const uint32_t s = p.qd->source;
+    const uint64_t zs0 = act ? zval(p, s, c) : 0ull;  // reads the z table
+    const uint64_t zs1 = act ? zval(p, s, (c + 1u) % 5u) : 0ull;
+    const uint64_t zs2 = act ? zval(p, s, (c + 2u) % 5u) : 0ull;
+    pdl_enter();
+    // warp-uniform steps of 4 rows: every warp stays whole for its shuffles
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = gridDim.x * blockDim.x / 32u;
+    for (uint64_t base = (uint64_t)warp * 4u; base < count; base += (uint64_t)nwarps * 4u)
+        last5_closed(p, (uint32_t)base + ((threadIdx.x & 31u) >> 3), count, np, zs0, zs1, zs2);
+}
+
 // PB: from the pair tail's sums of a larger query (at-most-k branch k-1).
 template <int LG, bool PB = false>
 __global__ void __launch_bounds__(kW2 * 32) k_last_v2(const V2Params p)
@@ -393,8 +411,10 @@ static bool pair_tail(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k)
 
 uint32_t atmost_first_branch(const Graph &g, uint32_t k)
 {
-    const uint32_t b = (pair_layer3(g, k) ? 4u : 3u) + 2u;  // first per-point layer + 2
-    return b < k ? b : 0u;
+    // first per-point layer + 2 (5, or 6 with the pair-label layer 3, where
+    // k' = 5 is the closed form over the k query's pair rows)
+    (void)g;
+    return 5u < k ? 5u : 0u;
 }
 
 uint32_t atmost_branches(const Graph &g, uint32_t k)
@@ -428,7 +448,8 @@ static void v2_layout(const Graph &g, uint32_t ppl, uint32_t chunk, uint32_t k, 
     // k = 2 and k = 3 are closed forms: no per-point state
     *py_w = k >= 3 ? (g.prod_list.count + 1 + 31) / 32 * 32 : 0;
     *pr2_w = k >= 4 ? (srows * k + 31) / 32 * 32 : 0;  // k = 4: the closed-form last layer's
-    *pr3_w = pair_layer3(g, k) ? (drows * pair_count(k) + 31) / 32 * 32 : 0;
+    // (k = 5: the closed-form last layer's)
+    *pr3_w = pair_layer3(g, k) || k == 5 ? (drows * pair_count(k) + 31) / 32 * 32 : 0;
     *tx_w = pair_layer3(g, k) && head_table(g) ? (uint64_t)std::max<uint32_t>(1, g.deep_list.nheads) * chunk : 0;
     *full_w = k >= 4 ? drows * chunk : 0;
     // whole 256-byte blocks: the next buffer (the carry table) is read with
@@ -618,6 +639,10 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     uint64_t py_w, pr2_w, pr3_w, tx_w, full_w, red_w;
     v2_layout(g, ppl, chunk, k, &py_w, &pr2_w, &pr3_w, &tx_w, &full_w, &red_w);
     const bool pair = pair_layer3(g, k);
+    // k = 5 over the whole range with the load flag: layer 3 in pair-label
+    // space and the last layer in closed form (no per-point state)
+    const bool closed5 = k == 5 && range.full(k) && g.k5_closed;
+    const bool prows = pair || closed5;  // layer 3's pair rows
     uint64_t *py = d_scratch;
     uint64_t *pr2 = py + py_w;
     uint64_t *pr3 = pr2 + pr2_w;
@@ -655,7 +680,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     // the first layer's grid when it runs
     const ZeroRows zr{k >= 3 ? py : nullptr, k >= 4 ? full0 : nullptr, k >= 4 ? full1 : nullptr,
                       k >= 4 ? red : nullptr, k >= 4 ? pr2 : nullptr, g.n, chunk, red_width, k,
-                      pair ? pr3 : nullptr, pair_count(k), carry, lrows, bred, rstride};
+                      prows ? pr3 : nullptr, pair_count(k), carry, lrows, bred, rstride};
     const bool zero_in_first = k >= 3 && g.prod_list.nitems > 0;
     if (!zero_in_first) {
         RR_CUDA(launch_pdl(k_zero_q, dim3(grid_cap(g.n, 256)), dim3(256), st, d_desc, zr));
@@ -723,7 +748,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         }
     }
 
-    if (pair) {
+    if (prows) {
         // layer 3 in pair-label space (independent of the point chunk), over
         // the deep rows with their state-row windows
         set_list(vp, g.deep_list, 1);
@@ -752,6 +777,40 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
     vp.tx = tx_w ? tx : nullptr;
     vp.dheads = g.deep_list.heads.as<uint32_t>();
     vp.ndheads = g.deep_list.nheads;
+    const uint32_t ntail3 = (uint32_t)g.tail3_list.count;
+    if (closed5 && ntail3) {
+        set_list(vp, g.tail3_list, 3);
+        vp.layer = 4;
+        const int tslot = timing_begin(st);
+        RR_CUDA(launch_pdl(k_last5, dim3(grid_cap(((uint64_t)ntail3 + 3) / 4 * 32, 256)), dim3(256), st, vp,
+                           ntail3, pair_count(5)));
+        timing_end(tslot, kTimeLast, st);
+        RR_LAUNCHED();
+        ++nk;
+    }
+    if (bfirst == 5 && pair && ntail3) {
+        // at-most-k branch k' = 5: its last layer in closed form over this
+        // query's pair rows (labels 0..4), beside the query
+        cudaStream_t bs = st;
+        if (side) {
+            RR_CUDA(cudaEventRecord(bev[0], st));
+            RR_CUDA(cudaStreamWaitEvent(side, bev[0], 0));
+            bs = side;
+            side_used = true;
+        }
+        V2Params vb = vp;
+        vb.qd = d_bdesc;
+        vb.k = 5;
+        vb.layer = 4;
+        vb.z = nullptr;  // branches are plain queries
+        set_list(vb, g.tail3_list, 3);
+        const int tslot = timing_begin(bs);
+        RR_CUDA(launch_pdl(k_last5, dim3(grid_cap(((uint64_t)ntail3 + 3) / 4 * 32, 256)), dim3(256), bs, vb,
+                           ntail3, pair_count(k)));
+        timing_end(tslot, kTimeLast, bs);
+        RR_LAUNCHED();
+        ++nk;
+    }
 
     if (k == 3 && g.win_list.count) {
         // last layer in closed form (no sieve points)
@@ -775,7 +834,7 @@ rr_status enqueue_query_v2(const Graph &g, uint32_t k, bool table, bool bitmap, 
         ++nk;
     }
     const uint64_t npts = range.stop(k) - range.first;
-    const uint64_t nchunks = k == 3 || closed4 ? 0 : (npts + chunk - 1) / chunk;
+    const uint64_t nchunks = k == 3 || closed4 || closed5 ? 0 : (npts + chunk - 1) / chunk;
     for (uint64_t c = 0; c < nchunks; ++c) {
         vp.chunk_base = range.first + (uint32_t)(c * chunk);
         rr_status s = RR_OK;

@@ -437,6 +437,104 @@ __device__ __forceinline__ void last4_closed(const V2Params &p, uint32_t ent, ui
         atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + w), (unsigned long long)val);
 }
 
+// ---------------------------------------------------------------------------
+// k = 5, last layer in closed form over the pair-label layer 3. The window of
+// tail-list entry e (tail v, head w) over v's deep rows sums to
+// x_v^L x_s^L sum_{i,j in L} dQ_ij (dQ the window's difference of the pair
+// prefix), and the last layer multiplies by y_{e,4} x_w^L. Summed over all L in
+// [5], a term w_a v_b s_c dQ_ij survives only when a, b, c, i, j are the five
+// labels, so with S_{ij} = dQ_ij + dQ_ji (the stored off-diagonal value) and
+// P_{bc} = v_b s_c + v_c s_b (2x2 permanents of z_v, z_s), e adds
+//     y_{e,4} sum_a w_a X_a,   X_a = sum over the three ways to split [5] \ {a}
+//                              into pairs {p, q} of S_p P_q + S_q P_p
+// to S[w] (56 products). Eight lanes take one entry, lane c < 5 owning label
+// c: it forms P over {c, c+1} and {c, c+2} (labels mod 5; the ten pairs once),
+// gathers the four others it needs over shuffles, and adds w_c X_c; 12
+// products a lane. The pair rows may belong to a larger query (at-most-k
+// branch k' = 5 of a query with the pair-label layer 3): labels 0..4 are the
+// first 15 values of their rows, np values apart. Runs of equal heads in a
+// warp are XORed before one atomic per run.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pair_index(uint32_t x, uint32_t y)
+{
+    const uint32_t hi = max(x, y), lo = min(x, y);
+    return hi * (hi + 1u) / 2u + lo;
+}
+
+// Called by whole warps; ent = a warp-aligned base / 8 + group (4 entries per
+// warp). zs0, zs1, zs2: z_{s,c}, z_{s,c+1}, z_{s,c+2} (labels mod 5) of the
+// lane's label c.
+__device__ __forceinline__ void last5_closed(const V2Params &p, uint32_t ent, uint32_t count, uint32_t np,
+                                             uint64_t zs0, uint64_t zs1, uint64_t zs2)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t c = (uint32_t)lane & 7u, gbase = (uint32_t)lane & ~7u, grp = (uint32_t)lane >> 3;
+    const bool act = c < 5u;
+    const bool has = ent < count;
+    const uint32_t w = has ? p.head[ent] : 0xffffffffu;
+    // the other four labels, and the six pairs among them in split order:
+    // (o0,o1 | o2,o3), (o0,o2 | o1,o3), (o0,o3 | o1,o2)
+    uint32_t o[4];
+#pragma unroll
+    for (uint32_t t = 0; t < 4; ++t) o[t] = t + (act && t >= c ? 1u : 0u);
+    constexpr uint32_t PA[6] = {0, 2, 0, 1, 0, 1}, PB[6] = {1, 3, 2, 3, 3, 2};
+    uint64_t S[6];
+    bool nz = false;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) S[t] = 0;
+    if (has && act) {
+        const uint64_t *ra = p.pr3 + (size_t)p.ia[ent] * np, *rb = p.pr3 + (size_t)p.ib[ent] * np;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const uint32_t q = pair_index(o[PA[t]], o[PB[t]]);
+            S[t] = ra[q] ^ rb[q];
+            nz |= S[t] != 0;
+        }
+    }
+    uint64_t val = 0;
+    if (__any_sync(0xffffffffu, nz)) {  // warp-uniform
+        const uint32_t v = has ? p.src[ent] : 0u;
+        const uint64_t zv = has && act ? zval(p, v, c) : 0ull;
+        const uint64_t zw = has && act ? zval(p, w, c) : 0ull;
+        const uint32_t c1 = act ? (c + 1u) % 5u : c, c2 = act ? (c + 2u) % 5u : c;
+        const uint64_t v1 = shfl64b(zv, (int)(gbase + c1)), v2 = shfl64b(zv, (int)(gbase + c2));
+        const uint64_t P1 = rr_mul(zv, zs1) ^ rr_mul(v1, zs0);  // P over {c, c+1}
+        const uint64_t P2 = rr_mul(zv, zs2) ^ rr_mul(v2, zs0);  // P over {c, c+2}
+        // pair {x, y}: d = y - x mod 5; lane x holds it as its P_d for d = 1, 2,
+        // else lane y as its P_{5-d}
+        uint64_t P[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const uint32_t x = o[PA[t]], y = o[PB[t]], d = (y + 5u - x) % 5u;
+            const uint32_t owner = d <= 2u ? x : y, slot = d <= 2u ? d : 5u - d;
+            const uint64_t t1 = shfl64b(P1, (int)(gbase + owner)), t2 = shfl64b(P2, (int)(gbase + owner));
+            P[t] = slot == 1u ? t1 : t2;
+        }
+        uint64_t X = 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) X ^= rr_mul(S[2 * m], P[2 * m + 1]) ^ rr_mul(S[2 * m + 1], P[2 * m]);
+        uint64_t sum = rr_mul(zw, X);  // zero on lanes 5..7
+        sum ^= shfl64x(sum, 1);
+        sum ^= shfl64x(sum, 2);
+        sum ^= shfl64x(sum, 4);
+        const uint32_t e = has ? p.eid[ent] : 0u;
+        val = rr_mul(sm_draw(p.qd->key_y, (uint64_t)e * 32u + 3u), sum);  // y_{e,4}
+        if (has && c == 0u && p.qd->E) p.qd->E[e] = val;  // one entry per edge
+    }
+    // XOR along the runs of equal heads (contiguous groups of 8 lanes)
+    const uint32_t prev = __shfl_sync(0xffffffffu, w, lane >= 8 ? lane - 8 : lane);
+    const uint32_t starts = __ballot_sync(0xffffffffu, c == 0u && (grp == 0u || prev != w));
+    const int run0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));  // first lane of the run
+#pragma unroll
+    for (int off = 8; off < 32; off <<= 1) {
+        const uint64_t ov = shfl64b(val, lane >= off ? lane - off : lane);
+        if (lane - off >= run0) val ^= ov;
+    }
+    const bool run_end = grp == 3u || ((starts >> (lane + 8 - (int)c)) & 1u);
+    if (has && c == 0u && run_end && val)
+        atomicXor(reinterpret_cast<unsigned long long *>(p.qd->S + w), (unsigned long long)val);
+}
+
 // Sums of a lane group's per-point values (acc, the lane's PPL points) over
 // the group's 32*PPL points holding each in-group label: lane j < LG returns
 // T_j -- the in-lane labels from U, the lane labels from the half-cube sums of

@@ -1,7 +1,7 @@
 """at-most-k with the smaller queries taken from the k query's own layers: for
 one seed the k'-vertex query's per-point layers agree with the k-vertex
-query's on the first 2^k' points, so rows k' >= 5 (>= 6 with the pair-label
-layer 3) come from the k query. Every row must equal the single query's
+query's on the first 2^k' points, so rows k' >= 5 come from the k query (k' =
+5 from its pair rows in closed form when layer 3 runs in pair-label space). Every row must equal the single query's
 witness and the lanes-only form's (load flag bit 6; bit 7 forces the branches
 on these small graphs), bit for bit: k = 6..12,
 one and several point chunks, layer 3 per point or in pair-label space, cut
