@@ -498,8 +498,13 @@ __device__ __forceinline__ void last5_closed(const V2Params &p, uint32_t ent, ui
         const uint64_t zw = has && act ? zval(p, w, c) : 0ull;
         const uint32_t c1 = act ? (c + 1u) % 5u : c, c2 = act ? (c + 2u) % 5u : c;
         const uint64_t v1 = shfl64b(zv, (int)(gbase + c1)), v2 = shfl64b(zv, (int)(gbase + c2));
-        const uint64_t P1 = rr_mul(zv, zs1) ^ rr_mul(v1, zs0);  // P over {c, c+1}
-        const uint64_t P2 = rr_mul(zv, zs2) ^ rr_mul(v2, zs0);  // P over {c, c+2}
+        uint64_t P1 = 0, P2 = 0;  // P over {c, c+1} and {c, c+2}
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t Ph = rr_mul(zv, h ? zs2 : zs1) ^ rr_mul(h ? v2 : v1, zs0);
+            if (h) P2 = Ph;
+            else P1 = Ph;
+        }
         // pair {x, y}: d = y - x mod 5; lane x holds it as its P_d for d = 1, 2,
         // else lane y as its P_{5-d}
         uint64_t P[6];
@@ -510,9 +515,16 @@ __device__ __forceinline__ void last5_closed(const V2Params &p, uint32_t ent, ui
             const uint64_t t1 = shfl64b(P1, (int)(gbase + owner)), t2 = shfl64b(P2, (int)(gbase + owner));
             P[t] = slot == 1u ? t1 : t2;
         }
+        // one split at a time (operands by select): two products in flight
         uint64_t X = 0;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) X ^= rr_mul(S[2 * m], P[2 * m + 1]) ^ rr_mul(S[2 * m + 1], P[2 * m]);
+#pragma unroll 1
+        for (int m = 0; m < 3; ++m) {
+            const uint64_t sa = m == 0 ? S[0] : (m == 1 ? S[2] : S[4]);
+            const uint64_t sb = m == 0 ? S[1] : (m == 1 ? S[3] : S[5]);
+            const uint64_t pa = m == 0 ? P[0] : (m == 1 ? P[2] : P[4]);
+            const uint64_t pb = m == 0 ? P[1] : (m == 1 ? P[3] : P[5]);
+            X ^= rr_mul(sa, pb) ^ rr_mul(sb, pa);
+        }
         uint64_t sum = rr_mul(zw, X);  // zero on lanes 5..7
         sum ^= shfl64x(sum, 1);
         sum ^= shfl64x(sum, 2);
