@@ -136,7 +136,8 @@ typedef struct {
  * pair-label space and its last layer in closed form (per row, y_{e,4} times
  * the sum over the splits of the five labels into one for z_w, a pair for z_v
  * and z_s and a pair for the window's pair sums) instead of per point (the
- * default: faster on the graphs measured). Results are bit-identical in every form. The pair
+ * default; the two measured within 4% of each other). Results are
+ * bit-identical in every form. The pair
  * rows ((deep rows + 1) * k(k+1)/2 words) and the head table (heads * chunk
  * words) are part of a query's scratch and, unlike the per-point state, do not
  * shrink with the point chunk: a server whose per-slot budget cannot hold them
