@@ -31,6 +31,8 @@ def main(argv=None) -> int:
     ap.add_argument("--batch-shape", default=None,
                     help="blocks per SM, ranges, max chunk of the batch (e.g. 5,2,1024), "
                          "as rr_set_batch_tuning")
+    ap.add_argument("--flags", type=int, default=0,
+                    help="rr_graph_load flags (capi.FLAG_*), e.g. 512 = k = 5 in closed form")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: one persistent batched launch of this many queries, "
                          "k ~ U{4..12}, odd ones coloured")
@@ -47,7 +49,7 @@ def main(argv=None) -> int:
     torch.cuda.set_device(0)
     if args.batch:
         qs = W.query_set(g, args.batch, 4, 12, W.GRAPH_SEED_BASE + 4)
-        with capi.Graph(g) as G:
+        with capi.Graph(g, args.flags) as G:
             if args.batch_shape:
                 capi.rr_set_batch_tuning(G.handle, *(int(x) for x in args.batch_shape.split(",")))
             d_w = torch.zeros((len(qs), g["n"]), dtype=torch.int64, device="cuda")
@@ -62,7 +64,7 @@ def main(argv=None) -> int:
             st.synchronize()
             print(f"{args.workload} batch of {len(qs)} ms {e0.elapsed_time(e1):.3f}")
         return 0
-    with capi.Graph(g) as G:
+    with capi.Graph(g, args.flags) as G:
         if args.shape:
             ppl, chunk = (int(x) for x in args.shape.lower().split("x"))
             capi.rr_set_tuning(G.handle, args.k, ppl, chunk)
